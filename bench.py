@@ -1,0 +1,344 @@
+#!/usr/bin/env python3
+"""RS-S benchmark on GB300: factor + solve of the 1024 x 1024 Laplace workload.
+
+A step is one pass of the whole hot path over one synthetic problem: every
+compressed level of the factorization (leaf kernel blocks, proxy ID,
+sparsification and LU, Schur updates, merge), the dense top LU, and one
+1-right-hand-side solve (upward sweep, top solve, downward sweep).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+
+Prints one JSON line (rank 0).  --impl reference times the CPU oracle on the
+host cores instead (a bounded sample of the same workload, scaled by N because
+the method is O(N)).  With N > 1 under torchrun every rank factors its own copy
+(replicas: the single-GPU path has no data exchange).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads as W  # noqa: E402
+
+WORKLOAD = "laplace_1024x1024_eps1e-6"
+METRIC = "RS-S factor s and solve RHS/s at N=1M, rel.res<=1e-5; serve p50/p99 latency"
+# FP64 FMA throughput of this GB300, measured with a DFMA loop over 152 SMs x 8
+# CTAs (1.195 TFLOP/s at a 1995 MHz SM clock); the fp64 mma.sync path measured
+# 1.05 TFLOP/s, so DFMA is the FP64 roof.
+FP64_PEAK_TFLOPS = 1.195
+CPU_SAMPLE_SIDE = 128           # oracle sample: the same workload on a 128 x 128 grid
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(W.WORKLOADS))
+    ap.add_argument("--multi-rhs", type=int, default=256)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------- clocks
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={self.FIELDS}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.seek(0)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.f.name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ----------------------------------------------------------------------------- residual
+def fft_relres(torch, pts_side, kind, h, kappa, x, b):
+    """||A x - b|| / ||b|| on the GPU with a zero-padded 2D FFT (A is BTTB on the grid).
+
+    A validation check of the result, separate from the hot path."""
+    s = pts_side
+    dev = x.device
+    d = torch.arange(-(s - 1), s, device=dev, dtype=torch.float64)
+    DY, DX = torch.meshgrid(d, d, indexing="ij")
+    r2 = (DX * DX + DY * DY) * (h * h)
+    r2[s - 1, s - 1] = 1.0
+    if kind == W.LAPLACE:
+        kv = -(h * h / (4 * math.pi)) * torch.log(r2)
+    else:
+        kr = kappa * torch.sqrt(r2)
+        kv = (h * h) * torch.complex(-0.25 * torch.special.bessel_y0(kr), 0.25 * torch.special.bessel_j0(kr))
+    kv[s - 1, s - 1] = 0
+    circ = torch.zeros((2 * s, 2 * s), dtype=kv.dtype, device=dev)
+    idx = torch.arange(-(s - 1), s, device=dev) % (2 * s)
+    circ[idx[:, None], idx[None, :]] = kv
+    kf = torch.fft.fft2(circ)
+    num = den = 0.0
+    for j in range(x.shape[1]):
+        pad = torch.zeros((2 * s, 2 * s), dtype=torch.complex128, device=dev)
+        pad[:s, :s] = x[:, j].reshape(s, s)
+        y = torch.fft.ifft2(kf * torch.fft.fft2(pad))[:s, :s].reshape(-1)
+        if not x.is_complex():
+            y = y.real
+        r = y + x[:, j] - b[:, j]            # diagonal entries are 1
+        num += float(torch.linalg.vector_norm(r)) ** 2
+        den += float(torch.linalg.vector_norm(b[:, j])) ** 2
+    return math.sqrt(num / den)
+
+
+# ----------------------------------------------------------------------------- CPU oracle
+CPU_SNIPPET = r"""
+import json, sys, time
+sys.path.insert(0, {root!r})
+import workloads as W
+from oracle import rss
+from oracle.rss import KernelSpec
+side, kind, kappa, eps, reps = {side}, {kind}, {kappa}, {eps}, {reps}
+pts = W.grid_points(side)
+spec = KernelSpec("laplace" if kind == W.LAPLACE else "helmholtz", h=1.0 / side, kappa=kappa)
+b = W.gaussian_rhs(side * side, 1, kind != W.LAPLACE, 1002)
+ts = []
+for _ in range(reps):
+    t0 = time.perf_counter()
+    fac = rss.factor(pts, spec, eps)
+    x = rss.solve(fac, b)
+    ts.append(time.perf_counter() - t0)
+print(json.dumps({{"times": ts}}))
+"""
+
+
+def run_oracle(w, reps):
+    """Time the oracle (factor + 1-RHS solve) on the sample grid, single-threaded."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = CPU_SNIPPET.format(root=ROOT, side=CPU_SAMPLE_SIDE, kind=w["kind"], kappa=w["kappa"],
+                              eps=w["eps"], reps=reps)
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
+                         check=True)
+    return json.loads(out.stdout.strip().splitlines()[-1])["times"]
+
+
+def cpu_block(w, times):
+    scale = (w["side"] / CPU_SAMPLE_SIDE) ** 2
+    return {"value": statistics.mean(times) * scale, "unit": "s", "cores": 1, "kind": "oracle",
+            "sample": (f"oracle factor + 1-RHS solve of the same workload on a {CPU_SAMPLE_SIDE}x"
+                       f"{CPU_SAMPLE_SIDE} grid ({len(times)} runs, mean "
+                       f"{statistics.mean(times):.2f} s), scaled by the point-count ratio "
+                       f"{scale:g} (the factorization is O(N))")}
+
+
+def reference_arm(args, w):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    for _ in range(args.warmup):
+        run_oracle(w, 1)
+    times = run_oracle(w, args.steps)
+    cb = cpu_block(w, times)
+    line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": "s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": cb["value"] * 1e3, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "n": w["side"] ** 2, "eps": w["eps"], "leaf": W.LEAF,
+                       "rhs": 1, "parallelism": "replicas"},
+            "cpu_baseline": cb,
+            "e2e": {"value": cb["value"], "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------- native arm
+def native_arm(args, w):
+    import torch
+
+    import paper_2310_15458_gb300 as P
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    side, eps = w["side"], w["eps"]
+    n = side * side
+    kind = w["kind"]
+    is_c = w["complex"]
+    h = 1.0 / side
+    pts = W.grid_points(side)
+    tree = P.rss_build_tree(pts, W.LEAF)
+    b_host = W.gaussian_rhs(n, 1, is_c, w["seed"])
+    tdt = torch.complex128 if is_c else torch.float64
+    b_dev = torch.from_numpy(np.ascontiguousarray(b_host.T)).to("cuda").T.contiguous()
+    stream = torch.cuda.current_stream()
+    x = torch.empty_like(b_dev)
+
+    def factor():
+        return P.rss_factor(tree, kind=kind, eps=eps, h=h, kappa=w["kappa"])
+
+    def step():
+        f = factor()
+        x.copy_(b_dev)
+        P.rss_solve(f, x.view(n, 1), stream=stream)
+        return f
+
+    for _ in range(args.warmup):
+        f = step()
+        del f
+    barrier()
+    clocks = Clocks(local)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    infos = []
+    for _ in range(args.steps):
+        f = step()
+        infos.append(P.rss_info(f))
+        if _ + 1 < args.steps:
+            del f
+    ev1.record(stream)
+    barrier()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    info = infos[-1]
+    relres = fft_relres(torch, side, kind, h, w["kappa"], x.view(n, 1), b_dev.view(n, 1))
+
+    # solve throughput on the resident factorization (1 and multi RHS)
+    def solve_rate(nrhs, reps):
+        bb = torch.randn(nrhs, n, dtype=torch.float64, device="cuda", generator=None)
+        if is_c:
+            bb = torch.complex(bb, torch.randn_like(bb))
+        xx = bb.clone().T
+        P.rss_solve(f, xx, stream=stream)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            xx.copy_(bb.T)
+            P.rss_solve(f, xx, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / reps
+        return t, nrhs / (t * 1e-3)
+
+    t1, r1 = solve_rate(1, 10)
+    tm, rm = solve_rate(args.multi_rhs, 2)
+
+    # end to end through the public API with host buffers
+    pts_h = np.ascontiguousarray(pts)
+    bh = np.ascontiguousarray(b_host[:, 0]).copy()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    tr = P.rss_build_tree(pts_h, W.LEAF)
+    fe = P.rss_factor(tr, kind=kind, eps=eps, h=h, kappa=w["kappa"])
+    P.rss_solve(fe, bh)
+    e2e_s = time.perf_counter() - t0
+    del fe, tr
+    esz = 16 if is_c else 8
+
+    # roofline of the dominant factor kernel (device time from CUDA events on the factor's stream)
+    gms = info["gpu_ms"]
+    dom = max(("id", "elim", "schur"), key=lambda k: gms[k])
+    launches = info["phase_launches"][dom]
+    flops = info["flops"][dom]
+    achieved = flops / (gms[dom] * 1e-3) / 1e12
+    kern = {"id": "k_id", "elim": "k_elim", "schur": "k_schur"}[dom]
+    solve_launches = 2 + 2 * info["batches"] + 1
+    line = {
+        "metric": METRIC, "value": ms / 1e3, "unit": "s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "c128" if is_c else "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "n": n, "eps": eps, "leaf": W.LEAF, "proxy_n": W.PROXY_N,
+                   "rhs": 1, "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "inputs larger than L2: the leaf stencil alone is "
+                         f"{n // W.LEAF * 25 * W.LEAF * W.LEAF * esz / 1e9:.1f} GB"},
+        "factor_s": info["ms"]["total"] / 1e3,
+        "solve_1rhs_ms": t1,
+        "solve_rhs_per_s": {"1": r1, str(args.multi_rhs): rm},
+        "relres": relres,
+        "phase_gpu_ms": gms,
+        "ranks": [{"side": L["side"], "k_mean": L["k_mean"], "k_max": L["k_max"]} for L in info["levels"]],
+        "ntop": info["ntop"],
+        "clocks": clk,
+        "e2e": {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": pts_h.nbytes + bh.nbytes,
+                "d2h_bytes_per_step": bh.nbytes},
+        "gpu_launches": args.steps * (info["launches"] + solve_launches),
+        "roofline": {"kernel": kern, "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                     "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                     "launches": launches, "avg_launch_ms": gms[dom] / max(launches, 1),
+                     "peak_source": "FP64 DFMA loop measured on this GB300 (no FP64 figure in "
+                                    "MEASURED_PEAKS.json)"},
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_block(w, run_oracle(w, 1))
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    w = W.WORKLOADS[args.workload]
+    if args.impl == "reference":
+        reference_arm(args, w)
+    else:
+        native_arm(args, w)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,127 @@
+/*
+ * rss.h -- C ABI of the GB300 strong-recursive-skeletonization (RS-S) library.
+ *
+ * RS-S factors a dense kernel matrix A (A_ij = K(x_i, x_j), i != j, paper
+ * Eq. 3) for points on a uniform planar grid into the product of per-box
+ * operators of Eq. (9) (Algorithm 1), then applies the factorization to
+ * right-hand sides (Section 2.5).  Every numerical step runs in the library's
+ * own sm_103a CUDA kernels; there is no CPU fallback.
+ *
+ * Conventions
+ *  - Every call returns an rss_status; nothing throws across the ABI.  On a
+ *    non-OK status, rss_last_error() gives a message (thread-local).
+ *  - Handles are opaque and owned by the library; release them with rss_free.
+ *  - Complex values are interleaved (re, im) pairs of doubles, the layout of
+ *    C99 double _Complex, numpy complex128 and torch.complex128.
+ *  - Matrices of right-hand sides are column-major: entry (i, j) at
+ *    b[i + j * ldb], i a point index in the caller's order.
+ *  - Input errors (bad sizes, points that are not a complete uniform grid,
+ *    unsupported parameters) return RSS_EINVAL before any GPU work.
+ *  - CUDA failures return RSS_ECUDA; device memory exhaustion RSS_ENOMEM; a
+ *    zero pivot in an LU returns RSS_ENUMERIC.
+ */
+#ifndef RSS_GB300_H
+#define RSS_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rss_tree rss_tree;
+typedef struct rss_factorization rss_factorization;
+
+typedef enum {
+  RSS_OK = 0,
+  RSS_EINVAL = 1,   /* invalid argument; nothing was launched */
+  RSS_ENOMEM = 2,   /* device or host allocation failed */
+  RSS_ECUDA = 3,    /* a CUDA runtime call or kernel launch failed */
+  RSS_ENUMERIC = 4, /* exact zero pivot in an LU factorization */
+  RSS_ETIMEOUT = 5, /* reserved: a bounded device wait expired */
+  RSS_EBUSY = 6     /* reserved */
+} rss_status;
+
+/* Kernel kinds.
+ *  RSS_LAPLACE    A_ij = -(h^2 / 2 pi) log |x_i - x_j|, real (paper Eq. 15).
+ *  RSS_HELMHOLTZ  A_ij = h^2 (i/4) H0^(1)(kappa |x_i - x_j|), complex (Eq. 18
+ *                 without the kappa^2 sqrt(b_i b_j) factor of Eq. 19).
+ *  RSS_TEST_POLY  A_ij = scale conj(w_i) w_j sum_d coef[d] (z_i - z_j)^d,
+ *                 z = x + i y, w = exp(i (phase_x x + phase_y y)), complex.
+ *  RSS_TEST_RPOLY the real part of sum_d coef[d] (z_i - z_j)^d times scale.
+ * The two test kinds have an exactly low-rank far field, so the whole
+ * factorization is exact up to rounding; they exist to verify the elimination
+ * bookkeeping against a dense solve and are not a workload of the paper. */
+enum { RSS_LAPLACE = 0, RSS_HELMHOLTZ = 1, RSS_TEST_POLY = 2, RSS_TEST_RPOLY = 3 };
+
+#define RSS_MAX_COEF 8
+
+typedef struct {
+  int kind;                       /* one of the kinds above */
+  double h;                       /* entry scale h (h^2 multiplies K); <= 0: the grid spacing */
+  double kappa;                   /* Helmholtz wavenumber */
+  double diag_re, diag_im;        /* A_ii */
+  int proxy_n;                    /* points on the proxy circle (Eq. 6); 0: 64 */
+  double proxy_radius_over_side;  /* proxy-circle radius / box side; 0: 1.25 */
+  double eps;                     /* ID tolerance (Definition 1), >= 0 */
+  int ncoef;                      /* test kernels: number of coefficients (<= RSS_MAX_COEF) */
+  double coef_re[RSS_MAX_COEF], coef_im[RSS_MAX_COEF];
+  double scale, phase_x, phase_y; /* test kernels */
+} rss_params;
+
+/* Build the quadtree of Section 2.1 for n points given as pts_xy[2*i],
+ * pts_xy[2*i+1] (host memory, read only during the call).  The points must be
+ * the n = s*s nodes of a uniform square grid (any origin and spacing, any
+ * order).  leaf is the number of points per leaf box, a square l*l with s/l
+ * a power of two.  On success *out holds a tree the caller releases with
+ * rss_free; a tree may be shared by several factorizations. */
+rss_status rss_build_tree(const double* pts_xy, int64_t n, int leaf, rss_tree** out);
+
+/* Factor A for the tree's points (Algorithm 1: per level, all boxes of one
+ * colour class in one batched launch per phase; the ID of Eq. 6, the
+ * elimination of Eq. 8, the Schur update of Remark 2, the merge of Section
+ * 2.4, a dense LU at the top).  stream is a cudaStream_t (NULL: the legacy
+ * default stream) on the current device.  The call returns when the
+ * factorization is complete.  *out is released with rss_free; the factor
+ * keeps its own copy of everything it needs from tree and params. */
+rss_status rss_factor(const rss_tree* tree, const rss_params* params, void* stream,
+                      rss_factorization** out);
+
+/* Overwrite b (n x nrhs, column-major, leading dimension ldb >= n, entries in
+ * the caller's point order) with the RS-S approximation of A^{-1} b
+ * (Section 2.5).  b may be device memory (the call is then asynchronous on
+ * stream) or host memory (the library stages it through the device and
+ * returns after the result is back).  Real factors take double, complex
+ * factors interleaved complex double.  Calls on distinct streams may run
+ * concurrently on the same factor (the factor is read only). */
+rss_status rss_solve(const rss_factorization* f, void* b, int64_t nrhs, int64_t ldb, void* stream);
+
+/* Release a tree or a factor (the handle is tagged).  NULL is ignored. */
+void rss_free(void* handle);
+
+/* Message for the last non-OK status returned on this thread. */
+const char* rss_last_error(void);
+
+/* JSON summary of a factor: sizes, ranks per level, phase times, bytes held. */
+rss_status rss_info(const rss_factorization* f, char* buf, size_t len);
+
+/* Inspection (used by the tests): skeleton ranks of the boxes of the level
+ * whose box grid has side `side` (row-major boxes), into k_out[side*side]. */
+rss_status rss_level_ranks(const rss_factorization* f, int side, int32_t* k_out);
+
+/* Inspection: the factor record of box `box` at level `side`, copied to host
+ * buffers (any pointer may be NULL to skip it).  Sizes are returned in
+ * sizes[0..3] = k, r, c, n.  Index lists are in the caller's point order:
+ * S (k), R (r), C (c, starting with S).  T is k x r, LU r x r (packed, with
+ * 0-based getrf pivots piv[r]), E is c x r, F is r x c, all column-major with
+ * leading dimension equal to the row count.  Returns RSS_EINVAL if the box
+ * had no redundant points at that level. */
+rss_status rss_box_record(const rss_factorization* f, int side, int box, int32_t* sizes,
+                          int64_t* S, int64_t* R, int64_t* C, void* T, void* LU,
+                          int32_t* piv, void* E, void* F);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

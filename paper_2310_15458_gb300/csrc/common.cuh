@@ -1,0 +1,156 @@
+// Shared device helpers: the complex-double type, fused arithmetic, kernel
+// entries of A (paper Eqs. 3, 15, 18) and host error plumbing.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstdio>
+#include <string>
+
+#include "../../include/rss.h"
+
+// ----------------------------------------------------------------- scalars
+struct zd {
+  double x, y;
+};
+
+__host__ __device__ inline zd mkz(double a, double b) { return zd{a, b}; }
+__host__ __device__ inline zd operator+(zd a, zd b) { return zd{a.x + b.x, a.y + b.y}; }
+__host__ __device__ inline zd operator-(zd a, zd b) { return zd{a.x - b.x, a.y - b.y}; }
+__host__ __device__ inline zd operator-(zd a) { return zd{-a.x, -a.y}; }
+__host__ __device__ inline zd operator*(zd a, zd b) {
+  return zd{a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+}
+__host__ __device__ inline zd operator*(double s, zd a) { return zd{s * a.x, s * a.y}; }
+
+__host__ __device__ inline double cj(double a) { return a; }
+__host__ __device__ inline zd cj(zd a) { return zd{a.x, -a.y}; }
+__host__ __device__ inline double abs2(double a) { return a * a; }
+__host__ __device__ inline double abs2(zd a) { return a.x * a.x + a.y * a.y; }
+__host__ __device__ inline double re(double a) { return a; }
+__host__ __device__ inline double re(zd a) { return a.x; }
+
+template <typename T> __host__ __device__ inline T zero();
+template <> __host__ __device__ inline double zero<double>() { return 0.0; }
+template <> __host__ __device__ inline zd zero<zd>() { return zd{0.0, 0.0}; }
+template <typename T> __host__ __device__ inline T from_re(double a);
+template <> __host__ __device__ inline double from_re<double>(double a) { return a; }
+template <> __host__ __device__ inline zd from_re<zd>(double a) { return zd{a, 0.0}; }
+
+// acc + a * b
+__device__ inline double mad(double acc, double a, double b) { return fma(a, b, acc); }
+__device__ inline zd mad(zd acc, zd a, zd b) {
+  return zd{fma(a.x, b.x, fma(-a.y, b.y, acc.x)), fma(a.x, b.y, fma(a.y, b.x, acc.y))};
+}
+// acc - a * b
+__device__ inline double msb(double acc, double a, double b) { return fma(-a, b, acc); }
+__device__ inline zd msb(zd acc, zd a, zd b) {
+  return zd{fma(-a.x, b.x, fma(a.y, b.y, acc.x)), fma(-a.x, b.y, fma(-a.y, b.x, acc.y))};
+}
+// acc + conj(a) * b
+__device__ inline double madc(double acc, double a, double b) { return fma(a, b, acc); }
+__device__ inline zd madc(zd acc, zd a, zd b) {
+  return zd{fma(a.x, b.x, fma(a.y, b.y, acc.x)), fma(a.x, b.y, fma(-a.y, b.x, acc.y))};
+}
+// acc - conj(a) * b
+__device__ inline double msbc(double acc, double a, double b) { return fma(-a, b, acc); }
+__device__ inline zd msbc(zd acc, zd a, zd b) {
+  return zd{fma(-a.x, b.x, fma(-a.y, b.y, acc.x)), fma(-a.x, b.y, fma(a.y, b.x, acc.y))};
+}
+__device__ inline double dv(double a, double b) { return a / b; }
+__device__ inline zd dv(zd a, zd b) {
+  double d = b.x * b.x + b.y * b.y;
+  return zd{(a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d};
+}
+__device__ inline double scl(double s, double a) { return s * a; }
+__device__ inline zd scl(double s, zd a) { return zd{s * a.x, s * a.y}; }
+
+__device__ inline double shfl_down(double v, int d) { return __shfl_down_sync(0xffffffffu, v, d); }
+__device__ inline zd shfl_down(zd v, int d) {
+  return zd{__shfl_down_sync(0xffffffffu, v.x, d), __shfl_down_sync(0xffffffffu, v.y, d)};
+}
+__device__ inline double shfl_xor(double v, int d) { return __shfl_xor_sync(0xffffffffu, v, d); }
+__device__ inline zd shfl_xor(zd v, int d) {
+  return zd{__shfl_xor_sync(0xffffffffu, v.x, d), __shfl_xor_sync(0xffffffffu, v.y, d)};
+}
+template <typename T> __device__ inline T warp_sum(T v) {
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) v = v + shfl_xor(v, d);
+  return v;
+}
+
+// ----------------------------------------------------------------- kernel entries
+struct KParams {
+  int kind;
+  double h2;        // h^2
+  double kappa;
+  double diag_re, diag_im;
+  int ncoef;
+  double cre[RSS_MAX_COEF], cim[RSS_MAX_COEF];
+  double scale, phx, phy;
+};
+
+// Grid geometry: point (ix, iy) sits at (x0 + ix hg, y0 + iy hg).
+struct Geo {
+  double x0, y0, hg;
+  int side;        // points per grid row
+};
+
+__device__ inline zd poly_sum(const KParams& kp, double dx, double dy) {
+  // Horner in z = dx + i dy
+  zd acc{0.0, 0.0};
+  for (int d = kp.ncoef - 1; d >= 0; --d) acc = acc * zd{dx, dy} + zd{kp.cre[d], kp.cim[d]};
+  return kp.scale * acc;
+}
+
+// K(p1, p2) for p1 != p2 (paper Eq. 3 with Eq. 15 or Eq. 18); p = absolute coordinates.
+__device__ inline double kval(const KParams& kp, double x1, double y1, double x2, double y2, double) {
+  double dx = x1 - x2, dy = y1 - y2;
+  if (kp.kind == RSS_LAPLACE) {
+    // -(h^2 / 2 pi) log r = -(h^2 / 4 pi) log r^2
+    return (-0.07957747154594767 * kp.h2) * log(fma(dx, dx, dy * dy));
+  }
+  return poly_sum(kp, dx, dy).x;  // RSS_TEST_RPOLY
+}
+__device__ inline zd kval(const KParams& kp, double x1, double y1, double x2, double y2, zd) {
+  double dx = x1 - x2, dy = y1 - y2;
+  if (kp.kind == RSS_HELMHOLTZ) {
+    double kr = kp.kappa * sqrt(fma(dx, dx, dy * dy));
+    // h^2 (i/4) (J0 + i Y0) = h^2 (-Y0/4 + i J0/4)
+    return zd{-0.25 * kp.h2 * y0(kr), 0.25 * kp.h2 * j0(kr)};
+  }
+  // RSS_TEST_POLY: conj(w1) w2 p(z1 - z2), w = exp(i (phx x + phy y))
+  zd p = poly_sum(kp, dx, dy);
+  double s, c;
+  sincos(kp.phx * (x2 - x1) + kp.phy * (y2 - y1), &s, &c);
+  return p * zd{c, s};
+}
+
+// Entry of A between grid points given as integer coordinates.
+template <typename T>
+__device__ inline T aval(const KParams& kp, const Geo& geo, int2 a, int2 b) {
+  if (a.x == b.x && a.y == b.y) {
+    T d;
+    if constexpr (sizeof(T) == sizeof(double)) d = from_re<T>(kp.diag_re);
+    else d = T{kp.diag_re, kp.diag_im};
+    return d;
+  }
+  return kval(kp, geo.x0 + a.x * geo.hg, geo.y0 + a.y * geo.hg, geo.x0 + b.x * geo.hg,
+              geo.y0 + b.y * geo.hg, T{});
+}
+
+// ----------------------------------------------------------------- host errors
+void rss_set_error(const std::string& msg);
+
+#define RSS_CUDA(call)                                                              \
+  do {                                                                              \
+    cudaError_t e_ = (call);                                                        \
+    if (e_ != cudaSuccess) {                                                        \
+      rss_set_error(std::string("CUDA error: ") + cudaGetErrorString(e_) + " at " + \
+                    __FILE__ + ":" + std::to_string(__LINE__));                     \
+      return e_ == cudaErrorMemoryAllocation ? RSS_ENOMEM : RSS_ECUDA;              \
+    }                                                                               \
+  } while (0)
+
+#define RSS_LAUNCHED() RSS_CUDA(cudaGetLastError())
+
+static inline unsigned cdiv(long long a, long long b) { return (unsigned)((a + b - 1) / b); }

@@ -1,0 +1,1012 @@
+// RS-S factorization on the device (Algorithm 1), batched by colour class.
+//
+// Per level (box grid side g >= 4) and per colour class (ix mod 3, iy mod 3),
+// all boxes of the class are pairwise more than distance 2 apart (Section 3),
+// so each phase handles the whole class in one launch:
+//   k_id      : proxy stack Y = [A_MB; K_PB; A_BM^*; K_BP^*] (Eqs. 4-6) and its
+//               column-pivoted Householder QR, truncated at eps (Definition 1);
+//   k_elim    : sparsification (Eq. 7), LU of X_RR, E = X_CR U^{-1} and
+//               F = L^{-1} P X_RC (Eq. 8);
+//   k_schur   : A_CC -= E F scattered into the stencil blocks (Remark 2);
+// then the merge to the parent level (Section 2.4) and a dense LU at the top.
+//
+// Matrix storage: for each box u of a level, 25 blocks A(u, v), v = u + (dx, dy),
+// |dx|, |dy| <= 2, each nmax x nmax column-major over the level-start point
+// lists of u and v.  A box's active points are a position list into its
+// level-start list (the skeleton after elimination); far pairs (distance > 2)
+// are never stored because they are never modified (Theorem 1).
+#include <algorithm>
+#include <chrono>
+#include <climits>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+
+#include "internal.h"
+
+namespace {
+
+constexpr double TIE_REL = 1e-9;        // pivot ties: relative window on squared norms
+constexpr double RECOMPUTE_REL = 1e-4;  // re-accumulate a downdated norm below this fraction
+constexpr int NT = 256;                 // threads per CTA for the per-box kernels
+
+template <typename T> struct LevelDev {
+  int g, nbox, nmax;
+  int* pts;    // nbox x nmax tree indices (level-start points)
+  int* n;      // nbox
+  int* act;    // nbox x nmax active positions
+  int* nact;   // nbox
+  T* blk;      // nbox x 25 x nmax x nmax
+};
+
+__device__ __forceinline__ int nbr_box(int u, int g, int dx, int dy) {
+  int bx = u % g + dx, by = u / g + dy;
+  return (bx < 0 || by < 0 || bx >= g || by >= g) ? -1 : by * g + bx;
+}
+__device__ __forceinline__ int off_index(int u, int v, int g) {
+  return (v / g - u / g + 2) * 5 + (v % g - u % g + 2);
+}
+__device__ __forceinline__ int cheb(int u, int v, int g) {
+  return max(abs(u % g - v % g), abs(u / g - v / g));
+}
+
+template <typename T> __device__ T block_sum(T v, T* sh) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) sh[warp] = v;
+  __syncthreads();
+  if (warp == 0) {
+    v = lane < nw ? sh[lane] : zero<T>();
+    v = warp_sum(v);
+    if (lane == 0) sh[0] = v;
+  }
+  __syncthreads();
+  return sh[0];
+}
+
+__device__ inline double warp_max(double v) {
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, d));
+  return v;
+}
+
+// ------------------------------------------------------------------ leaf generation
+template <typename T>
+__global__ void __launch_bounds__(NT) k_gen_blocks(LevelDev<T> L, const int2* __restrict__ ixy,
+                                                   KParams kp, Geo geo) {
+  const int u = blockIdx.x / 25, o = blockIdx.x % 25;
+  const int v = nbr_box(u, L.g, o % 5 - 2, o / 5 - 2);
+  if (v < 0) return;
+  const int nu = L.n[u], nv = L.n[v];
+  T* A = L.blk + ((size_t)u * 25 + o) * L.nmax * L.nmax;
+  for (int e = threadIdx.x; e < nu * nv; e += blockDim.x) {
+    const int i = e % nu, j = e / nu;
+    A[(size_t)j * L.nmax + i] = aval<T>(kp, geo, ixy[L.pts[u * L.nmax + i]], ixy[L.pts[v * L.nmax + j]]);
+  }
+}
+
+// ------------------------------------------------------------------ ID (Definition 1, Eq. 6)
+template <typename T> struct IdArgs {
+  LevelDev<T> L;
+  const int* boxes;   // colour class
+  int base;           // first box of this chunk within the class
+  T* Y;               // chunk workspace, one ldY x nmax slot per box
+  int ldY;
+  int* k_out;         // per class box
+  int* perm_out;      // class x nmax
+  T* T_ws;            // class x nmax x nmax (k x r, ld nmax)
+  const int2* ixy;
+  KParams kp;
+  Geo geo;
+  double eps;
+  int P;              // proxy points
+  double rho;         // proxy radius
+  double Lbox;        // box side
+};
+
+template <typename T> __global__ void __launch_bounds__(NT) k_id(IdArgs<T> a) {
+  extern __shared__ double sm[];
+  const LevelDev<T>& L = a.L;
+  const int nmax = L.nmax, g = L.g;
+  double* norms2 = sm;
+  double* ref = sm + nmax;
+  int* perm = reinterpret_cast<int*>(ref + nmax);
+  __shared__ int Mbox[16], Moff[17], s_nM, s_piv, s_stop;
+  __shared__ double s_thresh, s_tau;
+  __shared__ T s_scale, s_beta, s_red[32];
+  __shared__ double s_redd[32];
+
+  const int bi = a.base + blockIdx.x;
+  const int B = a.boxes[bi];
+  const size_t nn = (size_t)nmax * nmax;
+  const int n = L.n[B];
+  T* Y = a.Y + (size_t)blockIdx.x * a.ldY * nmax;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
+  const int ldY = a.ldY;
+
+  if (tid == 0) {
+    int cnt = 0, off = 0;
+    for (int dy = -2; dy <= 2; ++dy)
+      for (int dx = -2; dx <= 2; ++dx) {
+        if (max(abs(dx), abs(dy)) != 2) continue;
+        const int mb = nbr_box(B, g, dx, dy);
+        if (mb < 0) continue;
+        Mbox[cnt] = mb;
+        Moff[cnt] = off;
+        off += L.nact[mb];
+        ++cnt;
+      }
+    Moff[cnt] = off;
+    s_nM = cnt;
+  }
+  __syncthreads();
+  const int nM = s_nM, mh = Moff[nM], P = a.P;
+  const int m = 2 * (mh + P);
+  const int bx = B % g, by = B / g;
+  const double cx = a.geo.x0 - 0.5 * a.geo.hg + (bx + 0.5) * a.Lbox;
+  const double cy = a.geo.y0 - 0.5 * a.geo.hg + (by + 0.5) * a.Lbox;
+
+  // Y, column-major.  Column j = active point j of B (B is not yet eliminated,
+  // so its active list is the identity).
+  for (long long e = tid; e < (long long)m * n; e += blockDim.x) {
+    const int i = (int)(e % m), j = (int)(e / m);
+    T val;
+    if (i < mh || (i >= mh + P && i < 2 * mh + P)) {
+      const bool second = i >= mh;
+      const int ii = second ? i - mh - P : i;
+      int q = 0;
+      while (Moff[q + 1] <= ii) ++q;
+      const int mb = Mbox[q];
+      const int pm = L.act[mb * nmax + (ii - Moff[q])];
+      if (!second)
+        val = L.blk[((size_t)mb * 25 + off_index(mb, B, g)) * nn + (size_t)j * nmax + pm];
+      else
+        val = cj(L.blk[((size_t)B * 25 + off_index(B, mb, g)) * nn + (size_t)pm * nmax + j]);
+    } else {
+      const bool second = i >= 2 * mh + P;
+      const int p = second ? i - 2 * mh - P : i - mh;
+      double s, c;
+      sincospi(2.0 * p / P, &s, &c);
+      const double px = cx + a.rho * c, py = cy + a.rho * s;
+      const int2 q = a.ixy[L.pts[B * nmax + j]];
+      const double xj = a.geo.x0 + q.x * a.geo.hg, yj = a.geo.y0 + q.y * a.geo.hg;
+      val = second ? cj(kval(a.kp, xj, yj, px, py, T{})) : kval(a.kp, px, py, xj, yj, T{});
+    }
+    Y[(size_t)j * ldY + i] = val;
+  }
+  __syncthreads();
+  for (int c = warp; c < n; c += nwarp) {
+    double s = 0.0;
+    for (int i = lane; i < m; i += 32) s += abs2(Y[(size_t)c * ldY + i]);
+    s = warp_sum(s);
+    if (lane == 0) {
+      norms2[c] = s;
+      ref[c] = s;
+      perm[c] = c;
+    }
+  }
+  __syncthreads();
+  if (warp == 0) {
+    double s = 0.0;
+    for (int c = lane; c < n; c += 32) s += norms2[c];
+    s = warp_sum(s);
+    if (lane == 0) s_thresh = a.eps * a.eps * s;
+  }
+  __syncthreads();
+
+  int k = 0;
+  const int kmax = min(m, n);
+  while (k < kmax) {
+    if (warp == 0) {
+      double s = 0.0, mx = -1.0;
+      for (int c = k + lane; c < n; c += 32) {
+        s += norms2[c];
+        mx = fmax(mx, norms2[c]);
+      }
+      s = warp_sum(s);
+      mx = warp_max(mx);
+      const double thr = mx * (1.0 - TIE_REL);
+      int bp = INT_MAX, bc = -1;
+      for (int c = k + lane; c < n; c += 32)
+        if (norms2[c] >= thr && perm[c] < bp) {
+          bp = perm[c];
+          bc = c;
+        }
+      for (int d = 16; d > 0; d >>= 1) {
+        const int op = __shfl_xor_sync(0xffffffffu, bp, d), oc = __shfl_xor_sync(0xffffffffu, bc, d);
+        if (op < bp) {
+          bp = op;
+          bc = oc;
+        }
+      }
+      if (lane == 0) {
+        s_stop = (s <= s_thresh) || bc < 0;   // bc < 0 only if every norm is NaN
+        s_piv = bc;
+      }
+    }
+    __syncthreads();
+    if (s_stop) break;
+    const int p = s_piv;
+    if (p != k) {
+      for (int i = tid; i < m; i += blockDim.x) {
+        const T t = Y[(size_t)k * ldY + i];
+        Y[(size_t)k * ldY + i] = Y[(size_t)p * ldY + i];
+        Y[(size_t)p * ldY + i] = t;
+      }
+      if (tid == 0) {
+        int ti = perm[k]; perm[k] = perm[p]; perm[p] = ti;
+        double td = norms2[k]; norms2[k] = norms2[p]; norms2[p] = td;
+        td = ref[k]; ref[k] = ref[p]; ref[p] = td;
+      }
+    }
+    __syncthreads();
+    // Householder reflector H = I - tau v v^H, v_k = 1, H x = beta e_1
+    double s = 0.0;
+    for (int i = k + tid; i < m; i += blockDim.x) s += abs2(Y[(size_t)k * ldY + i]);
+    const double alpha2 = block_sum(s, s_redd);
+    if (tid == 0) {
+      const T x0 = Y[(size_t)k * ldY + k];
+      const double alpha = sqrt(alpha2);
+      if (alpha == 0.0) {
+        s_stop = 1;
+      } else {
+        const double ax0 = sqrt(abs2(x0));
+        T phase = from_re<T>(1.0);
+        if (ax0 != 0.0) phase = scl(1.0 / ax0, x0);
+        const T beta = scl(-alpha, phase);
+        s_beta = beta;
+        s_scale = x0 - beta;
+        s_tau = (alpha + ax0) / alpha;
+      }
+    }
+    __syncthreads();
+    if (s_stop) break;
+    {
+      const T d = s_scale;
+      for (int i = k + 1 + tid; i < m; i += blockDim.x) Y[(size_t)k * ldY + i] = dv(Y[(size_t)k * ldY + i], d);
+    }
+    __syncthreads();
+    if (tid == 0) Y[(size_t)k * ldY + k] = s_beta;
+    const double tau = s_tau;
+    const T* v = Y + (size_t)k * ldY;
+    for (int c = k + 1 + warp; c < n; c += nwarp) {
+      T* yc = Y + (size_t)c * ldY;
+      T d = zero<T>();
+      for (int i = k + lane; i < m; i += 32) d = madc(d, i == k ? from_re<T>(1.0) : v[i], yc[i]);
+      d = warp_sum(d);
+      const T td = scl(tau, d);
+      for (int i = k + lane; i < m; i += 32) yc[i] = msb(yc[i], i == k ? from_re<T>(1.0) : v[i], td);
+      __syncwarp();
+      double nv = 0.0;
+      if (lane == 0) nv = norms2[c] - abs2(yc[k]);
+      nv = __shfl_sync(0xffffffffu, nv, 0);
+      if (nv < RECOMPUTE_REL * ref[c]) {
+        double t = 0.0;
+        for (int i = k + 1 + lane; i < m; i += 32) t += abs2(yc[i]);
+        nv = warp_sum(t);
+        if (lane == 0) ref[c] = nv;
+      }
+      if (lane == 0) norms2[c] = nv;
+    }
+    __syncthreads();
+    ++k;
+  }
+  __syncthreads();
+  // T = R11^{-1} R12 (back substitution), k x r with ld nmax
+  const int r = n - k;
+  T* Tw = a.T_ws + (size_t)bi * nn;
+  for (int c = tid; c < r; c += blockDim.x) {
+    for (int i = k - 1; i >= 0; --i) {
+      T x = Y[(size_t)(k + c) * ldY + i];
+      for (int l = i + 1; l < k; ++l) x = msb(x, Y[(size_t)l * ldY + i], Tw[(size_t)c * nmax + l]);
+      Tw[(size_t)c * nmax + i] = dv(x, Y[(size_t)i * ldY + i]);
+    }
+  }
+  for (int c = tid; c < n; c += blockDim.x) a.perm_out[(size_t)bi * nmax + c] = perm[c];
+  if (tid == 0) a.k_out[bi] = k;
+}
+
+// ------------------------------------------------------------------ sparsify + LU (Eqs. 7, 8)
+template <typename T> struct ElimArgs {
+  LevelDev<T> L;
+  const BoxRec<T>* recs;
+  const int* cls_idx;       // class index of each record's box (row into perm/T_ws)
+  const int* perm_in;
+  const T* T_ws;
+  int* err;
+};
+
+template <typename T> __global__ void __launch_bounds__(NT) k_elim(ElimArgs<T> a) {
+  const LevelDev<T>& L = a.L;
+  const BoxRec<T> R = a.recs[blockIdx.x];
+  const int nmax = L.nmax, g = L.g, B = R.box, k = R.k, r = R.r, c = R.c;
+  const size_t nn = (size_t)nmax * nmax;
+  const int* perm = a.perm_in + (size_t)a.cls_idx[blockIdx.x] * nmax;
+  const T* Tw = a.T_ws + (size_t)a.cls_idx[blockIdx.x] * nn;
+  const int tid = threadIdx.x, bs = blockDim.x, lane = tid & 31, warp = tid >> 5;
+  __shared__ int nb[9], coff[10], s_piv, s_zero;
+  __shared__ int ord[9];
+  if (tid == 0) {
+    const int o9[9] = {4, 0, 1, 2, 3, 5, 6, 7, 8};
+    int off = 0;
+    for (int q = 0; q < 9; ++q) {
+      const int s = o9[q];
+      ord[q] = s;
+      nb[s] = nbr_box(B, g, s % 3 - 1, s / 3 - 1);
+      coff[q] = off;
+      off += s == 4 ? k : (nb[s] >= 0 ? L.nact[nb[s]] : 0);
+    }
+    coff[9] = off;
+  }
+  __syncthreads();
+  for (int i = tid; i < c; i += bs) {
+    int q = 0;
+    while (coff[q + 1] <= i) ++q;
+    const int s = ord[q], ii = i - coff[q], u = nb[s];
+    const int pos = s == 4 ? perm[ii] : L.act[u * nmax + ii];
+    R.cmap[i] = (s << 16) | pos;
+    R.idxC[i] = L.pts[u * nmax + pos];
+  }
+  for (int j = tid; j < r; j += bs) R.idxR[j] = L.pts[B * nmax + perm[k + j]];
+  for (int e = tid; e < k * r; e += bs) R.Tm[e] = Tw[(size_t)(e / k) * nmax + e % k];
+  __syncthreads();
+  // X_CR -> E (c x r), X_RC^T -> Ft (c x r)
+  for (long long e = tid; e < (long long)c * r; e += bs) {
+    const int i = (int)(e % c), j = (int)(e / c);
+    const int cm = R.cmap[i], s = cm >> 16, pos = cm & 0xffff, u = nb[s];
+    const T* Aub = L.blk + ((size_t)u * 25 + off_index(u, B, g)) * nn;   // rows of u, cols of B
+    const T* Abu = L.blk + ((size_t)B * 25 + off_index(B, u, g)) * nn;   // rows of B, cols of u
+    const int rj = perm[k + j];
+    T x = Aub[(size_t)rj * nmax + pos];
+    T y = Abu[(size_t)pos * nmax + rj];
+    for (int q = 0; q < k; ++q) {
+      const T t = Tw[(size_t)j * nmax + q];
+      x = msb(x, Aub[(size_t)perm[q] * nmax + pos], t);
+      y = msbc(y, t, Abu[(size_t)pos * nmax + perm[q]]);
+    }
+    R.E[i + (size_t)j * c] = x;
+    R.Ft[i + (size_t)j * c] = y;
+  }
+  __syncthreads();
+  // X_RR = A_RR - A_RS T - T^* X_SR  (X_SR = first k rows of X_CR)
+  const T* Abb = L.blk + ((size_t)B * 25 + 12) * nn;
+  for (int e = tid; e < r * r; e += bs) {
+    const int ai = e % r, bj = e / r;
+    T x = Abb[(size_t)perm[k + bj] * nmax + perm[k + ai]];
+    for (int q = 0; q < k; ++q) x = msb(x, Abb[(size_t)perm[q] * nmax + perm[k + ai]], Tw[(size_t)bj * nmax + q]);
+    for (int q = 0; q < k; ++q) x = msbc(x, Tw[(size_t)ai * nmax + q], R.E[q + (size_t)bj * c]);
+    R.LU[ai + (size_t)bj * r] = x;
+  }
+  __syncthreads();
+  // P X_RR = L U, partial pivoting (largest modulus, lowest row on ties)
+  T* LU = R.LU;
+  for (int j = 0; j < r; ++j) {
+    if (warp == 0) {
+      double mx = -1.0;
+      int mi = INT_MAX;
+      for (int i = j + lane; i < r; i += 32) {
+        const double v = abs2(LU[i + (size_t)j * r]);
+        if (v > mx) { mx = v; mi = i; }
+      }
+      for (int d = 16; d > 0; d >>= 1) {
+        const double om = __shfl_xor_sync(0xffffffffu, mx, d);
+        const int oi = __shfl_xor_sync(0xffffffffu, mi, d);
+        if (om > mx || (om == mx && oi < mi)) { mx = om; mi = oi; }
+      }
+      if (lane == 0) { s_piv = mi; s_zero = !(mx > 0.0); }
+    }
+    __syncthreads();
+    if (s_zero) {
+      if (tid == 0) atomicExch(a.err, (int)RSS_ENUMERIC);
+      return;
+    }
+    const int p = s_piv;
+    if (p != j)
+      for (int col = tid; col < r; col += bs) {
+        const T t = LU[j + (size_t)col * r];
+        LU[j + (size_t)col * r] = LU[p + (size_t)col * r];
+        LU[p + (size_t)col * r] = t;
+      }
+    if (tid == 0) R.piv[j] = p;
+    __syncthreads();
+    const T d = LU[j + (size_t)j * r];
+    for (int i = j + 1 + tid; i < r; i += bs) LU[i + (size_t)j * r] = dv(LU[i + (size_t)j * r], d);
+    __syncthreads();
+    const int w = r - j - 1;
+    for (int e = tid; e < w * w; e += bs) {
+      const int ii = j + 1 + e % w, jj = j + 1 + e / w;
+      LU[ii + (size_t)jj * r] = msb(LU[ii + (size_t)jj * r], LU[ii + (size_t)j * r], LU[j + (size_t)jj * r]);
+    }
+    __syncthreads();
+  }
+  // E = X_CR U^{-1} (row by row), F = L^{-1} P X_RC (column by column, kept transposed)
+  for (int i = tid; i < c; i += bs) {
+    T* e = R.E + i;
+    for (int j = 0; j < r; ++j) {
+      T x = e[(size_t)j * c];
+      for (int l = 0; l < j; ++l) x = msb(x, e[(size_t)l * c], LU[l + (size_t)j * r]);
+      e[(size_t)j * c] = dv(x, LU[j + (size_t)j * r]);
+    }
+    T* f = R.Ft + i;
+    for (int j = 0; j < r; ++j) {
+      const int p = R.piv[j];
+      if (p != j) {
+        const T t = f[(size_t)j * c];
+        f[(size_t)j * c] = f[(size_t)p * c];
+        f[(size_t)p * c] = t;
+      }
+    }
+    for (int j = 1; j < r; ++j) {
+      T x = f[(size_t)j * c];
+      for (int l = 0; l < j; ++l) x = msb(x, LU[j + (size_t)l * r], f[(size_t)l * c]);
+      f[(size_t)j * c] = x;
+    }
+  }
+  __syncthreads();
+  // B keeps only its skeleton
+  for (int q = tid; q < k; q += bs) L.act[B * nmax + q] = perm[q];
+  if (tid == 0) L.nact[B] = k;
+}
+
+// ------------------------------------------------------------------ Schur update A_CC -= E F
+template <typename T> __global__ void __launch_bounds__(NT) k_schur(LevelDev<T> L, const BoxRec<T>* recs) {
+  constexpr int TM = 64, KC = 16;
+  const BoxRec<T> R = recs[blockIdx.y];
+  const int c = R.c, r = R.r, nt = (c + TM - 1) / TM;
+  if ((int)blockIdx.x >= nt * nt) return;
+  const int i0 = (blockIdx.x % nt) * TM, j0 = (blockIdx.x / nt) * TM;
+  const int nmax = L.nmax, g = L.g;
+  const long long nn = (long long)nmax * nmax;
+  __shared__ T Es[KC][TM], Fs[KC][TM];
+  __shared__ long long rowb[TM], colb[TM];
+  const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+  if (tid < TM) {
+    const int i = i0 + tid;
+    if (i < c) {
+      const int cm = R.cmap[i], s = cm >> 16, pos = cm & 0xffff;
+      const int u = nbr_box(R.box, g, s % 3 - 1, s / 3 - 1);
+      rowb[tid] = (long long)u * 25 * nn + pos - (long long)((s / 3) * 5 + s % 3) * nn;
+    }
+  } else if (tid < 2 * TM) {
+    const int j = j0 + tid - TM;
+    if (j < c) {
+      const int cm = R.cmap[j], s = cm >> 16, pos = cm & 0xffff;
+      colb[tid - TM] = (long long)((s / 3) * 5 + s % 3 + 12) * nn + (long long)pos * nmax;
+    }
+  }
+  T acc[4][4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+#pragma unroll
+    for (int w = 0; w < 4; ++w) acc[q][w] = zero<T>();
+  for (int l0 = 0; l0 < r; l0 += KC) {
+    __syncthreads();
+    for (int e = tid; e < KC * TM; e += NT) {
+      const int ii = e % TM, ll = e / TM, l = l0 + ll;
+      Es[ll][ii] = (i0 + ii < c && l < r) ? R.E[i0 + ii + (size_t)l * c] : zero<T>();
+      Fs[ll][ii] = (j0 + ii < c && l < r) ? R.Ft[j0 + ii + (size_t)l * c] : zero<T>();
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int ll = 0; ll < KC; ++ll) {
+      T av[4], bv[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) { av[q] = Es[ll][tx + 16 * q]; bv[q] = Fs[ll][ty + 16 * q]; }
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int w = 0; w < 4; ++w) acc[q][w] = mad(acc[q][w], av[q], bv[w]);
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+#pragma unroll
+    for (int w = 0; w < 4; ++w) {
+      const int i = i0 + tx + 16 * q, j = j0 + ty + 16 * w;
+      if (i < c && j < c) {
+        T* p = L.blk + rowb[tx + 16 * q] + colb[ty + 16 * w];
+        *p = *p - acc[q][w];
+      }
+    }
+}
+
+// ------------------------------------------------------------------ merge (Section 2.4)
+template <typename T> __global__ void __launch_bounds__(NT) k_merge_pts(LevelDev<T> C, LevelDev<T> P) {
+  const int Pb = blockIdx.x, gp = P.g, px = Pb % gp, py = Pb / gp;
+  __shared__ int ch[4], off[5];
+  if (threadIdx.x == 0) {
+    int o = 0;
+    for (int q = 0; q < 4; ++q) {
+      ch[q] = (2 * py + q / 2) * C.g + 2 * px + q % 2;   // SW, SE, NW, NE
+      off[q] = o;
+      o += C.nact[ch[q]];
+    }
+    off[4] = o;
+    P.n[Pb] = o;
+    P.nact[Pb] = o;
+  }
+  __syncthreads();
+  for (int q = 0; q < 4; ++q)
+    for (int i = threadIdx.x; i < off[q + 1] - off[q]; i += blockDim.x)
+      P.pts[Pb * P.nmax + off[q] + i] = C.pts[ch[q] * C.nmax + C.act[ch[q] * C.nmax + i]];
+  for (int i = threadIdx.x; i < off[4]; i += blockDim.x) P.act[Pb * P.nmax + i] = i;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(NT) k_merge_blk(LevelDev<T> C, LevelDev<T> P, const int2* __restrict__ ixy,
+                                                  KParams kp, Geo geo) {
+  const int u = blockIdx.x / 25, o = blockIdx.x % 25;
+  const int v = nbr_box(u, P.g, o % 5 - 2, o / 5 - 2);
+  if (v < 0) return;
+  __shared__ int cu[4], cv[4], ou[5], ov[5];
+  if (threadIdx.x == 0) {
+    int a = 0, b = 0;
+    for (int q = 0; q < 4; ++q) {
+      cu[q] = (2 * (u / P.g) + q / 2) * C.g + 2 * (u % P.g) + q % 2;
+      cv[q] = (2 * (v / P.g) + q / 2) * C.g + 2 * (v % P.g) + q % 2;
+      ou[q] = a; a += C.nact[cu[q]];
+      ov[q] = b; b += C.nact[cv[q]];
+    }
+    ou[4] = a; ov[4] = b;
+  }
+  __syncthreads();
+  T* A = P.blk + ((size_t)u * 25 + o) * P.nmax * P.nmax;
+  const size_t cnn = (size_t)C.nmax * C.nmax;
+  for (int qa = 0; qa < 4; ++qa)
+    for (int qb = 0; qb < 4; ++qb) {
+      const int a = cu[qa], b = cv[qb], na = ou[qa + 1] - ou[qa], nb = ov[qb + 1] - ov[qb];
+      const int* acta = C.act + a * C.nmax;
+      const int* actb = C.act + b * C.nmax;
+      if (cheb(a, b, C.g) <= 2) {
+        const T* S = C.blk + ((size_t)a * 25 + off_index(a, b, C.g)) * cnn;
+        for (int e = threadIdx.x; e < na * nb; e += blockDim.x) {
+          const int i = e % na, j = e / na;
+          A[(size_t)(ov[qb] + j) * P.nmax + ou[qa] + i] = S[(size_t)actb[j] * C.nmax + acta[i]];
+        }
+      } else {   // never modified: kernel evaluation (Theorem 1)
+        for (int e = threadIdx.x; e < na * nb; e += blockDim.x) {
+          const int i = e % na, j = e / na;
+          A[(size_t)(ov[qb] + j) * P.nmax + ou[qa] + i] =
+              aval<T>(kp, geo, ixy[C.pts[a * C.nmax + acta[i]]], ixy[C.pts[b * C.nmax + actb[j]]]);
+        }
+      }
+    }
+}
+
+// ------------------------------------------------------------------ dense top
+template <typename T>
+__global__ void __launch_bounds__(NT) k_top_assemble(LevelDev<T> L, T* D, int ntop, int* top_idx, int4 offs_lo,
+                                                     int offs_hi) {
+  const int offs[5] = {offs_lo.x, offs_lo.y, offs_lo.z, offs_lo.w, offs_hi};
+  const int u = blockIdx.x / L.nbox, v = blockIdx.x % L.nbox;
+  const int nu = L.n[u], nv = L.n[v];
+  const T* A = L.blk + ((size_t)u * 25 + off_index(u, v, L.g)) * L.nmax * L.nmax;
+  for (int e = threadIdx.x; e < nu * nv; e += blockDim.x) {
+    const int i = e % nu, j = e / nu;
+    D[(size_t)(offs[v] + j) * ntop + offs[u] + i] = A[(size_t)j * L.nmax + i];
+  }
+  if (v == 0)
+    for (int i = threadIdx.x; i < nu; i += blockDim.x) top_idx[offs[u] + i] = L.pts[u * L.nmax + i];
+}
+
+template <typename T> __global__ void __launch_bounds__(1024) k_dense_lu(T* A, int n, int* piv, int* err) {
+  __shared__ int s_piv, s_zero;
+  const int tid = threadIdx.x, bs = blockDim.x, lane = tid & 31, warp = tid >> 5;
+  for (int j = 0; j < n; ++j) {
+    if (warp == 0) {
+      double mx = -1.0;
+      int mi = INT_MAX;
+      for (int i = j + lane; i < n; i += 32) {
+        const double v = abs2(A[i + (size_t)j * n]);
+        if (v > mx) { mx = v; mi = i; }
+      }
+      for (int d = 16; d > 0; d >>= 1) {
+        const double om = __shfl_xor_sync(0xffffffffu, mx, d);
+        const int oi = __shfl_xor_sync(0xffffffffu, mi, d);
+        if (om > mx || (om == mx && oi < mi)) { mx = om; mi = oi; }
+      }
+      if (lane == 0) { s_piv = mi; s_zero = !(mx > 0.0); }
+    }
+    __syncthreads();
+    if (s_zero) {
+      if (tid == 0) atomicExch(err, (int)RSS_ENUMERIC);
+      return;
+    }
+    const int p = s_piv;
+    if (p != j)
+      for (int col = tid; col < n; col += bs) {
+        const T t = A[j + (size_t)col * n];
+        A[j + (size_t)col * n] = A[p + (size_t)col * n];
+        A[p + (size_t)col * n] = t;
+      }
+    if (tid == 0) piv[j] = p;
+    __syncthreads();
+    const T d = A[j + (size_t)j * n];
+    for (int i = j + 1 + tid; i < n; i += bs) A[i + (size_t)j * n] = dv(A[i + (size_t)j * n], d);
+    __syncthreads();
+    const int w = n - j - 1;
+    for (int e = tid; e < w * w; e += bs) {
+      const int ii = j + 1 + e % w, jj = j + 1 + e / w;
+      A[ii + (size_t)jj * n] = msb(A[ii + (size_t)jj * n], A[ii + (size_t)j * n], A[j + (size_t)jj * n]);
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------------ host helpers
+template <typename T> struct HostLevel {
+  LevelDev<T> d{};
+  std::vector<int32_t> n, nact;
+};
+
+template <typename T> void free_level(HostLevel<T>& L) {
+  cudaFree(L.d.pts); cudaFree(L.d.n); cudaFree(L.d.act); cudaFree(L.d.nact); cudaFree(L.d.blk);
+  L.d = LevelDev<T>{};
+}
+
+template <typename T> rss_status alloc_level(HostLevel<T>& L, int g, int nmax, size_t& transient) {
+  L.d.g = g;
+  L.d.nbox = g * g;
+  L.d.nmax = nmax;
+  const size_t nb = (size_t)g * g;
+  RSS_CUDA(cudaMalloc(&L.d.pts, sizeof(int) * nb * nmax));
+  RSS_CUDA(cudaMalloc(&L.d.n, sizeof(int) * nb));
+  RSS_CUDA(cudaMalloc(&L.d.act, sizeof(int) * nb * nmax));
+  RSS_CUDA(cudaMalloc(&L.d.nact, sizeof(int) * nb));
+  const size_t bytes = sizeof(T) * nb * 25 * (size_t)nmax * nmax;
+  RSS_CUDA(cudaMalloc(&L.d.blk, bytes));
+  transient += bytes;
+  return RSS_OK;
+}
+
+// Device time of a phase: events recorded on the factor's stream around it.
+struct Ev {
+  cudaEvent_t a = nullptr, b = nullptr;
+  Ev() { cudaEventCreate(&a); cudaEventCreate(&b); }
+  ~Ev() { cudaEventDestroy(a); cudaEventDestroy(b); }
+  void start(cudaStream_t st) { cudaEventRecord(a, st); }
+  void stop(cudaStream_t st) { cudaEventRecord(b, st); }
+  double ms() {   // call after the stream has been synchronised
+    float t = 0.f;
+    cudaEventElapsedTime(&t, a, b);
+    return t;
+  }
+};
+
+struct Timer {
+  std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
+  double ms() const {
+    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  }
+};
+
+}  // namespace
+
+template <typename T>
+rss_status factor_impl(const rss_tree* tree, const rss_params* prm, cudaStream_t st, rss_factorization* f) {
+  Timer total;
+  f->n = tree->n;
+  f->side = tree->side;
+  f->leaf = tree->leaf;
+  f->gL = tree->gL;
+  f->geo = tree->geo;
+  f->tree_to_user = tree->tree_to_user;
+  const int P = f->params.proxy_n;
+  const double ratio = f->params.proxy_radius_over_side;
+  const double extent = tree->side * tree->geo.hg;
+  const int64_t N = tree->n;
+
+  RSS_CUDA(cudaMalloc(&f->d_user_to_tree, sizeof(int32_t) * N));
+  RSS_CUDA(cudaMemcpyAsync(f->d_user_to_tree, tree->user_to_tree.data(), sizeof(int32_t) * N,
+                           cudaMemcpyHostToDevice, st));
+  // integer grid coordinates of each tree index
+  std::vector<int2> hixy(N);
+  for (int64_t t = 0; t < N; ++t) {
+    const int b = (int)(t / tree->leaf), l = (int)(t % tree->leaf);
+    hixy[t] = make_int2((b % tree->gL) * tree->ls + l % tree->ls, (b / tree->gL) * tree->ls + l / tree->ls);
+  }
+  int2* d_ixy = static_cast<int2*>(f->arena.get(sizeof(int2) * N));
+  int* d_err = static_cast<int*>(f->arena.get(sizeof(int)));
+  if (!d_ixy || !d_err) { rss_set_error("rss_factor: device arena allocation failed"); return RSS_ENOMEM; }
+  RSS_CUDA(cudaMemcpyAsync(d_ixy, hixy.data(), sizeof(int2) * N, cudaMemcpyHostToDevice, st));
+  RSS_CUDA(cudaMemsetAsync(d_err, 0, sizeof(int), st));
+
+  // leaf level
+  size_t transient = 0;
+  HostLevel<T> cur;
+  int g = tree->gL;
+  {
+    rss_status s = alloc_level(cur, g, tree->leaf, transient);
+    if (s != RSS_OK) return s;
+    const int nbox = g * g, leaf = tree->leaf;
+    std::vector<int> hp((size_t)nbox * leaf), hn(nbox, leaf);
+    for (int b = 0; b < nbox; ++b)
+      for (int i = 0; i < leaf; ++i) hp[(size_t)b * leaf + i] = b * leaf + i;
+    std::vector<int> ha((size_t)nbox * leaf);
+    for (int b = 0; b < nbox; ++b)
+      for (int i = 0; i < leaf; ++i) ha[(size_t)b * leaf + i] = i;
+    RSS_CUDA(cudaMemcpyAsync(cur.d.pts, hp.data(), sizeof(int) * hp.size(), cudaMemcpyHostToDevice, st));
+    RSS_CUDA(cudaMemcpyAsync(cur.d.act, ha.data(), sizeof(int) * ha.size(), cudaMemcpyHostToDevice, st));
+    RSS_CUDA(cudaMemcpyAsync(cur.d.n, hn.data(), sizeof(int) * nbox, cudaMemcpyHostToDevice, st));
+    RSS_CUDA(cudaMemcpyAsync(cur.d.nact, hn.data(), sizeof(int) * nbox, cudaMemcpyHostToDevice, st));
+    RSS_CUDA(cudaStreamSynchronize(st));
+    cur.n = hn;
+    cur.nact = hn;
+    Timer tg;
+    Ev ev;
+    ev.start(st);
+    k_gen_blocks<T><<<nbox * 25, NT, 0, st>>>(cur.d, d_ixy, f->kp, f->geo);
+    RSS_LAUNCHED();
+    ev.stop(st);
+    RSS_CUDA(cudaStreamSynchronize(st));
+    f->t_gen += tg.ms();
+    f->g_gen += ev.ms();
+    f->launches += 1;
+  }
+
+  while (g >= 4) {
+    const int nbox = g * g, nmax = cur.d.nmax;
+    const size_t nn = (size_t)nmax * nmax;
+    const double Lbox = extent / g;
+    LevelInfo info;
+    info.side = g;
+    info.n = cur.n;
+    info.k = cur.n;
+    // colour classes
+    std::vector<int> cls;
+    std::vector<int> coff(10, 0);
+    for (int col = 0; col < 9; ++col) {
+      coff[col] = (int)cls.size();
+      for (int by = col / 3; by < g; by += 3)
+        for (int bx = col % 3; bx < g; bx += 3) cls.push_back(by * g + bx);
+    }
+    coff[9] = (int)cls.size();
+    int* d_cls = nullptr;
+    RSS_CUDA(cudaMalloc(&d_cls, sizeof(int) * cls.size()));
+    RSS_CUDA(cudaMemcpyAsync(d_cls, cls.data(), sizeof(int) * cls.size(), cudaMemcpyHostToDevice, st));
+    int maxcls = 0;
+    for (int col = 0; col < 9; ++col) maxcls = std::max(maxcls, coff[col + 1] - coff[col]);
+    int *d_k = nullptr, *d_perm = nullptr, *d_clsidx = nullptr;
+    T* d_Tws = nullptr;
+    RSS_CUDA(cudaMalloc(&d_k, sizeof(int) * maxcls));
+    RSS_CUDA(cudaMalloc(&d_perm, sizeof(int) * (size_t)maxcls * nmax));
+    RSS_CUDA(cudaMalloc(&d_clsidx, sizeof(int) * maxcls));
+    RSS_CUDA(cudaMalloc(&d_Tws, sizeof(T) * (size_t)maxcls * nn));
+    std::vector<int> hk(maxcls);
+
+    for (int col = 0; col < 9; ++col) {
+      const int nb = coff[col + 1] - coff[col];
+      if (nb == 0) continue;
+      const int* boxes = cls.data() + coff[col];
+      // rows of Y per box, from the host copy of the active counts
+      int mmax = 0;
+      std::vector<int> mrows(nb);
+      for (int q = 0; q < nb; ++q) {
+        const int B = boxes[q], bx = B % g, by = B / g;
+        int mh = 0;
+        for (int dy = -2; dy <= 2; ++dy)
+          for (int dx = -2; dx <= 2; ++dx) {
+            if (std::max(std::abs(dx), std::abs(dy)) != 2) continue;
+            const int x = bx + dx, y = by + dy;
+            if (x < 0 || y < 0 || x >= g || y >= g) continue;
+            mh += cur.nact[y * g + x];
+          }
+        mrows[q] = 2 * (mh + P);
+        mmax = std::max(mmax, mrows[q]);
+      }
+      const int ldY = (mmax + 1) & ~1;
+      const size_t slot = (size_t)ldY * nmax * sizeof(T);
+      const size_t ybudget = size_t(2) << 30;
+      const int chunk = (int)std::max<size_t>(1, std::min<size_t>(nb, ybudget / slot));
+      T* d_Y = nullptr;
+      RSS_CUDA(cudaMalloc(&d_Y, slot * chunk));
+      f->peak_transient = std::max(f->peak_transient, transient + slot * chunk);
+      Timer tid_;
+      Ev evid;
+      evid.start(st);
+      for (int c0 = 0; c0 < nb; c0 += chunk) {
+        IdArgs<T> a;
+        a.L = cur.d;
+        a.boxes = d_cls + coff[col];
+        a.base = c0;
+        a.Y = d_Y;
+        a.ldY = ldY;
+        a.k_out = d_k;
+        a.perm_out = d_perm;
+        a.T_ws = d_Tws;
+        a.ixy = d_ixy;
+        a.kp = f->kp;
+        a.geo = f->geo;
+        a.eps = f->params.eps;
+        a.P = P;
+        a.rho = ratio * Lbox;
+        a.Lbox = Lbox;
+        const int cnt = std::min(chunk, nb - c0);
+        const size_t smem = (size_t)nmax * (2 * sizeof(double) + sizeof(int));
+        k_id<T><<<cnt, NT, smem, st>>>(a);
+        RSS_LAUNCHED();
+        f->launches += 1;
+        f->n_id += 1;
+      }
+      evid.stop(st);
+      RSS_CUDA(cudaMemcpyAsync(hk.data(), d_k, sizeof(int) * nb, cudaMemcpyDeviceToHost, st));
+      RSS_CUDA(cudaStreamSynchronize(st));
+      cudaFree(d_Y);
+      f->t_id += tid_.ms();
+      f->g_id += evid.ms();
+      const double cf = sizeof(T) == sizeof(double) ? 1.0 : 4.0;
+      for (int q = 0; q < nb; ++q) {   // Householder CPQR: 4 (m-j)(n-j-1) per step, norms, T
+        const double m = mrows[q], n = cur.n[boxes[q]], k = hk[q];
+        double fl = 2.0 * m * n + k * k * (n - k);
+        for (int j = 0; j < hk[q]; ++j) fl += 4.0 * (m - j) * (n - j - 1);
+        f->f_id += cf * fl;
+      }
+
+      // records for the boxes that have redundant points
+      std::vector<BoxRec<T>> recs;
+      std::vector<int> clsidx;
+      int max_k = 0, max_r = 0, max_c = 0;
+      for (int q = 0; q < nb; ++q) {
+        const int B = boxes[q], bx = B % g, by = B / g;
+        const int k = hk[q], n = cur.n[B], r = n - k;
+        info.k[B] = k;
+        if (r <= 0) continue;
+        int c = k;
+        for (int dy = -1; dy <= 1; ++dy)
+          for (int dx = -1; dx <= 1; ++dx) {
+            if (!dx && !dy) continue;
+            const int x = bx + dx, y = by + dy;
+            if (x < 0 || y < 0 || x >= g || y >= g) continue;
+            c += cur.nact[y * g + x];
+          }
+        BoxRec<T> R{};
+        R.box = B; R.k = k; R.r = r; R.c = c;
+        R.Tm = static_cast<T*>(f->arena.get(sizeof(T) * (size_t)k * r));
+        R.LU = static_cast<T*>(f->arena.get(sizeof(T) * (size_t)r * r));
+        R.piv = static_cast<int*>(f->arena.get(sizeof(int) * r));
+        R.E = static_cast<T*>(f->arena.get(sizeof(T) * (size_t)c * r));
+        R.Ft = static_cast<T*>(f->arena.get(sizeof(T) * (size_t)c * r));
+        R.idxR = static_cast<int*>(f->arena.get(sizeof(int) * r));
+        R.idxC = static_cast<int*>(f->arena.get(sizeof(int) * c));
+        R.cmap = static_cast<int*>(f->arena.get(sizeof(int) * c));
+        if (!R.Tm || !R.LU || !R.piv || !R.E || !R.Ft || !R.idxR || !R.idxC || !R.cmap) {
+          rss_set_error("rss_factor: device arena allocation failed");
+          return RSS_ENOMEM;
+        }
+        recs.push_back(R);
+        clsidx.push_back(q);
+        {
+          const double cf = sizeof(T) == sizeof(double) ? 1.0 : 4.0;
+          const double K = k, Rr = r, Cc = c;
+          f->f_elim += cf * (4.0 * Cc * K * Rr + 4.0 * Rr * Rr * K + 2.0 * Rr * Rr * Rr / 3.0 + 2.0 * Cc * Rr * Rr);
+          f->f_schur += cf * 2.0 * Cc * Cc * Rr;
+        }
+        max_k = std::max(max_k, k); max_r = std::max(max_r, r); max_c = std::max(max_c, c);
+      }
+      for (int q = 0; q < nb; ++q)
+        if (cur.n[boxes[q]] - hk[q] > 0) cur.nact[boxes[q]] = hk[q];
+      if (recs.empty()) continue;
+      const int nrec = (int)recs.size();
+      BoxRec<T>* d_recs = static_cast<BoxRec<T>*>(f->arena.get(sizeof(BoxRec<T>) * nrec));
+      if (!d_recs) { rss_set_error("rss_factor: device arena allocation failed"); return RSS_ENOMEM; }
+      RSS_CUDA(cudaMemcpyAsync(d_recs, recs.data(), sizeof(BoxRec<T>) * nrec, cudaMemcpyHostToDevice, st));
+      RSS_CUDA(cudaMemcpyAsync(d_clsidx, clsidx.data(), sizeof(int) * nrec, cudaMemcpyHostToDevice, st));
+      Timer te;
+      Ev evel, evsc;
+      ElimArgs<T> ea;
+      ea.L = cur.d;
+      ea.recs = d_recs;
+      ea.cls_idx = d_clsidx;
+      ea.perm_in = d_perm;
+      ea.T_ws = d_Tws;
+      ea.err = d_err;
+      evel.start(st);
+      k_elim<T><<<nrec, NT, 0, st>>>(ea);
+      RSS_LAUNCHED();
+      evel.stop(st);
+      RSS_CUDA(cudaStreamSynchronize(st));
+      f->t_elim += te.ms();
+      Timer ts;
+      const int ntile = (max_c + 63) / 64;
+      evsc.start(st);
+      k_schur<T><<<dim3(ntile * ntile, nrec), NT, 0, st>>>(cur.d, d_recs);
+      RSS_LAUNCHED();
+      evsc.stop(st);
+      RSS_CUDA(cudaStreamSynchronize(st));
+      f->t_schur += ts.ms();
+      f->g_elim += evel.ms();
+      f->g_schur += evsc.ms();
+      f->launches += 2;
+      f->n_elim += 1;
+      f->n_schur += 1;
+      void* hcopy = std::malloc(sizeof(BoxRec<T>) * nrec);
+      if (!hcopy) { rss_set_error("rss_factor: host allocation failed"); return RSS_ENOMEM; }
+      std::memcpy(hcopy, recs.data(), sizeof(BoxRec<T>) * nrec);
+      f->rec_host.push_back(hcopy);
+      f->batches.push_back(Batch{g, col, nrec, d_recs, max_k, max_r, max_c});
+    }
+    cudaFree(d_cls); cudaFree(d_k); cudaFree(d_perm); cudaFree(d_clsidx); cudaFree(d_Tws);
+    int herr = 0;
+    RSS_CUDA(cudaMemcpy(&herr, d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (herr) { rss_set_error("rss_factor: zero pivot in the LU of a redundant block"); return RSS_ENUMERIC; }
+    f->levels.push_back(info);
+
+    // merge to the parent level
+    Timer tm;
+    const int gp = g / 2;
+    HostLevel<T> par;
+    par.n.assign(gp * gp, 0);
+    int pmax = 1;
+    for (int Pb = 0; Pb < gp * gp; ++Pb) {
+      const int px = Pb % gp, py = Pb / gp;
+      int s = 0;
+      for (int q = 0; q < 4; ++q) s += cur.nact[(2 * py + q / 2) * g + 2 * px + q % 2];
+      par.n[Pb] = s;
+      pmax = std::max(pmax, s);
+    }
+    if (pmax > 65535) { rss_set_error("rss_factor: box too large after merging"); return RSS_EINVAL; }
+    par.nact = par.n;
+    {
+      rss_status s = alloc_level(par, gp, pmax, transient);
+      if (s != RSS_OK) return s;
+    }
+    f->peak_transient = std::max(f->peak_transient, transient);
+    Ev evm;
+    evm.start(st);
+    k_merge_pts<T><<<gp * gp, NT, 0, st>>>(cur.d, par.d);
+    RSS_LAUNCHED();
+    k_merge_blk<T><<<gp * gp * 25, NT, 0, st>>>(cur.d, par.d, d_ixy, f->kp, f->geo);
+    RSS_LAUNCHED();
+    evm.stop(st);
+    RSS_CUDA(cudaStreamSynchronize(st));
+    f->g_merge += evm.ms();
+    f->launches += 2;
+    transient -= sizeof(T) * (size_t)nbox * 25 * nn;
+    free_level(cur);
+    cur = par;
+    g = gp;
+    f->t_merge += tm.ms();
+  }
+
+  // dense LU of everything still active (box grid side <= 2)
+  Timer tt;
+  {
+    const int nbox = g * g;
+    int offs[5] = {0, 0, 0, 0, 0};
+    for (int b = 0; b < nbox; ++b) offs[b + 1] = offs[b] + cur.n[b];
+    for (int b = nbox + 1; b < 5; ++b) offs[b] = offs[nbox];
+    const int ntop = offs[nbox];
+    f->ntop = ntop;
+    f->d_top_lu = f->arena.get(sizeof(T) * (size_t)ntop * ntop);
+    f->d_top_piv = static_cast<int*>(f->arena.get(sizeof(int) * ntop));
+    f->d_top_idx = static_cast<int*>(f->arena.get(sizeof(int) * ntop));
+    if (!f->d_top_lu || !f->d_top_piv || !f->d_top_idx) {
+      rss_set_error("rss_factor: device arena allocation failed");
+      return RSS_ENOMEM;
+    }
+    Ev evt;
+    evt.start(st);
+    k_top_assemble<T><<<nbox * nbox, NT, 0, st>>>(cur.d, static_cast<T*>(f->d_top_lu), ntop, f->d_top_idx,
+                                                  make_int4(offs[0], offs[1], offs[2], offs[3]), offs[4]);
+    RSS_LAUNCHED();
+    k_dense_lu<T><<<1, 1024, 0, st>>>(static_cast<T*>(f->d_top_lu), ntop, f->d_top_piv, d_err);
+    RSS_LAUNCHED();
+    evt.stop(st);
+    f->launches += 2;
+    RSS_CUDA(cudaStreamSynchronize(st));
+    f->g_top += evt.ms();
+    f->f_top += (sizeof(T) == sizeof(double) ? 1.0 : 4.0) * 2.0 * (double)ntop * ntop * ntop / 3.0;
+    free_level(cur);
+    int herr = 0;
+    RSS_CUDA(cudaMemcpy(&herr, d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (herr) { rss_set_error("rss_factor: zero pivot in the dense top LU"); return RSS_ENUMERIC; }
+  }
+  f->t_top += tt.ms();
+  f->t_total = total.ms();
+  return RSS_OK;
+}
+
+template rss_status factor_impl<double>(const rss_tree*, const rss_params*, cudaStream_t, rss_factorization*);
+template rss_status factor_impl<zd>(const rss_tree*, const rss_params*, cudaStream_t, rss_factorization*);

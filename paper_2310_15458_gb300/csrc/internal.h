@@ -1,0 +1,100 @@
+// Host-side objects behind the opaque rss_tree / rss_factor handles.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+
+enum : uint32_t { RSS_TAG_TREE = 0x52545245u, RSS_TAG_FACTOR = 0x52464143u };
+
+// Quadtree over a uniform grid (Section 2.1).  Tree order: leaf boxes
+// row-major over the leaf box grid, points row-major inside a leaf box.
+struct rss_tree {
+  uint32_t tag = RSS_TAG_TREE;
+  int64_t n = 0;
+  int side = 0;       // grid points per row
+  int leaf = 0;       // points per leaf box
+  int ls = 0;         // leaf box side in points
+  int gL = 0;         // leaf box grid side
+  Geo geo{};
+  std::vector<int32_t> user_to_tree;  // tree index of each user point
+  std::vector<int32_t> tree_to_user;
+};
+
+// One eliminated box (Eq. 8 / Eq. 9 record).  All pointers are device memory
+// inside the factor's arena.  Matrices are column-major.
+template <typename T> struct BoxRec {
+  int box, k, r, c;
+  T* Tm;        // k x r, ld k
+  T* LU;        // r x r packed LU of X_RR, ld r
+  int* piv;     // r getrf pivots (0-based)
+  T* E;         // c x r, ld c:  X_CR U_R^{-1}
+  T* Ft;        // c x r, ld c:  (L_R^{-1} P_R X_RC)^T (plain transpose)
+  int* idxR;    // r tree indices of R
+  int* idxC;    // c tree indices of C = S then the neighbours' active points
+  int* cmap;    // c entries (slot << 16 | position) used by the Schur update
+};
+
+struct Batch {
+  int side;       // box grid side of the level
+  int colour;
+  int nrec;
+  void* d_recs;   // BoxRec<T>[nrec] on the device
+  int max_k, max_r, max_c;
+};
+
+struct LevelInfo {
+  int side;
+  std::vector<int32_t> n;   // points per box at level start
+  std::vector<int32_t> k;   // skeleton rank per box
+};
+
+// Device memory arena: big chunks, bump allocation, freed together.
+struct Arena {
+  std::vector<void*> chunks;
+  char* cur = nullptr;
+  size_t left = 0;
+  size_t total = 0;
+  size_t chunk_min = size_t(256) << 20;
+  void* get(size_t bytes);   // nullptr on failure
+  void release();
+};
+
+struct rss_factorization {
+  uint32_t tag = RSS_TAG_FACTOR;
+  bool is_complex = false;
+  int64_t n = 0;
+  int side = 0, leaf = 0, gL = 0;
+  rss_params params{};
+  KParams kp{};
+  Geo geo{};
+  int32_t* d_user_to_tree = nullptr;   // n
+  std::vector<int32_t> tree_to_user;   // host copy, for inspection calls
+  Arena arena;
+  std::vector<Batch> batches;          // factor order
+  std::vector<void*> rec_host;         // host copies of the BoxRec arrays (owned)
+  std::vector<LevelInfo> levels;
+  // top dense block
+  int ntop = 0;
+  void* d_top_lu = nullptr;            // ntop x ntop
+  int* d_top_piv = nullptr;
+  int* d_top_idx = nullptr;            // tree indices
+  // wall times (ms, host clock around each synchronised phase) for rss_info
+  double t_gen = 0, t_id = 0, t_elim = 0, t_schur = 0, t_merge = 0, t_top = 0, t_total = 0;
+  // device times (ms, CUDA events on the factor's stream), algorithmic real
+  // flops (a complex multiply-add counts 8) and launch counts per phase
+  double g_gen = 0, g_id = 0, g_elim = 0, g_schur = 0, g_merge = 0, g_top = 0;
+  double f_id = 0, f_elim = 0, f_schur = 0, f_top = 0;
+  long long n_id = 0, n_elim = 0, n_schur = 0;
+  long long launches = 0;
+  size_t peak_transient = 0;
+};
+
+template <typename T> rss_status factor_impl(const rss_tree* tree, const rss_params* p,
+                                             cudaStream_t st, rss_factorization* f);
+template <typename T> rss_status solve_impl(const rss_factorization* f, T* b_dev, int64_t nrhs,
+                                            int64_t ldb, cudaStream_t st);
+void free_factor(rss_factorization* f);

@@ -1,0 +1,266 @@
+// Applying the factorization (Section 2.5): x = W_1 .. W_K A_top^{-1} V_K .. V_1 b.
+//
+// Upward sweep, boxes in factor order (each colour class in one launch):
+//   b_R -= T^* b_S;  b_R <- L_R^{-1} P_R b_R;  b_C -= E b_R          (apply V)
+// dense top solve, then the downward sweep in reverse order:
+//   y_R <- U_R^{-1} (y_R - F y_C);  y_S -= T y_R                       (apply W)
+// Boxes of one colour class touch disjoint entries of x, so a class is one
+// launch; the right-hand sides are split into chunks of RC columns.
+#include <algorithm>
+
+#include "internal.h"
+
+namespace {
+
+constexpr int NT = 256;
+
+template <typename T>
+__global__ void k_perm_in(const T* __restrict__ b, int64_t ldb, T* __restrict__ x, int64_t N, int nrhs,
+                          const int* __restrict__ u2t) {
+  const long long tot = (long long)N * nrhs;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
+    const long long i = e % N, j = e / N;
+    x[u2t[i] + j * N] = b[i + j * ldb];
+  }
+}
+
+template <typename T>
+__global__ void k_perm_out(T* __restrict__ b, int64_t ldb, const T* __restrict__ x, int64_t N, int nrhs,
+                           const int* __restrict__ u2t) {
+  const long long tot = (long long)N * nrhs;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
+    const long long i = e % N, j = e / N;
+    b[i + j * ldb] = x[u2t[i] + j * N];
+  }
+}
+
+template <typename T, int RC>
+__global__ void __launch_bounds__(NT) k_solve_up(const BoxRec<T>* __restrict__ recs, T* __restrict__ x, int64_t N,
+                                                 int nrhs) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const BoxRec<T> R = recs[blockIdx.x];
+  const int k = R.k, r = R.r, c = R.c;
+  const int q0 = blockIdx.y * RC, nq = min(RC, nrhs - q0);
+  T* bS = reinterpret_cast<T*>(smraw);   // k x RC
+  T* bR = bS + (size_t)k * RC;           // r x RC
+  const int tid = threadIdx.x, bs = blockDim.x;
+  T* xq = x + (int64_t)q0 * N;
+  for (int e = tid; e < k * RC; e += bs) {
+    const int s = e / RC, q = e % RC;
+    bS[e] = q < nq ? xq[R.idxC[s] + (int64_t)q * N] : zero<T>();
+  }
+  for (int e = tid; e < r * RC; e += bs) {
+    const int j = e / RC, q = e % RC;
+    bR[e] = q < nq ? xq[R.idxR[j] + (int64_t)q * N] : zero<T>();
+  }
+  __syncthreads();
+  for (int e = tid; e < r * RC; e += bs) {        // b_R -= T^* b_S
+    const int j = e / RC, q = e % RC;
+    T acc = bR[e];
+    for (int s = 0; s < k; ++s) acc = msbc(acc, R.Tm[s + (size_t)j * k], bS[s * RC + q]);
+    bR[e] = acc;
+  }
+  __syncthreads();
+  if (tid < RC)
+    for (int j = 0; j < r; ++j) {                 // P_R
+      const int p = R.piv[j];
+      if (p != j) {
+        const T t = bR[j * RC + tid];
+        bR[j * RC + tid] = bR[p * RC + tid];
+        bR[p * RC + tid] = t;
+      }
+    }
+  __syncthreads();
+  for (int j = 0; j + 1 < r; ++j) {               // L_R^{-1} (unit lower)
+    const int w = (r - j - 1) * RC;
+    for (int e = tid; e < w; e += bs) {
+      const int l = j + 1 + e / RC, q = e % RC;
+      bR[l * RC + q] = msb(bR[l * RC + q], R.LU[l + (size_t)j * r], bR[j * RC + q]);
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < r * RC; e += bs) {
+    const int j = e / RC, q = e % RC;
+    if (q < nq) xq[R.idxR[j] + (int64_t)q * N] = bR[e];
+  }
+  for (int i = tid; i < c; i += bs) {             // b_C -= E b_R
+    T acc[RC];
+#pragma unroll
+    for (int q = 0; q < RC; ++q) acc[q] = zero<T>();
+    for (int j = 0; j < r; ++j) {
+      const T e = R.E[i + (size_t)j * c];
+#pragma unroll
+      for (int q = 0; q < RC; ++q) acc[q] = mad(acc[q], e, bR[j * RC + q]);
+    }
+    const int gi = R.idxC[i];
+#pragma unroll
+    for (int q = 0; q < RC; ++q)
+      if (q < nq) xq[gi + (int64_t)q * N] = xq[gi + (int64_t)q * N] - acc[q];
+  }
+}
+
+template <typename T, int RC>
+__global__ void __launch_bounds__(NT) k_solve_down(const BoxRec<T>* __restrict__ recs, T* __restrict__ x,
+                                                   int64_t N, int nrhs) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const BoxRec<T> R = recs[blockIdx.x];
+  const int k = R.k, r = R.r, c = R.c;
+  const int q0 = blockIdx.y * RC, nq = min(RC, nrhs - q0);
+  T* yR = reinterpret_cast<T*>(smraw);   // r x RC
+  const int tid = threadIdx.x, bs = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = bs >> 5;
+  T* xq = x + (int64_t)q0 * N;
+  for (int j = warp; j < r; j += nw) {            // y_R - F y_C
+    T acc[RC];
+#pragma unroll
+    for (int q = 0; q < RC; ++q) acc[q] = zero<T>();
+    for (int i = lane; i < c; i += 32) {
+      const T fv = R.Ft[i + (size_t)j * c];
+      const int gi = R.idxC[i];
+#pragma unroll
+      for (int q = 0; q < RC; ++q)
+        if (q < nq) acc[q] = mad(acc[q], fv, xq[gi + (int64_t)q * N]);
+    }
+#pragma unroll
+    for (int q = 0; q < RC; ++q) acc[q] = warp_sum(acc[q]);
+    if (lane == 0) {
+      const int gj = R.idxR[j];
+#pragma unroll
+      for (int q = 0; q < RC; ++q) yR[j * RC + q] = q < nq ? xq[gj + (int64_t)q * N] - acc[q] : zero<T>();
+    }
+  }
+  __syncthreads();
+  for (int j = r - 1; j >= 0; --j) {              // U_R^{-1}
+    if (tid < RC) yR[j * RC + tid] = dv(yR[j * RC + tid], R.LU[j + (size_t)j * r]);
+    __syncthreads();
+    const int w = j * RC;
+    for (int e = tid; e < w; e += bs) {
+      const int l = e / RC, q = e % RC;
+      yR[l * RC + q] = msb(yR[l * RC + q], R.LU[l + (size_t)j * r], yR[j * RC + q]);
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < r * RC; e += bs) {
+    const int j = e / RC, q = e % RC;
+    if (q < nq) xq[R.idxR[j] + (int64_t)q * N] = yR[e];
+  }
+  for (int e = tid; e < k * RC; e += bs) {        // y_S -= T y_R
+    const int s = e / RC, q = e % RC;
+    if (q >= nq) continue;
+    T acc = zero<T>();
+    for (int j = 0; j < r; ++j) acc = mad(acc, R.Tm[s + (size_t)j * k], yR[j * RC + q]);
+    const int gs = R.idxC[s];
+    xq[gs + (int64_t)q * N] = xq[gs + (int64_t)q * N] - acc;
+  }
+}
+
+template <typename T, int RC>
+__global__ void __launch_bounds__(1024) k_top_solve(const T* __restrict__ LU, const int* __restrict__ piv,
+                                                    const int* __restrict__ idx, int n, T* __restrict__ x,
+                                                    int64_t N, int nrhs) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* z = reinterpret_cast<T*>(smraw);   // n x RC
+  const int q0 = blockIdx.x * RC, nq = min(RC, nrhs - q0);
+  const int tid = threadIdx.x, bs = blockDim.x;
+  T* xq = x + (int64_t)q0 * N;
+  for (int e = tid; e < n * RC; e += bs) {
+    const int i = e / RC, q = e % RC;
+    z[e] = q < nq ? xq[idx[i] + (int64_t)q * N] : zero<T>();
+  }
+  __syncthreads();
+  if (tid < RC)
+    for (int j = 0; j < n; ++j) {
+      const int p = piv[j];
+      if (p != j) {
+        const T t = z[j * RC + tid];
+        z[j * RC + tid] = z[p * RC + tid];
+        z[p * RC + tid] = t;
+      }
+    }
+  __syncthreads();
+  for (int j = 0; j + 1 < n; ++j) {
+    const int w = (n - j - 1) * RC;
+    for (int e = tid; e < w; e += bs) {
+      const int l = j + 1 + e / RC, q = e % RC;
+      z[l * RC + q] = msb(z[l * RC + q], LU[l + (size_t)j * n], z[j * RC + q]);
+    }
+    __syncthreads();
+  }
+  for (int j = n - 1; j >= 0; --j) {
+    if (tid < RC) z[j * RC + tid] = dv(z[j * RC + tid], LU[j + (size_t)j * n]);
+    __syncthreads();
+    const int w = j * RC;
+    for (int e = tid; e < w; e += bs) {
+      const int l = e / RC, q = e % RC;
+      z[l * RC + q] = msb(z[l * RC + q], LU[l + (size_t)j * n], z[j * RC + q]);
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < n * RC; e += bs) {
+    const int i = e / RC, q = e % RC;
+    if (q < nq) xq[idx[i] + (int64_t)q * N] = z[e];
+  }
+}
+
+template <typename T, int RC>
+rss_status sweeps(const rss_factorization* f, T* x, int64_t N, int nrhs, cudaStream_t st) {
+  const unsigned nchunk = cdiv(nrhs, RC);
+  RSS_CUDA(cudaFuncSetAttribute(k_solve_up<T, RC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+  RSS_CUDA(cudaFuncSetAttribute(k_solve_down<T, RC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+  for (const Batch& b : f->batches) {
+    const size_t smem = sizeof(T) * (size_t)(b.max_k + b.max_r) * RC;
+    k_solve_up<T, RC><<<dim3(b.nrec, nchunk), NT, smem, st>>>(static_cast<const BoxRec<T>*>(b.d_recs), x, N, nrhs);
+    RSS_LAUNCHED();
+  }
+  constexpr int RT = 4;
+  const size_t tsm = sizeof(T) * (size_t)f->ntop * RT;
+  if (tsm > 200 * 1024) {
+    rss_set_error("rss_solve: top block too large for the on-chip solve");
+    return RSS_EINVAL;
+  }
+  RSS_CUDA(cudaFuncSetAttribute(k_top_solve<T, RT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+  if (f->ntop > 0) {
+    k_top_solve<T, RT><<<cdiv(nrhs, RT), 1024, tsm, st>>>(static_cast<const T*>(f->d_top_lu), f->d_top_piv,
+                                                         f->d_top_idx, f->ntop, x, N, nrhs);
+    RSS_LAUNCHED();
+  }
+  for (auto it = f->batches.rbegin(); it != f->batches.rend(); ++it) {
+    const size_t smem = sizeof(T) * (size_t)it->max_r * RC;
+    k_solve_down<T, RC><<<dim3(it->nrec, nchunk), NT, smem, st>>>(static_cast<const BoxRec<T>*>(it->d_recs), x, N,
+                                                                 nrhs);
+    RSS_LAUNCHED();
+  }
+  return RSS_OK;
+}
+
+}  // namespace
+
+template <typename T>
+rss_status solve_impl(const rss_factorization* f, T* b, int64_t nrhs, int64_t ldb, cudaStream_t st) {
+  const int64_t N = f->n;
+  T* x = nullptr;
+  RSS_CUDA(cudaMallocAsync(&x, sizeof(T) * (size_t)N * nrhs, st));
+  const unsigned grid = std::min<long long>(cdiv((long long)N * nrhs, NT), 152LL * 16);
+  k_perm_in<T><<<grid, NT, 0, st>>>(b, ldb, x, N, (int)nrhs, f->d_user_to_tree);
+  rss_status s = RSS_OK;
+  if (cudaGetLastError() != cudaSuccess) {
+    rss_set_error("rss_solve: launch failed");
+    s = RSS_ECUDA;
+  }
+  if (s == RSS_OK) {
+    if (nrhs == 1) s = sweeps<T, 1>(f, x, N, (int)nrhs, st);
+    else if (nrhs <= 4) s = sweeps<T, 4>(f, x, N, (int)nrhs, st);
+    else s = sweeps<T, 8>(f, x, N, (int)nrhs, st);
+  }
+  if (s == RSS_OK) {
+    k_perm_out<T><<<grid, NT, 0, st>>>(b, ldb, x, N, (int)nrhs, f->d_user_to_tree);
+    if (cudaGetLastError() != cudaSuccess) {
+      rss_set_error("rss_solve: launch failed");
+      s = RSS_ECUDA;
+    }
+  }
+  cudaFreeAsync(x, st);
+  return s;
+}
+
+template rss_status solve_impl<double>(const rss_factorization*, double*, int64_t, int64_t, cudaStream_t);
+template rss_status solve_impl<zd>(const rss_factorization*, zd*, int64_t, int64_t, cudaStream_t);

@@ -1,0 +1,227 @@
+"""ctypes binding of the RS-S C ABI (``include/rss.h``), same names as the C calls.
+
+Only argument marshalling happens here.  Device buffers are torch tensors
+(``torch.float64`` or ``torch.complex128`` on CUDA); host buffers are numpy
+arrays.  Right-hand sides are n x nrhs column-major: a tensor of shape
+(n, nrhs) with stride (1, ldb), e.g. ``torch.empty(nrhs, n).T``, or a 1-D
+tensor of length n.
+"""
+from __future__ import annotations
+
+import ctypes
+import json
+import os
+
+import numpy as np
+
+LAPLACE, HELMHOLTZ, TEST_POLY, TEST_RPOLY = 0, 1, 2, 3
+MAX_COEF = 8
+_STATUS = {0: "RSS_OK", 1: "RSS_EINVAL", 2: "RSS_ENOMEM", 3: "RSS_ECUDA", 4: "RSS_ENUMERIC",
+           5: "RSS_ETIMEOUT", 6: "RSS_EBUSY"}
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def library_path() -> str:
+    return os.path.join(_HERE, "librss_gb300.so")
+
+
+class RSSError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("h", ctypes.c_double), ("kappa", ctypes.c_double),
+                ("diag_re", ctypes.c_double), ("diag_im", ctypes.c_double),
+                ("proxy_n", ctypes.c_int), ("proxy_radius_over_side", ctypes.c_double),
+                ("eps", ctypes.c_double), ("ncoef", ctypes.c_int),
+                ("coef_re", ctypes.c_double * MAX_COEF), ("coef_im", ctypes.c_double * MAX_COEF),
+                ("scale", ctypes.c_double), ("phase_x", ctypes.c_double),
+                ("phase_y", ctypes.c_double)]
+
+
+_lib = None
+
+
+def _load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = library_path()
+    if not os.path.exists(path):
+        raise ImportError(f"RS-S CUDA library not built: {path} is missing "
+                          "(run python -m paper_2310_15458_gb300.build)")
+    lib = ctypes.CDLL(path)
+    vp, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32
+    lib.rss_build_tree.argtypes = [vp, i64, ctypes.c_int, ctypes.POINTER(vp)]
+    lib.rss_factor.argtypes = [vp, ctypes.POINTER(_Params), vp, ctypes.POINTER(vp)]
+    lib.rss_solve.argtypes = [vp, vp, i64, i64, vp]
+    lib.rss_free.argtypes = [vp]
+    lib.rss_free.restype = None
+    lib.rss_last_error.restype = ctypes.c_char_p
+    lib.rss_info.argtypes = [vp, ctypes.c_char_p, ctypes.c_size_t]
+    lib.rss_level_ranks.argtypes = [vp, ctypes.c_int, ctypes.POINTER(i32)]
+    lib.rss_box_record.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(i32)] + [vp] * 8
+    for name in ("rss_build_tree", "rss_factor", "rss_solve", "rss_info", "rss_level_ranks",
+                 "rss_box_record"):
+        getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _check(status: int):
+    if status != 0:
+        raise RSSError(status, _load().rss_last_error().decode())
+
+
+def _stream_handle(stream) -> int | None:
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return torch.cuda.current_stream().cuda_stream or None
+        except ImportError:
+            pass
+        return None
+    return getattr(stream, "cuda_stream", stream) or None
+
+
+class Tree:
+    """Quadtree handle (rss_tree)."""
+
+    def __init__(self, handle, n, side, leaf):
+        self._h, self.n, self.side, self.leaf = handle, n, side, leaf
+
+    @property
+    def handle(self):
+        return self._h
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.rss_free(self._h)
+            self._h = None
+
+
+class Factor:
+    """Factorization handle (rss_factorization)."""
+
+    def __init__(self, handle, n, is_complex, tree):
+        self._h, self.n, self.is_complex, self.tree = handle, n, is_complex, tree
+
+    @property
+    def handle(self):
+        return self._h
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.rss_free(self._h)
+            self._h = None
+
+
+def rss_build_tree(points: np.ndarray, leaf: int = 64) -> Tree:
+    lib = _load()
+    pts = np.ascontiguousarray(points, dtype=np.float64)
+    if pts.ndim != 2 or pts.shape[1] != 2:
+        raise ValueError("points must have shape (n, 2)")
+    h = ctypes.c_void_p()
+    _check(lib.rss_build_tree(pts.ctypes.data, pts.shape[0], leaf, ctypes.byref(h)))
+    side = int(round(np.sqrt(pts.shape[0])))
+    return Tree(h, pts.shape[0], side, leaf)
+
+
+def rss_factor(tree: Tree, kind: int = LAPLACE, eps: float = 1e-6, h: float = 0.0,
+               kappa: float = 0.0, diag: complex = 1.0, proxy_n: int = 64,
+               proxy_radius_over_side: float = 1.25, coef=(), scale: float = 1.0,
+               phase=(0.0, 0.0), stream=None) -> Factor:
+    lib = _load()
+    p = _Params()
+    p.kind, p.h, p.kappa = kind, h, kappa
+    p.diag_re, p.diag_im = complex(diag).real, complex(diag).imag
+    p.proxy_n, p.proxy_radius_over_side, p.eps = proxy_n, proxy_radius_over_side, eps
+    coef = list(coef)
+    if len(coef) > MAX_COEF:
+        raise ValueError("too many coefficients")
+    p.ncoef = len(coef)
+    for i, c in enumerate(coef):
+        p.coef_re[i], p.coef_im[i] = complex(c).real, complex(c).imag
+    p.scale, p.phase_x, p.phase_y = scale, phase[0], phase[1]
+    out = ctypes.c_void_p()
+    _check(lib.rss_factor(tree.handle, ctypes.byref(p), _stream_handle(stream), ctypes.byref(out)))
+    return Factor(out, tree.n, kind in (HELMHOLTZ, TEST_POLY), tree)
+
+
+def rss_solve(f: Factor, b, stream=None):
+    """Overwrite b with A^{-1} b; returns b."""
+    lib = _load()
+    if isinstance(b, np.ndarray):
+        want = np.complex128 if f.is_complex else np.float64
+        if b.dtype != want:
+            raise TypeError(f"b must be {want.__name__}")
+        if b.ndim == 1:
+            nrhs, ldb = 1, b.shape[0]
+            if not b.flags.c_contiguous:
+                raise ValueError("b must be contiguous")
+        else:
+            if b.strides[0] != b.itemsize:
+                raise ValueError("b must be column-major (Fortran order)")
+            nrhs, ldb = b.shape[1], b.strides[1] // b.itemsize
+        if b.shape[0] != f.n:
+            raise ValueError("b has the wrong number of rows")
+        _check(lib.rss_solve(f.handle, b.ctypes.data, nrhs, ldb, _stream_handle(stream)))
+        return b
+    import torch
+    want = torch.complex128 if f.is_complex else torch.float64
+    if b.dtype != want:
+        raise TypeError(f"b must be {want}")
+    if b.dim() == 1:
+        if b.stride(0) != 1:
+            raise ValueError("b must be contiguous")
+        nrhs, ldb = 1, b.shape[0]
+    else:
+        if b.stride(0) != 1:
+            raise ValueError("b must be column-major: shape (n, nrhs), stride (1, ldb)")
+        nrhs, ldb = b.shape[1], max(b.stride(1), b.shape[0])
+    if b.shape[0] != f.n:
+        raise ValueError("b has the wrong number of rows")
+    _check(lib.rss_solve(f.handle, b.data_ptr(), nrhs, ldb, _stream_handle(stream)))
+    return b
+
+
+def rss_free(obj):
+    if obj is not None and getattr(obj, "_h", None):
+        _load().rss_free(obj._h)
+        obj._h = None
+
+
+def rss_info(f: Factor) -> dict:
+    buf = ctypes.create_string_buffer(1 << 16)
+    _check(_load().rss_info(f.handle, buf, len(buf)))
+    return json.loads(buf.value.decode())
+
+
+def rss_level_ranks(f: Factor, side: int) -> np.ndarray:
+    out = np.zeros(side * side, dtype=np.int32)
+    _check(_load().rss_level_ranks(f.handle, side, out.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))))
+    return out
+
+
+def rss_box_record(f: Factor, side: int, box: int) -> dict:
+    """S, R, C (caller's point indices), T, LU, piv, E, F of one eliminated box."""
+    lib = _load()
+    sizes = np.zeros(4, dtype=np.int32)
+    pi32 = ctypes.POINTER(ctypes.c_int32)
+    _check(lib.rss_box_record(f.handle, side, box, sizes.ctypes.data_as(pi32), *([None] * 8)))
+    k, r, c, n = (int(v) for v in sizes)
+    dt = np.complex128 if f.is_complex else np.float64
+    S, R, C = np.zeros(k, np.int64), np.zeros(r, np.int64), np.zeros(c, np.int64)
+    T = np.zeros((k, r), dt, order="F")
+    LU = np.zeros((r, r), dt, order="F")
+    piv = np.zeros(r, np.int32)
+    E = np.zeros((c, r), dt, order="F")
+    F = np.zeros((r, c), dt, order="F")
+    _check(lib.rss_box_record(f.handle, side, box, sizes.ctypes.data_as(pi32),
+                              S.ctypes.data, R.ctypes.data, C.ctypes.data, T.ctypes.data,
+                              LU.ctypes.data, piv.ctypes.data, E.ctypes.data, F.ctypes.data))
+    return dict(k=k, r=r, c=c, n=n, S=S, R=R, C=C, T=T, LU=LU, piv=piv, E=E, F=F)

@@ -1,0 +1,60 @@
+"""The C-ABI library builds, loads and exports every entry point of include/rss.h.
+
+Host-only calls (tree construction and its argument checks) run without a GPU.
+"""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2310_15458_gb300.build import build
+    path = build()
+    return ctypes.CDLL(path)
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "rss.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(rss_[a-z_]+)\s*\(", src)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert {"rss_build_tree", "rss_factor", "rss_solve", "rss_free"} <= set(names)
+    for name in names:
+        assert hasattr(lib, name), name
+
+
+def test_tree_validation_on_host():
+    import paper_2310_15458_gb300 as P
+    t = P.rss_build_tree(W.grid_points(64), 64)
+    assert t.n == 4096
+    pts, _ = W.shuffled(W.grid_points(32), 1)
+    assert P.rss_build_tree(pts, 16).n == 1024
+    bad = [W.grid_points(64)[:-1], W.grid_points(64) * np.array([1.0, 2.0])]
+    for b in bad:
+        with pytest.raises(P.RSSError, match="EINVAL"):
+            P.rss_build_tree(b, 64)
+    dup = W.grid_points(16)
+    dup[1] = dup[0]
+    with pytest.raises(P.RSSError, match="EINVAL"):
+        P.rss_build_tree(dup, 16)
+    with pytest.raises(P.RSSError, match="EINVAL"):
+        P.rss_build_tree(W.grid_points(24), 64)     # 24 / 8 = 3 is not a power of two
+
+
+def test_binding_refuses_missing_library(monkeypatch, tmp_path):
+    import paper_2310_15458_gb300.rss as R
+    monkeypatch.setattr(R, "_lib", None)
+    monkeypatch.setattr(R, "library_path", lambda: str(tmp_path / "missing.so"))
+    with pytest.raises(ImportError):
+        R._load()

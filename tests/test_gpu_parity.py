@@ -1,0 +1,238 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Element-wise comparisons on small and mid-size problems (several levels, ragged
+right-hand-side chunks), exactness against a dense solve where the answer is
+unique, and, at the full workload sizes in the launch configuration the bench
+uses, sampled box records that the oracle recomputes one by one plus the
+relative residual by FFT.
+
+Tolerances: every quantity is FP64 / complex128.  Both sides run the same
+sequence of operations on the same inputs, so integer outputs (ranks, skeleton
+and redundant index sets, LU pivots) must be identical.  The interpolation
+matrix T = R11^{-1} R12 comes from a triangular factor whose last kept diagonal
+entry is about eps ||Y||, so cond(R11) reaches ~1/eps and rounding differences
+of ~1e-16 grow to ~1e-16/eps in T and in everything computed from it (E, F,
+the LU of X_RR); the bound is 100x that, max(1e-10, 1e-14 / eps).  Solutions
+agree to 1e-9 relative, and every relative residual must be <= 10 eps (the
+target of the workloads).
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import workloads as W
+from oracle import rss as orss
+from oracle.dense import dense_matrix, fft_matvec, relres
+from oracle.rss import KernelSpec
+
+pytestmark = [pytest.mark.gpu, pytest.mark.filterwarnings("ignore::RuntimeWarning")]
+
+KIND = {"laplace": 0, "helmholtz": 1, "poly": 2, "rpoly": 3}
+
+
+@pytest.fixture(scope="module")
+def P():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2310_15458_gb300 as P
+    return P
+
+
+def gpu_factor(P, pts, spec, eps, leaf):
+    tree = P.rss_build_tree(pts, leaf)
+    return P.rss_factor(tree, kind=KIND[spec.kind], eps=eps, h=spec.h, kappa=spec.kappa,
+                        diag=spec.diag, coef=spec.coef, scale=spec.scale, phase=spec.phase)
+
+
+def gpu_solve(P, f, b):
+    b = np.asarray(b)
+    if b.ndim == 1:
+        bt = torch.from_numpy(b.copy()).cuda()
+    else:   # (n, nrhs) column-major
+        bt = torch.from_numpy(np.ascontiguousarray(b.T)).cuda().T
+    P.rss_solve(f, bt)
+    torch.cuda.synchronize()
+    return bt.cpu().numpy()
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+POLY = KernelSpec("poly", h=1 / 32, coef=(0.3, 0.5 - 0.2j, 0.7, 0.1 + 0.4j), scale=0.02, diag=1.0,
+                  phase=(3.0, -2.0))
+RPOLY = KernelSpec("rpoly", h=1 / 32, coef=(0.3, 0.5, -0.7, 0.4), scale=0.02, diag=1.0)
+
+
+@pytest.mark.parametrize("spec", [RPOLY, POLY], ids=["real", "complex"])
+def test_exact_low_rank_kernel_matches_dense_solve(P, spec):
+    """Exactly low-rank far field: the GPU factorization must invert A to rounding."""
+    side = 32
+    pts = W.grid_points(side)
+    f = gpu_factor(P, pts, spec, 1e-13, 16)
+    b = W.gaussian_rhs(side * side, 3, spec.is_complex, 5)
+    x = gpu_solve(P, f, b)
+    A = dense_matrix(pts, spec)
+    assert np.linalg.norm(A @ x - b) / np.linalg.norm(b) < 1e-12
+    fac = orss.factor(pts, spec, 1e-13, leaf=16)
+    for g in (8, 4):
+        assert np.array_equal(P.rss_level_ranks(f, g), fac.ranks[g])
+
+
+def rec_tol(eps):
+    return max(1e-10, 1e-14 / eps)
+
+
+def _compare_records(P, f, fac, tol):
+    """Every oracle box record against the GPU record of the same box."""
+    n_cmp = 0
+    for rec in fac.records:
+        g = P.rss_box_record(f, rec.side, rec.box)
+        assert g["k"] == rec.S.size and g["r"] == rec.R.size
+        assert np.array_equal(g["S"], rec.S) and np.array_equal(g["R"], rec.R)
+        assert np.array_equal(g["C"], rec.C)
+        assert np.array_equal(g["piv"], rec.piv)
+        for key, ref in (("T", rec.T), ("LU", rec.LU), ("E", rec.E), ("F", rec.F)):
+            if ref.size:
+                assert rel(g[key], ref) < tol, (rec.side, rec.box, key, rel(g[key], ref))
+        n_cmp += 1
+    return n_cmp
+
+
+def test_laplace_64x64_records_and_solution_match_oracle(P):
+    """The 64 x 64 Laplace workload (eps 1e-8): every box record and the solution."""
+    side, eps = 64, 1e-8
+    pts = W.grid_points(side)
+    spec = KernelSpec("laplace", h=1 / side)
+    f = gpu_factor(P, pts, spec, eps, 64)
+    fac = orss.factor(pts, spec, eps)
+    for g in (8, 4):
+        assert np.array_equal(P.rss_level_ranks(f, g), fac.ranks[g])
+    assert _compare_records(P, f, fac, rec_tol(eps)) == len(fac.records)
+    b = W.gaussian_rhs(side * side, 1, False, 1000)
+    x = gpu_solve(P, f, b)
+    xo = orss.solve(fac, b)
+    assert rel(x, xo) < 1e-9
+    assert relres(pts, spec, x, b) <= 10 * eps
+
+
+def test_helmholtz_records_and_solution_match_oracle(P):
+    side, eps = 32, 1e-6
+    pts = W.grid_points(side)
+    spec = KernelSpec("helmholtz", h=1 / side, kappa=25.0)
+    f = gpu_factor(P, pts, spec, eps, 16)
+    fac = orss.factor(pts, spec, eps, leaf=16)
+    for g in (8, 4):
+        assert np.array_equal(P.rss_level_ranks(f, g), fac.ranks[g])
+    assert _compare_records(P, f, fac, rec_tol(eps)) == len(fac.records)
+    b = W.gaussian_rhs(side * side, 3, True, 1001)
+    x = gpu_solve(P, f, b)
+    assert rel(x, orss.solve(fac, b)) < 1e-9
+    assert relres(pts, spec, x, b) <= 10 * eps
+
+
+def test_ragged_rhs_chunks_host_buffers_and_user_order(P):
+    """nrhs = 9 (a ragged chunk of 8), host-buffer solve == device solve, shuffled points."""
+    side, eps = 32, 1e-6
+    pts, perm = W.shuffled(W.grid_points(side), 3)
+    spec = KernelSpec("laplace", h=1 / side)
+    f = gpu_factor(P, pts, spec, eps, 16)
+    b = W.gaussian_rhs(side * side, 9, False, 44)
+    x_dev = gpu_solve(P, f, b)
+    x_host = np.asfortranarray(b.copy())
+    P.rss_solve(f, x_host)
+    assert np.array_equal(x_dev, x_host)
+    for j in range(9):                     # column j alone gives the same column
+        xj = gpu_solve(P, f, np.ascontiguousarray(b[:, j]))
+        assert np.array_equal(xj, x_dev[:, j])
+    f0 = gpu_factor(P, W.grid_points(side), spec, eps, 16)
+    x0 = gpu_solve(P, f0, b[np.argsort(perm)])
+    assert np.array_equal(x0[perm], x_dev)
+    assert relres(pts, spec, x_dev, b) <= 10 * eps
+
+
+@pytest.mark.parametrize("side,leaf", [(8, 64), (16, 64), (32, 16)])
+def test_degenerate_trees(P, side, leaf):
+    """One box, a 2 x 2 top only, and eps = 0 (no compression): all exact."""
+    pts = W.grid_points(side)
+    spec = KernelSpec("laplace", h=1 / side)
+    f = gpu_factor(P, pts, spec, 0.0, leaf)
+    b = W.gaussian_rhs(side * side, 2, False, 7)
+    x = gpu_solve(P, f, b)
+    xd = np.linalg.solve(dense_matrix(pts, spec), b)
+    assert rel(x, xd) < 1e-12
+
+
+def test_invalid_arguments(P):
+    pts = W.grid_points(16)
+    with pytest.raises(P.RSSError, match="EINVAL"):
+        P.rss_build_tree(pts[:-1], 16)
+    with pytest.raises(P.RSSError, match="EINVAL"):
+        P.rss_build_tree(pts + np.array([[1e-3, 0]] + [[0, 0]] * 255), 16)
+    t = P.rss_build_tree(pts, 16)
+    with pytest.raises(P.RSSError, match="EINVAL"):
+        P.rss_factor(t, eps=-1.0)
+    with pytest.raises(P.RSSError, match="EINVAL"):
+        P.rss_factor(t, kind=9)
+    f = P.rss_factor(t, eps=1e-6)
+    with pytest.raises(P.RSSError, match="EINVAL"):
+        P.rss_solve(f, torch.zeros(0, 256, dtype=torch.float64, device="cuda").T)
+
+
+# ---------------------------------------------------------------- full workload sizes
+def _leaf_colour0_boxes(g, count):
+    cand = [by * g + bx for by in range(0, g, 3) for bx in range(0, g, 3)]
+    idx = np.linspace(0, len(cand) - 1, count).round().astype(int)
+    return [cand[i] for i in idx]
+
+
+def _oracle_leaf_record(pts, spec, eps, g, B, leaf=64, nproxy=64, ratio=1.25):
+    """Oracle record of a first-colour leaf box: the blocks it reads are still
+    pure kernel values, so they are generated here from the kernel alone."""
+    grid = orss.grid_of(pts)
+    ls = int(round(np.sqrt(leaf)))
+    lb = (grid.iy // ls) * g + (grid.ix // ls)
+    local = (grid.iy % ls) * ls + (grid.ix % ls)
+    bx, by = B % g, B // g
+    near = [y * g + x for y in range(max(0, by - 2), min(g, by + 3))
+            for x in range(max(0, bx - 2), min(g, bx + 3))]
+    ptsl = {}
+    for b in near:
+        idx = np.flatnonzero(lb == b)
+        ptsl[b] = idx[np.argsort(local[idx])]
+    blocks = {}
+    for b1 in near:
+        for b2 in near:
+            if orss.chebyshev(b1, b2, g) <= 2:
+                blocks[(b1, b2)] = orss.entries(spec, pts, ptsl[b1], ptsl[b2])
+    L = grid.side * grid.hg / g
+    centre = (grid.x0 - grid.hg / 2 + (bx + 0.5) * L, grid.y0 - grid.hg / 2 + (by + 0.5) * L)
+    ptsd = dict(ptsl)
+    k, rec = orss.skeletonize_box(spec, pts, blocks, ptsd, B, g, eps, centre, ratio * L, nproxy)
+    return k, rec
+
+
+FULL = [("laplace_1024x1024_eps1e-6", 3), ("helmholtz_k25_256x256_eps1e-6", 3)]
+
+
+@pytest.mark.parametrize("name,nsample", FULL, ids=[n for n, _ in FULL])
+def test_full_size_sampled_records_and_residual(P, name, nsample):
+    w = W.WORKLOADS[name]
+    side, eps = w["side"], w["eps"]
+    pts = W.grid_points(side)
+    spec = KernelSpec("laplace" if w["kind"] == W.LAPLACE else "helmholtz", h=1 / side, kappa=w["kappa"])
+    f = gpu_factor(P, pts, spec, eps, W.LEAF)
+    g = side // 8
+    for B in _leaf_colour0_boxes(g, nsample):
+        k, rec = _oracle_leaf_record(pts, spec, eps, g, B)
+        assert P.rss_level_ranks(f, g)[B] == k
+        if rec is None:
+            continue
+        gr = P.rss_box_record(f, g, B)
+        assert np.array_equal(gr["S"], rec.S) and np.array_equal(gr["C"], rec.C)
+        for key, ref in (("T", rec.T), ("LU", rec.LU), ("E", rec.E), ("F", rec.F)):
+            assert rel(gr[key], ref) < rec_tol(eps), (B, key)
+    b = W.gaussian_rhs(side * side, min(w["nrhs"], 2), spec.is_complex, w["seed"])
+    x = gpu_solve(P, f, b)
+    assert relres(pts, spec, x, b) <= 10 * eps
