@@ -49,6 +49,8 @@ WORKLOADS = {
                                    eps=1e-8, nrhs=1, seed=1000),
     "helmholtz_k25_256x256_eps1e-6": dict(kind=HELMHOLTZ, side=256, complex=True,
                                            kappa=25.0, eps=1e-6, nrhs=16, seed=1001),
+    "laplace_256x256_eps1e-6": dict(kind=LAPLACE, side=256, complex=False, kappa=0.0,
+                                     eps=1e-6, nrhs=1, seed=1003),
     "laplace_1024x1024_eps1e-6": dict(kind=LAPLACE, side=1024, complex=False, kappa=0.0,
                                        eps=1e-6, nrhs=1, seed=1002),
     "helmholtz_k50_2048x2048_eps1e-6": dict(kind=HELMHOLTZ, side=2048, complex=True,
