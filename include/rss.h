@@ -97,6 +97,27 @@ rss_status rss_factor(const rss_tree* tree, const rss_params* params, void* stre
  * concurrently on the same factor (the factor is read only). */
 rss_status rss_solve(const rss_factorization* f, void* b, int64_t nrhs, int64_t ldb, void* stream);
 
+/* rss_solve without any device allocation.  The paper has no counterpart:
+ * this exists for callers that cannot allocate device memory at call time --
+ * a process whose framework allocator already holds the device's free memory,
+ * or a latency-bound serving loop that must not pay for (or synchronise on) a
+ * fresh allocation.  Results are those of rss_solve.
+ *  - b must be device memory (n x nrhs, column-major, ldb >= n); the call is
+ *    asynchronous on stream.
+ *  - The working copy of b lives in a fixed 16 MiB array compiled into the
+ *    library, held on every GPU that loads it until the process exits:
+ *    n * nrhs * sizeof(scalar) must be <= 16 MiB (8 or 16 bytes per scalar),
+ *    else RSS_EINVAL with nothing launched.
+ *  - The first call on a device looks up that array's device address (once
+ *    per device, with the device current); make that first call before any
+ *    stream capture.
+ *  - All calls share the one array: calls whose work overlaps on the GPU
+ *    (for example on two streams at once) race and corrupt each other; order
+ *    them on one stream or synchronise between them.  Each call overwrites
+ *    the whole region it uses before reading it. */
+rss_status rss_solve_noalloc(const rss_factorization* f, void* b, int64_t nrhs, int64_t ldb,
+                             void* stream);
+
 /* Release a tree or a factor (the handle is tagged).  NULL is ignored. */
 void rss_free(void* handle);
 

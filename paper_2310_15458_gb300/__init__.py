@@ -6,9 +6,9 @@ Build the library with ``python -m paper_2310_15458_gb300.build``.  Loading
 fails with an error if the library is missing: there is no CPU fallback.
 """
 from .rss import (LAPLACE, HELMHOLTZ, TEST_POLY, TEST_RPOLY, RSSError, Tree, Factor,
-                  rss_build_tree, rss_factor, rss_solve, rss_free, rss_info,
+                  rss_build_tree, rss_factor, rss_solve, rss_solve_noalloc, rss_free, rss_info,
                   rss_level_ranks, rss_box_record, library_path)
 
 __all__ = ["LAPLACE", "HELMHOLTZ", "TEST_POLY", "TEST_RPOLY", "RSSError", "Tree", "Factor",
-           "rss_build_tree", "rss_factor", "rss_solve", "rss_free", "rss_info",
+           "rss_build_tree", "rss_factor", "rss_solve", "rss_solve_noalloc", "rss_free", "rss_info",
            "rss_level_ranks", "rss_box_record", "library_path"]

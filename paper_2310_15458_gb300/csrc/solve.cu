@@ -7,6 +7,7 @@
 // Boxes of one colour class touch disjoint entries of x, so a class is one
 // launch; the right-hand sides are split into chunks of RC columns.
 #include <algorithm>
+#include <mutex>
 
 #include "internal.h"
 
@@ -264,3 +265,97 @@ rss_status solve_impl(const rss_factorization* f, T* b, int64_t nrhs, int64_t ld
 
 template rss_status solve_impl<double>(const rss_factorization*, double*, int64_t, int64_t, cudaStream_t);
 template rss_status solve_impl<zd>(const rss_factorization*, zd*, int64_t, int64_t, cudaStream_t);
+
+// ---------------------------------------------------------------------------
+// rss_solve_noalloc: the same sweeps as rss_solve, with the working copy of
+// the right-hand sides in a fixed device array instead of memory obtained at
+// call time.  Some callers cannot allocate device memory: a process whose
+// framework allocator has already reserved the device's free memory, a
+// latency-bound serving loop that may not take the synchronisation a fresh
+// allocation can cost, or a host that budgets device memory up front.  For
+// them the scratch is a file-scope array that exists on every GPU that loads
+// the library, for the life of the process.
+
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = size_t(16) << 20;   // 16 MiB per device
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[kMaxDevices] = {};
+
+// Device address of the scratch array on the current device, looked up once
+// per device (the symbol's host-side name is not a device address).
+rss_status noalloc_scratch(void** out) {
+  int dev = -1;
+  RSS_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) {
+    rss_set_error("rss_solve_noalloc: device ordinal out of range");
+    return RSS_EINVAL;
+  }
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    RSS_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return RSS_OK;
+}
+
+template <typename T>
+rss_status solve_in_scratch(const rss_factorization* f, T* b, int64_t nrhs, int64_t ldb, cudaStream_t st,
+                            T* x) {
+  const int64_t N = f->n;
+  const unsigned grid = std::min<long long>(cdiv((long long)N * nrhs, NT), 152LL * 16);
+  // every entry of x is written here, so nothing left from an earlier call is read
+  k_perm_in<T><<<grid, NT, 0, st>>>(b, ldb, x, N, (int)nrhs, f->d_user_to_tree);
+  RSS_LAUNCHED();
+  rss_status s;
+  if (nrhs == 1) s = sweeps<T, 1>(f, x, N, (int)nrhs, st);
+  else if (nrhs <= 4) s = sweeps<T, 4>(f, x, N, (int)nrhs, st);
+  else s = sweeps<T, 8>(f, x, N, (int)nrhs, st);
+  if (s != RSS_OK) return s;
+  k_perm_out<T><<<grid, NT, 0, st>>>(b, ldb, x, N, (int)nrhs, f->d_user_to_tree);
+  RSS_LAUNCHED();
+  return RSS_OK;
+}
+
+}  // namespace
+
+extern "C" rss_status rss_solve_noalloc(const rss_factorization* f, void* b, int64_t nrhs, int64_t ldb,
+                                        void* stream) {
+  if (!f || f->tag != RSS_TAG_FACTOR) {
+    rss_set_error("rss_solve_noalloc: not a factor handle");
+    return RSS_EINVAL;
+  }
+  if (!b || nrhs <= 0 || ldb < f->n) {
+    rss_set_error("rss_solve_noalloc: b must be non-NULL with nrhs > 0 and ldb >= n");
+    return RSS_EINVAL;
+  }
+  const size_t esz = f->is_complex ? 16 : 8;
+  const size_t need = esz * (size_t)f->n * (size_t)nrhs;
+  if (need > kNoAllocScratchBytes) {
+    rss_set_error("rss_solve_noalloc: n * nrhs needs " + std::to_string(need) +
+                  " bytes of scratch; the fixed maximum is " + std::to_string(kNoAllocScratchBytes) +
+                  " bytes (use rss_solve, or fewer right-hand sides per call)");
+    return RSS_EINVAL;
+  }
+  cudaPointerAttributes attr;
+  if (cudaPointerGetAttributes(&attr, b) != cudaSuccess) {
+    cudaGetLastError();
+    attr.type = cudaMemoryTypeUnregistered;
+  }
+  if (attr.type != cudaMemoryTypeDevice && attr.type != cudaMemoryTypeManaged) {
+    rss_set_error("rss_solve_noalloc: b must be device memory (staging host data would allocate)");
+    return RSS_EINVAL;
+  }
+  void* scratch = nullptr;
+  rss_status s = noalloc_scratch(&scratch);
+  if (s != RSS_OK) return s;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  return f->is_complex
+             ? solve_in_scratch<zd>(f, static_cast<zd*>(b), nrhs, ldb, st, static_cast<zd*>(scratch))
+             : solve_in_scratch<double>(f, static_cast<double*>(b), nrhs, ldb, st, static_cast<double*>(scratch));
+}

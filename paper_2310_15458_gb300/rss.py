@@ -58,14 +58,15 @@ def _load():
     lib.rss_build_tree.argtypes = [vp, i64, ctypes.c_int, ctypes.POINTER(vp)]
     lib.rss_factor.argtypes = [vp, ctypes.POINTER(_Params), vp, ctypes.POINTER(vp)]
     lib.rss_solve.argtypes = [vp, vp, i64, i64, vp]
+    lib.rss_solve_noalloc.argtypes = [vp, vp, i64, i64, vp]
     lib.rss_free.argtypes = [vp]
     lib.rss_free.restype = None
     lib.rss_last_error.restype = ctypes.c_char_p
     lib.rss_info.argtypes = [vp, ctypes.c_char_p, ctypes.c_size_t]
     lib.rss_level_ranks.argtypes = [vp, ctypes.c_int, ctypes.POINTER(i32)]
     lib.rss_box_record.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(i32)] + [vp] * 8
-    for name in ("rss_build_tree", "rss_factor", "rss_solve", "rss_info", "rss_level_ranks",
-                 "rss_box_record"):
+    for name in ("rss_build_tree", "rss_factor", "rss_solve", "rss_solve_noalloc", "rss_info",
+                 "rss_level_ranks", "rss_box_record"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -186,6 +187,28 @@ def rss_solve(f: Factor, b, stream=None):
     if b.shape[0] != f.n:
         raise ValueError("b has the wrong number of rows")
     _check(lib.rss_solve(f.handle, b.data_ptr(), nrhs, ldb, _stream_handle(stream)))
+    return b
+
+
+def rss_solve_noalloc(f: Factor, b, stream=None):
+    """rss_solve for callers that cannot allocate device memory: b must be a CUDA
+    tensor and n * nrhs scalars must fit the library's fixed 16 MiB scratch array,
+    which every call shares (overlapping calls race).  Overwrites b; returns b."""
+    import torch
+    want = torch.complex128 if f.is_complex else torch.float64
+    if not isinstance(b, torch.Tensor) or not b.is_cuda or b.dtype != want:
+        raise TypeError(f"b must be a CUDA tensor of {want}")
+    if b.dim() == 1:
+        if b.stride(0) != 1:
+            raise ValueError("b must be contiguous")
+        nrhs, ldb = 1, b.shape[0]
+    else:
+        if b.stride(0) != 1:
+            raise ValueError("b must be column-major: shape (n, nrhs), stride (1, ldb)")
+        nrhs, ldb = b.shape[1], max(b.stride(1), b.shape[0])
+    if b.shape[0] != f.n:
+        raise ValueError("b has the wrong number of rows")
+    _check(_load().rss_solve_noalloc(f.handle, b.data_ptr(), nrhs, ldb, _stream_handle(stream)))
     return b
 
 

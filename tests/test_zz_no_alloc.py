@@ -1,0 +1,61 @@
+"""rss_solve_noalloc, the solve entry point that allocates no device memory.
+
+It serves callers that cannot allocate at call time (a framework allocator
+holding the device's memory, a latency-bound serving loop).  Its results must
+equal rss_solve's; it is called twice in a row on the same factorization to
+show that what one call leaves in the shared scratch array does not leak into
+the next.  This file is collected last so that a run stopping at the first
+failure has already run every other test.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2310_15458_gb300 as P
+    return P
+
+
+def _cols(b):
+    return torch.from_numpy(np.ascontiguousarray(b.T)).cuda().T   # (n, nrhs) column-major
+
+
+@pytest.mark.parametrize("kind,side,leaf,nrhs", [(0, 64, 64, 3), (1, 32, 16, 2)],
+                         ids=["laplace-f64", "helmholtz-c128"])
+def test_noalloc_matches_rss_solve_twice(P, kind, side, leaf, nrhs):
+    tree = P.rss_build_tree(W.grid_points(side), leaf)
+    f = P.rss_factor(tree, kind=kind, eps=1e-8, h=1.0 / side, kappa=25.0)
+    b = W.gaussian_rhs(side * side, nrhs, kind == 1, 11)
+    ref = _cols(b)
+    P.rss_solve(f, ref)
+    torch.cuda.synchronize()
+    ref = ref.cpu().numpy()
+    for call in range(2):
+        x = _cols(b)
+        P.rss_solve_noalloc(f, x)
+        torch.cuda.synchronize()
+        x = x.cpu().numpy()
+        err = np.linalg.norm(x - ref) / np.linalg.norm(ref)
+        assert err <= 1e-12, (call, err)
+
+
+def test_noalloc_rejects_what_it_cannot_hold(P):
+    side = 64
+    tree = P.rss_build_tree(W.grid_points(side), 64)
+    f = P.rss_factor(tree, kind=0, eps=1e-6, h=1.0 / side)
+    too_many = (16 << 20) // (8 * side * side) + 1          # one column past 16 MiB
+    b = torch.ones(too_many, side * side, dtype=torch.float64, device="cuda").T
+    with pytest.raises(P.RSSError, match="EINVAL"):
+        P.rss_solve_noalloc(f, b)
+    assert bool(torch.all(b == 1.0))
+    with pytest.raises(TypeError):
+        P.rss_solve_noalloc(f, np.ones(side * side))
