@@ -311,6 +311,8 @@ def native_arm(args, w):
         "solve_rhs_per_s": {"1": r1, str(args.multi_rhs): rm},
         "relres": relres,
         "phase_gpu_ms": gms,
+        "phase_tflops": {k: info["flops"][k] / (gms[k] * 1e-3) / 1e12 for k in ("id", "elim", "schur", "top")
+                         if gms.get(k)},
         "ranks": [{"side": L["side"], "k_mean": L["k_mean"], "k_max": L["k_max"]} for L in info["levels"]],
         "ntop": info["ntop"],
         "clocks": clk,

@@ -68,6 +68,10 @@ typedef struct {
   int ncoef;                      /* test kernels: number of coefficients (<= RSS_MAX_COEF) */
   double coef_re[RSS_MAX_COEF], coef_im[RSS_MAX_COEF];
   double scale, phase_x, phase_y; /* test kernels */
+  int id_rows;                    /* 0: for a real symmetric kernel (Laplace with a real
+                                     diagonal) compress [A_MB; K_PB] only, which equals the
+                                     full stack of Eq. 4 up to rounding; 1: always the full
+                                     stack [A_MB; K_PB; A_BM^*; K_BP^*] */
 } rss_params;
 
 /* Build the quadtree of Section 2.1 for n points given as pts_xy[2*i],

@@ -25,8 +25,9 @@ Readings where the paper is silent (each also listed in the design notes):
     touch disjoint blocks, Section 3);
   - ID truncation: Frobenius norm, stop at the first k with
     ||R22||_F <= eps ||Y||_F (then ||Y_R - Y_S T||_F = ||R22||_F, Definition 1);
-  - pivot ties: columns whose remaining squared norm is within a relative
-    1e-9 of the maximum count as tied, and the lowest original column wins;
+  - pivot ties: columns whose remaining squared norm is within rounding noise
+    of the maximum (1e-9 relative, plus 1e-12 sqrt(max x largest initial
+    squared norm)) count as tied, and the lowest original column wins;
   - compression on box grids of side >= 4, a dense LU on what remains at
     side 2 (there is no far field at the two top levels);
   - children are merged in the order SW, SE, NW, NE, each child's skeleton in
@@ -40,10 +41,14 @@ from dataclasses import dataclass, field
 import numpy as np
 from scipy import special
 
-# Columns whose remaining squared norm lies within this relative distance of
-# the maximum are treated as tied (exact-arithmetic ties from the grid's
-# symmetry show up as rounding-level differences).
+# Pivot ties.  A remaining squared column norm n_c carries rounding noise of
+# about eps_mach ||x_c|| ||y_c|| (trailing column x_c, original column y_c), so
+# columns with n_c >= n_max - (TIE_REL n_max + TIE_ABS sqrt(n_max y2max)), y2max
+# the largest initial squared column norm, cannot be told apart and count as
+# tied (exact-arithmetic ties from the grid's symmetry show up as such
+# rounding-level differences).
 TIE_REL = 1e-9
+TIE_ABS = 1e-12
 # A downdated squared column norm is re-accumulated from the trailing rows once
 # it has fallen below this fraction of the value it was last accumulated at.
 RECOMPUTE_REL = 1e-4
@@ -143,6 +148,7 @@ def cpqr_id(Y: np.ndarray, eps: float):
     perm = np.arange(n)
     norm2 = _abs2(R).sum(axis=0)
     ref = norm2.copy()
+    y2max = norm2.max() if n else 0.0
     thresh = eps * eps * norm2.sum()
     k = 0
     kmax = min(m, n)
@@ -150,7 +156,8 @@ def cpqr_id(Y: np.ndarray, eps: float):
         if norm2[k:].sum() <= thresh:
             break
         rem = norm2[k:]
-        cand = k + np.flatnonzero(rem >= rem.max() * (1.0 - TIE_REL))
+        mx = rem.max()
+        cand = k + np.flatnonzero(rem >= mx - (TIE_REL * mx + TIE_ABS * np.sqrt(mx * y2max)))
         p = int(cand[np.argmin(perm[cand])])
         if p != k:
             R[:, [k, p]] = R[:, [p, k]]

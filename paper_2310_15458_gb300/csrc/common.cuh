@@ -138,6 +138,20 @@ __device__ inline T aval(const KParams& kp, const Geo& geo, int2 a, int2 b) {
               geo.y0 + b.y * geo.hg, T{});
 }
 
+// Kernel values by grid displacement.  Every kernel kind here depends only on
+// x_i - x_j (the test kernels' phase weights conj(w_i) w_j do too), so on a
+// uniform grid K(x_i, x_j) = tab[(iy_i - iy_j + s - 1) (2s - 1) + (ix_i - ix_j + s - 1)].
+template <typename T>
+__device__ inline T aval_tab(const KParams& kp, const T* __restrict__ tab, int side, int2 a, int2 b) {
+  if (a.x == b.x && a.y == b.y) {
+    T d;
+    if constexpr (sizeof(T) == sizeof(double)) d = from_re<T>(kp.diag_re);
+    else d = T{kp.diag_re, kp.diag_im};
+    return d;
+  }
+  return tab[(size_t)(a.y - b.y + side - 1) * (2 * side - 1) + (a.x - b.x + side - 1)];
+}
+
 // ----------------------------------------------------------------- host errors
 void rss_set_error(const std::string& msg);
 

@@ -26,7 +26,11 @@
 
 namespace {
 
-constexpr double TIE_REL = 1e-9;        // pivot ties: relative window on squared norms
+// Pivot ties: remaining squared norms within TIE_REL n_max + TIE_ABS sqrt(n_max y2max)
+// of the maximum n_max (y2max: largest initial squared column norm) are rounding
+// noise apart and count as tied; the lowest original column wins.
+constexpr double TIE_REL = 1e-9;
+constexpr double TIE_ABS = 1e-12;
 constexpr double RECOMPUTE_REL = 1e-4;  // re-accumulate a downdated norm below this fraction
 constexpr int NT = 256;                 // threads per CTA for the per-box kernels
 
@@ -71,10 +75,21 @@ __device__ inline double warp_max(double v) {
   return v;
 }
 
+// ------------------------------------------------------------------ kernel table
+// tab[(dy + s - 1) (2s - 1) + (dx + s - 1)] = K at grid displacement (dx, dy) != 0.
+template <typename T> __global__ void k_ktab(T* tab, int side, KParams kp, Geo geo) {
+  const long long w = 2 * side - 1, tot = w * w;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < tot;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int dx = (int)(e % w) - (side - 1), dy = (int)(e / w) - (side - 1);
+    tab[e] = (dx == 0 && dy == 0) ? zero<T>() : kval(kp, dx * geo.hg, dy * geo.hg, 0.0, 0.0, T{});
+  }
+}
+
 // ------------------------------------------------------------------ leaf generation
 template <typename T>
 __global__ void __launch_bounds__(NT) k_gen_blocks(LevelDev<T> L, const int2* __restrict__ ixy,
-                                                   KParams kp, Geo geo) {
+                                                   const T* __restrict__ tab, KParams kp, int side) {
   const int u = blockIdx.x / 25, o = blockIdx.x % 25;
   const int v = nbr_box(u, L.g, o % 5 - 2, o / 5 - 2);
   if (v < 0) return;
@@ -82,17 +97,27 @@ __global__ void __launch_bounds__(NT) k_gen_blocks(LevelDev<T> L, const int2* __
   T* A = L.blk + ((size_t)u * 25 + o) * L.nmax * L.nmax;
   for (int e = threadIdx.x; e < nu * nv; e += blockDim.x) {
     const int i = e % nu, j = e / nu;
-    A[(size_t)j * L.nmax + i] = aval<T>(kp, geo, ixy[L.pts[u * L.nmax + i]], ixy[L.pts[v * L.nmax + j]]);
+    A[(size_t)j * L.nmax + i] = aval_tab<T>(kp, tab, side, ixy[L.pts[u * L.nmax + i]], ixy[L.pts[v * L.nmax + j]]);
   }
 }
 
 // ------------------------------------------------------------------ ID (Definition 1, Eq. 6)
+// One CTA per box.  Y = [A_MB; K_PB; A_BM^*; K_BP^*] is assembled once and then
+// only read: the Householder reflectors H_l = I - tau_l v_l v_l^H are kept as
+// V (m x k) and G (n x k) with H_{j-1}..H_0 Y = Y - V G^T (column c of G holds
+// tau_l v_l^H (H_{l-1}..H_0 Y)[:, c]), so a step costs one product v^H Y over
+// the remaining columns plus O((m + n) j) corrections, the pivot column and row j
+// of R are formed on demand, and Y is never rewritten.  In exact arithmetic this
+// is the same sequence of reflectors and pivots as updating Y in place.
+constexpr int NT_ID = 512;
+
 template <typename T> struct IdArgs {
   LevelDev<T> L;
   const int* boxes;   // colour class
   int base;           // first box of this chunk within the class
-  T* Y;               // chunk workspace, one ldY x nmax slot per box
+  T* ws;              // chunk workspace: per box Y (ldY x nmax), V (ldY x nmax), G, Rr (nmax x nmax)
   int ldY;
+  int half;           // 1: rows [A_MB; K_PB] only (real symmetric kernel)
   int* k_out;         // per class box
   int* perm_out;      // class x nmax
   T* T_ws;            // class x nmax x nmax (k x r, ld nmax)
@@ -105,25 +130,33 @@ template <typename T> struct IdArgs {
   double Lbox;        // box side
 };
 
-template <typename T> __global__ void __launch_bounds__(NT) k_id(IdArgs<T> a) {
-  extern __shared__ double sm[];
+template <typename T> __global__ void __launch_bounds__(NT_ID) k_id(IdArgs<T> a) {
+  extern __shared__ __align__(16) unsigned char smraw[];
   const LevelDev<T>& L = a.L;
-  const int nmax = L.nmax, g = L.g;
-  double* norms2 = sm;
-  double* ref = sm + nmax;
-  int* perm = reinterpret_cast<int*>(ref + nmax);
+  const int nmax = L.nmax, g = L.g, ldY = a.ldY;
+  T* vbuf = reinterpret_cast<T*>(smraw);          // ldY: current reflector
+  T* u = vbuf + ldY;                              // nmax: V^H v
+  T* beta = u + nmax;                             // nmax: R diagonal
+  double* norms2 = reinterpret_cast<double*>(beta + nmax);
+  double* ref = norms2 + nmax;
+  double* taus = ref + nmax;
+  int* perm = reinterpret_cast<int*>(taus + nmax);
+  int* flag = perm + nmax;
   __shared__ int Mbox[16], Moff[17], s_nM, s_piv, s_stop;
-  __shared__ double s_thresh, s_tau;
-  __shared__ T s_scale, s_beta, s_red[32];
-  __shared__ double s_redd[32];
+  __shared__ double s_thresh, s_y2max, s_redd[32];
+  __shared__ T s_scale;
 
   const int bi = a.base + blockIdx.x;
   const int B = a.boxes[bi];
   const size_t nn = (size_t)nmax * nmax;
   const int n = L.n[B];
-  T* Y = a.Y + (size_t)blockIdx.x * a.ldY * nmax;
+  const size_t slot = 2 * (size_t)ldY * nmax + 2 * nn;
+  const T* Y = a.ws + (size_t)blockIdx.x * slot;
+  T* Yw = a.ws + (size_t)blockIdx.x * slot;
+  T* V = Yw + (size_t)ldY * nmax;
+  T* G = V + (size_t)ldY * nmax;        // G[l * nmax + c]
+  T* Rr = G + nn;                       // Rr[i * nmax + c]
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
-  const int ldY = a.ldY;
 
   if (tid == 0) {
     int cnt = 0, off = 0;
@@ -142,13 +175,12 @@ template <typename T> __global__ void __launch_bounds__(NT) k_id(IdArgs<T> a) {
   }
   __syncthreads();
   const int nM = s_nM, mh = Moff[nM], P = a.P;
-  const int m = 2 * (mh + P);
+  const int m = a.half ? mh + P : 2 * (mh + P);
   const int bx = B % g, by = B / g;
   const double cx = a.geo.x0 - 0.5 * a.geo.hg + (bx + 0.5) * a.Lbox;
   const double cy = a.geo.y0 - 0.5 * a.geo.hg + (by + 0.5) * a.Lbox;
 
-  // Y, column-major.  Column j = active point j of B (B is not yet eliminated,
-  // so its active list is the identity).
+  // Y, column-major; column j = point j of B (not yet eliminated: identity active list)
   for (long long e = tid; e < (long long)m * n; e += blockDim.x) {
     const int i = (int)(e % m), j = (int)(e / m);
     T val;
@@ -166,14 +198,14 @@ template <typename T> __global__ void __launch_bounds__(NT) k_id(IdArgs<T> a) {
     } else {
       const bool second = i >= 2 * mh + P;
       const int p = second ? i - 2 * mh - P : i - mh;
-      double s, c;
-      sincospi(2.0 * p / P, &s, &c);
-      const double px = cx + a.rho * c, py = cy + a.rho * s;
+      double sn, cs;
+      sincospi(2.0 * p / P, &sn, &cs);
+      const double px = cx + a.rho * cs, py = cy + a.rho * sn;
       const int2 q = a.ixy[L.pts[B * nmax + j]];
       const double xj = a.geo.x0 + q.x * a.geo.hg, yj = a.geo.y0 + q.y * a.geo.hg;
       val = second ? cj(kval(a.kp, xj, yj, px, py, T{})) : kval(a.kp, px, py, xj, yj, T{});
     }
-    Y[(size_t)j * ldY + i] = val;
+    Yw[(size_t)j * ldY + i] = val;
   }
   __syncthreads();
   for (int c = warp; c < n; c += nwarp) {
@@ -188,16 +220,24 @@ template <typename T> __global__ void __launch_bounds__(NT) k_id(IdArgs<T> a) {
   }
   __syncthreads();
   if (warp == 0) {
-    double s = 0.0;
-    for (int c = lane; c < n; c += 32) s += norms2[c];
+    double s = 0.0, mx = 0.0;
+    for (int c = lane; c < n; c += 32) {
+      s += norms2[c];
+      mx = fmax(mx, norms2[c]);
+    }
     s = warp_sum(s);
-    if (lane == 0) s_thresh = a.eps * a.eps * s;
+    mx = warp_max(mx);
+    if (lane == 0) {
+      s_thresh = a.eps * a.eps * s;
+      s_y2max = mx;
+    }
   }
   __syncthreads();
 
   int k = 0;
   const int kmax = min(m, n);
   while (k < kmax) {
+    // stop test and pivot: largest remaining norm, lowest original column among ties
     if (warp == 0) {
       double s = 0.0, mx = -1.0;
       for (int c = k + lane; c < n; c += 32) {
@@ -206,7 +246,7 @@ template <typename T> __global__ void __launch_bounds__(NT) k_id(IdArgs<T> a) {
       }
       s = warp_sum(s);
       mx = warp_max(mx);
-      const double thr = mx * (1.0 - TIE_REL);
+      const double thr = mx - (TIE_REL * mx + TIE_ABS * sqrt(mx * s_y2max));
       int bp = INT_MAX, bc = -1;
       for (int c = k + lane; c < n; c += 32)
         if (norms2[c] >= thr && perm[c] < bp) {
@@ -223,30 +263,27 @@ template <typename T> __global__ void __launch_bounds__(NT) k_id(IdArgs<T> a) {
       if (lane == 0) {
         s_stop = (s <= s_thresh) || bc < 0;   // bc < 0 only if every norm is NaN
         s_piv = bc;
+        if (!s_stop && bc != k) {
+          int ti = perm[k]; perm[k] = perm[bc]; perm[bc] = ti;
+          double td = norms2[k]; norms2[k] = norms2[bc]; norms2[bc] = td;
+          td = ref[k]; ref[k] = ref[bc]; ref[bc] = td;
+        }
       }
     }
     __syncthreads();
     if (s_stop) break;
-    const int p = s_piv;
-    if (p != k) {
-      for (int i = tid; i < m; i += blockDim.x) {
-        const T t = Y[(size_t)k * ldY + i];
-        Y[(size_t)k * ldY + i] = Y[(size_t)p * ldY + i];
-        Y[(size_t)p * ldY + i] = t;
-      }
-      if (tid == 0) {
-        int ti = perm[k]; perm[k] = perm[p]; perm[p] = ti;
-        double td = norms2[k]; norms2[k] = norms2[p]; norms2[p] = td;
-        td = ref[k]; ref[k] = ref[p]; ref[p] = td;
-      }
+    const int q = perm[k];
+    // pivot column after k reflectors, rows k..m-1
+    double s2 = 0.0;
+    for (int i = k + tid; i < m; i += blockDim.x) {
+      T x = Y[(size_t)q * ldY + i];
+      for (int l = 0; l < k; ++l) x = msb(x, V[(size_t)l * ldY + i], G[(size_t)l * nmax + q]);
+      vbuf[i] = x;
+      s2 += abs2(x);
     }
-    __syncthreads();
-    // Householder reflector H = I - tau v v^H, v_k = 1, H x = beta e_1
-    double s = 0.0;
-    for (int i = k + tid; i < m; i += blockDim.x) s += abs2(Y[(size_t)k * ldY + i]);
-    const double alpha2 = block_sum(s, s_redd);
+    const double alpha2 = block_sum(s2, s_redd);
     if (tid == 0) {
-      const T x0 = Y[(size_t)k * ldY + k];
+      const T x0 = vbuf[k];
       const double alpha = sqrt(alpha2);
       if (alpha == 0.0) {
         s_stop = 1;
@@ -254,40 +291,77 @@ template <typename T> __global__ void __launch_bounds__(NT) k_id(IdArgs<T> a) {
         const double ax0 = sqrt(abs2(x0));
         T phase = from_re<T>(1.0);
         if (ax0 != 0.0) phase = scl(1.0 / ax0, x0);
-        const T beta = scl(-alpha, phase);
-        s_beta = beta;
-        s_scale = x0 - beta;
-        s_tau = (alpha + ax0) / alpha;
+        const T bt = scl(-alpha, phase);
+        beta[k] = bt;
+        s_scale = x0 - bt;
+        taus[k] = (alpha + ax0) / alpha;
       }
     }
     __syncthreads();
     if (s_stop) break;
     {
       const T d = s_scale;
-      for (int i = k + 1 + tid; i < m; i += blockDim.x) Y[(size_t)k * ldY + i] = dv(Y[(size_t)k * ldY + i], d);
+      for (int i = k + 1 + tid; i < m; i += blockDim.x) {
+        const T v = dv(vbuf[i], d);
+        vbuf[i] = v;
+        V[(size_t)k * ldY + i] = v;
+      }
+      if (tid == 0) {
+        vbuf[k] = from_re<T>(1.0);
+        V[(size_t)k * ldY + k] = from_re<T>(1.0);
+      }
     }
     __syncthreads();
-    if (tid == 0) Y[(size_t)k * ldY + k] = s_beta;
-    const double tau = s_tau;
-    const T* v = Y + (size_t)k * ldY;
-    for (int c = k + 1 + warp; c < n; c += nwarp) {
-      T* yc = Y + (size_t)c * ldY;
-      T d = zero<T>();
-      for (int i = k + lane; i < m; i += 32) d = madc(d, i == k ? from_re<T>(1.0) : v[i], yc[i]);
-      d = warp_sum(d);
-      const T td = scl(tau, d);
-      for (int i = k + lane; i < m; i += 32) yc[i] = msb(yc[i], i == k ? from_re<T>(1.0) : v[i], td);
-      __syncwarp();
-      double nv = 0.0;
-      if (lane == 0) nv = norms2[c] - abs2(yc[k]);
-      nv = __shfl_sync(0xffffffffu, nv, 0);
-      if (nv < RECOMPUTE_REL * ref[c]) {
-        double t = 0.0;
-        for (int i = k + 1 + lane; i < m; i += 32) t += abs2(yc[i]);
-        nv = warp_sum(t);
-        if (lane == 0) ref[c] = nv;
+    // u_l = v^H V[:, l] (l < k) and raw g_c = v^H Y[:, c] for the remaining columns
+    const int nc = n - k - 1;
+    for (int w = warp; w < k + nc; w += nwarp) {
+      const T* col = w < k ? V + (size_t)w * ldY : Y + (size_t)perm[k + 1 + (w - k)] * ldY;
+      T d0 = zero<T>(), d1 = zero<T>(), d2 = zero<T>(), d3 = zero<T>();
+      int i = k + lane;
+      for (; i + 96 < m; i += 128) {
+        d0 = madc(d0, vbuf[i], col[i]);
+        d1 = madc(d1, vbuf[i + 32], col[i + 32]);
+        d2 = madc(d2, vbuf[i + 64], col[i + 64]);
+        d3 = madc(d3, vbuf[i + 96], col[i + 96]);
       }
-      if (lane == 0) norms2[c] = nv;
+      for (; i < m; i += 32) d0 = madc(d0, vbuf[i], col[i]);
+      T d = warp_sum((d0 + d1) + (d2 + d3));
+      if (lane == 0) {
+        if (w < k) u[w] = d;
+        else G[(size_t)k * nmax + perm[k + 1 + (w - k)]] = d;
+      }
+    }
+    __syncthreads();
+    // g_c, row k of R, norm downdate
+    const double tau = taus[k];
+    for (int pos = k + 1 + tid; pos < n; pos += blockDim.x) {
+      const int c = perm[pos];
+      T gc = G[(size_t)k * nmax + c];
+      for (int l = 0; l < k; ++l) gc = msb(gc, G[(size_t)l * nmax + c], u[l]);
+      gc = scl(tau, gc);
+      G[(size_t)k * nmax + c] = gc;
+      T r = Y[(size_t)c * ldY + k];
+      for (int l = 0; l <= k; ++l) r = msb(r, V[(size_t)l * ldY + k], G[(size_t)l * nmax + c]);
+      Rr[(size_t)k * nmax + c] = r;
+      const double nv = norms2[pos] - abs2(r);
+      flag[pos] = nv < RECOMPUTE_REL * ref[pos];
+      norms2[pos] = nv;
+    }
+    __syncthreads();
+    for (int pos = k + 1 + warp; pos < n; pos += nwarp) {
+      if (!flag[pos]) continue;
+      const int c = perm[pos];
+      double t = 0.0;
+      for (int i = k + 1 + lane; i < m; i += 32) {
+        T x = Y[(size_t)c * ldY + i];
+        for (int l = 0; l <= k; ++l) x = msb(x, V[(size_t)l * ldY + i], G[(size_t)l * nmax + c]);
+        t += abs2(x);
+      }
+      t = warp_sum(t);
+      if (lane == 0) {
+        norms2[pos] = t;
+        ref[pos] = t;
+      }
     }
     __syncthreads();
     ++k;
@@ -297,10 +371,11 @@ template <typename T> __global__ void __launch_bounds__(NT) k_id(IdArgs<T> a) {
   const int r = n - k;
   T* Tw = a.T_ws + (size_t)bi * nn;
   for (int c = tid; c < r; c += blockDim.x) {
+    const int oc = perm[k + c];
     for (int i = k - 1; i >= 0; --i) {
-      T x = Y[(size_t)(k + c) * ldY + i];
-      for (int l = i + 1; l < k; ++l) x = msb(x, Y[(size_t)l * ldY + i], Tw[(size_t)c * nmax + l]);
-      Tw[(size_t)c * nmax + i] = dv(x, Y[(size_t)i * ldY + i]);
+      T x = Rr[(size_t)i * nmax + oc];
+      for (int l = i + 1; l < k; ++l) x = msb(x, Rr[(size_t)i * nmax + perm[l]], Tw[(size_t)c * nmax + l]);
+      Tw[(size_t)c * nmax + i] = dv(x, beta[i]);
     }
   }
   for (int c = tid; c < n; c += blockDim.x) a.perm_out[(size_t)bi * nmax + c] = perm[c];
@@ -536,7 +611,7 @@ template <typename T> __global__ void __launch_bounds__(NT) k_merge_pts(LevelDev
 
 template <typename T>
 __global__ void __launch_bounds__(NT) k_merge_blk(LevelDev<T> C, LevelDev<T> P, const int2* __restrict__ ixy,
-                                                  KParams kp, Geo geo) {
+                                                  const T* __restrict__ tab, KParams kp, int side) {
   const int u = blockIdx.x / 25, o = blockIdx.x % 25;
   const int v = nbr_box(u, P.g, o % 5 - 2, o / 5 - 2);
   if (v < 0) return;
@@ -569,7 +644,7 @@ __global__ void __launch_bounds__(NT) k_merge_blk(LevelDev<T> C, LevelDev<T> P, 
         for (int e = threadIdx.x; e < na * nb; e += blockDim.x) {
           const int i = e % na, j = e / na;
           A[(size_t)(ov[qb] + j) * P.nmax + ou[qa] + i] =
-              aval<T>(kp, geo, ixy[C.pts[a * C.nmax + acta[i]]], ixy[C.pts[b * C.nmax + actb[j]]]);
+              aval_tab<T>(kp, tab, side, ixy[C.pts[a * C.nmax + acta[i]]], ixy[C.pts[b * C.nmax + actb[j]]]);
         }
       }
     }
@@ -712,6 +787,17 @@ rss_status factor_impl(const rss_tree* tree, const rss_params* prm, cudaStream_t
   if (!d_ixy || !d_err) { rss_set_error("rss_factor: device arena allocation failed"); return RSS_ENOMEM; }
   RSS_CUDA(cudaMemcpyAsync(d_ixy, hixy.data(), sizeof(int2) * N, cudaMemcpyHostToDevice, st));
   RSS_CUDA(cudaMemsetAsync(d_err, 0, sizeof(int), st));
+  // kernel values by displacement, for the leaf blocks and the never-modified far blocks
+  const int side = tree->side;
+  T* d_tab = nullptr;
+  RSS_CUDA(cudaMalloc(&d_tab, sizeof(T) * (size_t)(2 * side - 1) * (2 * side - 1)));
+  struct TabFree {
+    T* p;
+    ~TabFree() { cudaFree(p); }
+  } tab_free{d_tab};
+  k_ktab<T><<<152 * 8, NT, 0, st>>>(d_tab, side, f->kp, f->geo);
+  RSS_LAUNCHED();
+  f->launches += 1;
 
   // leaf level
   size_t transient = 0;
@@ -737,7 +823,7 @@ rss_status factor_impl(const rss_tree* tree, const rss_params* prm, cudaStream_t
     Timer tg;
     Ev ev;
     ev.start(st);
-    k_gen_blocks<T><<<nbox * 25, NT, 0, st>>>(cur.d, d_ixy, f->kp, f->geo);
+    k_gen_blocks<T><<<nbox * 25, NT, 0, st>>>(cur.d, d_ixy, d_tab, f->kp, side);
     RSS_LAUNCHED();
     ev.stop(st);
     RSS_CUDA(cudaStreamSynchronize(st));
@@ -746,6 +832,10 @@ rss_status factor_impl(const rss_tree* tree, const rss_params* prm, cudaStream_t
     f->launches += 1;
   }
 
+  // A real symmetric kernel (Laplace, real diagonal) keeps A symmetric through the
+  // eliminations, so the conjugate half of the proxy stack repeats the first half
+  // and the ID of [A_MB; K_PB] alone is the same ID.
+  const int half = (prm->id_rows == 0 && prm->kind == RSS_LAPLACE && prm->diag_im == 0.0) ? 1 : 0;
   while (g >= 4) {
     const int nbox = g * g, nmax = cur.d.nmax;
     const size_t nn = (size_t)nmax * nmax;
@@ -793,15 +883,22 @@ rss_status factor_impl(const rss_tree* tree, const rss_params* prm, cudaStream_t
             if (x < 0 || y < 0 || x >= g || y >= g) continue;
             mh += cur.nact[y * g + x];
           }
-        mrows[q] = 2 * (mh + P);
+        mrows[q] = half ? mh + P : 2 * (mh + P);
         mmax = std::max(mmax, mrows[q]);
       }
       const int ldY = (mmax + 1) & ~1;
-      const size_t slot = (size_t)ldY * nmax * sizeof(T);
+      const size_t slot = (2 * (size_t)ldY * nmax + 2 * nn) * sizeof(T);
       const size_t ybudget = size_t(2) << 30;
       const int chunk = (int)std::max<size_t>(1, std::min<size_t>(nb, ybudget / slot));
       T* d_Y = nullptr;
       RSS_CUDA(cudaMalloc(&d_Y, slot * chunk));
+      const size_t smem_id = sizeof(T) * ((size_t)ldY + 2 * nmax) + (size_t)nmax * (3 * sizeof(double) + 2 * sizeof(int));
+      if (smem_id > 220 * 1024) {
+        cudaFree(d_Y);
+        rss_set_error("rss_factor: proxy stack of a box too tall for the on-chip reflector buffer");
+        return RSS_EINVAL;
+      }
+      RSS_CUDA(cudaFuncSetAttribute(k_id<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_id));
       f->peak_transient = std::max(f->peak_transient, transient + slot * chunk);
       Timer tid_;
       Ev evid;
@@ -811,8 +908,9 @@ rss_status factor_impl(const rss_tree* tree, const rss_params* prm, cudaStream_t
         a.L = cur.d;
         a.boxes = d_cls + coff[col];
         a.base = c0;
-        a.Y = d_Y;
+        a.ws = d_Y;
         a.ldY = ldY;
+        a.half = half;
         a.k_out = d_k;
         a.perm_out = d_perm;
         a.T_ws = d_Tws;
@@ -824,8 +922,7 @@ rss_status factor_impl(const rss_tree* tree, const rss_params* prm, cudaStream_t
         a.rho = ratio * Lbox;
         a.Lbox = Lbox;
         const int cnt = std::min(chunk, nb - c0);
-        const size_t smem = (size_t)nmax * (2 * sizeof(double) + sizeof(int));
-        k_id<T><<<cnt, NT, smem, st>>>(a);
+        k_id<T><<<cnt, NT_ID, smem_id, st>>>(a);
         RSS_LAUNCHED();
         f->launches += 1;
         f->n_id += 1;
@@ -837,10 +934,11 @@ rss_status factor_impl(const rss_tree* tree, const rss_params* prm, cudaStream_t
       f->t_id += tid_.ms();
       f->g_id += evid.ms();
       const double cf = sizeof(T) == sizeof(double) ? 1.0 : 4.0;
-      for (int q = 0; q < nb; ++q) {   // Householder CPQR: 4 (m-j)(n-j-1) per step, norms, T
+      for (int q = 0; q < nb; ++q) {   // CPQR: norms, per step v^H Y and the k-column corrections, T
         const double m = mrows[q], n = cur.n[boxes[q]], k = hk[q];
         double fl = 2.0 * m * n + k * k * (n - k);
-        for (int j = 0; j < hk[q]; ++j) fl += 4.0 * (m - j) * (n - j - 1);
+        for (int j = 0; j < hk[q]; ++j)
+          fl += 2.0 * (m - j) * (n - j - 1) + 4.0 * (m - j) * j + 4.0 * (n - j) * j;
         f->f_id += cf * fl;
       }
 
@@ -957,7 +1055,7 @@ rss_status factor_impl(const rss_tree* tree, const rss_params* prm, cudaStream_t
     evm.start(st);
     k_merge_pts<T><<<gp * gp, NT, 0, st>>>(cur.d, par.d);
     RSS_LAUNCHED();
-    k_merge_blk<T><<<gp * gp * 25, NT, 0, st>>>(cur.d, par.d, d_ixy, f->kp, f->geo);
+    k_merge_blk<T><<<gp * gp * 25, NT, 0, st>>>(cur.d, par.d, d_ixy, d_tab, f->kp, side);
     RSS_LAUNCHED();
     evm.stop(st);
     RSS_CUDA(cudaStreamSynchronize(st));

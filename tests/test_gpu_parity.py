@@ -39,10 +39,11 @@ def P():
     return P
 
 
-def gpu_factor(P, pts, spec, eps, leaf):
+def gpu_factor(P, pts, spec, eps, leaf, full_stack=False):
     tree = P.rss_build_tree(pts, leaf)
     return P.rss_factor(tree, kind=KIND[spec.kind], eps=eps, h=spec.h, kappa=spec.kappa,
-                        diag=spec.diag, coef=spec.coef, scale=spec.scale, phase=spec.phase)
+                        diag=spec.diag, coef=spec.coef, scale=spec.scale, phase=spec.phase,
+                        full_stack=full_stack)
 
 
 def gpu_solve(P, f, b):
@@ -100,12 +101,16 @@ def _compare_records(P, f, fac, tol):
     return n_cmp
 
 
-def test_laplace_64x64_records_and_solution_match_oracle(P):
-    """The 64 x 64 Laplace workload (eps 1e-8): every box record and the solution."""
+@pytest.mark.parametrize("full_stack", [False, True], ids=["half-stack", "full-stack"])
+def test_laplace_64x64_records_and_solution_match_oracle(P, full_stack):
+    """The 64 x 64 Laplace workload (eps 1e-8): every box record and the solution.
+
+    The oracle always compresses the full stack of Eq. 4; the GPU's default for the
+    real symmetric Laplace kernel compresses its first half, which must give the same ID."""
     side, eps = 64, 1e-8
     pts = W.grid_points(side)
     spec = KernelSpec("laplace", h=1 / side)
-    f = gpu_factor(P, pts, spec, eps, 64)
+    f = gpu_factor(P, pts, spec, eps, 64, full_stack)
     fac = orss.factor(pts, spec, eps)
     for g in (8, 4):
         assert np.array_equal(P.rss_level_ranks(f, g), fac.ranks[g])
