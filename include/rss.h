@@ -72,6 +72,11 @@ typedef struct {
                                      diagonal) compress [A_MB; K_PB] only, which equals the
                                      full stack of Eq. 4 up to rounding; 1: always the full
                                      stack [A_MB; K_PB; A_BM^*; K_BP^*] */
+  int schur_path;                 /* 0: Schur update A_CC -= E F on the tensor cores where
+                                     it applies (real factors, r <= 112): E and F split into
+                                     eight 7-bit slices, exact integer products, FP64
+                                     recombination (accuracy of an FP64 product); 1: FP64
+                                     FMA kernel everywhere */
 } rss_params;
 
 /* Build the quadtree of Section 2.1 for n points given as pts_xy[2*i],

@@ -22,6 +22,8 @@
 #include <cstring>
 #include <vector>
 
+#include <cuda_bf16.h>
+
 #include "internal.h"
 
 namespace {
@@ -382,6 +384,43 @@ template <typename T> __global__ void __launch_bounds__(NT_ID) k_id(IdArgs<T> a)
   if (tid == 0) a.k_out[bi] = k;
 }
 
+// ------------------------------------------------------------------ digit slices
+// A row x_0..x_{r-1} with max |x_l| = m 2^e (m in [0.5, 1)) is written as
+// x_l = 2^e sum_{p=0}^{OZ_S-1} d_{p,l} 2^{-7(p+1)}, with signed digits
+// |d_0| <= 128 and |d_p| <= 64 (p >= 1), all exact in bf16; the truncation error
+// is below 2^(e-57), the rounding of x 2^(56-e) to an integer.
+__device__ inline uint16_t bf16_of_small_int(int d) {
+  const __nv_bfloat16 h = __float2bfloat16_rn((float)d);
+  return __bfloat16_as_ushort(h);
+}
+
+__device__ void oz_split_row(const double* __restrict__ src, int stride, int r, int kp, uint16_t* dst, int* eout) {
+  double mx = 0.0;
+  for (int l = 0; l < r; ++l) mx = fmax(mx, fabs(src[(size_t)l * stride]));
+  int e = 0;
+  if (mx > 0.0) frexp(mx, &e);
+  *eout = e;
+  const double scale = ldexp(1.0, 56 - e);
+  for (int l = 0; l < kp; l += 2) {
+    long long X0 = l < r ? llrint(src[(size_t)l * stride] * scale) : 0;
+    long long X1 = l + 1 < r ? llrint(src[(size_t)(l + 1) * stride] * scale) : 0;
+    int d0[OZ_S], d1[OZ_S];
+#pragma unroll
+    for (int p = OZ_S - 1; p >= 1; --p) {
+      d0[p] = (int)(((X0 + 64) & 127) - 64);
+      X0 = (X0 - d0[p]) >> OZ_BITS;
+      d1[p] = (int)(((X1 + 64) & 127) - 64);
+      X1 = (X1 - d1[p]) >> OZ_BITS;
+    }
+    d0[0] = (int)X0;
+    d1[0] = (int)X1;
+#pragma unroll
+    for (int p = 0; p < OZ_S; ++p)
+      *reinterpret_cast<uint32_t*>(dst + (size_t)p * kp + l) =
+          (uint32_t)bf16_of_small_int(d0[p]) | ((uint32_t)bf16_of_small_int(d1[p]) << 16);
+  }
+}
+
 // ------------------------------------------------------------------ sparsify + LU (Eqs. 7, 8)
 template <typename T> struct ElimArgs {
   LevelDev<T> L;
@@ -495,6 +534,30 @@ template <typename T> __global__ void __launch_bounds__(NT) k_elim(ElimArgs<T> a
     }
     __syncthreads();
   }
+  // explicit L^{-1} P and U^{-1} for the solve sweeps (one column per thread)
+  for (int j = tid; j < r; j += bs) {
+    T* li = R.LiP + (size_t)j * r;    // L^{-1} P e_j
+    for (int i = 0; i < r; ++i) li[i] = zero<T>();
+    int pos = j;                      // where e_j's 1 lands after the row exchanges
+    for (int i = 0; i < r; ++i) {
+      const int p = R.piv[i];
+      if (pos == i) pos = p;
+      else if (pos == p) pos = i;
+    }
+    li[pos] = from_re<T>(1.0);
+    for (int i = pos + 1; i < r; ++i) {
+      T x = li[i];
+      for (int l = pos; l < i; ++l) x = msb(x, LU[i + (size_t)l * r], li[l]);
+      li[i] = x;
+    }
+    T* ui = R.Ui + (size_t)j * r;     // U^{-1} e_j
+    for (int i = j + 1; i < r; ++i) ui[i] = zero<T>();
+    for (int i = j; i >= 0; --i) {
+      T x = i == j ? from_re<T>(1.0) : zero<T>();
+      for (int l = i + 1; l <= j; ++l) x = msb(x, LU[i + (size_t)l * r], ui[l]);
+      ui[i] = dv(x, LU[i + (size_t)i * r]);
+    }
+  }
   // E = X_CR U^{-1} (row by row), F = L^{-1} P X_RC (column by column, kept transposed)
   for (int i = tid; i < c; i += bs) {
     T* e = R.E + i;
@@ -519,6 +582,15 @@ template <typename T> __global__ void __launch_bounds__(NT) k_elim(ElimArgs<T> a
     }
   }
   __syncthreads();
+  if constexpr (sizeof(T) == sizeof(double)) {
+    if (R.Esl != nullptr)   // digit slices of E and F^T for the tensor-core Schur update
+      for (int i = tid; i < 2 * c; i += bs) {
+        const bool isE = i < c;
+        const int row = isE ? i : i - c;
+        oz_split_row((isE ? R.E : R.Ft) + row, c, r, R.kp,
+                     (isE ? R.Esl : R.Fsl) + (size_t)row * OZ_S * R.kp, (isE ? R.Eexp : R.Fexp) + row);
+      }
+  }
   // B keeps only its skeleton
   for (int q = tid; q < k; q += bs) L.act[B * nmax + q] = perm[q];
   if (tid == 0) L.nact[B] = k;
@@ -585,6 +657,132 @@ template <typename T> __global__ void __launch_bounds__(NT) k_schur(LevelDev<T> 
         *p = *p - acc[q][w];
       }
     }
+}
+
+// ------------------------------------------------------------------ Schur update on tensor cores
+// A_CC -= E F for real factors with E and F^T split into OZ_S digit slices.
+// (E F)_ij = 2^(e_i + f_j) sum_u 2^(-7(u+2)) G_u with G_u = sum_{p+q=u} D_p D'_q^T:
+// each G_u is a sum of integer products below 2^24, so bf16 MMAs with FP32
+// accumulation compute it exactly; groups u <= OZ_S-1 are kept (the rest lie
+// below 2^-56 of the row/column scale, the same order as an FP64 product's
+// rounding).  The groups are recombined exactly in two int64 accumulators and
+// rounded once to FP64.  64 x 64 tile per CTA, 8 warps of 32 x 16.
+__device__ __forceinline__ void mma_bf16(float* c, const uint32_t* a, const uint32_t* b) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+__global__ void __launch_bounds__(NT) k_schur_oz(LevelDev<double> L, const BoxRec<double>* recs) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const BoxRec<double> R = recs[blockIdx.y];
+  const int c = R.c, kp = R.kp, nt = (c + 63) / 64;
+  if ((int)blockIdx.x >= nt * nt) return;
+  const int i0 = (blockIdx.x % nt) * 64, j0 = (blockIdx.x / nt) * 64;
+  const int SA = OZ_S * kp + 8;                 // smem row stride in bf16 elements
+  uint16_t* As = reinterpret_cast<uint16_t*>(smraw);
+  uint16_t* Bs = As + 64 * SA;
+  __shared__ long long rowb[64], colb[64];
+  __shared__ int rexp[64], cexp[64];
+  const int nmax = L.nmax, g = L.g;
+  const long long nn = (long long)nmax * nmax;
+  const int tid = threadIdx.x;
+  for (int e = tid; e < 64 * kp; e += NT) {     // kp 16-byte chunks per row (OZ_S * 2 = 16)
+    const int row = e / kp, ch = e % kp;
+    uint4 va = make_uint4(0, 0, 0, 0), vb = va;
+    if (i0 + row < c) va = reinterpret_cast<const uint4*>(R.Esl + (size_t)(i0 + row) * OZ_S * kp)[ch];
+    if (j0 + row < c) vb = reinterpret_cast<const uint4*>(R.Fsl + (size_t)(j0 + row) * OZ_S * kp)[ch];
+    *reinterpret_cast<uint4*>(As + row * SA + ch * 8) = va;
+    *reinterpret_cast<uint4*>(Bs + row * SA + ch * 8) = vb;
+  }
+  if (tid < 64) {
+    const int i = i0 + tid;
+    if (i < c) {
+      const int cm = R.cmap[i], s = cm >> 16, pos = cm & 0xffff;
+      const int u = nbr_box(R.box, g, s % 3 - 1, s / 3 - 1);
+      rowb[tid] = (long long)u * 25 * nn + pos - (long long)((s / 3) * 5 + s % 3) * nn;
+      rexp[tid] = R.Eexp[i];
+    }
+  } else if (tid < 128) {
+    const int j = j0 + tid - 64;
+    if (j < c) {
+      const int cm = R.cmap[j], s = cm >> 16, pos = cm & 0xffff;
+      colb[tid - 64] = (long long)((s / 3) * 5 + s % 3 + 12) * nn + (long long)pos * nmax;
+      cexp[tid - 64] = R.Fexp[j];
+    }
+  }
+  __syncthreads();
+  const int warp = tid >> 5, lane = tid & 31, gq = lane >> 2, t4 = lane & 3;
+  const int m0 = (warp >> 2) * 32, n0 = (warp & 3) * 16;
+  long long hi[2][2][4], lo[2][2][4];
+#pragma unroll
+  for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+    for (int ni = 0; ni < 2; ++ni)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) { hi[mi][ni][e] = 0; lo[mi][ni][e] = 0; }
+  for (int u = 0; u < OZ_S; ++u) {
+    float cf[2][2][4];
+#pragma unroll
+    for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+      for (int ni = 0; ni < 2; ++ni)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) cf[mi][ni][e] = 0.f;
+    for (int p = 0; p <= u; ++p) {
+      const uint16_t* Ab = As + p * kp;
+      const uint16_t* Bb = Bs + (u - p) * kp;
+      for (int kk = 0; kk < kp; kk += 16) {
+        uint32_t af[2][4], bq[2][2];
+#pragma unroll
+        for (int mi = 0; mi < 2; ++mi) {
+          const uint16_t* a0 = Ab + (m0 + mi * 16 + gq) * SA + kk + 2 * t4;
+          af[mi][0] = *reinterpret_cast<const uint32_t*>(a0);
+          af[mi][1] = *reinterpret_cast<const uint32_t*>(a0 + 8 * SA);
+          af[mi][2] = *reinterpret_cast<const uint32_t*>(a0 + 8);
+          af[mi][3] = *reinterpret_cast<const uint32_t*>(a0 + 8 * SA + 8);
+        }
+#pragma unroll
+        for (int ni = 0; ni < 2; ++ni) {
+          const uint16_t* b0 = Bb + (n0 + ni * 8 + gq) * SA + kk + 2 * t4;
+          bq[ni][0] = *reinterpret_cast<const uint32_t*>(b0);
+          bq[ni][1] = *reinterpret_cast<const uint32_t*>(b0 + 8);
+        }
+#pragma unroll
+        for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+          for (int ni = 0; ni < 2; ++ni) mma_bf16(cf[mi][ni], af[mi], bq[ni]);
+      }
+    }
+#pragma unroll
+    for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+      for (int ni = 0; ni < 2; ++ni)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const long long gv = (long long)__float2int_rn(cf[mi][ni][e]);
+          if (u <= 2) hi[mi][ni][e] += gv << (OZ_BITS * (2 - u));
+          else lo[mi][ni][e] += gv << (OZ_BITS * (OZ_S - 1 - u));
+        }
+  }
+#pragma unroll
+  for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+    for (int ni = 0; ni < 2; ++ni)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int row = m0 + mi * 16 + gq + (e >= 2 ? 8 : 0);
+        const int col = n0 + ni * 8 + 2 * t4 + (e & 1);
+        if (i0 + row < c && j0 + col < c) {
+          // sum_u 2^(-7(u+2)) G_u = hi 2^-28 + lo 2^-63
+          double v = fma((double)hi[mi][ni][e], 0x1p-28, (double)lo[mi][ni][e] * 0x1p-63);
+          v = ldexp(v, rexp[row] + cexp[col]);
+          double* ptr = L.blk + rowb[row] + colb[col];
+          *ptr = *ptr - v;
+        }
+      }
 }
 
 // ------------------------------------------------------------------ merge (Section 2.4)
@@ -964,12 +1162,14 @@ rss_status factor_impl(const rss_tree* tree, const rss_params* prm, cudaStream_t
         R.Tm = static_cast<T*>(f->arena.get(sizeof(T) * (size_t)k * r));
         R.LU = static_cast<T*>(f->arena.get(sizeof(T) * (size_t)r * r));
         R.piv = static_cast<int*>(f->arena.get(sizeof(int) * r));
+        R.LiP = static_cast<T*>(f->arena.get(sizeof(T) * (size_t)r * r));
+        R.Ui = static_cast<T*>(f->arena.get(sizeof(T) * (size_t)r * r));
         R.E = static_cast<T*>(f->arena.get(sizeof(T) * (size_t)c * r));
         R.Ft = static_cast<T*>(f->arena.get(sizeof(T) * (size_t)c * r));
         R.idxR = static_cast<int*>(f->arena.get(sizeof(int) * r));
         R.idxC = static_cast<int*>(f->arena.get(sizeof(int) * c));
         R.cmap = static_cast<int*>(f->arena.get(sizeof(int) * c));
-        if (!R.Tm || !R.LU || !R.piv || !R.E || !R.Ft || !R.idxR || !R.idxC || !R.cmap) {
+        if (!R.Tm || !R.LU || !R.piv || !R.LiP || !R.Ui || !R.E || !R.Ft || !R.idxR || !R.idxC || !R.cmap) {
           rss_set_error("rss_factor: device arena allocation failed");
           return RSS_ENOMEM;
         }
@@ -987,6 +1187,34 @@ rss_status factor_impl(const rss_tree* tree, const rss_params* prm, cudaStream_t
         if (cur.n[boxes[q]] - hk[q] > 0) cur.nact[boxes[q]] = hk[q];
       if (recs.empty()) continue;
       const int nrec = (int)recs.size();
+      // tensor-core Schur update: real factors with r <= 96 (the slices of a
+      // 64-row tile of E and of F^T must fit in shared memory)
+      const bool oz = sizeof(T) == sizeof(double) && prm->schur_path == 0 && max_r <= 96;
+      void* d_oz = nullptr;
+      int kp_max = 0;
+      if (oz) {
+        size_t bytes = 0;
+        for (const BoxRec<T>& R : recs) {
+          const int kp = (R.r + 15) & ~15;
+          bytes += 2 * ((size_t)R.c * OZ_S * kp * sizeof(uint16_t) + 256) + 2 * ((size_t)R.c * sizeof(int) + 256);
+        }
+        RSS_CUDA(cudaMalloc(&d_oz, bytes));
+        char* p = static_cast<char*>(d_oz);
+        auto take = [&](size_t b) {
+          char* q = p;
+          p += (b + 255) & ~size_t(255);
+          return q;
+        };
+        for (BoxRec<T>& R : recs) {
+          R.kp = (R.r + 15) & ~15;
+          kp_max = std::max(kp_max, R.kp);
+          R.Esl = reinterpret_cast<uint16_t*>(take((size_t)R.c * OZ_S * R.kp * sizeof(uint16_t)));
+          R.Fsl = reinterpret_cast<uint16_t*>(take((size_t)R.c * OZ_S * R.kp * sizeof(uint16_t)));
+          R.Eexp = reinterpret_cast<int*>(take((size_t)R.c * sizeof(int)));
+          R.Fexp = reinterpret_cast<int*>(take((size_t)R.c * sizeof(int)));
+        }
+        f->peak_transient = std::max(f->peak_transient, transient + bytes);
+      }
       BoxRec<T>* d_recs = static_cast<BoxRec<T>*>(f->arena.get(sizeof(BoxRec<T>) * nrec));
       if (!d_recs) { rss_set_error("rss_factor: device arena allocation failed"); return RSS_ENOMEM; }
       RSS_CUDA(cudaMemcpyAsync(d_recs, recs.data(), sizeof(BoxRec<T>) * nrec, cudaMemcpyHostToDevice, st));
@@ -1009,10 +1237,20 @@ rss_status factor_impl(const rss_tree* tree, const rss_params* prm, cudaStream_t
       Timer ts;
       const int ntile = (max_c + 63) / 64;
       evsc.start(st);
-      k_schur<T><<<dim3(ntile * ntile, nrec), NT, 0, st>>>(cur.d, d_recs);
+      if (oz) {
+        if constexpr (sizeof(T) == sizeof(double)) {
+          const size_t smem = 2 * 64 * (size_t)(OZ_S * kp_max + 8) * sizeof(uint16_t);
+          RSS_CUDA(cudaFuncSetAttribute(k_schur_oz, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+          k_schur_oz<<<dim3(ntile * ntile, nrec), NT, smem, st>>>(cur.d, d_recs);
+        }
+      } else {
+        k_schur<T><<<dim3(ntile * ntile, nrec), NT, 0, st>>>(cur.d, d_recs);
+      }
       RSS_LAUNCHED();
       evsc.stop(st);
       RSS_CUDA(cudaStreamSynchronize(st));
+      if (d_oz) cudaFree(d_oz);
+      for (BoxRec<T>& R : recs) R.Esl = R.Fsl = nullptr, R.Eexp = R.Fexp = nullptr;
       f->t_schur += ts.ms();
       f->g_elim += evel.ms();
       f->g_schur += evsc.ms();

@@ -31,12 +31,24 @@ template <typename T> struct BoxRec {
   T* Tm;        // k x r, ld k
   T* LU;        // r x r packed LU of X_RR, ld r
   int* piv;     // r getrf pivots (0-based)
+  T* LiP;       // r x r, ld r: L_R^{-1} P_R (the solve applies it as one product)
+  T* Ui;        // r x r, ld r: U_R^{-1}
   T* E;         // c x r, ld c:  X_CR U_R^{-1}
   T* Ft;        // c x r, ld c:  (L_R^{-1} P_R X_RC)^T (plain transpose)
   int* idxR;    // r tree indices of R
   int* idxC;    // c tree indices of C = S then the neighbours' active points
   int* cmap;    // c entries (slot << 16 | position) used by the Schur update
+  // factor-time only: E and F^T split into bf16 digit slices for the
+  // tensor-core Schur update (null when the FP64 FMA kernel is used)
+  uint16_t* Esl;  // c x (OZ_S * kp) bf16, row i at Esl + i * OZ_S * kp, slice p at + p * kp
+  uint16_t* Fsl;
+  int* Eexp;      // c row exponents
+  int* Fexp;
+  int kp;         // r rounded up to a multiple of 16
 };
+
+constexpr int OZ_S = 8;      // digit slices per operand
+constexpr int OZ_BITS = 7;   // bits per slice
 
 struct Batch {
   int side;       // box grid side of the level

@@ -43,7 +43,8 @@ __global__ void __launch_bounds__(NT) k_solve_up(const BoxRec<T>* __restrict__ r
   const int k = R.k, r = R.r, c = R.c;
   const int q0 = blockIdx.y * RC, nq = min(RC, nrhs - q0);
   T* bS = reinterpret_cast<T*>(smraw);   // k x RC
-  T* bR = bS + (size_t)k * RC;           // r x RC
+  T* t = bS + (size_t)k * RC;            // r x RC
+  T* bR = t + (size_t)r * RC;            // r x RC
   const int tid = threadIdx.x, bs = blockDim.x;
   T* xq = x + (int64_t)q0 * N;
   for (int e = tid; e < k * RC; e += bs) {
@@ -52,38 +53,24 @@ __global__ void __launch_bounds__(NT) k_solve_up(const BoxRec<T>* __restrict__ r
   }
   for (int e = tid; e < r * RC; e += bs) {
     const int j = e / RC, q = e % RC;
-    bR[e] = q < nq ? xq[R.idxR[j] + (int64_t)q * N] : zero<T>();
+    t[e] = q < nq ? xq[R.idxR[j] + (int64_t)q * N] : zero<T>();
   }
   __syncthreads();
-  for (int e = tid; e < r * RC; e += bs) {        // b_R -= T^* b_S
+  for (int e = tid; e < r * RC; e += bs) {        // b_R - T^* b_S
     const int j = e / RC, q = e % RC;
-    T acc = bR[e];
+    T acc = t[e];
     for (int s = 0; s < k; ++s) acc = msbc(acc, R.Tm[s + (size_t)j * k], bS[s * RC + q]);
-    bR[e] = acc;
+    t[e] = acc;
   }
   __syncthreads();
-  if (tid < RC)
-    for (int j = 0; j < r; ++j) {                 // P_R
-      const int p = R.piv[j];
-      if (p != j) {
-        const T t = bR[j * RC + tid];
-        bR[j * RC + tid] = bR[p * RC + tid];
-        bR[p * RC + tid] = t;
-      }
-    }
-  __syncthreads();
-  for (int j = 0; j + 1 < r; ++j) {               // L_R^{-1} (unit lower)
-    const int w = (r - j - 1) * RC;
-    for (int e = tid; e < w; e += bs) {
-      const int l = j + 1 + e / RC, q = e % RC;
-      bR[l * RC + q] = msb(bR[l * RC + q], R.LU[l + (size_t)j * r], bR[j * RC + q]);
-    }
-    __syncthreads();
-  }
-  for (int e = tid; e < r * RC; e += bs) {
+  for (int e = tid; e < r * RC; e += bs) {        // L_R^{-1} P_R (b_R - T^* b_S)
     const int j = e / RC, q = e % RC;
-    if (q < nq) xq[R.idxR[j] + (int64_t)q * N] = bR[e];
+    T acc = zero<T>();
+    for (int l = 0; l < r; ++l) acc = mad(acc, R.LiP[j + (size_t)l * r], t[l * RC + q]);
+    bR[e] = acc;
+    if (q < nq) xq[R.idxR[j] + (int64_t)q * N] = acc;
   }
+  __syncthreads();
   for (int i = tid; i < c; i += bs) {             // b_C -= E b_R
     T acc[RC];
 #pragma unroll
@@ -107,7 +94,8 @@ __global__ void __launch_bounds__(NT) k_solve_down(const BoxRec<T>* __restrict__
   const BoxRec<T> R = recs[blockIdx.x];
   const int k = R.k, r = R.r, c = R.c;
   const int q0 = blockIdx.y * RC, nq = min(RC, nrhs - q0);
-  T* yR = reinterpret_cast<T*>(smraw);   // r x RC
+  T* t = reinterpret_cast<T*>(smraw);   // r x RC
+  T* yR = t + (size_t)r * RC;           // r x RC
   const int tid = threadIdx.x, bs = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = bs >> 5;
   T* xq = x + (int64_t)q0 * N;
   for (int j = warp; j < r; j += nw) {            // y_R - F y_C
@@ -126,24 +114,18 @@ __global__ void __launch_bounds__(NT) k_solve_down(const BoxRec<T>* __restrict__
     if (lane == 0) {
       const int gj = R.idxR[j];
 #pragma unroll
-      for (int q = 0; q < RC; ++q) yR[j * RC + q] = q < nq ? xq[gj + (int64_t)q * N] - acc[q] : zero<T>();
+      for (int q = 0; q < RC; ++q) t[j * RC + q] = q < nq ? xq[gj + (int64_t)q * N] - acc[q] : zero<T>();
     }
   }
   __syncthreads();
-  for (int j = r - 1; j >= 0; --j) {              // U_R^{-1}
-    if (tid < RC) yR[j * RC + tid] = dv(yR[j * RC + tid], R.LU[j + (size_t)j * r]);
-    __syncthreads();
-    const int w = j * RC;
-    for (int e = tid; e < w; e += bs) {
-      const int l = e / RC, q = e % RC;
-      yR[l * RC + q] = msb(yR[l * RC + q], R.LU[l + (size_t)j * r], yR[j * RC + q]);
-    }
-    __syncthreads();
-  }
-  for (int e = tid; e < r * RC; e += bs) {
+  for (int e = tid; e < r * RC; e += bs) {        // U_R^{-1} (y_R - F y_C)
     const int j = e / RC, q = e % RC;
-    if (q < nq) xq[R.idxR[j] + (int64_t)q * N] = yR[e];
+    T acc = zero<T>();
+    for (int l = j; l < r; ++l) acc = mad(acc, R.Ui[j + (size_t)l * r], t[l * RC + q]);
+    yR[e] = acc;
+    if (q < nq) xq[R.idxR[j] + (int64_t)q * N] = acc;
   }
+  __syncthreads();
   for (int e = tid; e < k * RC; e += bs) {        // y_S -= T y_R
     const int s = e / RC, q = e % RC;
     if (q >= nq) continue;
@@ -208,7 +190,7 @@ rss_status sweeps(const rss_factorization* f, T* x, int64_t N, int nrhs, cudaStr
   RSS_CUDA(cudaFuncSetAttribute(k_solve_up<T, RC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
   RSS_CUDA(cudaFuncSetAttribute(k_solve_down<T, RC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
   for (const Batch& b : f->batches) {
-    const size_t smem = sizeof(T) * (size_t)(b.max_k + b.max_r) * RC;
+    const size_t smem = sizeof(T) * (size_t)(b.max_k + 2 * b.max_r) * RC;
     k_solve_up<T, RC><<<dim3(b.nrec, nchunk), NT, smem, st>>>(static_cast<const BoxRec<T>*>(b.d_recs), x, N, nrhs);
     RSS_LAUNCHED();
   }
@@ -225,7 +207,7 @@ rss_status sweeps(const rss_factorization* f, T* x, int64_t N, int nrhs, cudaStr
     RSS_LAUNCHED();
   }
   for (auto it = f->batches.rbegin(); it != f->batches.rend(); ++it) {
-    const size_t smem = sizeof(T) * (size_t)it->max_r * RC;
+    const size_t smem = sizeof(T) * (size_t)2 * it->max_r * RC;
     k_solve_down<T, RC><<<dim3(it->nrec, nchunk), NT, smem, st>>>(static_cast<const BoxRec<T>*>(it->d_recs), x, N,
                                                                  nrhs);
     RSS_LAUNCHED();

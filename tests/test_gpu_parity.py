@@ -241,3 +241,24 @@ def test_full_size_sampled_records_and_residual(P, name, nsample):
     b = W.gaussian_rhs(side * side, min(w["nrhs"], 2), spec.is_complex, w["seed"])
     x = gpu_solve(P, f, b)
     assert relres(pts, spec, x, b) <= 10 * eps
+
+
+def test_tensor_core_schur_matches_fp64_schur(P):
+    """The split-digit tensor-core Schur update agrees with the FP64 FMA kernel."""
+    side, eps = 128, 1e-6
+    pts = W.grid_points(side)
+    tree = P.rss_build_tree(pts, 64)
+    f_tc = P.rss_factor(tree, kind=0, eps=eps, h=1 / side)
+    f_64 = P.rss_factor(tree, kind=0, eps=eps, h=1 / side, schur_fp64=True)
+    for g in (16, 8, 4):
+        assert np.array_equal(P.rss_level_ranks(f_tc, g), P.rss_level_ranks(f_64, g))
+    for g, box in ((16, 0), (16, 137), (8, 27), (4, 5)):
+        a, b = P.rss_box_record(f_tc, g, box), P.rss_box_record(f_64, g, box)
+        assert np.array_equal(a["S"], b["S"]) and np.array_equal(a["C"], b["C"])
+        for key in ("T", "E", "F", "LU"):
+            assert rel(a[key], b[key]) < rec_tol(eps), (g, box, key)
+    bvec = W.gaussian_rhs(side * side, 2, False, 21)
+    x_tc, x_64 = gpu_solve(P, f_tc, bvec), gpu_solve(P, f_64, bvec)
+    assert rel(x_tc, x_64) < 1e-12
+    spec = KernelSpec("laplace", h=1 / side)
+    assert relres(pts, spec, x_tc, bvec) <= 10 * eps
