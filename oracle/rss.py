@@ -26,8 +26,10 @@ Readings where the paper is silent (each also listed in the design notes):
   - ID truncation: Frobenius norm, stop at the first k with
     ||R22||_F <= eps ||Y||_F (then ||Y_R - Y_S T||_F = ||R22||_F, Definition 1);
   - pivot ties: columns whose remaining squared norm is within rounding noise
-    of the maximum (1e-9 relative, plus 1e-12 sqrt(max x largest initial
+    of the maximum (1e-6 relative, plus 1e-12 sqrt(max x largest initial
     squared norm)) count as tied, and the lowest original column wins;
+  - downdated column norms are re-accumulated once they fall below
+    sqrt(unit roundoff) of their last accumulated value (LAPACK's rule);
   - compression on box grids of side >= 4, a dense LU on what remains at
     side 2 (there is no far field at the two top levels);
   - children are merged in the order SW, SE, NW, NE, each child's skeleton in
@@ -47,11 +49,15 @@ from scipy import special
 # the largest initial squared column norm, cannot be told apart and count as
 # tied (exact-arithmetic ties from the grid's symmetry show up as such
 # rounding-level differences).
-TIE_REL = 1e-9
+TIE_REL = 1e-6
 TIE_ABS = 1e-12
 # A downdated squared column norm is re-accumulated from the trailing rows once
-# it has fallen below this fraction of the value it was last accumulated at.
-RECOMPUTE_REL = 1e-4
+# it has fallen below this fraction of the value it was last accumulated at
+# (sqrt of the unit roundoff, LAPACK geqp3's threshold).  Between
+# re-accumulations a downdated value is therefore accurate to about
+# eps_mach / RECOMPUTE_REL = 7e-9 relative per downdate (a few 1e-8 after many
+# steps), well inside the 1e-6 tie window above.
+RECOMPUTE_REL = 1.4901161193847656e-08
 
 
 # ---------------------------------------------------------------------------

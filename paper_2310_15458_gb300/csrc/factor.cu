@@ -31,9 +31,12 @@ namespace {
 // Pivot ties: remaining squared norms within TIE_REL n_max + TIE_ABS sqrt(n_max y2max)
 // of the maximum n_max (y2max: largest initial squared column norm) are rounding
 // noise apart and count as tied; the lowest original column wins.
-constexpr double TIE_REL = 1e-9;
+constexpr double TIE_REL = 1e-6;
 constexpr double TIE_ABS = 1e-12;
-constexpr double RECOMPUTE_REL = 1e-4;  // re-accumulate a downdated norm below this fraction
+// A downdated squared norm is re-accumulated once it falls below sqrt(unit
+// roundoff) of its last accumulated value (LAPACK geqp3's rule); between
+// re-accumulations it is accurate to a few 1e-8 relative, inside the tie window.
+constexpr double RECOMPUTE_REL = 1.4901161193847656e-08;
 constexpr int NT = 256;                 // threads per CTA for the per-box kernels
 
 template <typename T> struct LevelDev {
@@ -111,7 +114,7 @@ __global__ void __launch_bounds__(NT) k_gen_blocks(LevelDev<T> L, const int2* __
 // the remaining columns plus O((m + n) j) corrections, the pivot column and row j
 // of R are formed on demand, and Y is never rewritten.  In exact arithmetic this
 // is the same sequence of reflectors and pivots as updating Y in place.
-constexpr int NT_ID = 512;
+constexpr int NT_ID = 256;
 
 template <typename T> struct IdArgs {
   LevelDev<T> L;
@@ -132,7 +135,7 @@ template <typename T> struct IdArgs {
   double Lbox;        // box side
 };
 
-template <typename T> __global__ void __launch_bounds__(NT_ID) k_id(IdArgs<T> a) {
+template <typename T> __global__ void __launch_bounds__(NT_ID, 4) k_id(IdArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const LevelDev<T>& L = a.L;
   const int nmax = L.nmax, g = L.g, ldY = a.ldY;
@@ -302,9 +305,9 @@ template <typename T> __global__ void __launch_bounds__(NT_ID) k_id(IdArgs<T> a)
     __syncthreads();
     if (s_stop) break;
     {
-      const T d = s_scale;
+      const T d = dv(from_re<T>(1.0), s_scale);
       for (int i = k + 1 + tid; i < m; i += blockDim.x) {
-        const T v = dv(vbuf[i], d);
+        const T v = vbuf[i] * d;
         vbuf[i] = v;
         V[(size_t)k * ldY + i] = v;
       }
@@ -354,7 +357,21 @@ template <typename T> __global__ void __launch_bounds__(NT_ID) k_id(IdArgs<T> a)
       if (!flag[pos]) continue;
       const int c = perm[pos];
       double t = 0.0;
-      for (int i = k + 1 + lane; i < m; i += 32) {
+      int i = k + 1 + lane;
+      for (; i + 96 < m; i += 128) {   // four rows per lane in flight
+        T x0 = Y[(size_t)c * ldY + i], x1 = Y[(size_t)c * ldY + i + 32];
+        T x2 = Y[(size_t)c * ldY + i + 64], x3 = Y[(size_t)c * ldY + i + 96];
+        for (int l = 0; l <= k; ++l) {
+          const T gl = G[(size_t)l * nmax + c];
+          const T* vl = V + (size_t)l * ldY + i;
+          x0 = msb(x0, vl[0], gl);
+          x1 = msb(x1, vl[32], gl);
+          x2 = msb(x2, vl[64], gl);
+          x3 = msb(x3, vl[96], gl);
+        }
+        t += (abs2(x0) + abs2(x1)) + (abs2(x2) + abs2(x3));
+      }
+      for (; i < m; i += 32) {
         T x = Y[(size_t)c * ldY + i];
         for (int l = 0; l <= k; ++l) x = msb(x, V[(size_t)l * ldY + i], G[(size_t)l * nmax + c]);
         t += abs2(x);
@@ -1087,7 +1104,9 @@ rss_status factor_impl(const rss_tree* tree, const rss_params* prm, cudaStream_t
       const int ldY = (mmax + 1) & ~1;
       const size_t slot = (2 * (size_t)ldY * nmax + 2 * nn) * sizeof(T);
       const size_t ybudget = size_t(2) << 30;
-      const int chunk = (int)std::max<size_t>(1, std::min<size_t>(nb, ybudget / slot));
+      const int cap = (int)std::max<size_t>(1, std::min<size_t>(nb, ybudget / slot));
+      const int nchunks = (nb + cap - 1) / cap;
+      const int chunk = (nb + nchunks - 1) / nchunks;   // balanced chunks
       T* d_Y = nullptr;
       RSS_CUDA(cudaMalloc(&d_Y, slot * chunk));
       const size_t smem_id = sizeof(T) * ((size_t)ldY + 2 * nmax) + (size_t)nmax * (3 * sizeof(double) + 2 * sizeof(int));
