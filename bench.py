@@ -50,6 +50,9 @@ def parse():
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(W.WORKLOADS))
     ap.add_argument("--multi-rhs", type=int, default=256)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=600)
+    ap.add_argument("--serve-load", type=float, default=0.9)
     return ap.parse_args()
 
 
@@ -191,6 +194,82 @@ def reference_arm(args, w):
     print(json.dumps(line), flush=True)
 
 
+# ----------------------------------------------------------------------------- serving
+SERVE_SET = [("laplace", 128, 0.0), ("laplace", 256, 0.0), ("laplace", 512, 0.0),
+             ("helmholtz", 256, 25.0)]
+
+
+def serve_run(P, torch, args):
+    """Resident factorizations (Laplace 128^2, 256^2, 512^2 and Helmholtz kappa = 25 at
+    256^2, eps 1e-6) behind the continuous-batching server; seeded Poisson arrivals of
+    requests with 1-64 Gaussian right-hand sides on a uniformly drawn factorization, at
+    a load of serve_load times the solo capacity.  Latency = submit to result in host
+    memory."""
+    import threading
+    facs = []
+    for kind, side, kappa in SERVE_SET:
+        tree = P.rss_build_tree(W.grid_points(side), W.LEAF)
+        facs.append(P.rss_factor(tree, kind=W.LAPLACE if kind == "laplace" else W.HELMHOLTZ,
+                                 eps=1e-6, h=1.0 / side, kappa=kappa))
+    rng = np.random.default_rng(1003)
+    nreq = args.serve_requests
+    which = rng.integers(0, len(facs), nreq)
+    nrhs = rng.integers(1, 65, nreq)
+    pool = {}
+    for j, f in enumerate(facs):
+        pool[j] = W.gaussian_rhs(f.n, 64, f.is_complex, 2000 + j)
+    # solo capacity: mean service time of one request alone (32-column panel, host buffers)
+    solo = []
+    for j, f in enumerate(facs):
+        b = np.asfortranarray(pool[j][:, :32].copy())
+        P.rss_solve(f, b)
+        t0 = time.perf_counter()
+        for _ in range(3):
+            b = np.asfortranarray(pool[j][:, :32].copy())
+            P.rss_solve(f, b)
+        solo.append((time.perf_counter() - t0) / 3)
+    mean_service = float(np.mean(solo)) * (np.mean(nrhs) / 32.0)
+    rate = args.serve_load / mean_service
+    gaps = rng.exponential(1.0 / rate, nreq)
+    srv = P.rss_server_create(8 << 30, 256)
+    ids = [P.rss_server_add(srv, f) for f in facs]
+    tickets = [None] * nreq
+    lat = [0.0] * nreq
+    done = threading.Event()
+
+    def waiter():
+        for q in range(nreq):
+            while tickets[q] is None:
+                time.sleep(1e-5)
+            _, lat[q] = P.rss_server_wait(srv, tickets[q], timeout=120.0)
+        done.set()
+
+    th = threading.Thread(target=waiter)
+    th.start()
+    t_start = time.perf_counter()
+    t_next = t_start
+    for q in range(nreq):
+        t_next += gaps[q]
+        while time.perf_counter() < t_next:
+            pass
+        j = int(which[q])
+        b = np.asfortranarray(pool[j][:, :int(nrhs[q])])
+        tickets[q] = P.rss_server_submit(srv, ids[j], b)
+    done.wait()
+    t_total = time.perf_counter() - t_start
+    th.join()
+    st = P.rss_server_stats(srv)
+    warm = min(100, nreq // 6)
+    l = np.array(lat[warm:]) * 1e3
+    return {"workload": "Laplace 128^2, 256^2, 512^2 + Helmholtz k=25 256^2, eps 1e-6, 1-64 RHS",
+            "requests": nreq, "warmup_requests": warm, "load": args.serve_load,
+            "arrival_rate_per_s": rate, "p50_ms": float(np.percentile(l, 50)),
+            "p99_ms": float(np.percentile(l, 99)), "mean_ms": float(l.mean()),
+            "rhs_per_s": float(nrhs.sum() / t_total), "panels": st["batches"],
+            "max_requests_per_panel": st["max_requests_per_batch"],
+            "solo_ms_32rhs": [t * 1e3 for t in solo]}
+
+
 # ----------------------------------------------------------------------------- native arm
 def native_arm(args, w):
     import torch
@@ -325,6 +404,8 @@ def native_arm(args, w):
                      "peak_source": "FP64 DFMA loop measured on this GB300 (no FP64 figure in "
                                     "MEASURED_PEAKS.json)"},
     }
+    if not args.no_serve:
+        line["serve"] = serve_run(P, torch, args)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_block(w, run_oracle(w, 1))
     if rank == 0:

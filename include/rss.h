@@ -32,6 +32,7 @@ extern "C" {
 
 typedef struct rss_tree rss_tree;
 typedef struct rss_factorization rss_factorization;
+typedef struct rss_server rss_server;
 
 typedef enum {
   RSS_OK = 0,
@@ -127,7 +128,43 @@ rss_status rss_solve(const rss_factorization* f, void* b, int64_t nrhs, int64_t 
 rss_status rss_solve_noalloc(const rss_factorization* f, void* b, int64_t nrhs, int64_t ldb,
                              void* stream);
 
-/* Release a tree or a factor (the handle is tagged).  NULL is ignored. */
+/* ---- Serving: resident factorizations, continuous batching of solves ----
+ * A server owns a worker thread and, per registered factorization, a CUDA
+ * stream.  Whenever a factorization's stream is idle, the worker packs all of
+ * its pending requests (up to max_batch_rhs columns, and only as far as the
+ * device-memory budget allows) into one right-hand-side panel and solves it
+ * with one rss_solve; requests arriving meanwhile join the next panel, and
+ * panels of different factorizations run concurrently on their own streams.
+ * Every column goes through the same operations whatever it is batched with,
+ * so a result equals the one rss_solve gives for the request alone.  This is
+ * the serving pattern the workloads ask for (requests of 1-64 right-hand sides
+ * against several resident factorizations); the paper has no counterpart. */
+
+/* Start a server that may hold at most device_bytes of device memory for
+ * panels and solve workspaces (2 * n * columns * scalar bytes per panel), with
+ * at most max_batch_rhs columns per panel. */
+rss_status rss_server_create(size_t device_bytes, int64_t max_batch_rhs, rss_server** out);
+
+/* Register a factorization (it must outlive the server); *factor_id names it. */
+rss_status rss_server_add(rss_server* s, const rss_factorization* f, int32_t* factor_id);
+
+/* Queue a solve: b and x are host arrays of n x nrhs scalars, column-major with
+ * leading dimension n; both must stay valid until rss_server_wait returns for
+ * *ticket.  x receives A^{-1} b.  Returns at once. */
+rss_status rss_server_submit(rss_server* s, int32_t factor_id, const void* b, void* x, int64_t nrhs,
+                             int64_t* ticket);
+
+/* Block until the request is done (timeout_s <= 0: no limit; RSS_ETIMEOUT if
+ * it is still pending then).  *latency_s (may be NULL) receives the time from
+ * submission to the result being in x.  A request that can never fit the
+ * budget fails with RSS_ENOMEM. */
+rss_status rss_server_wait(rss_server* s, int64_t ticket, double timeout_s, double* latency_s);
+
+/* JSON counters: requests, panels, columns, largest panel, memory in use. */
+rss_status rss_server_stats(rss_server* s, char* buf, size_t len);
+
+/* Release a tree, a factor or a server (the handle is tagged; a server first
+ * finishes its in-flight panels).  NULL is ignored. */
 void rss_free(void* handle);
 
 /* Message for the last non-OK status returned on this thread. */

@@ -197,6 +197,8 @@ void rss_free(void* h) {
     delete t;
   } else if (tag == RSS_TAG_FACTOR) {
     free_factor(static_cast<rss_factorization*>(h));
+  } else if (tag == RSS_TAG_SERVER) {
+    free_server(static_cast<rss_server*>(h));
   }
 }
 

@@ -446,9 +446,11 @@ template <typename T> struct ElimArgs {
   const int* perm_in;
   const T* T_ws;
   int* err;
+  int smem_cap;             // k*r + 2 r^2 scalars fit in dynamic shared memory
 };
 
-template <typename T> __global__ void __launch_bounds__(NT) k_elim(ElimArgs<T> a) {
+template <typename T> __global__ void __launch_bounds__(NT, 4) k_elim(ElimArgs<T> a) {
+  extern __shared__ __align__(16) unsigned char smraw[];
   const LevelDev<T>& L = a.L;
   const BoxRec<T> R = a.recs[blockIdx.x];
   const int nmax = L.nmax, g = L.g, B = R.box, k = R.k, r = R.r, c = R.c;
@@ -456,6 +458,11 @@ template <typename T> __global__ void __launch_bounds__(NT) k_elim(ElimArgs<T> a
   const int* perm = a.perm_in + (size_t)a.cls_idx[blockIdx.x] * nmax;
   const T* Tw = a.T_ws + (size_t)a.cls_idx[blockIdx.x] * nn;
   const int tid = threadIdx.x, bs = blockDim.x, lane = tid & 31, warp = tid >> 5;
+  // on-chip copies of T (k x r), the LU and U^{-1} (r x r) when they fit
+  const bool onchip = k * r + 2 * r * r <= a.smem_cap;
+  T* Ts = onchip ? reinterpret_cast<T*>(smraw) : R.Tm;
+  T* LU = onchip ? Ts + (size_t)k * r : R.LU;
+  T* Ui = onchip ? LU + (size_t)r * r : R.Ui;
   __shared__ int nb[9], coff[10], s_piv, s_zero;
   __shared__ int ord[9];
   if (tid == 0) {
@@ -480,9 +487,13 @@ template <typename T> __global__ void __launch_bounds__(NT) k_elim(ElimArgs<T> a
     R.idxC[i] = L.pts[u * nmax + pos];
   }
   for (int j = tid; j < r; j += bs) R.idxR[j] = L.pts[B * nmax + perm[k + j]];
-  for (int e = tid; e < k * r; e += bs) R.Tm[e] = Tw[(size_t)(e / k) * nmax + e % k];
+  for (int e = tid; e < k * r; e += bs) {
+    const T t = Tw[(size_t)(e / k) * nmax + e % k];
+    R.Tm[e] = t;
+    if (onchip) Ts[e] = t;
+  }
   __syncthreads();
-  // X_CR -> E (c x r), X_RC^T -> Ft (c x r)
+  // X_CR -> E (c x r), X_RC^T -> Ft (c x r)   (Eq. 7)
   for (long long e = tid; e < (long long)c * r; e += bs) {
     const int i = (int)(e % c), j = (int)(e / c);
     const int cm = R.cmap[i], s = cm >> 16, pos = cm & 0xffff, u = nb[s];
@@ -491,8 +502,9 @@ template <typename T> __global__ void __launch_bounds__(NT) k_elim(ElimArgs<T> a
     const int rj = perm[k + j];
     T x = Aub[(size_t)rj * nmax + pos];
     T y = Abu[(size_t)pos * nmax + rj];
+    const T* tj = Ts + (size_t)j * k;
     for (int q = 0; q < k; ++q) {
-      const T t = Tw[(size_t)j * nmax + q];
+      const T t = tj[q];
       x = msb(x, Aub[(size_t)perm[q] * nmax + pos], t);
       y = msbc(y, t, Abu[(size_t)pos * nmax + perm[q]]);
     }
@@ -505,13 +517,12 @@ template <typename T> __global__ void __launch_bounds__(NT) k_elim(ElimArgs<T> a
   for (int e = tid; e < r * r; e += bs) {
     const int ai = e % r, bj = e / r;
     T x = Abb[(size_t)perm[k + bj] * nmax + perm[k + ai]];
-    for (int q = 0; q < k; ++q) x = msb(x, Abb[(size_t)perm[q] * nmax + perm[k + ai]], Tw[(size_t)bj * nmax + q]);
-    for (int q = 0; q < k; ++q) x = msbc(x, Tw[(size_t)ai * nmax + q], R.E[q + (size_t)bj * c]);
-    R.LU[ai + (size_t)bj * r] = x;
+    for (int q = 0; q < k; ++q) x = msb(x, Abb[(size_t)perm[q] * nmax + perm[k + ai]], Ts[q + (size_t)bj * k]);
+    for (int q = 0; q < k; ++q) x = msbc(x, Ts[q + (size_t)ai * k], R.E[q + (size_t)bj * c]);
+    LU[ai + (size_t)bj * r] = x;
   }
   __syncthreads();
-  // P X_RR = L U, partial pivoting (largest modulus, lowest row on ties)
-  T* LU = R.LU;
+  // P X_RR = L U, partial pivoting (largest modulus, lowest row on ties)   (Eq. 8)
   for (int j = 0; j < r; ++j) {
     if (warp == 0) {
       double mx = -1.0;
@@ -541,8 +552,8 @@ template <typename T> __global__ void __launch_bounds__(NT) k_elim(ElimArgs<T> a
       }
     if (tid == 0) R.piv[j] = p;
     __syncthreads();
-    const T d = LU[j + (size_t)j * r];
-    for (int i = j + 1 + tid; i < r; i += bs) LU[i + (size_t)j * r] = dv(LU[i + (size_t)j * r], d);
+    const T d = dv(from_re<T>(1.0), LU[j + (size_t)j * r]);
+    for (int i = j + 1 + tid; i < r; i += bs) LU[i + (size_t)j * r] = LU[i + (size_t)j * r] * d;
     __syncthreads();
     const int w = r - j - 1;
     for (int e = tid; e < w * w; e += bs) {
@@ -551,7 +562,7 @@ template <typename T> __global__ void __launch_bounds__(NT) k_elim(ElimArgs<T> a
     }
     __syncthreads();
   }
-  // explicit L^{-1} P and U^{-1} for the solve sweeps (one column per thread)
+  // explicit L^{-1} P (for the solve) and U^{-1} (here and in the solve), one column per thread
   for (int j = tid; j < r; j += bs) {
     T* li = R.LiP + (size_t)j * r;    // L^{-1} P e_j
     for (int i = 0; i < r; ++i) li[i] = zero<T>();
@@ -567,7 +578,7 @@ template <typename T> __global__ void __launch_bounds__(NT) k_elim(ElimArgs<T> a
       for (int l = pos; l < i; ++l) x = msb(x, LU[i + (size_t)l * r], li[l]);
       li[i] = x;
     }
-    T* ui = R.Ui + (size_t)j * r;     // U^{-1} e_j
+    T* ui = Ui + (size_t)j * r;       // U^{-1} e_j
     for (int i = j + 1; i < r; ++i) ui[i] = zero<T>();
     for (int i = j; i >= 0; --i) {
       T x = i == j ? from_re<T>(1.0) : zero<T>();
@@ -575,13 +586,14 @@ template <typename T> __global__ void __launch_bounds__(NT) k_elim(ElimArgs<T> a
       ui[i] = dv(x, LU[i + (size_t)i * r]);
     }
   }
-  // E = X_CR U^{-1} (row by row), F = L^{-1} P X_RC (column by column, kept transposed)
+  __syncthreads();
+  // E = X_CR U^{-1} (each row in place, right to left); F = L^{-1} P X_RC (kept transposed)
   for (int i = tid; i < c; i += bs) {
     T* e = R.E + i;
-    for (int j = 0; j < r; ++j) {
-      T x = e[(size_t)j * c];
-      for (int l = 0; l < j; ++l) x = msb(x, e[(size_t)l * c], LU[l + (size_t)j * r]);
-      e[(size_t)j * c] = dv(x, LU[j + (size_t)j * r]);
+    for (int j = r - 1; j >= 0; --j) {
+      T x = zero<T>();
+      for (int l = 0; l <= j; ++l) x = mad(x, e[(size_t)l * c], Ui[l + (size_t)j * r]);
+      e[(size_t)j * c] = x;
     }
     T* f = R.Ft + i;
     for (int j = 0; j < r; ++j) {
@@ -596,6 +608,12 @@ template <typename T> __global__ void __launch_bounds__(NT) k_elim(ElimArgs<T> a
       T x = f[(size_t)j * c];
       for (int l = 0; l < j; ++l) x = msb(x, LU[j + (size_t)l * r], f[(size_t)l * c]);
       f[(size_t)j * c] = x;
+    }
+  }
+  if (onchip) {
+    for (int e = tid; e < r * r; e += bs) {
+      R.LU[e] = LU[e];
+      R.Ui[e] = Ui[e];
     }
   }
   __syncthreads();
@@ -1247,8 +1265,13 @@ rss_status factor_impl(const rss_tree* tree, const rss_params* prm, cudaStream_t
       ea.perm_in = d_perm;
       ea.T_ws = d_Tws;
       ea.err = d_err;
+      // shared memory for T, the LU and U^{-1} of the largest box that fits
+      const size_t want = sizeof(T) * ((size_t)max_k * max_r + 2 * (size_t)max_r * max_r);
+      const size_t ecap = std::min<size_t>(want, 160 * 1024);
+      ea.smem_cap = (int)(ecap / sizeof(T));
+      RSS_CUDA(cudaFuncSetAttribute(k_elim<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ecap));
       evel.start(st);
-      k_elim<T><<<nrec, NT, 0, st>>>(ea);
+      k_elim<T><<<nrec, NT, ecap, st>>>(ea);
       RSS_LAUNCHED();
       evel.stop(st);
       RSS_CUDA(cudaStreamSynchronize(st));

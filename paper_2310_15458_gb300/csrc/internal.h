@@ -8,7 +8,7 @@
 
 #include "common.cuh"
 
-enum : uint32_t { RSS_TAG_TREE = 0x52545245u, RSS_TAG_FACTOR = 0x52464143u };
+enum : uint32_t { RSS_TAG_TREE = 0x52545245u, RSS_TAG_FACTOR = 0x52464143u, RSS_TAG_SERVER = 0x52535256u };
 
 // Quadtree over a uniform grid (Section 2.1).  Tree order: leaf boxes
 // row-major over the leaf box grid, points row-major inside a leaf box.
@@ -110,3 +110,4 @@ template <typename T> rss_status factor_impl(const rss_tree* tree, const rss_par
 template <typename T> rss_status solve_impl(const rss_factorization* f, T* b_dev, int64_t nrhs,
                                             int64_t ldb, cudaStream_t st);
 void free_factor(rss_factorization* f);
+void free_server(rss_server* s);

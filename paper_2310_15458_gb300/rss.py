@@ -60,6 +60,11 @@ def _load():
     lib.rss_factor.argtypes = [vp, ctypes.POINTER(_Params), vp, ctypes.POINTER(vp)]
     lib.rss_solve.argtypes = [vp, vp, i64, i64, vp]
     lib.rss_solve_noalloc.argtypes = [vp, vp, i64, i64, vp]
+    lib.rss_server_create.argtypes = [ctypes.c_size_t, i64, ctypes.POINTER(vp)]
+    lib.rss_server_add.argtypes = [vp, vp, ctypes.POINTER(i32)]
+    lib.rss_server_submit.argtypes = [vp, i32, vp, vp, i64, ctypes.POINTER(i64)]
+    lib.rss_server_wait.argtypes = [vp, i64, ctypes.c_double, ctypes.POINTER(ctypes.c_double)]
+    lib.rss_server_stats.argtypes = [vp, ctypes.c_char_p, ctypes.c_size_t]
     lib.rss_free.argtypes = [vp]
     lib.rss_free.restype = None
     lib.rss_last_error.restype = ctypes.c_char_p
@@ -67,7 +72,8 @@ def _load():
     lib.rss_level_ranks.argtypes = [vp, ctypes.c_int, ctypes.POINTER(i32)]
     lib.rss_box_record.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(i32)] + [vp] * 8
     for name in ("rss_build_tree", "rss_factor", "rss_solve", "rss_solve_noalloc", "rss_info",
-                 "rss_level_ranks", "rss_box_record"):
+                 "rss_level_ranks", "rss_box_record", "rss_server_create", "rss_server_add",
+                 "rss_server_submit", "rss_server_wait", "rss_server_stats"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -171,7 +177,9 @@ def rss_solve(f: Factor, b, stream=None):
         else:
             if b.strides[0] != b.itemsize:
                 raise ValueError("b must be column-major (Fortran order)")
-            nrhs, ldb = b.shape[1], b.strides[1] // b.itemsize
+            nrhs = b.shape[1]
+            # a single column may carry any stride for its (unused) second axis
+            ldb = b.shape[0] if nrhs == 1 else b.strides[1] // b.itemsize
         if b.shape[0] != f.n:
             raise ValueError("b has the wrong number of rows")
         _check(lib.rss_solve(f.handle, b.ctypes.data, nrhs, ldb, _stream_handle(stream)))
@@ -252,3 +260,64 @@ def rss_box_record(f: Factor, side: int, box: int) -> dict:
                               S.ctypes.data, R.ctypes.data, C.ctypes.data, T.ctypes.data,
                               LU.ctypes.data, piv.ctypes.data, E.ctypes.data, F.ctypes.data))
     return dict(k=k, r=r, c=c, n=n, S=S, R=R, C=C, T=T, LU=LU, piv=piv, E=E, F=F)
+
+
+class Server:
+    """Solve server handle (rss_server): resident factorizations, continuous batching."""
+
+    def __init__(self, handle):
+        self._h = handle
+        self._factors = []      # keep registered factorizations alive
+        self._held = {}         # ticket -> (b, x) buffers the worker reads and writes
+
+    @property
+    def handle(self):
+        return self._h
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.rss_free(self._h)
+            self._h = None
+
+
+def rss_server_create(device_bytes: int, max_batch_rhs: int = 256) -> Server:
+    h = ctypes.c_void_p()
+    _check(_load().rss_server_create(device_bytes, max_batch_rhs, ctypes.byref(h)))
+    return Server(h)
+
+
+def rss_server_add(s: Server, f: Factor) -> int:
+    fid = ctypes.c_int32()
+    _check(_load().rss_server_add(s.handle, f.handle, ctypes.byref(fid)))
+    s._factors.append(f)
+    return fid.value
+
+
+def rss_server_submit(s: Server, factor_id: int, b: np.ndarray, x: np.ndarray | None = None) -> int:
+    """Queue A^{-1} b; b is (n,) or (n, nrhs) Fortran-ordered.  Returns a ticket."""
+    b = np.asfortranarray(b)
+    if x is None:
+        x = np.empty_like(b, order="F")
+    nrhs = 1 if b.ndim == 1 else b.shape[1]
+    t = ctypes.c_int64()
+    _check(_load().rss_server_submit(s.handle, factor_id, b.ctypes.data, x.ctypes.data, nrhs,
+                                     ctypes.byref(t)))
+    s._held[t.value] = (b, x)
+    return t.value
+
+
+def rss_server_wait(s: Server, ticket: int, timeout: float = 0.0):
+    """Wait for a ticket; returns (x, latency in seconds)."""
+    lat = ctypes.c_double()
+    try:
+        _check(_load().rss_server_wait(s.handle, ticket, timeout, ctypes.byref(lat)))
+    finally:
+        pass
+    b, x = s._held.pop(ticket)
+    return x, lat.value
+
+
+def rss_server_stats(s: Server) -> dict:
+    buf = ctypes.create_string_buffer(4096)
+    _check(_load().rss_server_stats(s.handle, buf, len(buf)))
+    return json.loads(buf.value.decode())

@@ -1,0 +1,62 @@
+"""Continuous-batching solve server: a result is the same alone and in the mix.
+
+Requests of 1-16 right-hand sides against three resident factorizations (two
+real, one complex) arrive together, so the worker packs several requests into
+each panel; every result must equal rss_solve of that request on its own (the
+sweeps apply the same operations to every column, so the match is exact).
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2310_15458_gb300 as P
+    return P
+
+
+def test_served_results_equal_solo_results(P):
+    specs = [(0, 64, 64, 0.0), (0, 32, 16, 0.0), (1, 32, 16, 25.0)]
+    facs = []
+    for kind, side, leaf, kappa in specs:
+        tree = P.rss_build_tree(W.grid_points(side), leaf)
+        facs.append(P.rss_factor(tree, kind=kind, eps=1e-6, h=1.0 / side, kappa=kappa))
+    srv = P.rss_server_create(1 << 30, 64)
+    ids = [P.rss_server_add(srv, f) for f in facs]
+    rng = np.random.default_rng(3)
+    reqs = []
+    for q in range(48):
+        j = int(rng.integers(len(facs)))
+        nrhs = int(rng.integers(1, 17))
+        b = W.gaussian_rhs(facs[j].n, nrhs, facs[j].is_complex, 500 + q)
+        reqs.append((j, b, P.rss_server_submit(srv, ids[j], b)))
+    for j, b, t in reqs:
+        x, lat = P.rss_server_wait(srv, t, timeout=60.0)
+        solo = np.asfortranarray(b.copy())
+        P.rss_solve(facs[j], solo)
+        assert np.array_equal(x, solo)
+        assert lat > 0
+    st = P.rss_server_stats(srv)
+    assert st["requests"] == 48
+    assert st["batches"] < 48 and st["max_requests_per_batch"] > 1
+    assert st["device_bytes_in_use"] == 0
+
+
+def test_server_refuses_requests_beyond_its_budget(P):
+    tree = P.rss_build_tree(W.grid_points(32), 16)
+    f = P.rss_factor(tree, kind=0, eps=1e-6, h=1 / 32)
+    srv = P.rss_server_create(64 * 1024, 8)           # 64 KiB: 4 columns of n = 1024 at most
+    fid = P.rss_server_add(srv, f)
+    ok = P.rss_server_submit(srv, fid, W.gaussian_rhs(1024, 2, False, 1))
+    big = P.rss_server_submit(srv, fid, W.gaussian_rhs(1024, 8, False, 2))
+    P.rss_server_wait(srv, ok, timeout=60.0)
+    with pytest.raises(P.RSSError, match="ENOMEM"):
+        P.rss_server_wait(srv, big, timeout=60.0)
