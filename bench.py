@@ -270,6 +270,33 @@ def serve_run(P, torch, args):
             "solo_ms_32rhs": [t * 1e3 for t in solo]}
 
 
+# ----------------------------------------------------------------------------- replicas
+def max_over_ranks(torch, ms: float, dist, device) -> float:
+    """Max of the per-rank times (each rank factors its own copy: no data exchange)."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return ms
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def timed_replicas(torch, step, steps: int, warmup: int, dist, device, start, stop) -> float:
+    """warmup untimed steps, a barrier, `steps` timed steps, a barrier; returns the max
+    over ranks of ms per step.  start/stop bracket the timed region (CUDA events on the
+    GPU)."""
+    for _ in range(warmup):
+        step()
+    if dist is not None and dist.is_initialized():
+        dist.barrier()
+    start()
+    for _ in range(steps):
+        step()
+    ms = stop() / steps
+    if dist is not None and dist.is_initialized():
+        dist.barrier()
+    return max_over_ranks(torch, ms, dist, device)
+
+
 # ----------------------------------------------------------------------------- native arm
 def native_arm(args, w):
     import torch
@@ -329,10 +356,7 @@ def native_arm(args, w):
     barrier()
     clk = clocks.stop()
     ms = ev0.elapsed_time(ev1) / args.steps
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(torch, ms, dist, "cuda")
     info = infos[-1]
     relres = fft_relres(torch, side, kind, h, w["kappa"], x.view(n, 1), b_dev.view(n, 1))
 

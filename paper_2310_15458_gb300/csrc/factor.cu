@@ -20,6 +20,7 @@
 #include <climits>
 #include <cstdlib>
 #include <cstring>
+#include <memory>
 #include <vector>
 
 #include <cuda_bf16.h>
@@ -983,6 +984,30 @@ struct Ev {
   }
 };
 
+// Grow-only device buffer (freed with the factorization's host frame).
+struct GrowBuf {
+  void* p = nullptr;
+  size_t cap = 0;
+  bool ensure(size_t bytes) {
+    if (bytes <= cap) return true;
+    if (p) {
+      cudaDeviceSynchronize();   // earlier launches may still read the old buffer
+      cudaFree(p);
+    }
+    p = nullptr;
+    cap = 0;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    cap = bytes;
+    return true;
+  }
+  ~GrowBuf() {
+    if (p) cudaFree(p);
+  }
+};
+
 struct Timer {
   std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
   double ms() const {
@@ -1032,6 +1057,8 @@ rss_status factor_impl(const rss_tree* tree, const rss_params* prm, cudaStream_t
   RSS_LAUNCHED();
   f->launches += 1;
 
+  // workspaces reused across colour classes and levels
+  GrowBuf gb_cls, gb_k, gb_perm, gb_clsidx, gb_Tws, gb_Y, gb_oz;
   // leaf level
   size_t transient = 0;
   HostLevel<T> cur;
@@ -1086,18 +1113,22 @@ rss_status factor_impl(const rss_tree* tree, const rss_params* prm, cudaStream_t
         for (int bx = col % 3; bx < g; bx += 3) cls.push_back(by * g + bx);
     }
     coff[9] = (int)cls.size();
-    int* d_cls = nullptr;
-    RSS_CUDA(cudaMalloc(&d_cls, sizeof(int) * cls.size()));
-    RSS_CUDA(cudaMemcpyAsync(d_cls, cls.data(), sizeof(int) * cls.size(), cudaMemcpyHostToDevice, st));
     int maxcls = 0;
     for (int col = 0; col < 9; ++col) maxcls = std::max(maxcls, coff[col + 1] - coff[col]);
-    int *d_k = nullptr, *d_perm = nullptr, *d_clsidx = nullptr;
-    T* d_Tws = nullptr;
-    RSS_CUDA(cudaMalloc(&d_k, sizeof(int) * maxcls));
-    RSS_CUDA(cudaMalloc(&d_perm, sizeof(int) * (size_t)maxcls * nmax));
-    RSS_CUDA(cudaMalloc(&d_clsidx, sizeof(int) * maxcls));
-    RSS_CUDA(cudaMalloc(&d_Tws, sizeof(T) * (size_t)maxcls * nn));
+    if (!gb_cls.ensure(sizeof(int) * cls.size()) || !gb_k.ensure(sizeof(int) * maxcls) ||
+        !gb_perm.ensure(sizeof(int) * (size_t)maxcls * nmax) || !gb_clsidx.ensure(sizeof(int) * maxcls) ||
+        !gb_Tws.ensure(sizeof(T) * (size_t)maxcls * nn)) {
+      rss_set_error("rss_factor: device workspace allocation failed");
+      return RSS_ENOMEM;
+    }
+    int* d_cls = static_cast<int*>(gb_cls.p);
+    int* d_k = static_cast<int*>(gb_k.p);
+    int* d_perm = static_cast<int*>(gb_perm.p);
+    int* d_clsidx = static_cast<int*>(gb_clsidx.p);
+    T* d_Tws = static_cast<T*>(gb_Tws.p);
+    RSS_CUDA(cudaMemcpyAsync(d_cls, cls.data(), sizeof(int) * cls.size(), cudaMemcpyHostToDevice, st));
     std::vector<int> hk(maxcls);
+    std::vector<std::pair<int, std::unique_ptr<Ev>>> evs;   // phase (0 id, 1 elim, 2 schur), events
 
     for (int col = 0; col < 9; ++col) {
       const int nb = coff[col + 1] - coff[col];
@@ -1125,19 +1156,21 @@ rss_status factor_impl(const rss_tree* tree, const rss_params* prm, cudaStream_t
       const int cap = (int)std::max<size_t>(1, std::min<size_t>(nb, ybudget / slot));
       const int nchunks = (nb + cap - 1) / cap;
       const int chunk = (nb + nchunks - 1) / nchunks;   // balanced chunks
-      T* d_Y = nullptr;
-      RSS_CUDA(cudaMalloc(&d_Y, slot * chunk));
+      if (!gb_Y.ensure(slot * chunk)) {
+        rss_set_error("rss_factor: device workspace allocation failed");
+        return RSS_ENOMEM;
+      }
+      T* d_Y = static_cast<T*>(gb_Y.p);
       const size_t smem_id = sizeof(T) * ((size_t)ldY + 2 * nmax) + (size_t)nmax * (3 * sizeof(double) + 2 * sizeof(int));
       if (smem_id > 220 * 1024) {
-        cudaFree(d_Y);
         rss_set_error("rss_factor: proxy stack of a box too tall for the on-chip reflector buffer");
         return RSS_EINVAL;
       }
       RSS_CUDA(cudaFuncSetAttribute(k_id<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_id));
       f->peak_transient = std::max(f->peak_transient, transient + slot * chunk);
       Timer tid_;
-      Ev evid;
-      evid.start(st);
+      evs.emplace_back(0, std::make_unique<Ev>());
+      evs.back().second->start(st);
       for (int c0 = 0; c0 < nb; c0 += chunk) {
         IdArgs<T> a;
         a.L = cur.d;
@@ -1162,12 +1195,10 @@ rss_status factor_impl(const rss_tree* tree, const rss_params* prm, cudaStream_t
         f->launches += 1;
         f->n_id += 1;
       }
-      evid.stop(st);
+      evs.back().second->stop(st);
       RSS_CUDA(cudaMemcpyAsync(hk.data(), d_k, sizeof(int) * nb, cudaMemcpyDeviceToHost, st));
       RSS_CUDA(cudaStreamSynchronize(st));
-      cudaFree(d_Y);
       f->t_id += tid_.ms();
-      f->g_id += evid.ms();
       const double cf = sizeof(T) == sizeof(double) ? 1.0 : 4.0;
       for (int q = 0; q < nb; ++q) {   // CPQR: norms, per step v^H Y and the k-column corrections, T
         const double m = mrows[q], n = cur.n[boxes[q]], k = hk[q];
@@ -1227,7 +1258,6 @@ rss_status factor_impl(const rss_tree* tree, const rss_params* prm, cudaStream_t
       // tensor-core Schur update: real factors with r <= 96 (the slices of a
       // 64-row tile of E and of F^T must fit in shared memory)
       const bool oz = sizeof(T) == sizeof(double) && prm->schur_path == 0 && max_r <= 96;
-      void* d_oz = nullptr;
       int kp_max = 0;
       if (oz) {
         size_t bytes = 0;
@@ -1235,8 +1265,11 @@ rss_status factor_impl(const rss_tree* tree, const rss_params* prm, cudaStream_t
           const int kp = (R.r + 15) & ~15;
           bytes += 2 * ((size_t)R.c * OZ_S * kp * sizeof(uint16_t) + 256) + 2 * ((size_t)R.c * sizeof(int) + 256);
         }
-        RSS_CUDA(cudaMalloc(&d_oz, bytes));
-        char* p = static_cast<char*>(d_oz);
+        if (!gb_oz.ensure(bytes)) {
+          rss_set_error("rss_factor: device workspace allocation failed");
+          return RSS_ENOMEM;
+        }
+        char* p = static_cast<char*>(gb_oz.p);
         auto take = [&](size_t b) {
           char* q = p;
           p += (b + 255) & ~size_t(255);
@@ -1256,8 +1289,6 @@ rss_status factor_impl(const rss_tree* tree, const rss_params* prm, cudaStream_t
       if (!d_recs) { rss_set_error("rss_factor: device arena allocation failed"); return RSS_ENOMEM; }
       RSS_CUDA(cudaMemcpyAsync(d_recs, recs.data(), sizeof(BoxRec<T>) * nrec, cudaMemcpyHostToDevice, st));
       RSS_CUDA(cudaMemcpyAsync(d_clsidx, clsidx.data(), sizeof(int) * nrec, cudaMemcpyHostToDevice, st));
-      Timer te;
-      Ev evel, evsc;
       ElimArgs<T> ea;
       ea.L = cur.d;
       ea.recs = d_recs;
@@ -1270,15 +1301,14 @@ rss_status factor_impl(const rss_tree* tree, const rss_params* prm, cudaStream_t
       const size_t ecap = std::min<size_t>(want, 160 * 1024);
       ea.smem_cap = (int)(ecap / sizeof(T));
       RSS_CUDA(cudaFuncSetAttribute(k_elim<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ecap));
-      evel.start(st);
+      evs.emplace_back(1, std::make_unique<Ev>());
+      evs.back().second->start(st);
       k_elim<T><<<nrec, NT, ecap, st>>>(ea);
       RSS_LAUNCHED();
-      evel.stop(st);
-      RSS_CUDA(cudaStreamSynchronize(st));
-      f->t_elim += te.ms();
-      Timer ts;
+      evs.back().second->stop(st);
       const int ntile = (max_c + 63) / 64;
-      evsc.start(st);
+      evs.emplace_back(2, std::make_unique<Ev>());
+      evs.back().second->start(st);
       if (oz) {
         if constexpr (sizeof(T) == sizeof(double)) {
           const size_t smem = 2 * 64 * (size_t)(OZ_S * kp_max + 8) * sizeof(uint16_t);
@@ -1289,13 +1319,8 @@ rss_status factor_impl(const rss_tree* tree, const rss_params* prm, cudaStream_t
         k_schur<T><<<dim3(ntile * ntile, nrec), NT, 0, st>>>(cur.d, d_recs);
       }
       RSS_LAUNCHED();
-      evsc.stop(st);
-      RSS_CUDA(cudaStreamSynchronize(st));
-      if (d_oz) cudaFree(d_oz);
+      evs.back().second->stop(st);
       for (BoxRec<T>& R : recs) R.Esl = R.Fsl = nullptr, R.Eexp = R.Fexp = nullptr;
-      f->t_schur += ts.ms();
-      f->g_elim += evel.ms();
-      f->g_schur += evsc.ms();
       f->launches += 2;
       f->n_elim += 1;
       f->n_schur += 1;
@@ -1305,7 +1330,12 @@ rss_status factor_impl(const rss_tree* tree, const rss_params* prm, cudaStream_t
       f->rec_host.push_back(hcopy);
       f->batches.push_back(Batch{g, col, nrec, d_recs, max_k, max_r, max_c});
     }
-    cudaFree(d_cls); cudaFree(d_k); cudaFree(d_perm); cudaFree(d_clsidx); cudaFree(d_Tws);
+    RSS_CUDA(cudaStreamSynchronize(st));
+    for (auto& pe : evs) {
+      const double ms = pe.second->ms();
+      (pe.first == 0 ? f->g_id : pe.first == 1 ? f->g_elim : f->g_schur) += ms;
+      (pe.first == 1 ? f->t_elim : pe.first == 2 ? f->t_schur : f->t_gen) += pe.first ? ms : 0.0;
+    }
     int herr = 0;
     RSS_CUDA(cudaMemcpy(&herr, d_err, sizeof(int), cudaMemcpyDeviceToHost));
     if (herr) { rss_set_error("rss_factor: zero pivot in the LU of a redundant block"); return RSS_ENUMERIC; }
