@@ -447,10 +447,59 @@ template <typename T> struct ElimArgs {
   const int* perm_in;
   const T* T_ws;
   int* err;
-  int smem_cap;             // k*r + 2 r^2 scalars fit in dynamic shared memory
+  int smem_cap;             // scalars of dynamic shared memory available
 };
 
-template <typename T> __global__ void __launch_bounds__(NT, 4) k_elim(ElimArgs<T> a) {
+constexpr int EP = 64;      // rows of C per panel
+
+// Register-blocked panel product on shared memory: out(i, j) = init(i, j) +
+// sum_l A[l][i] * B(l, j) for the EP x r panel; thread (tx, ty) owns rows
+// tx + 16 a (a < 4) and columns ty + 16 b (b < NB).  A is [l][EP] in shared
+// memory, B(l, j) is read through bfun.  TRI: B is upper triangular (B(l, j) = 0
+// for l > j), so each thread stops at its last column.
+template <typename T, int NB, bool TRI, typename BF, typename IF, typename OF>
+__device__ __forceinline__ void panel_gemm(const T* __restrict__ A, int nl, int rows, int r, BF bfun, IF init,
+                                           OF out) {
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  T acc[4][NB];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+      const int i = tx + 16 * a, j = ty + 16 * b;
+      acc[a][b] = (i < rows && j < r) ? init(i, j) : zero<T>();
+    }
+  const int lend = TRI ? min(nl, ty + 16 * (NB - 1) + 1) : nl;
+  for (int l = 0; l < lend; ++l) {
+    T av[4], bv[NB];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) av[a] = A[l * EP + tx + 16 * a];
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+      const int j = ty + 16 * b;
+      bv[b] = (j < r && (!TRI || l <= j)) ? bfun(l, j) : zero<T>();
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < NB; ++b) acc[a][b] = mad(acc[a][b], av[a], bv[b]);
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+      const int i = tx + 16 * a, j = ty + 16 * b;
+      if (i < rows && j < r) out(i, j, acc[a][b]);
+    }
+}
+
+// ------------------------------------------------------------------ sparsify + LU (Eqs. 7, 8)
+// k_elim_lu (one CTA per box): C map, X_SR, X_RR, P X_RR = L U, U^{-1}, L^{-1}
+// and L^{-1} P.  k_elim_panels (one CTA per 64-row panel of C): X_CR, X_RC and
+// E = X_CR U^{-1}, F = L^{-1} P X_RC (kept as F^T), from shared-memory panels.
+// Boxes too large for the panel kernel's shared memory get E and F here, row by
+// row from global memory.
+template <typename T> __global__ void __launch_bounds__(NT, 4) k_elim_lu(ElimArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const LevelDev<T>& L = a.L;
   const BoxRec<T> R = a.recs[blockIdx.x];
@@ -459,13 +508,11 @@ template <typename T> __global__ void __launch_bounds__(NT, 4) k_elim(ElimArgs<T
   const int* perm = a.perm_in + (size_t)a.cls_idx[blockIdx.x] * nmax;
   const T* Tw = a.T_ws + (size_t)a.cls_idx[blockIdx.x] * nn;
   const int tid = threadIdx.x, bs = blockDim.x, lane = tid & 31, warp = tid >> 5;
-  // on-chip copies of T (k x r), the LU and U^{-1} (r x r) when they fit
   const bool onchip = k * r + 2 * r * r <= a.smem_cap;
   T* Ts = onchip ? reinterpret_cast<T*>(smraw) : R.Tm;
   T* LU = onchip ? Ts + (size_t)k * r : R.LU;
-  T* Ui = onchip ? LU + (size_t)r * r : R.Ui;
-  __shared__ int nb[9], coff[10], s_piv, s_zero;
-  __shared__ int ord[9];
+  T* Wb = onchip ? LU + (size_t)r * r : nullptr;   // scratch for building the inverses
+  __shared__ int nb[9], coff[10], s_piv, s_zero, ord[9];
   if (tid == 0) {
     const int o9[9] = {4, 0, 1, 2, 3, 5, 6, 7, 8};
     int off = 0;
@@ -494,27 +541,16 @@ template <typename T> __global__ void __launch_bounds__(NT, 4) k_elim(ElimArgs<T
     if (onchip) Ts[e] = t;
   }
   __syncthreads();
-  // X_CR -> E (c x r), X_RC^T -> Ft (c x r)   (Eq. 7)
-  for (long long e = tid; e < (long long)c * r; e += bs) {
-    const int i = (int)(e % c), j = (int)(e / c);
-    const int cm = R.cmap[i], s = cm >> 16, pos = cm & 0xffff, u = nb[s];
-    const T* Aub = L.blk + ((size_t)u * 25 + off_index(u, B, g)) * nn;   // rows of u, cols of B
-    const T* Abu = L.blk + ((size_t)B * 25 + off_index(B, u, g)) * nn;   // rows of B, cols of u
-    const int rj = perm[k + j];
-    T x = Aub[(size_t)rj * nmax + pos];
-    T y = Abu[(size_t)pos * nmax + rj];
-    const T* tj = Ts + (size_t)j * k;
-    for (int q = 0; q < k; ++q) {
-      const T t = tj[q];
-      x = msb(x, Aub[(size_t)perm[q] * nmax + pos], t);
-      y = msbc(y, t, Abu[(size_t)pos * nmax + perm[q]]);
-    }
-    R.E[i + (size_t)j * c] = x;
-    R.Ft[i + (size_t)j * c] = y;
+  const T* Abb = L.blk + ((size_t)B * 25 + 12) * nn;
+  // X_SR = A_SR - A_SS T into E's first k rows (the rows of S in C)
+  for (int e = tid; e < k * r; e += bs) {
+    const int si = e % k, j = e / k;
+    T x = Abb[(size_t)perm[k + j] * nmax + perm[si]];
+    for (int q = 0; q < k; ++q) x = msb(x, Abb[(size_t)perm[q] * nmax + perm[si]], Ts[q + (size_t)j * k]);
+    R.E[si + (size_t)j * c] = x;
   }
   __syncthreads();
-  // X_RR = A_RR - A_RS T - T^* X_SR  (X_SR = first k rows of X_CR)
-  const T* Abb = L.blk + ((size_t)B * 25 + 12) * nn;
+  // X_RR = A_RR - A_RS T - T^* X_SR
   for (int e = tid; e < r * r; e += bs) {
     const int ai = e % r, bj = e / r;
     T x = Abb[(size_t)perm[k + bj] * nmax + perm[k + ai]];
@@ -563,73 +599,192 @@ template <typename T> __global__ void __launch_bounds__(NT, 4) k_elim(ElimArgs<T
     }
     __syncthreads();
   }
-  // explicit L^{-1} P (for the solve) and U^{-1} (here and in the solve), one column per thread
-  for (int j = tid; j < r; j += bs) {
-    T* li = R.LiP + (size_t)j * r;    // L^{-1} P e_j
-    for (int i = 0; i < r; ++i) li[i] = zero<T>();
-    int pos = j;                      // where e_j's 1 lands after the row exchanges
-    for (int i = 0; i < r; ++i) {
-      const int p = R.piv[i];
-      if (pos == i) pos = p;
-      else if (pos == p) pos = i;
-    }
-    li[pos] = from_re<T>(1.0);
-    for (int i = pos + 1; i < r; ++i) {
-      T x = li[i];
-      for (int l = pos; l < i; ++l) x = msb(x, LU[i + (size_t)l * r], li[l]);
-      li[i] = x;
-    }
-    T* ui = Ui + (size_t)j * r;       // U^{-1} e_j
-    for (int i = j + 1; i < r; ++i) ui[i] = zero<T>();
-    for (int i = j; i >= 0; --i) {
-      T x = i == j ? from_re<T>(1.0) : zero<T>();
-      for (int l = i + 1; l <= j; ++l) x = msb(x, LU[i + (size_t)l * r], ui[l]);
-      ui[i] = dv(x, LU[i + (size_t)i * r]);
-    }
-  }
-  __syncthreads();
-  // E = X_CR U^{-1} (each row in place, right to left); F = L^{-1} P X_RC (kept transposed)
-  for (int i = tid; i < c; i += bs) {
-    T* e = R.E + i;
-    for (int j = r - 1; j >= 0; --j) {
-      T x = zero<T>();
-      for (int l = 0; l <= j; ++l) x = mad(x, e[(size_t)l * c], Ui[l + (size_t)j * r]);
-      e[(size_t)j * c] = x;
-    }
-    T* f = R.Ft + i;
-    for (int j = 0; j < r; ++j) {
-      const int p = R.piv[j];
-      if (p != j) {
-        const T t = f[(size_t)j * c];
-        f[(size_t)j * c] = f[(size_t)p * c];
-        f[(size_t)p * c] = t;
+  // U^{-1}, L^{-1} and L^{-1} P, one column per thread (built in shared memory
+  // when it fits, then copied out)
+  for (int which = 0; which < 3; ++which) {
+    T* dst = which == 0 ? R.Ui : which == 1 ? R.Li : R.LiP;
+    T* W = onchip ? Wb : dst;
+    for (int j = tid; j < r; j += bs) {
+      T* w = W + (size_t)j * r;
+      if (which == 0) {               // U^{-1} e_j
+        for (int i = j + 1; i < r; ++i) w[i] = zero<T>();
+        for (int i = j; i >= 0; --i) {
+          T x = i == j ? from_re<T>(1.0) : zero<T>();
+          for (int l = i + 1; l <= j; ++l) x = msb(x, LU[i + (size_t)l * r], w[l]);
+          w[i] = dv(x, LU[i + (size_t)i * r]);
+        }
+      } else {
+        int pos = j;                  // L^{-1} e_j, or L^{-1} P e_j: e_j moved by the exchanges
+        if (which == 2)
+          for (int i = 0; i < r; ++i) {
+            const int p = R.piv[i];
+            if (pos == i) pos = p;
+            else if (pos == p) pos = i;
+          }
+        for (int i = 0; i < pos; ++i) w[i] = zero<T>();
+        w[pos] = from_re<T>(1.0);
+        for (int i = pos + 1; i < r; ++i) {
+          T x = zero<T>();
+          for (int l = pos; l < i; ++l) x = msb(x, LU[i + (size_t)l * r], w[l]);
+          w[i] = x;
+        }
       }
     }
-    for (int j = 1; j < r; ++j) {
-      T x = f[(size_t)j * c];
-      for (int l = 0; l < j; ++l) x = msb(x, LU[j + (size_t)l * r], f[(size_t)l * c]);
-      f[(size_t)j * c] = x;
+    if (onchip) {
+      __syncthreads();
+      for (int e = tid; e < r * r; e += bs) dst[e] = Wb[e];
+      __syncthreads();
     }
   }
-  if (onchip) {
-    for (int e = tid; e < r * r; e += bs) {
-      R.LU[e] = LU[e];
-      R.Ui[e] = Ui[e];
-    }
-  }
+  if (onchip)
+    for (int e = tid; e < r * r; e += bs) R.LU[e] = LU[e];
   __syncthreads();
-  if constexpr (sizeof(T) == sizeof(double)) {
-    if (R.Esl != nullptr)   // digit slices of E and F^T for the tensor-core Schur update
-      for (int i = tid; i < 2 * c; i += bs) {
-        const bool isE = i < c;
-        const int row = isE ? i : i - c;
-        oz_split_row((isE ? R.E : R.Ft) + row, c, r, R.kp,
-                     (isE ? R.Esl : R.Fsl) + (size_t)row * OZ_S * R.kp, (isE ? R.Eexp : R.Fexp) + row);
+  if (!R.panels) {
+    // E and F^T row by row from global memory
+    for (long long e = tid; e < (long long)c * r; e += bs) {
+      const int i = (int)(e % c), j = (int)(e / c);
+      const int cm = R.cmap[i], s = cm >> 16, pos = cm & 0xffff, u = nb[s];
+      const T* Aub = L.blk + ((size_t)u * 25 + off_index(u, B, g)) * nn;
+      const T* Abu = L.blk + ((size_t)B * 25 + off_index(B, u, g)) * nn;
+      const int rj = perm[k + j];
+      T x = Aub[(size_t)rj * nmax + pos];
+      T y = Abu[(size_t)pos * nmax + rj];
+      for (int q = 0; q < k; ++q) {
+        const T t = Ts[q + (size_t)j * k];
+        x = msb(x, Aub[(size_t)perm[q] * nmax + pos], t);
+        y = msbc(y, t, Abu[(size_t)pos * nmax + perm[q]]);
       }
+      R.E[i + (size_t)j * c] = x;
+      R.Ft[i + (size_t)j * c] = y;
+    }
+    __syncthreads();
+    for (int i = tid; i < c; i += bs) {
+      T* e = R.E + i;
+      for (int j = r - 1; j >= 0; --j) {
+        T x = zero<T>();
+        for (int l = 0; l <= j; ++l) x = mad(x, e[(size_t)l * c], R.Ui[l + (size_t)j * r]);
+        e[(size_t)j * c] = x;
+      }
+      T* f = R.Ft + i;
+      for (int j = 0; j < r; ++j) {
+        const int p = R.piv[j];
+        if (p != j) {
+          const T t = f[(size_t)j * c];
+          f[(size_t)j * c] = f[(size_t)p * c];
+          f[(size_t)p * c] = t;
+        }
+      }
+      for (int j = 1; j < r; ++j) {
+        T x = f[(size_t)j * c];
+        for (int l = 0; l < j; ++l) x = msb(x, R.LU[j + (size_t)l * r], f[(size_t)l * c]);
+        f[(size_t)j * c] = x;
+      }
+    }
+    __syncthreads();
+    if constexpr (sizeof(T) == sizeof(double)) {
+      if (R.Esl != nullptr)
+        for (int i = tid; i < 2 * c; i += bs) {
+          const bool isE = i < c;
+          const int row = isE ? i : i - c;
+          oz_split_row((isE ? R.E : R.Ft) + row, c, r, R.kp,
+                       (isE ? R.Esl : R.Fsl) + (size_t)row * OZ_S * R.kp, (isE ? R.Eexp : R.Fexp) + row);
+        }
+    }
   }
   // B keeps only its skeleton
   for (int q = tid; q < k; q += bs) L.act[B * nmax + q] = perm[q];
   if (tid == 0) L.nact[B] = k;
+}
+
+template <typename T, int NB>
+__device__ void elim_panel_body(const ElimArgs<T>& a, const BoxRec<T>& R, unsigned char* smraw, int p0, int rows) {
+  const LevelDev<T>& L = a.L;
+  const int nmax = L.nmax, g = L.g, B = R.box, k = R.k, r = R.r, c = R.c, n = k + r;
+  const size_t nn = (size_t)nmax * nmax;
+  const int* perm = a.perm_in + (size_t)a.cls_idx[blockIdx.y] * nmax;
+  const int tid = threadIdx.x, bs = blockDim.x;
+  T* Ts = reinterpret_cast<T*>(smraw);     // k x r
+  T* Ms = Ts + (size_t)k * r;              // r x r: U^{-1}, then L^{-1}
+  T* As = Ms + (size_t)r * r;              // n x EP
+  T* Xs = As + (size_t)n * EP;             // r x EP
+  int* sinv = reinterpret_cast<int*>(Xs + (size_t)r * EP);
+  for (int e = tid; e < k * r; e += bs) Ts[e] = R.Tm[e];
+  for (int e = tid; e < r * r; e += bs) Ms[e] = R.Ui[e];
+  for (int e = tid; e < rows * n; e += bs) {   // rows of A(u, B), columns of B in pivot order
+    const int ii = e % rows, col = e / rows;
+    const int cm = R.cmap[p0 + ii], s = cm >> 16, pos = cm & 0xffff;
+    const int u = nbr_box(B, g, s % 3 - 1, s / 3 - 1);
+    As[col * EP + ii] = L.blk[((size_t)u * 25 + off_index(u, B, g)) * nn + (size_t)perm[col] * nmax + pos];
+  }
+  if (tid == 0) {   // P_R v = v[sigma]: the row exchanges applied to the identity
+    int* sig = sinv + r;
+    for (int i = 0; i < r; ++i) sig[i] = i;
+    for (int i = 0; i < r; ++i) {
+      const int p = R.piv[i], t = sig[i];
+      sig[i] = sig[p];
+      sig[p] = t;
+    }
+    for (int i = 0; i < r; ++i) sinv[sig[i]] = i;
+  }
+  __syncthreads();
+  // X_CR = A_CR - A_CS T, then E = X_CR U^{-1}
+  panel_gemm<T, NB, false>(As, k, rows, r, [&](int q, int j) { return -Ts[q + (size_t)j * k]; },
+                           [&](int i, int j) { return As[(k + j) * EP + i]; },
+                           [&](int i, int j, T v) { Xs[j * EP + i] = v; });
+  __syncthreads();
+  panel_gemm<T, NB, true>(Xs, r, rows, r, [&](int l, int j) { return Ms[l + (size_t)j * r]; },
+                          [&](int, int) { return zero<T>(); },
+                          [&](int i, int j, T v) { R.E[p0 + i + (size_t)j * c] = v; });
+  __syncthreads();
+  for (int e = tid; e < r * r; e += bs) Ms[e] = R.Li[e];
+  for (int e = tid; e < rows * n; e += bs) {   // columns of A(B, u), rows of B in pivot order
+    const int row = e % n, ii = e / n;
+    const int cm = R.cmap[p0 + ii], s = cm >> 16, pos = cm & 0xffff;
+    const int u = nbr_box(B, g, s % 3 - 1, s / 3 - 1);
+    As[row * EP + ii] = L.blk[((size_t)B * 25 + off_index(B, u, g)) * nn + (size_t)pos * nmax + perm[row]];
+  }
+  __syncthreads();
+  // X_RC^T = A_RC^T - A_SC^T conj(T), columns placed in the order of P_R
+  panel_gemm<T, NB, false>(As, k, rows, r, [&](int q, int j) { return -cj(Ts[q + (size_t)j * k]); },
+                           [&](int i, int j) { return As[(k + j) * EP + i]; },
+                           [&](int i, int j, T v) { Xs[sinv[j] * EP + i] = v; });
+  __syncthreads();
+  // F^T = (P_R X_RC)^T (L_R^{-1})^T, (L^{-1})^T upper triangular
+  panel_gemm<T, NB, true>(Xs, r, rows, r, [&](int l, int j) { return Ms[j + (size_t)l * r]; },
+                          [&](int, int) { return zero<T>(); },
+                          [&](int i, int j, T v) { R.Ft[p0 + i + (size_t)j * c] = v; });
+  __syncthreads();
+  if constexpr (sizeof(T) == sizeof(double)) {
+    if (R.Esl != nullptr)   // digit slices of this panel's rows of E and F^T
+      for (int e = tid; e < 2 * rows; e += bs) {
+        const bool isE = e < rows;
+        const int row = p0 + (isE ? e : e - rows);
+        oz_split_row((isE ? R.E : R.Ft) + row, c, r, R.kp,
+                     (isE ? R.Esl : R.Fsl) + (size_t)row * OZ_S * R.kp, (isE ? R.Eexp : R.Fexp) + row);
+      }
+  }
+}
+
+template <typename T> size_t panel_smem_bytes(int k, int r) {
+  return sizeof(T) * ((size_t)k * r + (size_t)r * r + (size_t)(k + r) * EP + (size_t)r * EP) +
+         2 * sizeof(int) * (size_t)r;
+}
+
+template <typename T> __global__ void __launch_bounds__(NT, 2) k_elim_panels(ElimArgs<T> a) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const BoxRec<T> R = a.recs[blockIdx.y];
+  if (!R.panels) return;
+  const int p0 = blockIdx.x * EP;
+  if (p0 >= R.c) return;
+  const int rows = min(EP, R.c - p0);
+  switch ((R.r + 15) / 16) {
+    case 1: elim_panel_body<T, 1>(a, R, smraw, p0, rows); break;
+    case 2: elim_panel_body<T, 2>(a, R, smraw, p0, rows); break;
+    case 3: elim_panel_body<T, 3>(a, R, smraw, p0, rows); break;
+    case 4: elim_panel_body<T, 4>(a, R, smraw, p0, rows); break;
+    case 5: elim_panel_body<T, 5>(a, R, smraw, p0, rows); break;
+    default: elim_panel_body<T, 6>(a, R, smraw, p0, rows); break;
+  }
 }
 
 // ------------------------------------------------------------------ Schur update A_CC -= E F
@@ -1212,6 +1367,7 @@ rss_status factor_impl(const rss_tree* tree, const rss_params* prm, cudaStream_t
       std::vector<BoxRec<T>> recs;
       std::vector<int> clsidx;
       int max_k = 0, max_r = 0, max_c = 0;
+      size_t pan_max = 0;
       for (int q = 0; q < nb; ++q) {
         const int B = boxes[q], bx = B % g, by = B / g;
         const int k = hk[q], n = cur.n[B], r = n - k;
@@ -1232,12 +1388,19 @@ rss_status factor_impl(const rss_tree* tree, const rss_params* prm, cudaStream_t
         R.piv = static_cast<int*>(f->arena.get(sizeof(int) * r));
         R.LiP = static_cast<T*>(f->arena.get(sizeof(T) * (size_t)r * r));
         R.Ui = static_cast<T*>(f->arena.get(sizeof(T) * (size_t)r * r));
+        R.Li = static_cast<T*>(f->arena.get(sizeof(T) * (size_t)r * r));
+        {
+          const size_t pb = panel_smem_bytes<T>(k, r);
+          R.panels = (r <= 96 && pb <= 200 * 1024) ? 1 : 0;
+          if (R.panels) pan_max = std::max(pan_max, pb);
+        }
         R.E = static_cast<T*>(f->arena.get(sizeof(T) * (size_t)c * r));
         R.Ft = static_cast<T*>(f->arena.get(sizeof(T) * (size_t)c * r));
         R.idxR = static_cast<int*>(f->arena.get(sizeof(int) * r));
         R.idxC = static_cast<int*>(f->arena.get(sizeof(int) * c));
         R.cmap = static_cast<int*>(f->arena.get(sizeof(int) * c));
-        if (!R.Tm || !R.LU || !R.piv || !R.LiP || !R.Ui || !R.E || !R.Ft || !R.idxR || !R.idxC || !R.cmap) {
+        if (!R.Tm || !R.LU || !R.piv || !R.LiP || !R.Ui || !R.Li || !R.E || !R.Ft || !R.idxR || !R.idxC ||
+            !R.cmap) {
           rss_set_error("rss_factor: device arena allocation failed");
           return RSS_ENOMEM;
         }
@@ -1296,15 +1459,21 @@ rss_status factor_impl(const rss_tree* tree, const rss_params* prm, cudaStream_t
       ea.perm_in = d_perm;
       ea.T_ws = d_Tws;
       ea.err = d_err;
-      // shared memory for T, the LU and U^{-1} of the largest box that fits
+      // shared memory of the per-box kernel: T and the LU of the largest box that fits
       const size_t want = sizeof(T) * ((size_t)max_k * max_r + 2 * (size_t)max_r * max_r);
       const size_t ecap = std::min<size_t>(want, 160 * 1024);
       ea.smem_cap = (int)(ecap / sizeof(T));
-      RSS_CUDA(cudaFuncSetAttribute(k_elim<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ecap));
+      RSS_CUDA(cudaFuncSetAttribute(k_elim_lu<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ecap));
       evs.emplace_back(1, std::make_unique<Ev>());
       evs.back().second->start(st);
-      k_elim<T><<<nrec, NT, ecap, st>>>(ea);
+      k_elim_lu<T><<<nrec, NT, ecap, st>>>(ea);
       RSS_LAUNCHED();
+      if (pan_max > 0) {
+        RSS_CUDA(cudaFuncSetAttribute(k_elim_panels<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pan_max));
+        k_elim_panels<T><<<dim3((max_c + EP - 1) / EP, nrec), NT, pan_max, st>>>(ea);
+        RSS_LAUNCHED();
+        f->launches += 1;
+      }
       evs.back().second->stop(st);
       const int ntile = (max_c + 63) / 64;
       evs.emplace_back(2, std::make_unique<Ev>());

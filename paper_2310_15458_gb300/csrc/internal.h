@@ -33,6 +33,8 @@ template <typename T> struct BoxRec {
   int* piv;     // r getrf pivots (0-based)
   T* LiP;       // r x r, ld r: L_R^{-1} P_R (the solve applies it as one product)
   T* Ui;        // r x r, ld r: U_R^{-1}
+  T* Li;        // r x r, ld r: L_R^{-1} (unit lower), factor time only
+  int panels;   // 1: E and F^T are formed by the panel kernel
   T* E;         // c x r, ld c:  X_CR U_R^{-1}
   T* Ft;        // c x r, ld c:  (L_R^{-1} P_R X_RC)^T (plain transpose)
   int* idxR;    // r tree indices of R
