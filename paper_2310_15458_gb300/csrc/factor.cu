@@ -855,9 +855,11 @@ template <typename T> __global__ void __launch_bounds__(NT) k_schur(LevelDev<T> 
 // (E F)_ij = 2^(e_i + f_j) sum_u 2^(-7(u+2)) G_u with G_u = sum_{p+q=u} D_p D'_q^T:
 // each G_u is a sum of integer products below 2^24, so bf16 MMAs with FP32
 // accumulation compute it exactly; groups u <= OZ_S-1 are kept (the rest lie
-// below 2^-56 of the row/column scale, the same order as an FP64 product's
-// rounding).  The groups are recombined exactly in two int64 accumulators and
-// rounded once to FP64.  64 x 64 tile per CTA, 8 warps of 32 x 16.
+// below 2^-56 of the row/column scale, the order of an FP64 product's rounding).
+// The groups are gathered in one int64 W = sum_u G_u 2^(39-7u) (the last two by
+// rounding right shifts, an error below 2^-53 of the scale), so
+// (E F)_ij = W 2^(e_i + f_j - 53): one conversion and one scaling per entry.
+// 64 x 64 tile per CTA, 8 warps of 32 x 16, fragments loaded with ldmatrix.
 __device__ __forceinline__ void mma_bf16(float* c, const uint32_t* a, const uint32_t* b) {
   asm volatile(
       "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
@@ -866,13 +868,25 @@ __device__ __forceinline__ void mma_bf16(float* c, const uint32_t* a, const uint
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
 }
 
+__device__ __forceinline__ void ldsm_x4(uint32_t* d, const void* smem_row) {
+  const unsigned addr = (unsigned)__cvta_generic_to_shared(smem_row);
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(d[0]), "=r"(d[1]), "=r"(d[2]), "=r"(d[3])
+               : "r"(addr));
+}
+
+// 2^e as a double for the normal range, from its bit pattern
+__device__ __forceinline__ double pow2(int e) {
+  return (e > -1023 && e < 1024) ? __longlong_as_double((long long)(e + 1023) << 52) : ldexp(1.0, e);
+}
+
 __global__ void __launch_bounds__(NT) k_schur_oz(LevelDev<double> L, const BoxRec<double>* recs) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const BoxRec<double> R = recs[blockIdx.y];
   const int c = R.c, kp = R.kp, nt = (c + 63) / 64;
   if ((int)blockIdx.x >= nt * nt) return;
   const int i0 = (blockIdx.x % nt) * 64, j0 = (blockIdx.x / nt) * 64;
-  const int SA = OZ_S * kp + 8;                 // smem row stride in bf16 elements
+  const int SA = OZ_S * kp + 8;                 // smem row stride in bf16 elements (16-byte rows)
   uint16_t* As = reinterpret_cast<uint16_t*>(smraw);
   uint16_t* Bs = As + 64 * SA;
   __shared__ long long rowb[64], colb[64];
@@ -907,13 +921,17 @@ __global__ void __launch_bounds__(NT) k_schur_oz(LevelDev<double> L, const BoxRe
   __syncthreads();
   const int warp = tid >> 5, lane = tid & 31, gq = lane >> 2, t4 = lane & 3;
   const int m0 = (warp >> 2) * 32, n0 = (warp & 3) * 16;
-  long long hi[2][2][4], lo[2][2][4];
+  // ldmatrix row addresses: A tiles (rows m0 + mi*16 + lane%16, k + 8*(lane/16)),
+  // B pair of n8 tiles (rows n0 + 8*(lane/16) + lane%8, k + 8*((lane/8)%2))
+  const int a_row = lane & 15, a_k = (lane >> 4) * 8;
+  const int b_row = ((lane >> 4) << 3) + (lane & 7), b_k = ((lane >> 3) & 1) * 8;
+  long long W[2][2][4];
 #pragma unroll
   for (int mi = 0; mi < 2; ++mi)
 #pragma unroll
     for (int ni = 0; ni < 2; ++ni)
 #pragma unroll
-      for (int e = 0; e < 4; ++e) { hi[mi][ni][e] = 0; lo[mi][ni][e] = 0; }
+      for (int e = 0; e < 4; ++e) W[mi][ni][e] = 0;
   for (int u = 0; u < OZ_S; ++u) {
     float cf[2][2][4];
 #pragma unroll
@@ -926,27 +944,18 @@ __global__ void __launch_bounds__(NT) k_schur_oz(LevelDev<double> L, const BoxRe
       const uint16_t* Ab = As + p * kp;
       const uint16_t* Bb = Bs + (u - p) * kp;
       for (int kk = 0; kk < kp; kk += 16) {
-        uint32_t af[2][4], bq[2][2];
+        uint32_t af[2][4], bq[4];
+#pragma unroll
+        for (int mi = 0; mi < 2; ++mi) ldsm_x4(af[mi], Ab + (m0 + mi * 16 + a_row) * SA + kk + a_k);
+        ldsm_x4(bq, Bb + (n0 + b_row) * SA + kk + b_k);
 #pragma unroll
         for (int mi = 0; mi < 2; ++mi) {
-          const uint16_t* a0 = Ab + (m0 + mi * 16 + gq) * SA + kk + 2 * t4;
-          af[mi][0] = *reinterpret_cast<const uint32_t*>(a0);
-          af[mi][1] = *reinterpret_cast<const uint32_t*>(a0 + 8 * SA);
-          af[mi][2] = *reinterpret_cast<const uint32_t*>(a0 + 8);
-          af[mi][3] = *reinterpret_cast<const uint32_t*>(a0 + 8 * SA + 8);
+          mma_bf16(cf[mi][0], af[mi], bq);
+          mma_bf16(cf[mi][1], af[mi], bq + 2);
         }
-#pragma unroll
-        for (int ni = 0; ni < 2; ++ni) {
-          const uint16_t* b0 = Bb + (n0 + ni * 8 + gq) * SA + kk + 2 * t4;
-          bq[ni][0] = *reinterpret_cast<const uint32_t*>(b0);
-          bq[ni][1] = *reinterpret_cast<const uint32_t*>(b0 + 8);
-        }
-#pragma unroll
-        for (int mi = 0; mi < 2; ++mi)
-#pragma unroll
-          for (int ni = 0; ni < 2; ++ni) mma_bf16(cf[mi][ni], af[mi], bq[ni]);
       }
     }
+    const int sh = 39 - OZ_BITS * u;
 #pragma unroll
     for (int mi = 0; mi < 2; ++mi)
 #pragma unroll
@@ -954,8 +963,7 @@ __global__ void __launch_bounds__(NT) k_schur_oz(LevelDev<double> L, const BoxRe
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
           const long long gv = (long long)__float2int_rn(cf[mi][ni][e]);
-          if (u <= 2) hi[mi][ni][e] += gv << (OZ_BITS * (2 - u));
-          else lo[mi][ni][e] += gv << (OZ_BITS * (OZ_S - 1 - u));
+          W[mi][ni][e] += sh >= 0 ? (gv << sh) : ((gv + (1LL << (-sh - 1))) >> (-sh));
         }
   }
 #pragma unroll
@@ -967,9 +975,7 @@ __global__ void __launch_bounds__(NT) k_schur_oz(LevelDev<double> L, const BoxRe
         const int row = m0 + mi * 16 + gq + (e >= 2 ? 8 : 0);
         const int col = n0 + ni * 8 + 2 * t4 + (e & 1);
         if (i0 + row < c && j0 + col < c) {
-          // sum_u 2^(-7(u+2)) G_u = hi 2^-28 + lo 2^-63
-          double v = fma((double)hi[mi][ni][e], 0x1p-28, (double)lo[mi][ni][e] * 0x1p-63);
-          v = ldexp(v, rexp[row] + cexp[col]);
+          const double v = (double)W[mi][ni][e] * pow2(rexp[row] + cexp[col] - 53);
           double* ptr = L.blk + rowb[row] + colb[col];
           *ptr = *ptr - v;
         }
