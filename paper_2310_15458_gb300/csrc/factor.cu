@@ -1061,17 +1061,35 @@ __global__ void __launch_bounds__(NT) k_top_assemble(LevelDev<T> L, T* D, int nt
     for (int i = threadIdx.x; i < nu; i += blockDim.x) top_idx[offs[u] + i] = L.pts[u * L.nmax + i];
 }
 
-template <typename T> __global__ void __launch_bounds__(1024) k_dense_lu(T* A, int n, int* piv, int* err) {
-  __shared__ int s_piv, s_zero;
-  const int tid = threadIdx.x, bs = blockDim.x, lane = tid & 31, warp = tid >> 5;
-  for (int j = 0; j < n; ++j) {
+// Blocked right-looking LU with partial pivoting for the dense top block (the
+// same pivot sequence as the unblocked algorithm): per panel of 32 columns,
+// k_lu_panel factors A[jb:n, jb:jb+32] in one CTA, k_lu_swap_trsm applies the
+// panel's row exchanges to the other columns and forms U12 = L11^{-1} A12, and
+// k_lu_update subtracts L21 U12 from the trailing block across the GPU.
+constexpr int LB = 32;
+
+template <typename T> __global__ void __launch_bounds__(1024) k_lu_panel(T* A, int n, int jb, int* piv, int* err) {
+  __shared__ double s_mx[32];
+  __shared__ int s_mi[32], s_piv, s_zero;
+  const int tid = threadIdx.x, bs = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = bs >> 5;
+  const int je = min(n, jb + LB);
+  for (int j = jb; j < je; ++j) {
+    double mx = -1.0;
+    int mi = INT_MAX;
+    for (int i = j + tid; i < n; i += bs) {
+      const double v = abs2(A[i + (size_t)j * n]);
+      if (v > mx) { mx = v; mi = i; }
+    }
+    for (int d = 16; d > 0; d >>= 1) {
+      const double om = __shfl_xor_sync(0xffffffffu, mx, d);
+      const int oi = __shfl_xor_sync(0xffffffffu, mi, d);
+      if (om > mx || (om == mx && oi < mi)) { mx = om; mi = oi; }
+    }
+    if (lane == 0) { s_mx[warp] = mx; s_mi[warp] = mi; }
+    __syncthreads();
     if (warp == 0) {
-      double mx = -1.0;
-      int mi = INT_MAX;
-      for (int i = j + lane; i < n; i += 32) {
-        const double v = abs2(A[i + (size_t)j * n]);
-        if (v > mx) { mx = v; mi = i; }
-      }
+      mx = lane < nw ? s_mx[lane] : -1.0;
+      mi = lane < nw ? s_mi[lane] : INT_MAX;
       for (int d = 16; d > 0; d >>= 1) {
         const double om = __shfl_xor_sync(0xffffffffu, mx, d);
         const int oi = __shfl_xor_sync(0xffffffffu, mi, d);
@@ -1085,24 +1103,89 @@ template <typename T> __global__ void __launch_bounds__(1024) k_dense_lu(T* A, i
       return;
     }
     const int p = s_piv;
-    if (p != j)
-      for (int col = tid; col < n; col += bs) {
-        const T t = A[j + (size_t)col * n];
-        A[j + (size_t)col * n] = A[p + (size_t)col * n];
-        A[p + (size_t)col * n] = t;
-      }
+    if (p != j && tid < je - jb) {   // exchange rows j and p inside the panel
+      const int col = jb + tid;
+      const T t = A[j + (size_t)col * n];
+      A[j + (size_t)col * n] = A[p + (size_t)col * n];
+      A[p + (size_t)col * n] = t;
+    }
     if (tid == 0) piv[j] = p;
     __syncthreads();
-    const T d = A[j + (size_t)j * n];
-    for (int i = j + 1 + tid; i < n; i += bs) A[i + (size_t)j * n] = dv(A[i + (size_t)j * n], d);
+    const T d = dv(from_re<T>(1.0), A[j + (size_t)j * n]);
+    for (int i = j + 1 + tid; i < n; i += bs) A[i + (size_t)j * n] = A[i + (size_t)j * n] * d;
     __syncthreads();
-    const int w = n - j - 1;
-    for (int e = tid; e < w * w; e += bs) {
-      const int ii = j + 1 + e % w, jj = j + 1 + e / w;
-      A[ii + (size_t)jj * n] = msb(A[ii + (size_t)jj * n], A[ii + (size_t)j * n], A[j + (size_t)jj * n]);
+    const int w = je - j - 1;
+    for (long long e = tid; e < (long long)(n - j - 1) * w; e += bs) {
+      const int i = j + 1 + (int)(e % (n - j - 1)), col = j + 1 + (int)(e / (n - j - 1));
+      A[i + (size_t)col * n] = msb(A[i + (size_t)col * n], A[i + (size_t)j * n], A[j + (size_t)col * n]);
     }
     __syncthreads();
   }
+}
+
+// one thread per column outside the panel: row exchanges, then (right of the
+// panel) U12 = L11^{-1} A12 by forward substitution
+template <typename T> __global__ void k_lu_swap_trsm(T* A, int n, int jb, const int* piv) {
+  const int je = min(n, jb + LB);
+  int col = blockIdx.x * blockDim.x + threadIdx.x;
+  if (col >= n - (je - jb)) return;
+  if (col >= jb) col += je - jb;
+  T* a = A + (size_t)col * n;
+  for (int j = jb; j < je; ++j) {
+    const int p = piv[j];
+    if (p != j) {
+      const T t = a[j];
+      a[j] = a[p];
+      a[p] = t;
+    }
+  }
+  if (col >= je)
+    for (int i = jb + 1; i < je; ++i) {
+      T x = a[i];
+      for (int l = jb; l < i; ++l) x = msb(x, A[i + (size_t)l * n], a[l]);
+      a[i] = x;
+    }
+}
+
+// A22 -= L21 U12, 64 x 64 tiles
+template <typename T> __global__ void __launch_bounds__(NT) k_lu_update(T* A, int n, int jb) {
+  const int je = min(n, jb + LB), m = n - je;
+  const int nt = (m + 63) / 64;
+  const int i0 = je + (blockIdx.x % nt) * 64, j0 = je + (blockIdx.x / nt) * 64;
+  constexpr int KC = 16;
+  __shared__ T Ls[KC][64], Us[KC][64];
+  const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+  const int kb = je - jb;
+  T acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = zero<T>();
+  for (int l0 = 0; l0 < kb; l0 += KC) {
+    __syncthreads();
+    for (int e = tid; e < KC * 64; e += NT) {
+      const int l = l0 + e / 64, ii = e % 64;
+      Ls[e / 64][ii] = (l < kb && i0 + ii < n) ? A[i0 + ii + (size_t)(jb + l) * n] : zero<T>();
+      Us[e / 64][ii] = (l < kb && j0 + ii < n) ? A[jb + l + (size_t)(j0 + ii) * n] : zero<T>();
+    }
+    __syncthreads();
+    for (int l = 0; l < KC; ++l) {
+      T av[4], bv[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) { av[a] = Ls[l][tx + 16 * a]; bv[a] = Us[l][ty + 16 * a]; }
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = mad(acc[a][b], av[a], bv[b]);
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int i = i0 + tx + 16 * a, j = j0 + ty + 16 * b;
+      if (i < n && j < n) A[i + (size_t)j * n] = A[i + (size_t)j * n] - acc[a][b];
+    }
 }
 
 // ------------------------------------------------------------------ host helpers
@@ -1574,10 +1657,25 @@ rss_status factor_impl(const rss_tree* tree, const rss_params* prm, cudaStream_t
     k_top_assemble<T><<<nbox * nbox, NT, 0, st>>>(cur.d, static_cast<T*>(f->d_top_lu), ntop, f->d_top_idx,
                                                   make_int4(offs[0], offs[1], offs[2], offs[3]), offs[4]);
     RSS_LAUNCHED();
-    k_dense_lu<T><<<1, 1024, 0, st>>>(static_cast<T*>(f->d_top_lu), ntop, f->d_top_piv, d_err);
-    RSS_LAUNCHED();
+    for (int jb = 0; jb < ntop; jb += LB) {
+      T* A = static_cast<T*>(f->d_top_lu);
+      k_lu_panel<T><<<1, 1024, 0, st>>>(A, ntop, jb, f->d_top_piv, d_err);
+      RSS_LAUNCHED();
+      const int others = ntop - std::min(LB, ntop - jb);
+      if (others > 0) {
+        k_lu_swap_trsm<T><<<cdiv(others, 128), 128, 0, st>>>(A, ntop, jb, f->d_top_piv);
+        RSS_LAUNCHED();
+      }
+      const int m = ntop - std::min(ntop, jb + LB);
+      if (m > 0) {
+        const int nt = (m + 63) / 64;
+        k_lu_update<T><<<nt * nt, NT, 0, st>>>(A, ntop, jb);
+        RSS_LAUNCHED();
+      }
+      f->launches += 3;
+    }
     evt.stop(st);
-    f->launches += 2;
+    f->launches += 1;
     RSS_CUDA(cudaStreamSynchronize(st));
     f->g_top += evt.ms();
     f->f_top += (sizeof(T) == sizeof(double) ? 1.0 : 4.0) * 2.0 * (double)ntop * ntop * ntop / 3.0;

@@ -96,18 +96,22 @@ __global__ void __launch_bounds__(NT) k_solve_down(const BoxRec<T>* __restrict__
   const int q0 = blockIdx.y * RC, nq = min(RC, nrhs - q0);
   T* t = reinterpret_cast<T*>(smraw);   // r x RC
   T* yR = t + (size_t)r * RC;           // r x RC
+  T* yC = yR + (size_t)r * RC;          // c x RC: y_C gathered once
   const int tid = threadIdx.x, bs = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = bs >> 5;
   T* xq = x + (int64_t)q0 * N;
+  for (int e = tid; e < c * RC; e += bs) {
+    const int i = e / RC, q = e % RC;
+    yC[e] = q < nq ? xq[R.idxC[i] + (int64_t)q * N] : zero<T>();
+  }
+  __syncthreads();
   for (int j = warp; j < r; j += nw) {            // y_R - F y_C
     T acc[RC];
 #pragma unroll
     for (int q = 0; q < RC; ++q) acc[q] = zero<T>();
     for (int i = lane; i < c; i += 32) {
       const T fv = R.Ft[i + (size_t)j * c];
-      const int gi = R.idxC[i];
 #pragma unroll
-      for (int q = 0; q < RC; ++q)
-        if (q < nq) acc[q] = mad(acc[q], fv, xq[gi + (int64_t)q * N]);
+      for (int q = 0; q < RC; ++q) acc[q] = mad(acc[q], fv, yC[i * RC + q]);
     }
 #pragma unroll
     for (int q = 0; q < RC; ++q) acc[q] = warp_sum(acc[q]);
@@ -136,6 +140,8 @@ __global__ void __launch_bounds__(NT) k_solve_down(const BoxRec<T>* __restrict__
   }
 }
 
+// Dense top solve, blocked by 32: one warp solves each diagonal block (no
+// block-wide barrier per row), then all threads update the rows below (above).
 template <typename T, int RC>
 __global__ void __launch_bounds__(1024) k_top_solve(const T* __restrict__ LU, const int* __restrict__ piv,
                                                     const int* __restrict__ idx, int n, T* __restrict__ x,
@@ -143,7 +149,7 @@ __global__ void __launch_bounds__(1024) k_top_solve(const T* __restrict__ LU, co
   extern __shared__ __align__(16) unsigned char smraw[];
   T* z = reinterpret_cast<T*>(smraw);   // n x RC
   const int q0 = blockIdx.x * RC, nq = min(RC, nrhs - q0);
-  const int tid = threadIdx.x, bs = blockDim.x;
+  const int tid = threadIdx.x, bs = blockDim.x, lane = tid & 31, warp = tid >> 5;
   T* xq = x + (int64_t)q0 * N;
   for (int e = tid; e < n * RC; e += bs) {
     const int i = e / RC, q = e % RC;
@@ -160,21 +166,46 @@ __global__ void __launch_bounds__(1024) k_top_solve(const T* __restrict__ LU, co
       }
     }
   __syncthreads();
-  for (int j = 0; j + 1 < n; ++j) {
-    const int w = (n - j - 1) * RC;
-    for (int e = tid; e < w; e += bs) {
-      const int l = j + 1 + e / RC, q = e % RC;
-      z[l * RC + q] = msb(z[l * RC + q], LU[l + (size_t)j * n], z[j * RC + q]);
+  // forward: unit lower L
+  for (int jb = 0; jb < n; jb += 32) {
+    const int je = min(n, jb + 32);
+    if (warp == 0) {
+      for (int j = jb; j < je; ++j) {
+        const int l = jb + lane;
+        if (l > j && l < je)
+          for (int q = 0; q < RC; ++q) z[l * RC + q] = msb(z[l * RC + q], LU[l + (size_t)j * n], z[j * RC + q]);
+        __syncwarp();
+      }
+    }
+    __syncthreads();
+    for (int e = tid; e < (n - je) * RC; e += bs) {
+      const int l = je + e / RC, q = e % RC;
+      T acc = z[l * RC + q];
+      for (int j = jb; j < je; ++j) acc = msb(acc, LU[l + (size_t)j * n], z[j * RC + q]);
+      z[l * RC + q] = acc;
     }
     __syncthreads();
   }
-  for (int j = n - 1; j >= 0; --j) {
-    if (tid < RC) z[j * RC + tid] = dv(z[j * RC + tid], LU[j + (size_t)j * n]);
+  // backward: upper U
+  for (int je = n; je > 0; je -= 32) {
+    const int jb = max(0, je - 32);
+    if (warp == 0) {
+      for (int j = je - 1; j >= jb; --j) {
+        if (lane == 0)
+          for (int q = 0; q < RC; ++q) z[j * RC + q] = dv(z[j * RC + q], LU[j + (size_t)j * n]);
+        __syncwarp();
+        const int l = jb + lane;
+        if (l < j)
+          for (int q = 0; q < RC; ++q) z[l * RC + q] = msb(z[l * RC + q], LU[l + (size_t)j * n], z[j * RC + q]);
+        __syncwarp();
+      }
+    }
     __syncthreads();
-    const int w = j * RC;
-    for (int e = tid; e < w; e += bs) {
+    for (int e = tid; e < jb * RC; e += bs) {
       const int l = e / RC, q = e % RC;
-      z[l * RC + q] = msb(z[l * RC + q], LU[l + (size_t)j * n], z[j * RC + q]);
+      T acc = z[l * RC + q];
+      for (int j = jb; j < je; ++j) acc = msb(acc, LU[l + (size_t)j * n], z[j * RC + q]);
+      z[l * RC + q] = acc;
     }
     __syncthreads();
   }
@@ -207,7 +238,7 @@ rss_status sweeps(const rss_factorization* f, T* x, int64_t N, int nrhs, cudaStr
     RSS_LAUNCHED();
   }
   for (auto it = f->batches.rbegin(); it != f->batches.rend(); ++it) {
-    const size_t smem = sizeof(T) * (size_t)2 * it->max_r * RC;
+    const size_t smem = sizeof(T) * (size_t)(2 * it->max_r + it->max_c) * RC;
     k_solve_down<T, RC><<<dim3(it->nrec, nchunk), NT, smem, st>>>(static_cast<const BoxRec<T>*>(it->d_recs), x, N,
                                                                  nrhs);
     RSS_LAUNCHED();
