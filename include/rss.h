@@ -78,6 +78,10 @@ typedef struct {
                                      eight 7-bit slices, exact integer products, FP64
                                      recombination (accuracy of an FP64 product); 1: FP64
                                      FMA kernel everywhere */
+  int id_cluster;                 /* colour classes with fewer boxes than the GPU has room for:
+                                     0 spreads each box's ID over a thread-block cluster of
+                                     up to 8 CTAs, > 0 caps the cluster size (1: one CTA per
+                                     box), -1 is the same as 1 */
 } rss_params;
 
 /* Build the quadtree of Section 2.1 for n points given as pts_xy[2*i],

@@ -72,6 +72,13 @@ __device__ inline double shfl_xor(double v, int d) { return __shfl_xor_sync(0xff
 __device__ inline zd shfl_xor(zd v, int d) {
   return zd{__shfl_xor_sync(0xffffffffu, v.x, d), __shfl_xor_sync(0xffffffffu, v.y, d)};
 }
+// loads that bypass L1 (data written by another CTA of the cluster)
+__device__ inline double ld_l2(const double* p) { return __ldcg(p); }
+__device__ inline zd ld_l2(const zd* p) {
+  const double2 v = __ldcg(reinterpret_cast<const double2*>(p));
+  return zd{v.x, v.y};
+}
+
 template <typename T> __device__ inline T warp_sum(T v) {
 #pragma unroll
   for (int d = 16; d > 0; d >>= 1) v = v + shfl_xor(v, d);

@@ -23,6 +23,7 @@
 #include <memory>
 #include <vector>
 
+#include <cooperative_groups.h>
 #include <cuda_bf16.h>
 
 #include "internal.h"
@@ -387,6 +388,301 @@ template <typename T> __global__ void __launch_bounds__(NT_ID, 4) k_id(IdArgs<T>
     ++k;
   }
   __syncthreads();
+  // T = R11^{-1} R12 (back substitution), k x r with ld nmax
+  const int r = n - k;
+  T* Tw = a.T_ws + (size_t)bi * nn;
+  for (int c = tid; c < r; c += blockDim.x) {
+    const int oc = perm[k + c];
+    for (int i = k - 1; i >= 0; --i) {
+      T x = Rr[(size_t)i * nmax + oc];
+      for (int l = i + 1; l < k; ++l) x = msb(x, Rr[(size_t)i * nmax + perm[l]], Tw[(size_t)c * nmax + l]);
+      Tw[(size_t)c * nmax + i] = dv(x, beta[i]);
+    }
+  }
+  for (int c = tid; c < n; c += blockDim.x) a.perm_out[(size_t)bi * nmax + c] = perm[c];
+  if (tid == 0) a.k_out[bi] = k;
+}
+
+// ------------------------------------------------------------------ ID on a thread-block cluster
+// For colour classes too small to fill the GPU: a cluster of Q CTAs works on one
+// box, CTA q owning a contiguous slice of the rows of Y (and of V).  Every CTA
+// keeps an identical copy of the small state (norms, permutation, G, rows of R)
+// and makes the same decisions; the sums over rows (column norms, the pivot
+// column's norm, v^H Y, v^H V, re-accumulated norms) are formed per CTA and
+// added through distributed shared memory in rank order, so all CTAs see the
+// same bits.  Every CTA reaches every cluster barrier the same number of times.
+template <typename T> __global__ void __launch_bounds__(NT_ID) k_id_cl(IdArgs<T> a) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  const int Q = (int)cl.num_blocks(), rank = (int)cl.block_rank();
+  const LevelDev<T>& L = a.L;
+  const int nmax = L.nmax, g = L.g, ldY = a.ldY;
+  const int rp = (ldY + Q - 1) / Q;                // rows per CTA (upper bound)
+  T* vbuf = reinterpret_cast<T*>(smraw);           // rp: owned rows of the reflector
+  T* u = vbuf + rp;                                // nmax
+  T* beta = u + nmax;                              // nmax
+  T* part = beta + nmax;                           // 2 x (2 nmax): partial sums, double buffered
+  double* norms2 = reinterpret_cast<double*>(part + 4 * nmax);
+  double* ref = norms2 + nmax;
+  double* taus = ref + nmax;
+  int* perm = reinterpret_cast<int*>(taus + nmax);
+  int* flag = perm + nmax;
+  __shared__ int Mbox[16], Moff[17], s_nM, s_stop;
+  __shared__ double s_thresh, s_y2max;
+  __shared__ T s_scale;
+
+  const int box_local = blockIdx.x / Q;
+  const int bi = a.base + box_local;
+  const int B = a.boxes[bi];
+  const size_t nn = (size_t)nmax * nmax;
+  const int n = L.n[B];
+  const size_t slot = 2 * (size_t)ldY * nmax + 2 * nn * Q;
+  T* Yw = a.ws + (size_t)box_local * slot;
+  const T* Y = Yw;
+  T* V = Yw + (size_t)ldY * nmax;
+  T* G = V + (size_t)ldY * nmax + 2 * nn * rank;   // this CTA's copy: G[l * nmax + c]
+  T* Rr = G + nn;                                   // Rr[i * nmax + c]
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
+  int pb = 0;                                       // partial-sum buffer in use
+
+  // sum the Q CTAs' partial vectors part[pb][0..len) in rank order into out[]
+  auto cluster_sum = [&](int len, T* out) {
+    cl.sync();
+    for (int e = tid; e < len; e += blockDim.x) {
+      T s = zero<T>();
+      for (int q = 0; q < Q; ++q) s = s + cl.map_shared_rank(part + pb * 2 * nmax, q)[e];
+      out[e] = s;
+    }
+    pb ^= 1;
+    __syncthreads();
+  };
+
+  if (tid == 0) {
+    int cnt = 0, off = 0;
+    for (int dy = -2; dy <= 2; ++dy)
+      for (int dx = -2; dx <= 2; ++dx) {
+        if (max(abs(dx), abs(dy)) != 2) continue;
+        const int mb = nbr_box(B, g, dx, dy);
+        if (mb < 0) continue;
+        Mbox[cnt] = mb;
+        Moff[cnt] = off;
+        off += L.nact[mb];
+        ++cnt;
+      }
+    Moff[cnt] = off;
+    s_nM = cnt;
+  }
+  __syncthreads();
+  const int nM = s_nM, mh = Moff[nM], P = a.P;
+  const int m = a.half ? mh + P : 2 * (mh + P);
+  const int r0 = min(m, rank * rp), r1 = min(m, r0 + rp);
+  const int bx = B % g, by = B / g;
+  const double cx = a.geo.x0 - 0.5 * a.geo.hg + (bx + 0.5) * a.Lbox;
+  const double cy = a.geo.y0 - 0.5 * a.geo.hg + (by + 0.5) * a.Lbox;
+  // owned rows of Y
+  const int mr = r1 - r0;
+  for (long long e = tid; e < (long long)mr * n; e += blockDim.x) {
+    const int i = r0 + (int)(e % mr), j = (int)(e / mr);
+    T val;
+    if (i < mh || (i >= mh + P && i < 2 * mh + P)) {
+      const bool second = i >= mh;
+      const int ii = second ? i - mh - P : i;
+      int q = 0;
+      while (Moff[q + 1] <= ii) ++q;
+      const int mb = Mbox[q];
+      const int pm = L.act[mb * nmax + (ii - Moff[q])];
+      if (!second)
+        val = L.blk[((size_t)mb * 25 + off_index(mb, B, g)) * nn + (size_t)j * nmax + pm];
+      else
+        val = cj(L.blk[((size_t)B * 25 + off_index(B, mb, g)) * nn + (size_t)pm * nmax + j]);
+    } else {
+      const bool second = i >= 2 * mh + P;
+      const int p = second ? i - 2 * mh - P : i - mh;
+      double sn, cs;
+      sincospi(2.0 * p / P, &sn, &cs);
+      const double px = cx + a.rho * cs, py = cy + a.rho * sn;
+      const int2 q = a.ixy[L.pts[B * nmax + j]];
+      const double xj = a.geo.x0 + q.x * a.geo.hg, yj = a.geo.y0 + q.y * a.geo.hg;
+      val = second ? cj(kval(a.kp, xj, yj, px, py, T{})) : kval(a.kp, px, py, xj, yj, T{});
+    }
+    Yw[(size_t)j * ldY + i] = val;
+  }
+  __syncthreads();
+  // column norms: partials over owned rows, summed across the cluster
+  for (int c = warp; c < n; c += nwarp) {
+    double s = 0.0;
+    for (int i = r0 + lane; i < r1; i += 32) s += abs2(Y[(size_t)c * ldY + i]);
+    s = warp_sum(s);
+    if (lane == 0) part[pb * 2 * nmax + c] = from_re<T>(s);
+  }
+  cluster_sum(n, u);   // (u used as scratch)
+  for (int c = tid; c < n; c += blockDim.x) {
+    norms2[c] = re(u[c]);
+    ref[c] = norms2[c];
+    perm[c] = c;
+  }
+  __syncthreads();
+  if (warp == 0) {
+    double s = 0.0, mx = 0.0;
+    for (int c = lane; c < n; c += 32) {
+      s += norms2[c];
+      mx = fmax(mx, norms2[c]);
+    }
+    s = warp_sum(s);
+    mx = warp_max(mx);
+    if (lane == 0) {
+      s_thresh = a.eps * a.eps * s;
+      s_y2max = mx;
+    }
+  }
+  __syncthreads();
+
+  int k = 0;
+  const int kmax = min(m, n);
+  while (k < kmax) {
+    if (warp == 0) {   // stop test and pivot (identical in every CTA)
+      double s = 0.0, mx = -1.0;
+      for (int c = k + lane; c < n; c += 32) {
+        s += norms2[c];
+        mx = fmax(mx, norms2[c]);
+      }
+      s = warp_sum(s);
+      mx = warp_max(mx);
+      const double thr = mx - (TIE_REL * mx + TIE_ABS * sqrt(mx * s_y2max));
+      int bp = INT_MAX, bc = -1;
+      for (int c = k + lane; c < n; c += 32)
+        if (norms2[c] >= thr && perm[c] < bp) {
+          bp = perm[c];
+          bc = c;
+        }
+      for (int d = 16; d > 0; d >>= 1) {
+        const int op = __shfl_xor_sync(0xffffffffu, bp, d), oc = __shfl_xor_sync(0xffffffffu, bc, d);
+        if (op < bp) {
+          bp = op;
+          bc = oc;
+        }
+      }
+      if (lane == 0) {
+        s_stop = (s <= s_thresh) || bc < 0;
+        if (!s_stop && bc != k) {
+          int ti = perm[k]; perm[k] = perm[bc]; perm[bc] = ti;
+          double td = norms2[k]; norms2[k] = norms2[bc]; norms2[bc] = td;
+          td = ref[k]; ref[k] = ref[bc]; ref[bc] = td;
+        }
+      }
+    }
+    __syncthreads();
+    if (s_stop) break;
+    const int q = perm[k];
+    // owned rows of the pivot column after k reflectors; partial norm and x0
+    double s2 = 0.0;
+    for (int i = max(k, r0) + tid; i < r1; i += blockDim.x) {
+      T x = Y[(size_t)q * ldY + i];
+      for (int l = 0; l < k; ++l) x = msb(x, V[(size_t)l * ldY + i], G[(size_t)l * nmax + q]);
+      vbuf[i - r0] = x;
+      s2 += abs2(x);
+    }
+    s2 = warp_sum(s2);
+    if (lane == 0) part[pb * 2 * nmax + 2 + warp] = from_re<T>(s2);
+    if (tid == 0) part[pb * 2 * nmax + 0] = zero<T>();
+    __syncthreads();
+    if (tid == 0) {
+      double t = 0.0;
+      for (int w = 0; w < nwarp; ++w) t += re(part[pb * 2 * nmax + 2 + w]);
+      part[pb * 2 * nmax + 0] = from_re<T>(t);
+      part[pb * 2 * nmax + 1] = (k >= r0 && k < r1) ? vbuf[k - r0] : zero<T>();
+    }
+    cluster_sum(2, u + nmax - 2);   // u[nmax-2] = alpha^2, u[nmax-1] = x0
+    if (tid == 0) {
+      const T x0 = u[nmax - 1];
+      const double alpha = sqrt(re(u[nmax - 2]));
+      if (alpha == 0.0) {
+        s_stop = 1;
+      } else {
+        const double ax0 = sqrt(abs2(x0));
+        T phase = from_re<T>(1.0);
+        if (ax0 != 0.0) phase = scl(1.0 / ax0, x0);
+        const T bt = scl(-alpha, phase);
+        beta[k] = bt;
+        s_scale = x0 - bt;
+        taus[k] = (alpha + ax0) / alpha;
+      }
+    }
+    __syncthreads();
+    if (s_stop) break;
+    {
+      const T d = dv(from_re<T>(1.0), s_scale);
+      for (int i = max(k + 1, r0) + tid; i < r1; i += blockDim.x) {
+        const T v = vbuf[i - r0] * d;
+        vbuf[i - r0] = v;
+        V[(size_t)k * ldY + i] = v;
+      }
+      if (tid == 0 && k >= r0 && k < r1) {
+        vbuf[k - r0] = from_re<T>(1.0);
+        V[(size_t)k * ldY + k] = from_re<T>(1.0);
+      }
+    }
+    __syncthreads();
+    // partials of u_l = v^H V[:, l] (l < k) and g_c = v^H Y[:, c] over owned rows
+    const int nc = n - k - 1;
+    const int ib = max(k, r0);
+    for (int w = warp; w < k + nc; w += nwarp) {
+      const T* col = w < k ? V + (size_t)w * ldY : Y + (size_t)perm[k + 1 + (w - k)] * ldY;
+      T d0 = zero<T>(), d1 = zero<T>(), d2 = zero<T>(), d3 = zero<T>();
+      int i = ib + lane;
+      for (; i + 96 < r1; i += 128) {
+        d0 = madc(d0, vbuf[i - r0], col[i]);
+        d1 = madc(d1, vbuf[i + 32 - r0], col[i + 32]);
+        d2 = madc(d2, vbuf[i + 64 - r0], col[i + 64]);
+        d3 = madc(d3, vbuf[i + 96 - r0], col[i + 96]);
+      }
+      for (; i < r1; i += 32) d0 = madc(d0, vbuf[i - r0], col[i]);
+      const T d = warp_sum((d0 + d1) + (d2 + d3));
+      if (lane == 0) part[pb * 2 * nmax + w] = d;
+    }
+    cluster_sum(k + nc, u);   // u[0..k): v^H V, u[k..k+nc): raw g for positions k+1..
+    // g_c, row k of R, norm downdate (identical in every CTA; own copies of G, Rr)
+    const double tau = taus[k];
+    for (int pos = k + 1 + tid; pos < n; pos += blockDim.x) {
+      const int c = perm[pos];
+      T gc = u[k + (pos - k - 1)];
+      for (int l = 0; l < k; ++l) gc = msb(gc, G[(size_t)l * nmax + c], u[l]);
+      gc = scl(tau, gc);
+      G[(size_t)k * nmax + c] = gc;
+      T r = ld_l2(Y + (size_t)c * ldY + k);   // row k may belong to another CTA
+      for (int l = 0; l <= k; ++l) r = msb(r, ld_l2(V + (size_t)l * ldY + k), G[(size_t)l * nmax + c]);
+      Rr[(size_t)k * nmax + c] = r;
+      const double nv = norms2[pos] - abs2(r);
+      flag[pos] = nv < RECOMPUTE_REL * ref[pos];
+      norms2[pos] = nv;
+    }
+    __syncthreads();
+    // re-accumulation of flagged norms: partials over owned rows
+    for (int pos = k + 1 + warp; pos < n; pos += nwarp) {
+      double t = 0.0;
+      if (flag[pos]) {
+        const int c = perm[pos];
+        for (int i = max(k + 1, r0) + lane; i < r1; i += 32) {
+          T x = Y[(size_t)c * ldY + i];
+          for (int l = 0; l <= k; ++l) x = msb(x, V[(size_t)l * ldY + i], G[(size_t)l * nmax + c]);
+          t += abs2(x);
+        }
+        t = warp_sum(t);
+      }
+      if (lane == 0) part[pb * 2 * nmax + pos] = from_re<T>(t);
+    }
+    cluster_sum(n, u);
+    for (int pos = k + 1 + tid; pos < n; pos += blockDim.x)
+      if (flag[pos]) {
+        norms2[pos] = re(u[pos]);
+        ref[pos] = norms2[pos];
+      }
+    __syncthreads();
+    ++k;
+  }
+  cl.sync();   // every CTA is done reading its peers' shared memory
+  if (rank != 0) return;
   // T = R11^{-1} R12 (back substitution), k x r with ld nmax
   const int r = n - k;
   T* Tw = a.T_ws + (size_t)bi * nn;
@@ -1395,7 +1691,12 @@ rss_status factor_impl(const rss_tree* tree, const rss_params* prm, cudaStream_t
         mmax = std::max(mmax, mrows[q]);
       }
       const int ldY = (mmax + 1) & ~1;
-      const size_t slot = (2 * (size_t)ldY * nmax + 2 * nn) * sizeof(T);
+      // cluster of Q CTAs per box when the class is too small to fill the GPU
+      int Q = 1;
+      if (prm->id_cluster >= 0)
+        while (Q < 8 && (long long)nb * Q * 2 <= 2 * 152) Q *= 2;
+      if (prm->id_cluster > 0) Q = std::min(Q, prm->id_cluster);
+      const size_t slot = (2 * (size_t)ldY * nmax + 2 * nn * Q) * sizeof(T);
       const size_t ybudget = size_t(2) << 30;
       const int cap = (int)std::max<size_t>(1, std::min<size_t>(nb, ybudget / slot));
       const int nchunks = (nb + cap - 1) / cap;
@@ -1411,6 +1712,10 @@ rss_status factor_impl(const rss_tree* tree, const rss_params* prm, cudaStream_t
         return RSS_EINVAL;
       }
       RSS_CUDA(cudaFuncSetAttribute(k_id<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_id));
+      const size_t smem_cl = sizeof(T) * ((size_t)(ldY + Q - 1) / Q + 6 * (size_t)nmax) +
+                             (size_t)nmax * (3 * sizeof(double) + 2 * sizeof(int));
+      if (Q > 1)
+        RSS_CUDA(cudaFuncSetAttribute(k_id_cl<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cl));
       f->peak_transient = std::max(f->peak_transient, transient + slot * chunk);
       Timer tid_;
       evs.emplace_back(0, std::make_unique<Ev>());
@@ -1434,7 +1739,23 @@ rss_status factor_impl(const rss_tree* tree, const rss_params* prm, cudaStream_t
         a.rho = ratio * Lbox;
         a.Lbox = Lbox;
         const int cnt = std::min(chunk, nb - c0);
-        k_id<T><<<cnt, NT_ID, smem_id, st>>>(a);
+        if (Q > 1) {
+          cudaLaunchConfig_t cfg = {};
+          cfg.gridDim = dim3(cnt * Q);
+          cfg.blockDim = dim3(NT_ID);
+          cfg.dynamicSmemBytes = smem_cl;
+          cfg.stream = st;
+          cudaLaunchAttribute attr[1];
+          attr[0].id = cudaLaunchAttributeClusterDimension;
+          attr[0].val.clusterDim.x = Q;
+          attr[0].val.clusterDim.y = 1;
+          attr[0].val.clusterDim.z = 1;
+          cfg.attrs = attr;
+          cfg.numAttrs = 1;
+          RSS_CUDA(cudaLaunchKernelEx(&cfg, k_id_cl<T>, a));
+        } else {
+          k_id<T><<<cnt, NT_ID, smem_id, st>>>(a);
+        }
         RSS_LAUNCHED();
         f->launches += 1;
         f->n_id += 1;

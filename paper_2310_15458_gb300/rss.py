@@ -40,7 +40,7 @@ class _Params(ctypes.Structure):
                 ("coef_re", ctypes.c_double * MAX_COEF), ("coef_im", ctypes.c_double * MAX_COEF),
                 ("scale", ctypes.c_double), ("phase_x", ctypes.c_double),
                 ("phase_y", ctypes.c_double), ("id_rows", ctypes.c_int),
-                ("schur_path", ctypes.c_int)]
+                ("schur_path", ctypes.c_int), ("id_cluster", ctypes.c_int)]
 
 
 _lib = None
@@ -143,7 +143,7 @@ def rss_factor(tree: Tree, kind: int = LAPLACE, eps: float = 1e-6, h: float = 0.
                kappa: float = 0.0, diag: complex = 1.0, proxy_n: int = 64,
                proxy_radius_over_side: float = 1.25, coef=(), scale: float = 1.0,
                phase=(0.0, 0.0), full_stack: bool = False, schur_fp64: bool = False,
-               stream=None) -> Factor:
+               id_cluster: int = 0, stream=None) -> Factor:
     lib = _load()
     p = _Params()
     p.kind, p.h, p.kappa = kind, h, kappa
@@ -158,6 +158,7 @@ def rss_factor(tree: Tree, kind: int = LAPLACE, eps: float = 1e-6, h: float = 0.
     p.scale, p.phase_x, p.phase_y = scale, phase[0], phase[1]
     p.id_rows = 1 if full_stack else 0
     p.schur_path = 1 if schur_fp64 else 0
+    p.id_cluster = id_cluster
     out = ctypes.c_void_p()
     _check(lib.rss_factor(tree.handle, ctypes.byref(p), _stream_handle(stream), ctypes.byref(out)))
     return Factor(out, tree.n, kind in (HELMHOLTZ, TEST_POLY), tree)

@@ -262,3 +262,27 @@ def test_tensor_core_schur_matches_fp64_schur(P):
     assert rel(x_tc, x_64) < 1e-12
     spec = KernelSpec("laplace", h=1 / side)
     assert relres(pts, spec, x_tc, bvec) <= 10 * eps
+
+
+@pytest.mark.parametrize("kind", ["laplace", "helmholtz"])
+def test_cluster_id_matches_single_cta_id(P, kind):
+    """Spreading a box's ID over a thread-block cluster gives the same ranks, skeletons
+    and solution as one CTA per box (the row sums are only regrouped)."""
+    side, eps = 64, 1e-7
+    pts = W.grid_points(side)
+    spec = KernelSpec(kind, h=1 / side, kappa=25.0)
+    tree = P.rss_build_tree(pts, 16)
+    fc = P.rss_factor(tree, kind=KIND[kind], eps=eps, h=1 / side, kappa=25.0)
+    f1 = P.rss_factor(tree, kind=KIND[kind], eps=eps, h=1 / side, kappa=25.0, id_cluster=-1)
+    for g in (16, 8, 4):
+        assert np.array_equal(P.rss_level_ranks(fc, g), P.rss_level_ranks(f1, g))
+    fac = orss.factor(pts, spec, eps, leaf=16)
+    for rec in fac.records[::max(1, len(fac.records) // 6)]:
+        a, b = P.rss_box_record(fc, rec.side, rec.box), P.rss_box_record(f1, rec.side, rec.box)
+        assert np.array_equal(a["S"], b["S"])
+        assert rel(a["T"], b["T"]) < rec_tol(eps)
+    for g in (16, 8, 4):
+        assert np.array_equal(P.rss_level_ranks(fc, g), fac.ranks[g])
+    bvec = W.gaussian_rhs(side * side, 2, spec.is_complex, 31)
+    x = gpu_solve(P, fc, bvec)
+    assert rel(x, orss.solve(fac, bvec)) < 1e-9
