@@ -789,6 +789,42 @@ __device__ __forceinline__ void panel_gemm(const T* __restrict__ A, int nl, int 
     }
 }
 
+// Complex rows: real and imaginary parts share the row scale (the largest |Re|,
+// |Im| of the row) and are split into OZ_S slices each; a row holds the OZ_S
+// real slices followed by the OZ_S imaginary slices.
+__device__ void oz_split_row(const zd* __restrict__ src, int stride, int r, int kp, uint16_t* dst, int* eout) {
+  double mx = 0.0;
+  for (int l = 0; l < r; ++l) {
+    const zd v = src[(size_t)l * stride];
+    mx = fmax(mx, fmax(fabs(v.x), fabs(v.y)));
+  }
+  int e = 0;
+  if (mx > 0.0) frexp(mx, &e);
+  *eout = e;
+  const double scale = ldexp(1.0, 56 - e);
+  for (int part = 0; part < 2; ++part)
+    for (int l = 0; l < kp; l += 2) {
+      const zd v0 = l < r ? src[(size_t)l * stride] : zd{0.0, 0.0};
+      const zd v1 = l + 1 < r ? src[(size_t)(l + 1) * stride] : zd{0.0, 0.0};
+      long long X0 = llrint((part ? v0.y : v0.x) * scale);
+      long long X1 = llrint((part ? v1.y : v1.x) * scale);
+      int d0[OZ_S], d1[OZ_S];
+#pragma unroll
+      for (int p = OZ_S - 1; p >= 1; --p) {
+        d0[p] = (int)(((X0 + 64) & 127) - 64);
+        X0 = (X0 - d0[p]) >> OZ_BITS;
+        d1[p] = (int)(((X1 + 64) & 127) - 64);
+        X1 = (X1 - d1[p]) >> OZ_BITS;
+      }
+      d0[0] = (int)X0;
+      d1[0] = (int)X1;
+#pragma unroll
+      for (int p = 0; p < OZ_S; ++p)
+        *reinterpret_cast<uint32_t*>(dst + (size_t)(part * OZ_S + p) * kp + l) =
+            (uint32_t)bf16_of_small_int(d0[p]) | ((uint32_t)bf16_of_small_int(d1[p]) << 16);
+    }
+}
+
 // ------------------------------------------------------------------ sparsify + LU (Eqs. 7, 8)
 // k_elim_lu (one CTA per box): C map, X_SR, X_RR, P X_RR = L U, U^{-1}, L^{-1}
 // and L^{-1} P.  k_elim_panels (one CTA per 64-row panel of C): X_CR, X_RC and
@@ -977,14 +1013,14 @@ template <typename T> __global__ void __launch_bounds__(NT, 4) k_elim_lu(ElimArg
       }
     }
     __syncthreads();
-    if constexpr (sizeof(T) == sizeof(double)) {
-      if (R.Esl != nullptr)
-        for (int i = tid; i < 2 * c; i += bs) {
-          const bool isE = i < c;
-          const int row = isE ? i : i - c;
-          oz_split_row((isE ? R.E : R.Ft) + row, c, r, R.kp,
-                       (isE ? R.Esl : R.Fsl) + (size_t)row * OZ_S * R.kp, (isE ? R.Eexp : R.Fexp) + row);
-        }
+    if (R.Esl != nullptr) {
+      const int ns = sizeof(T) == sizeof(double) ? OZ_S : 2 * OZ_S;   // slices per row
+      for (int i = tid; i < 2 * c; i += bs) {
+        const bool isE = i < c;
+        const int row = isE ? i : i - c;
+        oz_split_row((isE ? R.E : R.Ft) + row, c, r, R.kp,
+                     (isE ? R.Esl : R.Fsl) + (size_t)row * ns * R.kp, (isE ? R.Eexp : R.Fexp) + row);
+      }
     }
   }
   // B keeps only its skeleton
@@ -1050,14 +1086,14 @@ __device__ void elim_panel_body(const ElimArgs<T>& a, const BoxRec<T>& R, unsign
                           [&](int, int) { return zero<T>(); },
                           [&](int i, int j, T v) { R.Ft[p0 + i + (size_t)j * c] = v; });
   __syncthreads();
-  if constexpr (sizeof(T) == sizeof(double)) {
-    if (R.Esl != nullptr)   // digit slices of this panel's rows of E and F^T
-      for (int e = tid; e < 2 * rows; e += bs) {
-        const bool isE = e < rows;
-        const int row = p0 + (isE ? e : e - rows);
-        oz_split_row((isE ? R.E : R.Ft) + row, c, r, R.kp,
-                     (isE ? R.Esl : R.Fsl) + (size_t)row * OZ_S * R.kp, (isE ? R.Eexp : R.Fexp) + row);
-      }
+  if (R.Esl != nullptr) {   // digit slices of this panel's rows of E and F^T
+    const int ns = sizeof(T) == sizeof(double) ? OZ_S : 2 * OZ_S;
+    for (int e = tid; e < 2 * rows; e += bs) {
+      const bool isE = e < rows;
+      const int row = p0 + (isE ? e : e - rows);
+      oz_split_row((isE ? R.E : R.Ft) + row, c, r, R.kp,
+                   (isE ? R.Esl : R.Fsl) + (size_t)row * ns * R.kp, (isE ? R.Eexp : R.Fexp) + row);
+    }
   }
 }
 
@@ -1276,6 +1312,128 @@ __global__ void __launch_bounds__(NT) k_schur_oz(LevelDev<double> L, const BoxRe
           *ptr = *ptr - v;
         }
       }
+}
+
+// Complex factors: Re(E F) = Er Fr^T - Ei Fi^T and Im(E F) = Er Fi^T + Ei Fr^T
+// (F^T rows split as Fr, Fi), each group sum exact as in the real case; the
+// sign of -Ei is flipped on the bf16 fragment bits.  64 x 32 tile per CTA,
+// 8 warps of 16 x 16.
+__device__ __forceinline__ void neg_bf16x2(uint32_t* a) {
+#pragma unroll
+  for (int i = 0; i < 4; ++i) a[i] ^= 0x80008000u;
+}
+
+__global__ void __launch_bounds__(NT) k_schur_oz_c(LevelDev<zd> L, const BoxRec<zd>* recs) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const BoxRec<zd> R = recs[blockIdx.y];
+  const int c = R.c, kp = R.kp;
+  const int ntr = (c + 63) / 64, ntc = (c + 31) / 32;
+  if ((int)blockIdx.x >= ntr * ntc) return;
+  const int i0 = (blockIdx.x % ntr) * 64, j0 = (blockIdx.x / ntr) * 32;
+  const int SA = 2 * OZ_S * kp + 8;             // row: 8 real then 8 imaginary slices
+  uint16_t* As = reinterpret_cast<uint16_t*>(smraw);
+  uint16_t* Bs = As + 64 * SA;
+  __shared__ long long rowb[64], colb[32];
+  __shared__ int rexp[64], cexp[32];
+  const int nmax = L.nmax, g = L.g;
+  const long long nn = (long long)nmax * nmax;
+  const int tid = threadIdx.x;
+  const int chunks = 2 * kp;                    // 16-byte chunks per row
+  for (int e = tid; e < 64 * chunks; e += NT) {
+    const int row = e / chunks, ch = e % chunks;
+    uint4 va = make_uint4(0, 0, 0, 0);
+    if (i0 + row < c) va = reinterpret_cast<const uint4*>(R.Esl + (size_t)(i0 + row) * 2 * OZ_S * kp)[ch];
+    *reinterpret_cast<uint4*>(As + row * SA + ch * 8) = va;
+  }
+  for (int e = tid; e < 32 * chunks; e += NT) {
+    const int row = e / chunks, ch = e % chunks;
+    uint4 vb = make_uint4(0, 0, 0, 0);
+    if (j0 + row < c) vb = reinterpret_cast<const uint4*>(R.Fsl + (size_t)(j0 + row) * 2 * OZ_S * kp)[ch];
+    *reinterpret_cast<uint4*>(Bs + row * SA + ch * 8) = vb;
+  }
+  if (tid < 64) {
+    const int i = i0 + tid;
+    if (i < c) {
+      const int cm = R.cmap[i], s = cm >> 16, pos = cm & 0xffff;
+      const int u = nbr_box(R.box, g, s % 3 - 1, s / 3 - 1);
+      rowb[tid] = (long long)u * 25 * nn + pos - (long long)((s / 3) * 5 + s % 3) * nn;
+      rexp[tid] = R.Eexp[i];
+    }
+  } else if (tid < 96) {
+    const int j = j0 + tid - 64;
+    if (j < c) {
+      const int cm = R.cmap[j], s = cm >> 16, pos = cm & 0xffff;
+      colb[tid - 64] = (long long)((s / 3) * 5 + s % 3 + 12) * nn + (long long)pos * nmax;
+      cexp[tid - 64] = R.Fexp[j];
+    }
+  }
+  __syncthreads();
+  const int warp = tid >> 5, lane = tid & 31, gq = lane >> 2, t4 = lane & 3;
+  const int m0 = (warp >> 1) * 16, n0 = (warp & 1) * 16;
+  const int a_row = lane & 15, a_k = (lane >> 4) * 8;
+  const int b_row = ((lane >> 4) << 3) + (lane & 7), b_k = ((lane >> 3) & 1) * 8;
+  long long Wr[2][4], Wi[2][4];
+#pragma unroll
+  for (int ni = 0; ni < 2; ++ni)
+#pragma unroll
+    for (int e = 0; e < 4; ++e) { Wr[ni][e] = 0; Wi[ni][e] = 0; }
+  for (int u = 0; u < OZ_S; ++u) {
+    float cr[2][4], ci[2][4];
+#pragma unroll
+    for (int ni = 0; ni < 2; ++ni)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) { cr[ni][e] = 0.f; ci[ni][e] = 0.f; }
+    for (int p = 0; p <= u; ++p) {
+      const uint16_t* Ar = As + p * kp;
+      const uint16_t* Ai = As + (OZ_S + p) * kp;
+      const uint16_t* Br = Bs + (u - p) * kp;
+      const uint16_t* Bi = Bs + (OZ_S + u - p) * kp;
+      for (int kk = 0; kk < kp; kk += 16) {
+        uint32_t ar[4], ai[4], br[4], bi[4];
+        ldsm_x4(ar, Ar + (m0 + a_row) * SA + kk + a_k);
+        ldsm_x4(ai, Ai + (m0 + a_row) * SA + kk + a_k);
+        ldsm_x4(br, Br + (n0 + b_row) * SA + kk + b_k);
+        ldsm_x4(bi, Bi + (n0 + b_row) * SA + kk + b_k);
+#pragma unroll
+        for (int ni = 0; ni < 2; ++ni) {
+          mma_bf16(cr[ni], ar, br + 2 * ni);
+          mma_bf16(ci[ni], ar, bi + 2 * ni);
+          mma_bf16(ci[ni], ai, br + 2 * ni);
+        }
+        neg_bf16x2(ai);
+#pragma unroll
+        for (int ni = 0; ni < 2; ++ni) mma_bf16(cr[ni], ai, bi + 2 * ni);
+      }
+    }
+    const int sh = 39 - OZ_BITS * u;
+#pragma unroll
+    for (int ni = 0; ni < 2; ++ni)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const long long gr = (long long)__float2int_rn(cr[ni][e]);
+        const long long gi = (long long)__float2int_rn(ci[ni][e]);
+        if (sh >= 0) {
+          Wr[ni][e] += gr << sh;
+          Wi[ni][e] += gi << sh;
+        } else {
+          Wr[ni][e] += (gr + (1LL << (-sh - 1))) >> (-sh);
+          Wi[ni][e] += (gi + (1LL << (-sh - 1))) >> (-sh);
+        }
+      }
+  }
+#pragma unroll
+  for (int ni = 0; ni < 2; ++ni)
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int row = m0 + gq + (e >= 2 ? 8 : 0);
+      const int col = n0 + ni * 8 + 2 * t4 + (e & 1);
+      if (i0 + row < c && j0 + col < c) {
+        const double s = pow2(rexp[row] + cexp[col] - 53);
+        zd* ptr = L.blk + rowb[row] + colb[col];
+        const zd o = *ptr;
+        *ptr = zd{o.x - (double)Wr[ni][e] * s, o.y - (double)Wi[ni][e] * s};
+      }
+    }
 }
 
 // ------------------------------------------------------------------ merge (Section 2.4)
@@ -1830,13 +1988,14 @@ rss_status factor_impl(const rss_tree* tree, const rss_params* prm, cudaStream_t
       const int nrec = (int)recs.size();
       // tensor-core Schur update: real factors with r <= 96 (the slices of a
       // 64-row tile of E and of F^T must fit in shared memory)
-      const bool oz = sizeof(T) == sizeof(double) && prm->schur_path == 0 && max_r <= 96;
+      const bool oz = prm->schur_path == 0 && max_r <= (sizeof(T) == sizeof(double) ? 96 : 64);
+      const int ns = sizeof(T) == sizeof(double) ? OZ_S : 2 * OZ_S;   // slices per row
       int kp_max = 0;
       if (oz) {
         size_t bytes = 0;
         for (const BoxRec<T>& R : recs) {
           const int kp = (R.r + 15) & ~15;
-          bytes += 2 * ((size_t)R.c * OZ_S * kp * sizeof(uint16_t) + 256) + 2 * ((size_t)R.c * sizeof(int) + 256);
+          bytes += 2 * ((size_t)R.c * ns * kp * sizeof(uint16_t) + 256) + 2 * ((size_t)R.c * sizeof(int) + 256);
         }
         if (!gb_oz.ensure(bytes)) {
           rss_set_error("rss_factor: device workspace allocation failed");
@@ -1851,8 +2010,8 @@ rss_status factor_impl(const rss_tree* tree, const rss_params* prm, cudaStream_t
         for (BoxRec<T>& R : recs) {
           R.kp = (R.r + 15) & ~15;
           kp_max = std::max(kp_max, R.kp);
-          R.Esl = reinterpret_cast<uint16_t*>(take((size_t)R.c * OZ_S * R.kp * sizeof(uint16_t)));
-          R.Fsl = reinterpret_cast<uint16_t*>(take((size_t)R.c * OZ_S * R.kp * sizeof(uint16_t)));
+          R.Esl = reinterpret_cast<uint16_t*>(take((size_t)R.c * ns * R.kp * sizeof(uint16_t)));
+          R.Fsl = reinterpret_cast<uint16_t*>(take((size_t)R.c * ns * R.kp * sizeof(uint16_t)));
           R.Eexp = reinterpret_cast<int*>(take((size_t)R.c * sizeof(int)));
           R.Fexp = reinterpret_cast<int*>(take((size_t)R.c * sizeof(int)));
         }
@@ -1893,6 +2052,11 @@ rss_status factor_impl(const rss_tree* tree, const rss_params* prm, cudaStream_t
           const size_t smem = 2 * 64 * (size_t)(OZ_S * kp_max + 8) * sizeof(uint16_t);
           RSS_CUDA(cudaFuncSetAttribute(k_schur_oz, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
           k_schur_oz<<<dim3(ntile * ntile, nrec), NT, smem, st>>>(cur.d, d_recs);
+        } else {
+          const size_t smem = (64 + 32) * (size_t)(2 * OZ_S * kp_max + 8) * sizeof(uint16_t);
+          RSS_CUDA(cudaFuncSetAttribute(k_schur_oz_c, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+          const int ntc = (max_c + 31) / 32;
+          k_schur_oz_c<<<dim3(ntile * ntc, nrec), NT, smem, st>>>(cur.d, d_recs);
         }
       } else {
         k_schur<T><<<dim3(ntile * ntile, nrec), NT, 0, st>>>(cur.d, d_recs);

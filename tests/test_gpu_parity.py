@@ -286,3 +286,24 @@ def test_cluster_id_matches_single_cta_id(P, kind):
     bvec = W.gaussian_rhs(side * side, 2, spec.is_complex, 31)
     x = gpu_solve(P, fc, bvec)
     assert rel(x, orss.solve(fac, bvec)) < 1e-9
+
+
+def test_tensor_core_schur_complex_matches_fp64_schur(P):
+    """Complex factors: the split-digit tensor-core Schur update agrees with the FP64 kernel."""
+    side, eps = 128, 1e-6
+    pts = W.grid_points(side)
+    tree = P.rss_build_tree(pts, 64)
+    f_tc = P.rss_factor(tree, kind=1, eps=eps, h=1 / side, kappa=25.0)
+    f_64 = P.rss_factor(tree, kind=1, eps=eps, h=1 / side, kappa=25.0, schur_fp64=True)
+    for g in (16, 8, 4):
+        assert np.array_equal(P.rss_level_ranks(f_tc, g), P.rss_level_ranks(f_64, g))
+    for g, box in ((16, 0), (16, 137), (8, 27), (4, 5)):
+        a, b = P.rss_box_record(f_tc, g, box), P.rss_box_record(f_64, g, box)
+        assert np.array_equal(a["S"], b["S"]) and np.array_equal(a["C"], b["C"])
+        for key in ("T", "E", "F", "LU"):
+            assert rel(a[key], b[key]) < rec_tol(eps), (g, box, key)
+    bvec = W.gaussian_rhs(side * side, 2, True, 23)
+    x_tc, x_64 = gpu_solve(P, f_tc, bvec), gpu_solve(P, f_64, bvec)
+    assert rel(x_tc, x_64) < 1e-12
+    spec = KernelSpec("helmholtz", h=1 / side, kappa=25.0)
+    assert relres(pts, spec, x_tc, bvec) <= 10 * eps
