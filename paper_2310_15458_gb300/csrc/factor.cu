@@ -21,6 +21,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <memory>
+#include <type_traits>
 #include <vector>
 
 #include <cooperative_groups.h>
@@ -746,47 +747,79 @@ template <typename T> struct ElimArgs {
   int smem_cap;             // scalars of dynamic shared memory available
 };
 
-constexpr int EP = 64;      // rows of C per panel
+constexpr int PKC = 16;     // rows of a panel product's right operand staged per chunk
 
-// Register-blocked panel product on shared memory: out(i, j) = init(i, j) +
-// sum_l A[l][i] * B(l, j) for the EP x r panel; thread (tx, ty) owns rows
-// tx + 16 a (a < 4) and columns ty + 16 b (b < NB).  A is [l][EP] in shared
-// memory, B(l, j) is read through bfun.  TRI: B is upper triangular (B(l, j) = 0
-// for l > j), so each thread stops at its last column.
-template <typename T, int NB, bool TRI, typename BF, typename IF, typename OF>
-__device__ __forceinline__ void panel_gemm(const T* __restrict__ A, int nl, int rows, int r, BF bfun, IF init,
+// Register-blocked panel product: out(i, j) = init(i, j) + sum_l A_l[i] B(l, j)
+// for the rows i < rows of a panel of 16 MA rows and the columns j of the block
+// [j0, min(r, j0 + 16 NB)).  arow(l) points at row l of the left operand (16 MA
+// scalars in shared memory); B(l, j) is read through bfun in chunks of PKC rows
+// staged in Bs (PKC x (16 NB + 1)).  Thread (tx, ty) owns rows tx + 16 a and
+// columns j0 + ty + 16 b.  TRI: B is upper triangular (B(l, j) = 0 for l > j).
+// Every thread of the block calls it; out() runs after a barrier, so it may
+// overwrite what init() reads.
+template <typename T, int MA, int NB, bool TRI, typename AR, typename BF, typename IF, typename OF>
+__device__ __forceinline__ void panel_gemm(AR arow, int nl, int rows, int j0, int r, T* Bs, BF bfun, IF init,
                                            OF out) {
+  constexpr int RB = 16 * NB + 1;
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  T acc[4][NB];
+  T acc[MA][NB];
 #pragma unroll
-  for (int a = 0; a < 4; ++a)
+  for (int a = 0; a < MA; ++a)
 #pragma unroll
     for (int b = 0; b < NB; ++b) {
-      const int i = tx + 16 * a, j = ty + 16 * b;
+      const int i = tx + 16 * a, j = j0 + ty + 16 * b;
       acc[a][b] = (i < rows && j < r) ? init(i, j) : zero<T>();
     }
-  const int lend = TRI ? min(nl, ty + 16 * (NB - 1) + 1) : nl;
-  for (int l = 0; l < lend; ++l) {
-    T av[4], bv[NB];
-#pragma unroll
-    for (int a = 0; a < 4; ++a) av[a] = A[l * EP + tx + 16 * a];
-#pragma unroll
-    for (int b = 0; b < NB; ++b) {
-      const int j = ty + 16 * b;
-      bv[b] = (j < r && (!TRI || l <= j)) ? bfun(l, j) : zero<T>();
+  const int jw = min(16 * NB, r - j0);                              // columns in the block
+  const int lend = TRI ? min(nl, j0 + jw) : nl;                     // rows of B that can be nonzero
+  const int tend = TRI ? min(lend, j0 + ty + 16 * (NB - 1) + 1) : lend;   // this thread's last row
+  for (int l0 = 0; l0 < lend; l0 += PKC) {
+    __syncthreads();
+    for (int e = threadIdx.x; e < PKC * 16 * NB; e += blockDim.x) {
+      const int ll = e % PKC, jj = e / PKC, l = l0 + ll, j = j0 + jj;
+      Bs[ll * RB + jj] = (l < lend && jj < jw && (!TRI || l <= j)) ? bfun(l, j) : zero<T>();
     }
+    __syncthreads();
+    const int le = min(PKC, tend - l0);
+    for (int ll = 0; ll < le; ++ll) {
+      const T* ar = arow(l0 + ll);
+      T av[MA], bv[NB];
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
+      for (int a = 0; a < MA; ++a) av[a] = ar[tx + 16 * a];
 #pragma unroll
-      for (int b = 0; b < NB; ++b) acc[a][b] = mad(acc[a][b], av[a], bv[b]);
+      for (int b = 0; b < NB; ++b) bv[b] = Bs[ll * RB + ty + 16 * b];
+#pragma unroll
+      for (int a = 0; a < MA; ++a)
+#pragma unroll
+        for (int b = 0; b < NB; ++b) acc[a][b] = mad(acc[a][b], av[a], bv[b]);
+    }
   }
+  __syncthreads();
 #pragma unroll
-  for (int a = 0; a < 4; ++a)
+  for (int a = 0; a < MA; ++a)
 #pragma unroll
     for (int b = 0; b < NB; ++b) {
-      const int i = tx + 16 * a, j = ty + 16 * b;
+      const int i = tx + 16 * a, j = j0 + ty + 16 * b;
       if (i < rows && j < r) out(i, j, acc[a][b]);
     }
+}
+
+// Calls f(std::integral_constant<int, NB>) for every 16 NBMAX-column block of
+// [0, r), NB = the block's column groups of 16.
+template <int NBMAX, typename F> __device__ __forceinline__ void for_col_blocks(int r, F f) {
+  for (int j0 = 0; j0 < r; j0 += 16 * NBMAX) {
+    const int nb = (min(r - j0, 16 * NBMAX) + 15) / 16;
+    switch (nb) {
+      case 1: f(j0, std::integral_constant<int, 1>{}); break;
+      case 2: if constexpr (NBMAX >= 2) f(j0, std::integral_constant<int, 2>{}); break;
+      case 3: if constexpr (NBMAX >= 3) f(j0, std::integral_constant<int, 3>{}); break;
+      case 4: if constexpr (NBMAX >= 4) f(j0, std::integral_constant<int, 4>{}); break;
+      case 5: if constexpr (NBMAX >= 5) f(j0, std::integral_constant<int, 5>{}); break;
+      case 6: if constexpr (NBMAX >= 6) f(j0, std::integral_constant<int, 6>{}); break;
+      case 7: if constexpr (NBMAX >= 7) f(j0, std::integral_constant<int, 7>{}); break;
+      default: if constexpr (NBMAX >= 8) f(j0, std::integral_constant<int, 8>{}); break;
+    }
+  }
 }
 
 // Complex rows: real and imaginary parts share the row scale (the largest |Re|,
@@ -827,7 +860,7 @@ __device__ void oz_split_row(const zd* __restrict__ src, int stride, int r, int 
 
 // ------------------------------------------------------------------ sparsify + LU (Eqs. 7, 8)
 // k_elim_lu (one CTA per box): C map, X_SR, X_RR, P X_RR = L U, U^{-1}, L^{-1}
-// and L^{-1} P.  k_elim_panels (one CTA per 64-row panel of C): X_CR, X_RC and
+// and L^{-1} P.  k_elim_panels (one CTA per 16-, 32- or 64-row panel of C): X_CR, X_RC and
 // E = X_CR U^{-1}, F = L^{-1} P X_RC (kept as F^T), from shared-memory panels.
 // Boxes too large for the panel kernel's shared memory get E and F here, row by
 // row from global memory.
@@ -840,10 +873,14 @@ template <typename T> __global__ void __launch_bounds__(NT, 4) k_elim_lu(ElimArg
   const int* perm = a.perm_in + (size_t)a.cls_idx[blockIdx.x] * nmax;
   const T* Tw = a.T_ws + (size_t)a.cls_idx[blockIdx.x] * nn;
   const int tid = threadIdx.x, bs = blockDim.x, lane = tid & 31, warp = tid >> 5;
-  const bool onchip = k * r + 2 * r * r <= a.smem_cap;
-  T* Ts = onchip ? reinterpret_cast<T*>(smraw) : R.Tm;
-  T* LU = onchip ? Ts + (size_t)k * r : R.LU;
-  T* Wb = onchip ? LU + (size_t)r * r : nullptr;   // scratch for building the inverses
+  // on chip: LU (r x r), then one region holding T until X_RR is formed and
+  // the inverses while they are built
+  int* sperm = reinterpret_cast<int*>(smraw);   // 2 r: exchange order and its inverse
+  unsigned char* smT = smraw + ((2 * r * sizeof(int) + 15) & ~size_t(15));
+  const bool onchip = (size_t)r * r + (size_t)max(k * r, r * r) <= (size_t)a.smem_cap;
+  T* LU = onchip ? reinterpret_cast<T*>(smT) : R.LU;
+  T* Ts = onchip ? LU + (size_t)r * r : R.Tm;
+  T* Wb = onchip ? Ts : nullptr;
   __shared__ int nb[9], coff[10], s_piv, s_zero, ord[9];
   if (tid == 0) {
     const int o9[9] = {4, 0, 1, 2, 3, 5, 6, 7, 8};
@@ -931,10 +968,11 @@ template <typename T> __global__ void __launch_bounds__(NT, 4) k_elim_lu(ElimArg
     }
     __syncthreads();
   }
-  // U^{-1}, L^{-1} and L^{-1} P, one column per thread (built in shared memory
-  // when it fits, then copied out)
-  for (int which = 0; which < 3; ++which) {
-    T* dst = which == 0 ? R.Ui : which == 1 ? R.Li : R.LiP;
+  // U^{-1} and L^{-1}, one column per thread (built in shared memory when it
+  // fits, then copied out); L^{-1} P is L^{-1} with its columns permuted:
+  // P e_j = e_{pos(j)} for pos the inverse of the exchange order sig (P v = v[sig])
+  for (int which = 0; which < 2; ++which) {
+    T* dst = which == 0 ? R.Ui : R.Li;
     T* W = onchip ? Wb : dst;
     for (int j = tid; j < r; j += bs) {
       T* w = W + (size_t)j * r;
@@ -945,28 +983,36 @@ template <typename T> __global__ void __launch_bounds__(NT, 4) k_elim_lu(ElimArg
           for (int l = i + 1; l <= j; ++l) x = msb(x, LU[i + (size_t)l * r], w[l]);
           w[i] = dv(x, LU[i + (size_t)i * r]);
         }
-      } else {
-        int pos = j;                  // L^{-1} e_j, or L^{-1} P e_j: e_j moved by the exchanges
-        if (which == 2)
-          for (int i = 0; i < r; ++i) {
-            const int p = R.piv[i];
-            if (pos == i) pos = p;
-            else if (pos == p) pos = i;
-          }
-        for (int i = 0; i < pos; ++i) w[i] = zero<T>();
-        w[pos] = from_re<T>(1.0);
-        for (int i = pos + 1; i < r; ++i) {
+      } else {                        // L^{-1} e_j
+        for (int i = 0; i < j; ++i) w[i] = zero<T>();
+        w[j] = from_re<T>(1.0);
+        for (int i = j + 1; i < r; ++i) {
           T x = zero<T>();
-          for (int l = pos; l < i; ++l) x = msb(x, LU[i + (size_t)l * r], w[l]);
+          for (int l = j; l < i; ++l) x = msb(x, LU[i + (size_t)l * r], w[l]);
           w[i] = x;
         }
       }
     }
-    if (onchip) {
-      __syncthreads();
+    __syncthreads();
+    if (onchip)
       for (int e = tid; e < r * r; e += bs) dst[e] = Wb[e];
+    if (which == 1) {
+      if (tid == 0) {
+        for (int i = 0; i < r; ++i) sperm[i] = i;
+        for (int i = 0; i < r; ++i) {
+          const int p = R.piv[i], t = sperm[i];
+          sperm[i] = sperm[p];
+          sperm[p] = t;
+        }
+        for (int i = 0; i < r; ++i) sperm[r + sperm[i]] = i;
+      }
       __syncthreads();
+      for (int e = tid; e < r * r; e += bs) {
+        const int i = e % r, j = e / r;
+        R.LiP[e] = W[i + (size_t)sperm[r + j] * r];
+      }
     }
+    __syncthreads();
   }
   if (onchip)
     for (int e = tid; e < r * r; e += bs) R.LU[e] = LU[e];
@@ -982,7 +1028,7 @@ template <typename T> __global__ void __launch_bounds__(NT, 4) k_elim_lu(ElimArg
       T x = Aub[(size_t)rj * nmax + pos];
       T y = Abu[(size_t)pos * nmax + rj];
       for (int q = 0; q < k; ++q) {
-        const T t = Ts[q + (size_t)j * k];
+        const T t = R.Tm[q + (size_t)j * k];
         x = msb(x, Aub[(size_t)perm[q] * nmax + pos], t);
         y = msbc(y, t, Abu[(size_t)pos * nmax + perm[q]]);
       }
@@ -1028,63 +1074,77 @@ template <typename T> __global__ void __launch_bounds__(NT, 4) k_elim_lu(ElimArg
   if (tid == 0) L.nact[B] = k;
 }
 
-template <typename T, int NB>
+// One panel of 16 MA rows of C.  The rows of A(u, B) (columns of B in pivot
+// order) sit in shared memory as [column][row]; X_CR overwrites the R columns in
+// place, then E = X_CR U^{-1} goes to global memory; the same buffer then takes
+// the columns of A(B, u) for X_RC and F^T = (L^{-1} P_R X_RC)^T.  The right
+// operands (T, U^{-1}, L^{-1}) are staged from global memory in chunks, so any
+// rank fits.
+template <typename T, int MA, int NBMAX>
 __device__ void elim_panel_body(const ElimArgs<T>& a, const BoxRec<T>& R, unsigned char* smraw, int p0, int rows) {
+  constexpr int EPR = 16 * MA;
   const LevelDev<T>& L = a.L;
   const int nmax = L.nmax, g = L.g, B = R.box, k = R.k, r = R.r, c = R.c, n = k + r;
   const size_t nn = (size_t)nmax * nmax;
   const int* perm = a.perm_in + (size_t)a.cls_idx[blockIdx.y] * nmax;
   const int tid = threadIdx.x, bs = blockDim.x;
-  T* Ts = reinterpret_cast<T*>(smraw);     // k x r
-  T* Ms = Ts + (size_t)k * r;              // r x r: U^{-1}, then L^{-1}
-  T* As = Ms + (size_t)r * r;              // n x EP
-  T* Xs = As + (size_t)n * EP;             // r x EP
-  int* sinv = reinterpret_cast<int*>(Xs + (size_t)r * EP);
-  for (int e = tid; e < k * r; e += bs) Ts[e] = R.Tm[e];
-  for (int e = tid; e < r * r; e += bs) Ms[e] = R.Ui[e];
+  T* As = reinterpret_cast<T*>(smraw);                 // n x EPR
+  T* Bs = As + (size_t)n * EPR;                        // PKC x (16 NBMAX + 1)
+  int* sig = reinterpret_cast<int*>(Bs + PKC * (16 * NBMAX + 1));   // r
+  const T* __restrict__ Tm = R.Tm;
+  const T* __restrict__ Ui = R.Ui;
+  const T* __restrict__ Li = R.Li;
   for (int e = tid; e < rows * n; e += bs) {   // rows of A(u, B), columns of B in pivot order
     const int ii = e % rows, col = e / rows;
     const int cm = R.cmap[p0 + ii], s = cm >> 16, pos = cm & 0xffff;
     const int u = nbr_box(B, g, s % 3 - 1, s / 3 - 1);
-    As[col * EP + ii] = L.blk[((size_t)u * 25 + off_index(u, B, g)) * nn + (size_t)perm[col] * nmax + pos];
+    As[col * EPR + ii] = L.blk[((size_t)u * 25 + off_index(u, B, g)) * nn + (size_t)perm[col] * nmax + pos];
   }
-  if (tid == 0) {   // P_R v = v[sigma]: the row exchanges applied to the identity
-    int* sig = sinv + r;
+  if (tid == 0) {   // P_R v = v[sig]: the row exchanges applied to the identity
     for (int i = 0; i < r; ++i) sig[i] = i;
     for (int i = 0; i < r; ++i) {
       const int p = R.piv[i], t = sig[i];
       sig[i] = sig[p];
       sig[p] = t;
     }
-    for (int i = 0; i < r; ++i) sinv[sig[i]] = i;
   }
   __syncthreads();
-  // X_CR = A_CR - A_CS T, then E = X_CR U^{-1}
-  panel_gemm<T, NB, false>(As, k, rows, r, [&](int q, int j) { return -Ts[q + (size_t)j * k]; },
-                           [&](int i, int j) { return As[(k + j) * EP + i]; },
-                           [&](int i, int j, T v) { Xs[j * EP + i] = v; });
+  auto plain = [&](int l) { return As + (size_t)l * EPR; };
+  auto rcol = [&](int l) { return As + (size_t)(k + l) * EPR; };
+  // X_CR = A_CR - A_CS T, in place
+  for_col_blocks<NBMAX>(r, [&](int j0, auto nbc) {
+    panel_gemm<T, MA, decltype(nbc)::value, false>(
+        plain, k, rows, j0, r, Bs, [&](int q, int j) { return -Tm[q + (size_t)j * k]; },
+        [&](int i, int j) { return As[(k + j) * EPR + i]; }, [&](int i, int j, T v) { As[(k + j) * EPR + i] = v; });
+  });
+  // E = X_CR U^{-1}
+  for_col_blocks<NBMAX>(r, [&](int j0, auto nbc) {
+    panel_gemm<T, MA, decltype(nbc)::value, true>(
+        rcol, r, rows, j0, r, Bs, [&](int l, int j) { return Ui[l + (size_t)j * r]; },
+        [&](int, int) { return zero<T>(); }, [&](int i, int j, T v) { R.E[p0 + i + (size_t)j * c] = v; });
+  });
   __syncthreads();
-  panel_gemm<T, NB, true>(Xs, r, rows, r, [&](int l, int j) { return Ms[l + (size_t)j * r]; },
-                          [&](int, int) { return zero<T>(); },
-                          [&](int i, int j, T v) { R.E[p0 + i + (size_t)j * c] = v; });
-  __syncthreads();
-  for (int e = tid; e < r * r; e += bs) Ms[e] = R.Li[e];
   for (int e = tid; e < rows * n; e += bs) {   // columns of A(B, u), rows of B in pivot order
     const int row = e % n, ii = e / n;
     const int cm = R.cmap[p0 + ii], s = cm >> 16, pos = cm & 0xffff;
     const int u = nbr_box(B, g, s % 3 - 1, s / 3 - 1);
-    As[row * EP + ii] = L.blk[((size_t)B * 25 + off_index(B, u, g)) * nn + (size_t)pos * nmax + perm[row]];
+    As[row * EPR + ii] = L.blk[((size_t)B * 25 + off_index(B, u, g)) * nn + (size_t)pos * nmax + perm[row]];
   }
   __syncthreads();
-  // X_RC^T = A_RC^T - A_SC^T conj(T), columns placed in the order of P_R
-  panel_gemm<T, NB, false>(As, k, rows, r, [&](int q, int j) { return -cj(Ts[q + (size_t)j * k]); },
-                           [&](int i, int j) { return As[(k + j) * EP + i]; },
-                           [&](int i, int j, T v) { Xs[sinv[j] * EP + i] = v; });
-  __syncthreads();
-  // F^T = (P_R X_RC)^T (L_R^{-1})^T, (L^{-1})^T upper triangular
-  panel_gemm<T, NB, true>(Xs, r, rows, r, [&](int l, int j) { return Ms[j + (size_t)l * r]; },
-                          [&](int, int) { return zero<T>(); },
-                          [&](int i, int j, T v) { R.Ft[p0 + i + (size_t)j * c] = v; });
+  // X_RC^T = A_RC^T - A_SC^T conj(T), in place
+  for_col_blocks<NBMAX>(r, [&](int j0, auto nbc) {
+    panel_gemm<T, MA, decltype(nbc)::value, false>(
+        plain, k, rows, j0, r, Bs, [&](int q, int j) { return -cj(Tm[q + (size_t)j * k]); },
+        [&](int i, int j) { return As[(k + j) * EPR + i]; }, [&](int i, int j, T v) { As[(k + j) * EPR + i] = v; });
+  });
+  // F^T = (P_R X_RC)^T (L_R^{-1})^T: row l of P_R X_RC is row sig[l] of X_RC;
+  // (L^{-1})^T is upper triangular
+  auto prow = [&](int l) { return As + (size_t)(k + sig[l]) * EPR; };
+  for_col_blocks<NBMAX>(r, [&](int j0, auto nbc) {
+    panel_gemm<T, MA, decltype(nbc)::value, true>(
+        prow, r, rows, j0, r, Bs, [&](int l, int j) { return Li[j + (size_t)l * r]; },
+        [&](int, int) { return zero<T>(); }, [&](int i, int j, T v) { R.Ft[p0 + i + (size_t)j * c] = v; });
+  });
   __syncthreads();
   if (R.Esl != nullptr) {   // digit slices of this panel's rows of E and F^T
     const int ns = sizeof(T) == sizeof(double) ? OZ_S : 2 * OZ_S;
@@ -1097,26 +1157,20 @@ __device__ void elim_panel_body(const ElimArgs<T>& a, const BoxRec<T>& R, unsign
   }
 }
 
-template <typename T> size_t panel_smem_bytes(int k, int r) {
-  return sizeof(T) * ((size_t)k * r + (size_t)r * r + (size_t)(k + r) * EP + (size_t)r * EP) +
-         2 * sizeof(int) * (size_t)r;
+template <typename T> constexpr int panel_nbmax() { return sizeof(T) == sizeof(double) ? 6 : 4; }
+
+// shared memory of one panel CTA of 16 MA rows for a box with n = k + r points
+template <typename T> size_t panel_smem_bytes(int MA, int n, int r) {
+  return sizeof(T) * ((size_t)n * 16 * MA + (size_t)PKC * (16 * panel_nbmax<T>() + 1)) + sizeof(int) * (size_t)r;
 }
 
-template <typename T> __global__ void __launch_bounds__(NT, 2) k_elim_panels(ElimArgs<T> a) {
+template <typename T, int MA> __global__ void __launch_bounds__(NT, 2) k_elim_panels(ElimArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const BoxRec<T> R = a.recs[blockIdx.y];
   if (!R.panels) return;
-  const int p0 = blockIdx.x * EP;
+  const int p0 = blockIdx.x * 16 * MA;
   if (p0 >= R.c) return;
-  const int rows = min(EP, R.c - p0);
-  switch ((R.r + 15) / 16) {
-    case 1: elim_panel_body<T, 1>(a, R, smraw, p0, rows); break;
-    case 2: elim_panel_body<T, 2>(a, R, smraw, p0, rows); break;
-    case 3: elim_panel_body<T, 3>(a, R, smraw, p0, rows); break;
-    case 4: elim_panel_body<T, 4>(a, R, smraw, p0, rows); break;
-    case 5: elim_panel_body<T, 5>(a, R, smraw, p0, rows); break;
-    default: elim_panel_body<T, 6>(a, R, smraw, p0, rows); break;
-  }
+  elim_panel_body<T, MA, panel_nbmax<T>()>(a, R, smraw, p0, min(16 * MA, R.c - p0));
 }
 
 // ------------------------------------------------------------------ Schur update A_CC -= E F
@@ -1935,7 +1989,6 @@ rss_status factor_impl(const rss_tree* tree, const rss_params* prm, cudaStream_t
       std::vector<BoxRec<T>> recs;
       std::vector<int> clsidx;
       int max_k = 0, max_r = 0, max_c = 0;
-      size_t pan_max = 0;
       for (int q = 0; q < nb; ++q) {
         const int B = boxes[q], bx = B % g, by = B / g;
         const int k = hk[q], n = cur.n[B], r = n - k;
@@ -1957,11 +2010,6 @@ rss_status factor_impl(const rss_tree* tree, const rss_params* prm, cudaStream_t
         R.LiP = static_cast<T*>(f->arena.get(sizeof(T) * (size_t)r * r));
         R.Ui = static_cast<T*>(f->arena.get(sizeof(T) * (size_t)r * r));
         R.Li = static_cast<T*>(f->arena.get(sizeof(T) * (size_t)r * r));
-        {
-          const size_t pb = panel_smem_bytes<T>(k, r);
-          R.panels = (r <= 96 && pb <= 200 * 1024) ? 1 : 0;
-          if (R.panels) pan_max = std::max(pan_max, pb);
-        }
         R.E = static_cast<T*>(f->arena.get(sizeof(T) * (size_t)c * r));
         R.Ft = static_cast<T*>(f->arena.get(sizeof(T) * (size_t)c * r));
         R.idxR = static_cast<int*>(f->arena.get(sizeof(int) * r));
@@ -1986,6 +2034,21 @@ rss_status factor_impl(const rss_tree* tree, const rss_params* prm, cudaStream_t
         if (cur.n[boxes[q]] - hk[q] > 0) cur.nact[boxes[q]] = hk[q];
       if (recs.empty()) continue;
       const int nrec = (int)recs.size();
+      // panel kernel shape: the widest panel (16 MA rows) whose shared memory
+      // leaves room for two CTAs per SM; boxes beyond 200 KB take the row path
+      int pan_ma = 1;
+      size_t pan_max = 0;
+      {
+        int max_n = 0;
+        for (const BoxRec<T>& R : recs) max_n = std::max(max_n, R.k + R.r);
+        for (int ma : {4, 2, 1})
+          if (panel_smem_bytes<T>(ma, max_n, max_r) <= 110 * 1024) { pan_ma = ma; break; }
+        for (BoxRec<T>& R : recs) {
+          const size_t pb = panel_smem_bytes<T>(pan_ma, R.k + R.r, R.r);
+          R.panels = pb <= 200 * 1024 ? 1 : 0;
+          if (R.panels) pan_max = std::max(pan_max, pb);
+        }
+      }
       // tensor-core Schur update: real factors with r <= 96 (the slices of a
       // 64-row tile of E and of F^T must fit in shared memory)
       const bool oz = prm->schur_path == 0 && max_r <= (sizeof(T) == sizeof(double) ? 96 : 64);
@@ -2029,17 +2092,26 @@ rss_status factor_impl(const rss_tree* tree, const rss_params* prm, cudaStream_t
       ea.T_ws = d_Tws;
       ea.err = d_err;
       // shared memory of the per-box kernel: T and the LU of the largest box that fits
-      const size_t want = sizeof(T) * ((size_t)max_k * max_r + 2 * (size_t)max_r * max_r);
-      const size_t ecap = std::min<size_t>(want, 160 * 1024);
-      ea.smem_cap = (int)(ecap / sizeof(T));
+      const size_t ints = (2 * (size_t)max_r * sizeof(int) + 15) & ~size_t(15);
+      const size_t want =
+          sizeof(T) * ((size_t)max_r * max_r + std::max((size_t)max_k * max_r, (size_t)max_r * max_r)) + ints;
+      const size_t ecap = std::min<size_t>(want, 200 * 1024);
+      ea.smem_cap = (int)((ecap - ints) / sizeof(T));
       RSS_CUDA(cudaFuncSetAttribute(k_elim_lu<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ecap));
       evs.emplace_back(1, std::make_unique<Ev>());
       evs.back().second->start(st);
       k_elim_lu<T><<<nrec, NT, ecap, st>>>(ea);
       RSS_LAUNCHED();
       if (pan_max > 0) {
-        RSS_CUDA(cudaFuncSetAttribute(k_elim_panels<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pan_max));
-        k_elim_panels<T><<<dim3((max_c + EP - 1) / EP, nrec), NT, pan_max, st>>>(ea);
+        auto launch_panels = [&](auto kern, int rows) -> cudaError_t {
+          cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pan_max);
+          if (e != cudaSuccess) return e;
+          kern<<<dim3((max_c + rows - 1) / rows, nrec), NT, pan_max, st>>>(ea);
+          return cudaGetLastError();
+        };
+        RSS_CUDA(pan_ma == 4   ? launch_panels(k_elim_panels<T, 4>, 64)
+                 : pan_ma == 2 ? launch_panels(k_elim_panels<T, 2>, 32)
+                               : launch_panels(k_elim_panels<T, 1>, 16));
         RSS_LAUNCHED();
         f->launches += 1;
       }
