@@ -73,11 +73,14 @@ typedef struct {
                                      diagonal) compress [A_MB; K_PB] only, which equals the
                                      full stack of Eq. 4 up to rounding; 1: always the full
                                      stack [A_MB; K_PB; A_BM^*; K_BP^*] */
-  int schur_path;                 /* 0: Schur update A_CC -= E F on the tensor cores where
-                                     it applies (real factors, r <= 112): E and F split into
-                                     eight 7-bit slices, exact integer products, FP64
-                                     recombination (accuracy of an FP64 product); 1: FP64
-                                     FMA kernel everywhere */
+  int schur_path;                 /* 0: the dense products of the elimination on the tensor
+                                     cores where they apply: the Schur update A_CC -= E F
+                                     (real factors with r <= 96, complex with r <= 64) and,
+                                     for real factors with n_B <= 128, E = A_CB W_E and
+                                     F^T = A_BC^T W_F; operands split into eight 7-bit
+                                     slices with row and column scales, exact integer
+                                     products, FP64 recombination (accuracy of an FP64
+                                     product); 1: FP64 FMA kernels everywhere */
   int id_cluster;                 /* colour classes with fewer boxes than the GPU has room for:
                                      0 spreads each box's ID over a thread-block cluster of
                                      up to 8 CTAs, > 0 caps the cluster size (1: one CTA per

@@ -699,6 +699,27 @@ template <typename T> __global__ void __launch_bounds__(NT_ID) k_id_cl(IdArgs<T>
   if (tid == 0) a.k_out[bi] = k;
 }
 
+// ------------------------------------------------------------------ tensor-core helpers
+__device__ __forceinline__ void mma_bf16(float* c, const uint32_t* a, const uint32_t* b) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+__device__ __forceinline__ void ldsm_x4(uint32_t* d, const void* smem_row) {
+  const unsigned addr = (unsigned)__cvta_generic_to_shared(smem_row);
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(d[0]), "=r"(d[1]), "=r"(d[2]), "=r"(d[3])
+               : "r"(addr));
+}
+
+// 2^e as a double for the normal range, from its bit pattern
+__device__ __forceinline__ double pow2(int e) {
+  return (e > -1023 && e < 1024) ? __longlong_as_double((long long)(e + 1023) << 52) : ldexp(1.0, e);
+}
+
 // ------------------------------------------------------------------ digit slices
 // A row x_0..x_{r-1} with max |x_l| = m 2^e (m in [0.5, 1)) is written as
 // x_l = 2^e sum_{p=0}^{OZ_S-1} d_{p,l} 2^{-7(p+1)}, with signed digits
@@ -1017,7 +1038,27 @@ template <typename T> __global__ void __launch_bounds__(NT, 4) k_elim_lu(ElimArg
   if (onchip)
     for (int e = tid; e < r * r; e += bs) R.LU[e] = LU[e];
   __syncthreads();
-  if (!R.panels) {
+  if (R.ozp) {
+    // W_E = [-T U^{-1}; U^{-1}] and W_F = [-(L^{-1} P T^*)^T; (L^{-1} P)^T], n x r, ld n:
+    // E = X_CR U^{-1} = A_CB W_E and F^T = (L^{-1} P X_RC)^T = A_BC^T W_F (Eqs. 7, 8)
+    const int n = k + r;
+    for (int e = tid; e < n * r; e += bs) {
+      const int l = e % n, j = e / n;
+      T we, wf;
+      if (l < k) {
+        we = zero<T>();
+        for (int m = 0; m <= j; ++m) we = msb(we, R.Tm[l + (size_t)m * k], R.Ui[m + (size_t)j * r]);
+        wf = zero<T>();
+        for (int m = 0; m < r; ++m) wf = msb(wf, R.LiP[j + (size_t)m * r], cj(R.Tm[l + (size_t)m * k]));
+      } else {
+        we = l - k <= j ? R.Ui[(l - k) + (size_t)j * r] : zero<T>();
+        wf = R.LiP[j + (size_t)(l - k) * r];
+      }
+      R.We[e] = we;
+      R.Wf[e] = wf;
+    }
+  }
+  if (!R.panels && !R.ozp) {
     // E and F^T row by row from global memory
     for (long long e = tid; e < (long long)c * r; e += bs) {
       const int i = (int)(e % c), j = (int)(e / c);
@@ -1167,10 +1208,162 @@ template <typename T> size_t panel_smem_bytes(int MA, int n, int r) {
 template <typename T, int MA> __global__ void __launch_bounds__(NT, 2) k_elim_panels(ElimArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const BoxRec<T> R = a.recs[blockIdx.y];
-  if (!R.panels) return;
+  if (!R.panels || R.ozp) return;
   const int p0 = blockIdx.x * 16 * MA;
   if (p0 >= R.c) return;
   elim_panel_body<T, MA, panel_nbmax<T>()>(a, R, smraw, p0, min(16 * MA, R.c - p0));
+}
+
+// ------------------------------------------------------------------ E and F on the tensor cores
+// One vector x_0..x_{len-1} (x_l = val(l)) shared by G consecutive lanes, cut
+// into OZ_S signed 7-bit digit slices as oz_split_row does: 2^e with e the
+// exponent of max |x_l|, x_l 2^(56-e) rounded to an integer, digits stored at
+// dst[p * ldd + l] for l < lenp (zeros past len).  Every lane of the warp calls
+// it (the maximum is a shuffle reduction); inactive groups pass len = 0 and
+// store = false.
+template <int G, typename VF>
+__device__ __forceinline__ void oz_split_vec(VF val, int len, int lenp, uint16_t* dst, int ldd, int* eout,
+                                             bool store) {
+  const int gl = threadIdx.x & (G - 1);
+  double mx = 0.0;
+  for (int l = gl; l < len; l += G) mx = fmax(mx, fabs(val(l)));
+#pragma unroll
+  for (int d = G / 2; d > 0; d >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, d));
+  if (!store) return;
+  int e = 0;
+  if (mx > 0.0) frexp(mx, &e);
+  if (gl == 0) *eout = e;
+  const double scale = ldexp(1.0, 56 - e);
+  for (int l = 2 * gl; l < lenp; l += 2 * G) {
+    long long X0 = l < len ? llrint(val(l) * scale) : 0;
+    long long X1 = l + 1 < len ? llrint(val(l + 1) * scale) : 0;
+    int d0[OZ_S], d1[OZ_S];
+#pragma unroll
+    for (int p = OZ_S - 1; p >= 1; --p) {
+      d0[p] = (int)(((X0 + 64) & 127) - 64);
+      X0 = (X0 - d0[p]) >> OZ_BITS;
+      d1[p] = (int)(((X1 + 64) & 127) - 64);
+      X1 = (X1 - d1[p]) >> OZ_BITS;
+    }
+    d0[0] = (int)X0;
+    d1[0] = (int)X1;
+#pragma unroll
+    for (int p = 0; p < OZ_S; ++p)
+      *reinterpret_cast<uint32_t*>(dst + (size_t)p * ldd + l) =
+          (uint32_t)bf16_of_small_int(d0[p]) | ((uint32_t)bf16_of_small_int(d1[p]) << 16);
+  }
+}
+
+// Real factors: E = A_CB W_E and F^T = A_BC^T W_F for one 64-row panel of C,
+// with the panel rows and the columns of W cut into digit slices (row and
+// column scales) and the slice products summed exactly on the tensor cores as
+// in the Schur update; E (F^T) = W 2^(e_i + f_j - 53) from one int64 per entry.
+// W is taken 32 columns at a time.  The rows of E and F^T are then sliced for
+// the Schur update.
+constexpr int OZ_NCH = 32;
+
+__global__ void __launch_bounds__(NT, 2) k_elim_oz(ElimArgs<double> a) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const BoxRec<double> R = a.recs[blockIdx.y];
+  if (!R.ozp) return;
+  const int p0 = blockIdx.x * 64;
+  if (p0 >= R.c) return;
+  const LevelDev<double>& L = a.L;
+  const int nmax = L.nmax, g = L.g, B = R.box, k = R.k, r = R.r, c = R.c, n = k + r;
+  const int np = (n + 15) & ~15, SA = OZ_S * np + 8;
+  const size_t nn = (size_t)nmax * nmax;
+  const int* perm = a.perm_in + (size_t)a.cls_idx[blockIdx.y] * nmax;
+  uint16_t* As = reinterpret_cast<uint16_t*>(smraw);   // 64 x SA: panel rows
+  uint16_t* Bs = As + 64 * SA;                         // OZ_NCH x SA: columns of W
+  __shared__ int rexp[64], cexp[OZ_NCH], ru[64], rpos[64];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, gq = lane >> 2, t4 = lane & 3;
+  const int rows = min(64, c - p0);
+  if (tid < 64) {
+    ru[tid] = -1;
+    rpos[tid] = 0;
+    if (tid < rows) {
+      const int cm = R.cmap[p0 + tid], s = cm >> 16;
+      ru[tid] = nbr_box(B, g, s % 3 - 1, s / 3 - 1);
+      rpos[tid] = cm & 0xffff;
+    }
+  }
+  __syncthreads();
+  const int m0 = (warp >> 1) * 16, n0 = (warp & 1) * 16;
+  const int a_row = lane & 15, a_k = (lane >> 4) * 8;
+  const int b_row = ((lane >> 4) << 3) + (lane & 7), b_k = ((lane >> 3) & 1) * 8;
+  for (int pass = 0; pass < 2; ++pass) {
+    const double* __restrict__ Wm = pass == 0 ? R.We : R.Wf;
+    double* out = pass == 0 ? R.E : R.Ft;
+    {   // panel rows: A(u, B)[pos, perm[l]] (pass 0) or A(B, u)[perm[l], pos] (pass 1)
+      const int row = tid >> 2, u = ru[row], pos = rpos[row];
+      const double* base = nullptr;
+      if (u >= 0)
+        base = pass == 0 ? L.blk + ((size_t)u * 25 + off_index(u, B, g)) * nn + pos
+                         : L.blk + ((size_t)B * 25 + off_index(B, u, g)) * nn + (size_t)pos * nmax;
+      const size_t ls = pass == 0 ? (size_t)nmax : 1;
+      oz_split_vec<4>([&](int l) { return base[(size_t)perm[l] * ls]; }, u >= 0 ? n : 0, np, As + row * SA, np,
+                      &rexp[row], true);
+    }
+    for (int jc = 0; jc < r; jc += OZ_NCH) {
+      __syncthreads();
+      {   // columns jc .. jc + 31 of W
+        const int col = tid >> 3, j = jc + col;
+        const double* wc = Wm + (size_t)j * n;
+        oz_split_vec<8>([&](int l) { return wc[l]; }, j < r ? n : 0, np, Bs + col * SA, np, &cexp[col], true);
+      }
+      __syncthreads();
+      long long W[2][4];
+#pragma unroll
+      for (int ni = 0; ni < 2; ++ni)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) W[ni][e] = 0;
+      for (int u = 0; u < OZ_S; ++u) {
+        float cf[2][4];
+#pragma unroll
+        for (int ni = 0; ni < 2; ++ni)
+#pragma unroll
+          for (int e = 0; e < 4; ++e) cf[ni][e] = 0.f;
+        for (int p = 0; p <= u; ++p) {
+          const uint16_t* Ab = As + p * np + (m0 + a_row) * SA + a_k;
+          const uint16_t* Bb = Bs + (u - p) * np + (n0 + b_row) * SA + b_k;
+          for (int kk = 0; kk < np; kk += 16) {
+            uint32_t af[4], bq[4];
+            ldsm_x4(af, Ab + kk);
+            ldsm_x4(bq, Bb + kk);
+            mma_bf16(cf[0], af, bq);
+            mma_bf16(cf[1], af, bq + 2);
+          }
+        }
+        const int sh = 39 - OZ_BITS * u;
+#pragma unroll
+        for (int ni = 0; ni < 2; ++ni)
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const long long gv = (long long)__float2int_rn(cf[ni][e]);
+            W[ni][e] += sh >= 0 ? (gv << sh) : ((gv + (1LL << (-sh - 1))) >> (-sh));
+          }
+      }
+#pragma unroll
+      for (int ni = 0; ni < 2; ++ni)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int row = m0 + gq + (e >= 2 ? 8 : 0);
+          const int col = n0 + ni * 8 + 2 * t4 + (e & 1), j = jc + col;
+          if (row < rows && j < r)
+            out[(size_t)(p0 + row) + (size_t)j * c] = (double)W[ni][e] * pow2(rexp[row] + cexp[col] - 53);
+        }
+    }
+    __syncthreads();
+    if (R.Esl != nullptr) {   // digit slices of this panel's rows of E (F^T) for the Schur update
+      const int row = tid >> 2;
+      const bool act = row < rows;
+      const double* src = out + (size_t)(p0 + row);
+      uint16_t* dst = (pass == 0 ? R.Esl : R.Fsl) + (size_t)(p0 + (act ? row : 0)) * OZ_S * R.kp;
+      int* ex = (pass == 0 ? R.Eexp : R.Fexp) + p0 + (act ? row : 0);
+      oz_split_vec<4>([&](int l) { return src[(size_t)l * c]; }, act ? r : 0, R.kp, dst, R.kp, ex, act);
+    }
+    __syncthreads();
+  }
 }
 
 // ------------------------------------------------------------------ Schur update A_CC -= E F
@@ -1246,26 +1439,6 @@ template <typename T> __global__ void __launch_bounds__(NT) k_schur(LevelDev<T> 
 // rounding right shifts, an error below 2^-53 of the scale), so
 // (E F)_ij = W 2^(e_i + f_j - 53): one conversion and one scaling per entry.
 // 64 x 64 tile per CTA, 8 warps of 32 x 16, fragments loaded with ldmatrix.
-__device__ __forceinline__ void mma_bf16(float* c, const uint32_t* a, const uint32_t* b) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-      "{%0,%1,%2,%3};\n"
-      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-}
-
-__device__ __forceinline__ void ldsm_x4(uint32_t* d, const void* smem_row) {
-  const unsigned addr = (unsigned)__cvta_generic_to_shared(smem_row);
-  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-               : "=r"(d[0]), "=r"(d[1]), "=r"(d[2]), "=r"(d[3])
-               : "r"(addr));
-}
-
-// 2^e as a double for the normal range, from its bit pattern
-__device__ __forceinline__ double pow2(int e) {
-  return (e > -1023 && e < 1024) ? __longlong_as_double((long long)(e + 1023) << 52) : ldexp(1.0, e);
-}
-
 __global__ void __launch_bounds__(NT) k_schur_oz(LevelDev<double> L, const BoxRec<double>* recs) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const BoxRec<double> R = recs[blockIdx.y];
@@ -1810,7 +1983,7 @@ rss_status factor_impl(const rss_tree* tree, const rss_params* prm, cudaStream_t
   f->launches += 1;
 
   // workspaces reused across colour classes and levels
-  GrowBuf gb_cls, gb_k, gb_perm, gb_clsidx, gb_Tws, gb_Y, gb_oz;
+  GrowBuf gb_cls, gb_k, gb_perm, gb_clsidx, gb_Tws, gb_Y, gb_oz, gb_w;
   // leaf level
   size_t transient = 0;
   HostLevel<T> cur;
@@ -2046,9 +2219,36 @@ rss_status factor_impl(const rss_tree* tree, const rss_params* prm, cudaStream_t
         for (BoxRec<T>& R : recs) {
           const size_t pb = panel_smem_bytes<T>(pan_ma, R.k + R.r, R.r);
           R.panels = pb <= 200 * 1024 ? 1 : 0;
-          if (R.panels) pan_max = std::max(pan_max, pb);
         }
       }
+      // E = A_CB W_E and F^T = A_BC^T W_F on the tensor cores: real factors,
+      // n <= 128 (the slices of a 64-row panel and of 32 columns of W fit in
+      // shared memory)
+      int ozp_np = 0;
+      if (sizeof(T) == sizeof(double) && prm->schur_path == 0) {
+        size_t bytes = 0;
+        for (const BoxRec<T>& R : recs)
+          if (R.k + R.r <= 128) bytes += 2 * (((size_t)(R.k + R.r) * R.r * sizeof(T) + 255) & ~size_t(255));
+        if (bytes > 0) {
+          if (!gb_w.ensure(bytes)) {
+            rss_set_error("rss_factor: device workspace allocation failed");
+            return RSS_ENOMEM;
+          }
+          char* p = static_cast<char*>(gb_w.p);
+          for (BoxRec<T>& R : recs) {
+            if (R.k + R.r > 128) continue;
+            const size_t b = ((size_t)(R.k + R.r) * R.r * sizeof(T) + 255) & ~size_t(255);
+            R.We = reinterpret_cast<T*>(p);
+            R.Wf = reinterpret_cast<T*>(p + b);
+            p += 2 * b;
+            R.ozp = 1;
+            ozp_np = std::max(ozp_np, (R.k + R.r + 15) & ~15);
+          }
+          f->peak_transient = std::max(f->peak_transient, transient + bytes);
+        }
+      }
+      for (const BoxRec<T>& R : recs)
+        if (R.panels && !R.ozp) pan_max = std::max(pan_max, panel_smem_bytes<T>(pan_ma, R.k + R.r, R.r));
       // tensor-core Schur update: real factors with r <= 96 (the slices of a
       // 64-row tile of E and of F^T must fit in shared memory)
       const bool oz = prm->schur_path == 0 && max_r <= (sizeof(T) == sizeof(double) ? 96 : 64);
@@ -2114,6 +2314,15 @@ rss_status factor_impl(const rss_tree* tree, const rss_params* prm, cudaStream_t
                                : launch_panels(k_elim_panels<T, 1>, 16));
         RSS_LAUNCHED();
         f->launches += 1;
+      }
+      if constexpr (sizeof(T) == sizeof(double)) {
+        if (ozp_np > 0) {
+          const int smem = (64 + OZ_NCH) * (OZ_S * ozp_np + 8) * (int)sizeof(uint16_t);
+          RSS_CUDA(cudaFuncSetAttribute(k_elim_oz, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+          k_elim_oz<<<dim3((max_c + 63) / 64, nrec), NT, smem, st>>>(ea);
+          RSS_LAUNCHED();
+          f->launches += 1;
+        }
       }
       evs.back().second->stop(st);
       const int ntile = (max_c + 63) / 64;

@@ -47,6 +47,12 @@ template <typename T> struct BoxRec {
   int* Eexp;      // c row exponents
   int* Fexp;
   int kp;         // r rounded up to a multiple of 16
+  // factor-time only, tensor-core panel path (ozp = 1): with the columns of B
+  // in pivot order, E = A_CB W_E and F^T = A_BC^T W_F (n x r each, ld n), where
+  // W_E = [-T U^{-1}; U^{-1}] and W_F = [-(L^{-1} P T^*)^T; (L^{-1} P)^T]
+  T* We;
+  T* Wf;
+  int ozp;
 };
 
 constexpr int OZ_S = 8;      // digit slices per operand

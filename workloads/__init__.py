@@ -51,6 +51,8 @@ WORKLOADS = {
                                            kappa=25.0, eps=1e-6, nrhs=16, seed=1001),
     "laplace_256x256_eps1e-6": dict(kind=LAPLACE, side=256, complex=False, kappa=0.0,
                                      eps=1e-6, nrhs=1, seed=1003),
+    "laplace_512x512_eps1e-6": dict(kind=LAPLACE, side=512, complex=False, kappa=0.0,
+                                     eps=1e-6, nrhs=1, seed=1005),
     "laplace_1024x1024_eps1e-6": dict(kind=LAPLACE, side=1024, complex=False, kappa=0.0,
                                        eps=1e-6, nrhs=1, seed=1002),
     "helmholtz_k50_2048x2048_eps1e-6": dict(kind=HELMHOLTZ, side=2048, complex=True,
