@@ -119,8 +119,17 @@ __global__ void __launch_bounds__(NT) k_gen_blocks(LevelDev<T> L, const int2* __
 // is the same sequence of reflectors and pivots as updating Y in place.
 constexpr int NT_ID = 256;
 
-template <typename T> struct IdArgs {
-  LevelDev<T> L;
+// T: arithmetic of the ID; S: scalar of the matrix.  T = double with S = zd is
+// the complex symmetric case (Helmholtz): there A_BM^* = conj(A_MB) and
+// K_BP^* = conj(K_PB) hold through the eliminations (T stays real, so the
+// Schur updates keep A complex symmetric), the stack is [X; conj X] with
+// X = [A_MB; K_PB], and its Gram matrix 2 Re(X^H X) is that of the real matrix
+// sqrt(2) [Re X; Im X].  Column-pivoted QR sees Y only through its Gram matrix
+// (norms, pivots, R up to unimodular row scales, ||R22||, T = R11^{-1} R12), so
+// the real stack [Re X; Im X] gives the same ID with T real, at a quarter of
+// the arithmetic.
+template <typename T, typename S = T> struct IdArgs {
+  LevelDev<S> L;
   const int* boxes;   // colour class
   int base;           // first box of this chunk within the class
   T* ws;              // chunk workspace: per box Y (ldY x nmax), V (ldY x nmax), G, Rr (nmax x nmax)
@@ -128,7 +137,7 @@ template <typename T> struct IdArgs {
   int half;           // 1: rows [A_MB; K_PB] only (real symmetric kernel)
   int* k_out;         // per class box
   int* perm_out;      // class x nmax
-  T* T_ws;            // class x nmax x nmax (k x r, ld nmax)
+  S* T_ws;            // class x nmax x nmax (k x r, ld nmax)
   const int2* ixy;
   KParams kp;
   Geo geo;
@@ -138,9 +147,54 @@ template <typename T> struct IdArgs {
   double Lbox;        // box side
 };
 
-template <typename T> __global__ void __launch_bounds__(NT_ID, 4) k_id(IdArgs<T> a) {
+template <typename T, typename S> __device__ inline S id_store(T v) {
+  if constexpr (std::is_same<T, S>::value) return v;
+  else return S{v, 0.0};
+}
+template <typename T, typename S> __device__ inline T id_load(S v) {
+  if constexpr (std::is_same<T, S>::value) return v;
+  else return v.x;
+}
+
+// Entry (i, j) of the proxy stack of box B (Eq. 6): rows [A_MB; K_PB] then
+// [A_BM^*; K_BP^*]; with T real and S complex, [Re X; Im X] for X = [A_MB; K_PB].
+// Mbox/Moff: the distance-2 boxes and their row offsets, mh = their active rows,
+// (cx, cy) the box centre; column j is point j of B (identity active list).
+template <typename T, typename S>
+__device__ __forceinline__ T id_entry(const IdArgs<T, S>& a, int B, int i, int j, int mh, const int* Mbox,
+                                      const int* Moff, double cx, double cy) {
+  const LevelDev<S>& L = a.L;
+  const int nmax = L.nmax, g = L.g, P = a.P;
+  const size_t nn = (size_t)nmax * nmax;
+  constexpr bool split = !std::is_same<T, S>::value;
+  bool second = i >= mh + P;                // conjugate half (or imaginary parts)
+  const int ii = second ? i - mh - P : i;   // row of X
+  S v;
+  if (ii < mh) {
+    int q = 0;
+    while (Moff[q + 1] <= ii) ++q;
+    const int mb = Mbox[q];
+    const int pm = L.act[mb * nmax + (ii - Moff[q])];
+    if (split || !second)
+      v = L.blk[((size_t)mb * 25 + off_index(mb, B, g)) * nn + (size_t)j * nmax + pm];
+    else
+      v = cj(L.blk[((size_t)B * 25 + off_index(B, mb, g)) * nn + (size_t)pm * nmax + j]);
+  } else {
+    const int p = ii - mh;
+    double sn, cs;
+    sincospi(2.0 * p / P, &sn, &cs);
+    const double px = cx + a.rho * cs, py = cy + a.rho * sn;
+    const int2 q = a.ixy[L.pts[B * nmax + j]];
+    const double xj = a.geo.x0 + q.x * a.geo.hg, yj = a.geo.y0 + q.y * a.geo.hg;
+    v = (!split && second) ? cj(kval(a.kp, xj, yj, px, py, S{})) : kval(a.kp, px, py, xj, yj, S{});
+  }
+  if constexpr (split) return second ? v.y : v.x;
+  else return v;
+}
+
+template <typename T, typename S = T> __global__ void __launch_bounds__(NT_ID, 4) k_id(IdArgs<T, S> a) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  const LevelDev<T>& L = a.L;
+  const LevelDev<S>& L = a.L;
   const int nmax = L.nmax, g = L.g, ldY = a.ldY;
   T* vbuf = reinterpret_cast<T*>(smraw);          // ldY: current reflector
   T* u = vbuf + ldY;                              // nmax: V^H v
@@ -191,29 +245,7 @@ template <typename T> __global__ void __launch_bounds__(NT_ID, 4) k_id(IdArgs<T>
   // Y, column-major; column j = point j of B (not yet eliminated: identity active list)
   for (long long e = tid; e < (long long)m * n; e += blockDim.x) {
     const int i = (int)(e % m), j = (int)(e / m);
-    T val;
-    if (i < mh || (i >= mh + P && i < 2 * mh + P)) {
-      const bool second = i >= mh;
-      const int ii = second ? i - mh - P : i;
-      int q = 0;
-      while (Moff[q + 1] <= ii) ++q;
-      const int mb = Mbox[q];
-      const int pm = L.act[mb * nmax + (ii - Moff[q])];
-      if (!second)
-        val = L.blk[((size_t)mb * 25 + off_index(mb, B, g)) * nn + (size_t)j * nmax + pm];
-      else
-        val = cj(L.blk[((size_t)B * 25 + off_index(B, mb, g)) * nn + (size_t)pm * nmax + j]);
-    } else {
-      const bool second = i >= 2 * mh + P;
-      const int p = second ? i - 2 * mh - P : i - mh;
-      double sn, cs;
-      sincospi(2.0 * p / P, &sn, &cs);
-      const double px = cx + a.rho * cs, py = cy + a.rho * sn;
-      const int2 q = a.ixy[L.pts[B * nmax + j]];
-      const double xj = a.geo.x0 + q.x * a.geo.hg, yj = a.geo.y0 + q.y * a.geo.hg;
-      val = second ? cj(kval(a.kp, xj, yj, px, py, T{})) : kval(a.kp, px, py, xj, yj, T{});
-    }
-    Yw[(size_t)j * ldY + i] = val;
+    Yw[(size_t)j * ldY + i] = id_entry(a, B, i, j, mh, Mbox, Moff, cx, cy);
   }
   __syncthreads();
   for (int c = warp; c < n; c += nwarp) {
@@ -391,13 +423,14 @@ template <typename T> __global__ void __launch_bounds__(NT_ID, 4) k_id(IdArgs<T>
   __syncthreads();
   // T = R11^{-1} R12 (back substitution), k x r with ld nmax
   const int r = n - k;
-  T* Tw = a.T_ws + (size_t)bi * nn;
+  S* Tw = a.T_ws + (size_t)bi * nn;
   for (int c = tid; c < r; c += blockDim.x) {
     const int oc = perm[k + c];
     for (int i = k - 1; i >= 0; --i) {
       T x = Rr[(size_t)i * nmax + oc];
-      for (int l = i + 1; l < k; ++l) x = msb(x, Rr[(size_t)i * nmax + perm[l]], Tw[(size_t)c * nmax + l]);
-      Tw[(size_t)c * nmax + i] = dv(x, beta[i]);
+      for (int l = i + 1; l < k; ++l)
+        x = msb(x, Rr[(size_t)i * nmax + perm[l]], id_load<T, S>(Tw[(size_t)c * nmax + l]));
+      Tw[(size_t)c * nmax + i] = id_store<T, S>(dv(x, beta[i]));
     }
   }
   for (int c = tid; c < n; c += blockDim.x) a.perm_out[(size_t)bi * nmax + c] = perm[c];
@@ -412,12 +445,12 @@ template <typename T> __global__ void __launch_bounds__(NT_ID, 4) k_id(IdArgs<T>
 // column's norm, v^H Y, v^H V, re-accumulated norms) are formed per CTA and
 // added through distributed shared memory in rank order, so all CTAs see the
 // same bits.  Every CTA reaches every cluster barrier the same number of times.
-template <typename T> __global__ void __launch_bounds__(NT_ID) k_id_cl(IdArgs<T> a) {
+template <typename T, typename S = T> __global__ void __launch_bounds__(NT_ID) k_id_cl(IdArgs<T, S> a) {
   extern __shared__ __align__(16) unsigned char smraw[];
   namespace cg = cooperative_groups;
   cg::cluster_group cl = cg::this_cluster();
   const int Q = (int)cl.num_blocks(), rank = (int)cl.block_rank();
-  const LevelDev<T>& L = a.L;
+  const LevelDev<S>& L = a.L;
   const int nmax = L.nmax, g = L.g, ldY = a.ldY;
   const int rp = (ldY + Q - 1) / Q;                // rows per CTA (upper bound)
   T* vbuf = reinterpret_cast<T*>(smraw);           // rp: owned rows of the reflector
@@ -485,29 +518,7 @@ template <typename T> __global__ void __launch_bounds__(NT_ID) k_id_cl(IdArgs<T>
   const int mr = r1 - r0;
   for (long long e = tid; e < (long long)mr * n; e += blockDim.x) {
     const int i = r0 + (int)(e % mr), j = (int)(e / mr);
-    T val;
-    if (i < mh || (i >= mh + P && i < 2 * mh + P)) {
-      const bool second = i >= mh;
-      const int ii = second ? i - mh - P : i;
-      int q = 0;
-      while (Moff[q + 1] <= ii) ++q;
-      const int mb = Mbox[q];
-      const int pm = L.act[mb * nmax + (ii - Moff[q])];
-      if (!second)
-        val = L.blk[((size_t)mb * 25 + off_index(mb, B, g)) * nn + (size_t)j * nmax + pm];
-      else
-        val = cj(L.blk[((size_t)B * 25 + off_index(B, mb, g)) * nn + (size_t)pm * nmax + j]);
-    } else {
-      const bool second = i >= 2 * mh + P;
-      const int p = second ? i - 2 * mh - P : i - mh;
-      double sn, cs;
-      sincospi(2.0 * p / P, &sn, &cs);
-      const double px = cx + a.rho * cs, py = cy + a.rho * sn;
-      const int2 q = a.ixy[L.pts[B * nmax + j]];
-      const double xj = a.geo.x0 + q.x * a.geo.hg, yj = a.geo.y0 + q.y * a.geo.hg;
-      val = second ? cj(kval(a.kp, xj, yj, px, py, T{})) : kval(a.kp, px, py, xj, yj, T{});
-    }
-    Yw[(size_t)j * ldY + i] = val;
+    Yw[(size_t)j * ldY + i] = id_entry(a, B, i, j, mh, Mbox, Moff, cx, cy);
   }
   __syncthreads();
   // column norms: partials over owned rows, summed across the cluster
@@ -686,13 +697,14 @@ template <typename T> __global__ void __launch_bounds__(NT_ID) k_id_cl(IdArgs<T>
   if (rank != 0) return;
   // T = R11^{-1} R12 (back substitution), k x r with ld nmax
   const int r = n - k;
-  T* Tw = a.T_ws + (size_t)bi * nn;
+  S* Tw = a.T_ws + (size_t)bi * nn;
   for (int c = tid; c < r; c += blockDim.x) {
     const int oc = perm[k + c];
     for (int i = k - 1; i >= 0; --i) {
       T x = Rr[(size_t)i * nmax + oc];
-      for (int l = i + 1; l < k; ++l) x = msb(x, Rr[(size_t)i * nmax + perm[l]], Tw[(size_t)c * nmax + l]);
-      Tw[(size_t)c * nmax + i] = dv(x, beta[i]);
+      for (int l = i + 1; l < k; ++l)
+        x = msb(x, Rr[(size_t)i * nmax + perm[l]], id_load<T, S>(Tw[(size_t)c * nmax + l]));
+      Tw[(size_t)c * nmax + i] = id_store<T, S>(dv(x, beta[i]));
     }
   }
   for (int c = tid; c < n; c += blockDim.x) a.perm_out[(size_t)bi * nmax + c] = perm[c];
@@ -1726,6 +1738,35 @@ __global__ void __launch_bounds__(NT) k_merge_blk(LevelDev<T> C, LevelDev<T> P, 
     }
 }
 
+// Child level kept for the merge only: its blocks restricted to the active
+// points (the merge reads nothing else), so the full blocks can be freed
+// before the parent level is allocated.  out: nbox x 25 x kmax x kmax.
+template <typename T>
+__global__ void __launch_bounds__(NT) k_compact_blk(LevelDev<T> C, T* __restrict__ out, int* __restrict__ pts_out,
+                                                    int kmax) {
+  const int u = blockIdx.x / 25, o = blockIdx.x % 25;
+  const int v = nbr_box(u, C.g, o % 5 - 2, o / 5 - 2);
+  const int nu = C.nact[u];
+  if (o == 0)
+    for (int i = threadIdx.x; i < nu; i += blockDim.x) pts_out[(size_t)u * kmax + i] = C.pts[u * C.nmax + C.act[u * C.nmax + i]];
+  if (v < 0) return;
+  const int nv = C.nact[v];
+  const T* S = C.blk + ((size_t)u * 25 + o) * C.nmax * C.nmax;
+  T* D = out + ((size_t)u * 25 + o) * kmax * kmax;
+  const int* au = C.act + u * C.nmax;
+  const int* av = C.act + v * C.nmax;
+  for (int e = threadIdx.x; e < nu * nv; e += blockDim.x) {
+    const int i = e % nu, j = e / nu;
+    D[(size_t)j * kmax + i] = S[(size_t)av[j] * C.nmax + au[i]];
+  }
+}
+
+__global__ void k_iota_rows(int* act, int nbox, int kmax) {
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < (long long)nbox * kmax;
+       e += (long long)gridDim.x * blockDim.x)
+    act[e] = (int)(e % kmax);
+}
+
 // ------------------------------------------------------------------ dense top
 template <typename T>
 __global__ void __launch_bounds__(NT) k_top_assemble(LevelDev<T> L, T* D, int ntop, int* top_idx, int4 offs_lo,
@@ -1890,7 +1931,14 @@ template <typename T> rss_status alloc_level(HostLevel<T>& L, int g, int nmax, s
   RSS_CUDA(cudaMalloc(&L.d.act, sizeof(int) * nb * nmax));
   RSS_CUDA(cudaMalloc(&L.d.nact, sizeof(int) * nb));
   const size_t bytes = sizeof(T) * nb * 25 * (size_t)nmax * nmax;
-  RSS_CUDA(cudaMalloc(&L.d.blk, bytes));
+  if (cudaMalloc(&L.d.blk, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    L.d.blk = nullptr;
+    rss_set_error("rss_factor: out of device memory for the stencil blocks of the " + std::to_string(g) + " x " +
+                  std::to_string(g) + " level (" + std::to_string(bytes >> 20) + " MiB, " + std::to_string(nmax) +
+                  " points per box)");
+    return RSS_ENOMEM;
+  }
   transient += bytes;
   return RSS_OK;
 }
@@ -2021,6 +2069,9 @@ rss_status factor_impl(const rss_tree* tree, const rss_params* prm, cudaStream_t
   // eliminations, so the conjugate half of the proxy stack repeats the first half
   // and the ID of [A_MB; K_PB] alone is the same ID.
   const int half = (prm->id_rows == 0 && prm->kind == RSS_LAPLACE && prm->diag_im == 0.0) ? 1 : 0;
+  // A complex symmetric kernel (Helmholtz): the ID of the real stack
+  // [Re X; Im X], X = [A_MB; K_PB], which is the ID of the full stack (T real).
+  const bool split = std::is_same<T, zd>::value && prm->id_rows == 0 && prm->kind == RSS_HELMHOLTZ;
   while (g >= 4) {
     const int nbox = g * g, nmax = cur.d.nmax;
     const size_t nn = (size_t)nmax * nmax;
@@ -2081,75 +2132,85 @@ rss_status factor_impl(const rss_tree* tree, const rss_params* prm, cudaStream_t
       if (prm->id_cluster >= 0)
         while (Q < 8 && (long long)nb * Q * 2 <= 2 * 152) Q *= 2;
       if (prm->id_cluster > 0) Q = std::min(Q, prm->id_cluster);
-      const size_t slot = (2 * (size_t)ldY * nmax + 2 * nn * Q) * sizeof(T);
-      const size_t ybudget = size_t(2) << 30;
-      const int cap = (int)std::max<size_t>(1, std::min<size_t>(nb, ybudget / slot));
-      const int nchunks = (nb + cap - 1) / cap;
-      const int chunk = (nb + nchunks - 1) / nchunks;   // balanced chunks
-      if (!gb_Y.ensure(slot * chunk)) {
-        rss_set_error("rss_factor: device workspace allocation failed");
-        return RSS_ENOMEM;
-      }
-      T* d_Y = static_cast<T*>(gb_Y.p);
-      const size_t smem_id = sizeof(T) * ((size_t)ldY + 2 * nmax) + (size_t)nmax * (3 * sizeof(double) + 2 * sizeof(int));
-      if (smem_id > 220 * 1024) {
-        rss_set_error("rss_factor: proxy stack of a box too tall for the on-chip reflector buffer");
-        return RSS_EINVAL;
-      }
-      RSS_CUDA(cudaFuncSetAttribute(k_id<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_id));
-      const size_t smem_cl = sizeof(T) * ((size_t)(ldY + Q - 1) / Q + 6 * (size_t)nmax) +
-                             (size_t)nmax * (3 * sizeof(double) + 2 * sizeof(int));
-      if (Q > 1)
-        RSS_CUDA(cudaFuncSetAttribute(k_id_cl<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cl));
-      f->peak_transient = std::max(f->peak_transient, transient + slot * chunk);
       Timer tid_;
       evs.emplace_back(0, std::make_unique<Ev>());
       evs.back().second->start(st);
-      for (int c0 = 0; c0 < nb; c0 += chunk) {
-        IdArgs<T> a;
-        a.L = cur.d;
-        a.boxes = d_cls + coff[col];
-        a.base = c0;
-        a.ws = d_Y;
-        a.ldY = ldY;
-        a.half = half;
-        a.k_out = d_k;
-        a.perm_out = d_perm;
-        a.T_ws = d_Tws;
-        a.ixy = d_ixy;
-        a.kp = f->kp;
-        a.geo = f->geo;
-        a.eps = f->params.eps;
-        a.P = P;
-        a.rho = ratio * Lbox;
-        a.Lbox = Lbox;
-        const int cnt = std::min(chunk, nb - c0);
-        if (Q > 1) {
-          cudaLaunchConfig_t cfg = {};
-          cfg.gridDim = dim3(cnt * Q);
-          cfg.blockDim = dim3(NT_ID);
-          cfg.dynamicSmemBytes = smem_cl;
-          cfg.stream = st;
-          cudaLaunchAttribute attr[1];
-          attr[0].id = cudaLaunchAttributeClusterDimension;
-          attr[0].val.clusterDim.x = Q;
-          attr[0].val.clusterDim.y = 1;
-          attr[0].val.clusterDim.z = 1;
-          cfg.attrs = attr;
-          cfg.numAttrs = 1;
-          RSS_CUDA(cudaLaunchKernelEx(&cfg, k_id_cl<T>, a));
-        } else {
-          k_id<T><<<cnt, NT_ID, smem_id, st>>>(a);
+      // TC: arithmetic of the ID (double for the complex symmetric real stack)
+      auto run_id = [&](auto tag) -> rss_status {
+        using TC = decltype(tag);
+        const size_t slot = (2 * (size_t)ldY * nmax + 2 * nn * Q) * sizeof(TC);
+        const size_t ybudget = size_t(2) << 30;
+        const int cap = (int)std::max<size_t>(1, std::min<size_t>(nb, ybudget / slot));
+        const int nchunks = (nb + cap - 1) / cap;
+        const int chunk = (nb + nchunks - 1) / nchunks;   // balanced chunks
+        if (!gb_Y.ensure(slot * chunk)) {
+          rss_set_error("rss_factor: device workspace allocation failed");
+          return RSS_ENOMEM;
         }
-        RSS_LAUNCHED();
-        f->launches += 1;
-        f->n_id += 1;
+        TC* d_Y = static_cast<TC*>(gb_Y.p);
+        const size_t smem_id =
+            sizeof(TC) * ((size_t)ldY + 2 * nmax) + (size_t)nmax * (3 * sizeof(double) + 2 * sizeof(int));
+        if (smem_id > 220 * 1024) {
+          rss_set_error("rss_factor: proxy stack of a box too tall for the on-chip reflector buffer");
+          return RSS_EINVAL;
+        }
+        RSS_CUDA(cudaFuncSetAttribute(k_id<TC, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_id));
+        const size_t smem_cl = sizeof(TC) * ((size_t)(ldY + Q - 1) / Q + 6 * (size_t)nmax) +
+                               (size_t)nmax * (3 * sizeof(double) + 2 * sizeof(int));
+        if (Q > 1)
+          RSS_CUDA(cudaFuncSetAttribute(k_id_cl<TC, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cl));
+        f->peak_transient = std::max(f->peak_transient, transient + slot * chunk);
+        for (int c0 = 0; c0 < nb; c0 += chunk) {
+          IdArgs<TC, T> a;
+          a.L = cur.d;
+          a.boxes = d_cls + coff[col];
+          a.base = c0;
+          a.ws = d_Y;
+          a.ldY = ldY;
+          a.half = half;
+          a.k_out = d_k;
+          a.perm_out = d_perm;
+          a.T_ws = d_Tws;
+          a.ixy = d_ixy;
+          a.kp = f->kp;
+          a.geo = f->geo;
+          a.eps = f->params.eps;
+          a.P = P;
+          a.rho = ratio * Lbox;
+          a.Lbox = Lbox;
+          const int cnt = std::min(chunk, nb - c0);
+          if (Q > 1) {
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3(cnt * Q);
+            cfg.blockDim = dim3(NT_ID);
+            cfg.dynamicSmemBytes = smem_cl;
+            cfg.stream = st;
+            cudaLaunchAttribute attr[1];
+            attr[0].id = cudaLaunchAttributeClusterDimension;
+            attr[0].val.clusterDim.x = Q;
+            attr[0].val.clusterDim.y = 1;
+            attr[0].val.clusterDim.z = 1;
+            cfg.attrs = attr;
+            cfg.numAttrs = 1;
+            RSS_CUDA(cudaLaunchKernelEx(&cfg, k_id_cl<TC, T>, a));
+          } else {
+            k_id<TC, T><<<cnt, NT_ID, smem_id, st>>>(a);
+          }
+          RSS_LAUNCHED();
+          f->launches += 1;
+          f->n_id += 1;
+        }
+        return RSS_OK;
+      };
+      {
+        const rss_status s_id = split ? run_id(double{}) : run_id(T{});
+        if (s_id != RSS_OK) return s_id;
       }
       evs.back().second->stop(st);
       RSS_CUDA(cudaMemcpyAsync(hk.data(), d_k, sizeof(int) * nb, cudaMemcpyDeviceToHost, st));
       RSS_CUDA(cudaStreamSynchronize(st));
       f->t_id += tid_.ms();
-      const double cf = sizeof(T) == sizeof(double) ? 1.0 : 4.0;
+      const double cf = (sizeof(T) == sizeof(double) || split) ? 1.0 : 4.0;
       for (int q = 0; q < nb; ++q) {   // CPQR: norms, per step v^H Y and the k-column corrections, T
         const double m = mrows[q], n = cur.n[boxes[q]], k = hk[q];
         double fl = 2.0 * m * n + k * k * (n - k);
@@ -2381,6 +2442,38 @@ rss_status factor_impl(const rss_tree* tree, const rss_params* prm, cudaStream_t
     if (pmax > 65535) { rss_set_error("rss_factor: box too large after merging"); return RSS_EINVAL; }
     par.nact = par.n;
     {
+      // when the parent's blocks do not fit beside the child's, keep only the
+      // child's active entries (all the merge reads) and free the rest first
+      size_t fr = 0, tot = 0;
+      RSS_CUDA(cudaMemGetInfo(&fr, &tot));
+      const size_t pbytes = sizeof(T) * (size_t)gp * gp * 25 * (size_t)pmax * pmax;
+      if (pbytes + (size_t(4) << 30) > fr) {
+        int kmax = 1;
+        for (int b = 0; b < nbox; ++b) kmax = std::max(kmax, cur.nact[b]);
+        const size_t cbytes = sizeof(T) * (size_t)nbox * 25 * (size_t)kmax * kmax;
+        T* cblk = nullptr;
+        int *cpts = nullptr, *cact = nullptr;
+        RSS_CUDA(cudaMalloc(&cblk, cbytes));
+        RSS_CUDA(cudaMalloc(&cpts, sizeof(int) * (size_t)nbox * kmax));
+        RSS_CUDA(cudaMalloc(&cact, sizeof(int) * (size_t)nbox * kmax));
+        k_compact_blk<T><<<nbox * 25, NT, 0, st>>>(cur.d, cblk, cpts, kmax);
+        RSS_LAUNCHED();
+        k_iota_rows<<<1024, NT, 0, st>>>(cact, nbox, kmax);
+        RSS_LAUNCHED();
+        RSS_CUDA(cudaStreamSynchronize(st));
+        f->launches += 2;
+        cudaFree(cur.d.blk);
+        cudaFree(cur.d.pts);
+        cudaFree(cur.d.act);
+        transient -= sizeof(T) * (size_t)nbox * 25 * nn;
+        transient += cbytes;
+        cur.d.blk = cblk;
+        cur.d.pts = cpts;
+        cur.d.act = cact;
+        cur.d.nmax = kmax;
+      }
+    }
+    {
       rss_status s = alloc_level(par, gp, pmax, transient);
       if (s != RSS_OK) return s;
     }
@@ -2395,7 +2488,7 @@ rss_status factor_impl(const rss_tree* tree, const rss_params* prm, cudaStream_t
     RSS_CUDA(cudaStreamSynchronize(st));
     f->g_merge += evm.ms();
     f->launches += 2;
-    transient -= sizeof(T) * (size_t)nbox * 25 * nn;
+    transient -= sizeof(T) * (size_t)nbox * 25 * (size_t)cur.d.nmax * cur.d.nmax;
     free_level(cur);
     cur = par;
     g = gp;

@@ -101,6 +101,33 @@ def test_cpqr_exact_low_rank_and_ties():
     assert perm[0] < 3
 
 
+def test_cpqr_of_conjugate_stack_equals_real_stack():
+    """[X; conj X] and [Re X; Im X] have proportional Gram matrices (2 Re X^H X),
+    so column-pivoted QR gives both the same pivots and rank, and T is real."""
+    rng = np.random.default_rng(11)
+    U = rng.standard_normal((120, 12)) + 1j * rng.standard_normal((120, 12))
+    V = rng.standard_normal((12, 40)) + 1j * rng.standard_normal((12, 40))
+    X = (U * np.logspace(0, -11, 12)) @ V
+    kc, pc, Tc, _ = cpqr_id(np.vstack([X, X.conj()]), 1e-7)
+    kr, pr, Tr, _ = cpqr_id(np.vstack([X.real, X.imag]), 1e-7)
+    assert kc == kr and 0 < kc < 40
+    assert np.array_equal(pc, pr)
+    assert np.abs(Tc.imag).max() <= 1e-10 * np.abs(Tc).max()
+    assert np.abs(Tc.real - Tr).max() <= 1e-10 * np.abs(Tr).max()
+
+
+def test_helmholtz_interpolation_matrices_stay_real():
+    """A complex symmetric kernel keeps A complex symmetric through the
+    eliminations (T real up to rounding), so every box's stack has the form
+    [X; conj X]: the premise of computing the Helmholtz ID in real arithmetic."""
+    side = 32
+    fac = factor(W.grid_points(side), KernelSpec("helmholtz", h=1 / side, kappa=25.0), 1e-6, leaf=16)
+    assert len(fac.records) > 0
+    for rec in fac.records:
+        if rec.T.size:
+            assert np.abs(rec.T.imag).max() <= 1e-8 * max(1.0, np.abs(rec.T).max())
+
+
 def test_cpqr_zero_matrix():
     k, perm, T, _ = cpqr_id(np.zeros((10, 4)), 1e-6)
     assert k == 0 and T.shape == (0, 4)
