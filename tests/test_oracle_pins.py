@@ -108,12 +108,15 @@ def test_cpqr_of_conjugate_stack_equals_real_stack():
     U = rng.standard_normal((120, 12)) + 1j * rng.standard_normal((120, 12))
     V = rng.standard_normal((12, 40)) + 1j * rng.standard_normal((12, 40))
     X = (U * np.logspace(0, -11, 12)) @ V
-    kc, pc, Tc, _ = cpqr_id(np.vstack([X, X.conj()]), 1e-7)
-    kr, pr, Tr, _ = cpqr_id(np.vstack([X.real, X.imag]), 1e-7)
+    eps = 1e-7
+    kc, pc, Tc, _ = cpqr_id(np.vstack([X, X.conj()]), eps)
+    kr, pr, Tr, _ = cpqr_id(np.vstack([X.real, X.imag]), eps)
     assert kc == kr and 0 < kc < 40
     assert np.array_equal(pc, pr)
-    assert np.abs(Tc.imag).max() <= 1e-10 * np.abs(Tc).max()
-    assert np.abs(Tc.real - Tr).max() <= 1e-10 * np.abs(Tr).max()
+    # rounding in T grows with cond(R11), up to about 1/eps at the truncation
+    tol = 1e-14 / eps
+    assert np.abs(Tc.imag).max() <= tol * np.abs(Tc).max()
+    assert np.abs(Tc.real - Tr).max() <= tol * np.abs(Tr).max()
 
 
 def test_helmholtz_interpolation_matrices_stay_real():
