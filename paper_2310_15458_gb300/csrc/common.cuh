@@ -79,6 +79,27 @@ __device__ inline zd ld_l2(const zd* p) {
   return zd{v.x, v.y};
 }
 
+// Asynchronous global -> shared copies (cp.async): a thread issues all its
+// copies before waiting once, so a staging loop costs one memory latency
+// instead of one per element.  Both addresses must be aligned to the size.
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+template <typename T> __device__ __forceinline__ void cp_async_el(T* smem, const T* gmem) {
+  if constexpr (sizeof(T) == 8) cp_async8(smem, gmem);
+  else cp_async16(smem, gmem);
+}
+// wait for this thread's copies; a __syncthreads() must follow before other
+// threads read them
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
 template <typename T> __device__ inline T warp_sum(T v) {
 #pragma unroll
   for (int d = 16; d > 0; d >>= 1) v = v + shfl_xor(v, d);

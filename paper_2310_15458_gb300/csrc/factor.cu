@@ -1467,12 +1467,14 @@ __global__ void __launch_bounds__(NT) k_schur_oz(LevelDev<double> L, const BoxRe
   const int tid = threadIdx.x;
   for (int e = tid; e < 64 * kp; e += NT) {     // kp 16-byte chunks per row (OZ_S * 2 = 16)
     const int row = e / kp, ch = e % kp;
-    uint4 va = make_uint4(0, 0, 0, 0), vb = va;
-    if (i0 + row < c) va = reinterpret_cast<const uint4*>(R.Esl + (size_t)(i0 + row) * OZ_S * kp)[ch];
-    if (j0 + row < c) vb = reinterpret_cast<const uint4*>(R.Fsl + (size_t)(j0 + row) * OZ_S * kp)[ch];
-    *reinterpret_cast<uint4*>(As + row * SA + ch * 8) = va;
-    *reinterpret_cast<uint4*>(Bs + row * SA + ch * 8) = vb;
+    uint16_t* da = As + row * SA + ch * 8;
+    uint16_t* db = Bs + row * SA + ch * 8;
+    if (i0 + row < c) cp_async16(da, R.Esl + (size_t)(i0 + row) * OZ_S * kp + ch * 8);
+    else *reinterpret_cast<uint4*>(da) = make_uint4(0, 0, 0, 0);
+    if (j0 + row < c) cp_async16(db, R.Fsl + (size_t)(j0 + row) * OZ_S * kp + ch * 8);
+    else *reinterpret_cast<uint4*>(db) = make_uint4(0, 0, 0, 0);
   }
+  cp_async_wait_all();
   if (tid < 64) {
     const int i = i0 + tid;
     if (i < c) {
@@ -1580,16 +1582,17 @@ __global__ void __launch_bounds__(NT) k_schur_oz_c(LevelDev<zd> L, const BoxRec<
   const int chunks = 2 * kp;                    // 16-byte chunks per row
   for (int e = tid; e < 64 * chunks; e += NT) {
     const int row = e / chunks, ch = e % chunks;
-    uint4 va = make_uint4(0, 0, 0, 0);
-    if (i0 + row < c) va = reinterpret_cast<const uint4*>(R.Esl + (size_t)(i0 + row) * 2 * OZ_S * kp)[ch];
-    *reinterpret_cast<uint4*>(As + row * SA + ch * 8) = va;
+    uint16_t* da = As + row * SA + ch * 8;
+    if (i0 + row < c) cp_async16(da, R.Esl + (size_t)(i0 + row) * 2 * OZ_S * kp + ch * 8);
+    else *reinterpret_cast<uint4*>(da) = make_uint4(0, 0, 0, 0);
   }
   for (int e = tid; e < 32 * chunks; e += NT) {
     const int row = e / chunks, ch = e % chunks;
-    uint4 vb = make_uint4(0, 0, 0, 0);
-    if (j0 + row < c) vb = reinterpret_cast<const uint4*>(R.Fsl + (size_t)(j0 + row) * 2 * OZ_S * kp)[ch];
-    *reinterpret_cast<uint4*>(Bs + row * SA + ch * 8) = vb;
+    uint16_t* db = Bs + row * SA + ch * 8;
+    if (j0 + row < c) cp_async16(db, R.Fsl + (size_t)(j0 + row) * 2 * OZ_S * kp + ch * 8);
+    else *reinterpret_cast<uint4*>(db) = make_uint4(0, 0, 0, 0);
   }
+  cp_async_wait_all();
   if (tid < 64) {
     const int i = i0 + tid;
     if (i < c) {
@@ -2507,7 +2510,8 @@ rss_status factor_impl(const rss_tree* tree, const rss_params* prm, cudaStream_t
     f->d_top_lu = f->arena.get(sizeof(T) * (size_t)ntop * ntop);
     f->d_top_piv = static_cast<int*>(f->arena.get(sizeof(int) * ntop));
     f->d_top_idx = static_cast<int*>(f->arena.get(sizeof(int) * ntop));
-    if (!f->d_top_lu || !f->d_top_piv || !f->d_top_idx) {
+    f->d_top_inv = f->arena.get(sizeof(T) * (size_t)ntop * ntop);
+    if (!f->d_top_lu || !f->d_top_piv || !f->d_top_idx || !f->d_top_inv) {
       rss_set_error("rss_factor: device arena allocation failed");
       return RSS_ENOMEM;
     }
@@ -2533,11 +2537,17 @@ rss_status factor_impl(const rss_tree* tree, const rss_params* prm, cudaStream_t
       }
       f->launches += 3;
     }
+    if (ntop > 0) {
+      rss_status si = top_inverse<T>(static_cast<const T*>(f->d_top_lu), f->d_top_piv, ntop,
+                                     static_cast<T*>(f->d_top_inv), st);
+      if (si != RSS_OK) return si;
+      f->launches += 3;
+    }
     evt.stop(st);
     f->launches += 1;
     RSS_CUDA(cudaStreamSynchronize(st));
     f->g_top += evt.ms();
-    f->f_top += (sizeof(T) == sizeof(double) ? 1.0 : 4.0) * 2.0 * (double)ntop * ntop * ntop / 3.0;
+    f->f_top += (sizeof(T) == sizeof(double) ? 1.0 : 4.0) * (2.0 / 3.0 + 2.0) * (double)ntop * ntop * ntop;
     free_level(cur);
     int herr = 0;
     RSS_CUDA(cudaMemcpy(&herr, d_err, sizeof(int), cudaMemcpyDeviceToHost));

@@ -102,6 +102,7 @@ struct rss_factorization {
   void* d_top_lu = nullptr;            // ntop x ntop
   int* d_top_piv = nullptr;
   int* d_top_idx = nullptr;            // tree indices
+  void* d_top_inv = nullptr;           // ntop x ntop: A_top^{-1}, applied by the solve
   // wall times (ms, host clock around each synchronised phase) for rss_info
   double t_gen = 0, t_id = 0, t_elim = 0, t_schur = 0, t_merge = 0, t_top = 0, t_total = 0;
   // device times (ms, CUDA events on the factor's stream), algorithmic real
@@ -117,5 +118,6 @@ template <typename T> rss_status factor_impl(const rss_tree* tree, const rss_par
                                              cudaStream_t st, rss_factorization* f);
 template <typename T> rss_status solve_impl(const rss_factorization* f, T* b_dev, int64_t nrhs,
                                             int64_t ldb, cudaStream_t st);
+template <typename T> rss_status top_inverse(const T* LU, const int* piv, int n, T* Ainv, cudaStream_t st);
 void free_factor(rss_factorization* f);
 void free_server(rss_server* s);

@@ -35,16 +35,34 @@ __global__ void k_perm_out(T* __restrict__ b, int64_t ldb, const T* __restrict__
   }
 }
 
+// ------------------------------------------------------------------ sweep kernels
+// Rows of C per CTA in the row-chunked kernels; every loop over a factor block
+// reads it down columns, so a warp's loads are contiguous.
+constexpr int SW_NT = 128;
+constexpr int SW_ROWS = 128;
+// Per-box kernels whose FP64 work runs one thread per row of R: 64-thread CTAs,
+// so the busy warps of consecutive CTAs fall on all four SM sub-partitions
+// (an FP64 instruction occupies its sub-partition's pipe for the same time
+// with one active lane or 32).
+constexpr int SW_NT_R = 64;
+constexpr int SW_ROWS_D = 64;   // rows of C per CTA in the downward sweep
+
+// Upward sweep, part 1 (one CTA per box): b_R <- L_R^{-1} P_R (b_R - T^* b_S).
+// One thread per row of R (no warp reductions: an FP64 instruction costs the
+// same with one lane or 32).  T and L^{-1} P are staged in shared memory with
+// coalesced loads when they fit in sm_cap scalars.
 template <typename T, int RC>
-__global__ void __launch_bounds__(NT) k_solve_up(const BoxRec<T>* __restrict__ recs, T* __restrict__ x, int64_t N,
-                                                 int nrhs) {
+__global__ void __launch_bounds__(SW_NT_R) k_up_r(const BoxRec<T>* __restrict__ recs, T* __restrict__ x, int64_t N,
+                                                int nrhs, int sm_cap) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const BoxRec<T> R = recs[blockIdx.x];
-  const int k = R.k, r = R.r, c = R.c;
-  const int q0 = blockIdx.y * RC, nq = min(RC, nrhs - q0);
+  const int k = R.k, r = R.r, ldt = k | 1;
+  const int q0 = blockIdx.z * RC, nq = min(RC, nrhs - q0);
   T* bS = reinterpret_cast<T*>(smraw);   // k x RC
   T* t = bS + (size_t)k * RC;            // r x RC
-  T* bR = t + (size_t)r * RC;            // r x RC
+  T* Ts = t + (size_t)r * RC;            // T, ld k|1
+  T* Ls = Ts + (size_t)ldt * r;          // L^{-1} P, ld r
+  const bool stage = (size_t)(k + r) * RC + (size_t)ldt * r + (size_t)r * r <= (size_t)sm_cap;
   const int tid = threadIdx.x, bs = blockDim.x;
   T* xq = x + (int64_t)q0 * N;
   for (int e = tid; e < k * RC; e += bs) {
@@ -55,30 +73,73 @@ __global__ void __launch_bounds__(NT) k_solve_up(const BoxRec<T>* __restrict__ r
     const int j = e / RC, q = e % RC;
     t[e] = q < nq ? xq[R.idxR[j] + (int64_t)q * N] : zero<T>();
   }
-  __syncthreads();
-  for (int e = tid; e < r * RC; e += bs) {        // b_R - T^* b_S
-    const int j = e / RC, q = e % RC;
-    T acc = t[e];
-    for (int s = 0; s < k; ++s) acc = msbc(acc, R.Tm[s + (size_t)j * k], bS[s * RC + q]);
-    t[e] = acc;
+  if (stage) {
+    for (int e = tid; e < k * r; e += bs) cp_async_el(Ts + (e / k) * ldt + e % k, R.Tm + e);
+    for (int e = tid; e < r * r; e += bs) cp_async_el(Ls + e, R.LiP + e);
+    cp_async_wait_all();
   }
   __syncthreads();
-  for (int e = tid; e < r * RC; e += bs) {        // L_R^{-1} P_R (b_R - T^* b_S)
-    const int j = e / RC, q = e % RC;
-    T acc = zero<T>();
-    for (int l = 0; l < r; ++l) acc = mad(acc, R.LiP[j + (size_t)l * r], t[l * RC + q]);
-    bR[e] = acc;
-    if (q < nq) xq[R.idxR[j] + (int64_t)q * N] = acc;
+  const T* Tsrc = stage ? Ts : R.Tm;
+  const int tl = stage ? ldt : k;
+  const T* Lsrc = stage ? Ls : R.LiP;
+  for (int j = tid; j < r; j += bs) {    // t_j -= sum_s conj(T_sj) b_s
+    T acc[RC];
+#pragma unroll
+    for (int q = 0; q < RC; ++q) acc[q] = t[j * RC + q];
+    for (int s2 = 0; s2 < k; ++s2) {
+      const T tv = Tsrc[s2 + (size_t)j * tl];
+#pragma unroll
+      for (int q = 0; q < RC; ++q) acc[q] = msbc(acc[q], tv, bS[s2 * RC + q]);
+    }
+#pragma unroll
+    for (int q = 0; q < RC; ++q) t[j * RC + q] = acc[q];
   }
   __syncthreads();
-  for (int i = tid; i < c; i += bs) {             // b_C -= E b_R
+  for (int j = tid; j < r; j += bs) {    // b_R = L^{-1} P t
     T acc[RC];
 #pragma unroll
     for (int q = 0; q < RC; ++q) acc[q] = zero<T>();
-    for (int j = 0; j < r; ++j) {
-      const T e = R.E[i + (size_t)j * c];
+#pragma unroll 4
+    for (int l = 0; l < r; ++l) {
+      const T lv = Lsrc[j + (size_t)l * r];
 #pragma unroll
-      for (int q = 0; q < RC; ++q) acc[q] = mad(acc[q], e, bR[j * RC + q]);
+      for (int q = 0; q < RC; ++q) acc[q] = mad(acc[q], lv, t[l * RC + q]);
+    }
+    const int gj = R.idxR[j];
+#pragma unroll
+    for (int q = 0; q < RC; ++q)
+      if (q < nq) xq[gj + (int64_t)q * N] = acc[q];
+  }
+}
+
+// Upward sweep, part 2 (one CTA per SW_ROWS rows of C): b_C -= E b_R.
+template <typename T, int RC>
+__global__ void __launch_bounds__(SW_NT) k_up_c(const BoxRec<T>* __restrict__ recs, T* __restrict__ x, int64_t N,
+                                                int nrhs) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const BoxRec<T> R = recs[blockIdx.y];
+  const int r = R.r, c = R.c, i0 = blockIdx.x * SW_ROWS;
+  if (i0 >= c) return;
+  const int q0 = blockIdx.z * RC, nq = min(RC, nrhs - q0);
+  T* bR = reinterpret_cast<T*>(smraw);   // r x RC
+  const int tid = threadIdx.x, bs = blockDim.x;
+  T* xq = x + (int64_t)q0 * N;
+  for (int e = tid; e < r * RC; e += bs) {
+    const int j = e / RC, q = e % RC;
+    bR[e] = q < nq ? xq[R.idxR[j] + (int64_t)q * N] : zero<T>();
+  }
+  __syncthreads();
+  const int i1 = min(c, i0 + SW_ROWS);
+  for (int i = i0 + tid; i < i1; i += bs) {
+    T acc[RC];
+#pragma unroll
+    for (int q = 0; q < RC; ++q) acc[q] = zero<T>();
+    const T* __restrict__ Ei = R.E + i;
+#pragma unroll 8
+    for (int j = 0; j < r; ++j) {
+      const T ev = Ei[(size_t)j * c];
+#pragma unroll
+      for (int q = 0; q < RC; ++q) acc[q] = mad(acc[q], ev, bR[j * RC + q]);
     }
     const int gi = R.idxC[i];
 #pragma unroll
@@ -87,57 +148,159 @@ __global__ void __launch_bounds__(NT) k_solve_up(const BoxRec<T>* __restrict__ r
   }
 }
 
+// Downward sweep (one CTA per SW_ROWS_D rows of C): partial sums of F y_C over
+// the CTA's rows, one thread per row of R from the CTA's block of F^T staged in
+// shared memory (ld SW_ROWS_D + 1) when it fits in sm_cap scalars.  The last CTA
+// of the box to finish (a counter, no waiting) adds the partial sums, forms
+// y_R <- U^{-1} (y_R - F y_C) and y_S -= T y_R.  Every CTA has read its rows of
+// y_C (which include y_S) before it counts itself in, so the last one may
+// overwrite y_S.
 template <typename T, int RC>
-__global__ void __launch_bounds__(NT) k_solve_down(const BoxRec<T>* __restrict__ recs, T* __restrict__ x,
-                                                   int64_t N, int nrhs) {
+__global__ void __launch_bounds__(SW_NT_R) k_down(const BoxRec<T>* __restrict__ recs, T* __restrict__ x, int64_t N,
+                                                int nrhs, T* __restrict__ part, int* __restrict__ cnt, int nch_max,
+                                                int rmax, int sm_cap) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  const BoxRec<T> R = recs[blockIdx.x];
-  const int k = R.k, r = R.r, c = R.c;
-  const int q0 = blockIdx.y * RC, nq = min(RC, nrhs - q0);
-  T* t = reinterpret_cast<T*>(smraw);   // r x RC
-  T* yR = t + (size_t)r * RC;           // r x RC
-  T* yC = yR + (size_t)r * RC;          // c x RC: y_C gathered once
-  const int tid = threadIdx.x, bs = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = bs >> 5;
+  constexpr int LDF = SW_ROWS_D + 1;
+  const BoxRec<T> R = recs[blockIdx.y];
+  const int k = R.k, r = R.r, c = R.c, nch = (c + SW_ROWS_D - 1) / SW_ROWS_D;
+  if ((int)blockIdx.x >= nch) return;
+  const int i0 = blockIdx.x * SW_ROWS_D, rows = min(SW_ROWS_D, c - i0);
+  const int q0 = blockIdx.z * RC, nq = min(RC, nrhs - q0);
+  const int tid = threadIdx.x, bs = blockDim.x;
+  T* yC = reinterpret_cast<T*>(smraw);   // SW_ROWS_D x RC
+  T* Fs = yC + (size_t)SW_ROWS_D * RC;     // rows x r, ld LDF
+  __shared__ int s_last;
   T* xq = x + (int64_t)q0 * N;
-  for (int e = tid; e < c * RC; e += bs) {
+  const size_t box = (size_t)blockIdx.z * gridDim.y + blockIdx.y;
+  const bool stage = (size_t)SW_ROWS_D * RC + (size_t)LDF * r <= (size_t)sm_cap;
+  for (int e = tid; e < rows * RC; e += bs) {
     const int i = e / RC, q = e % RC;
-    yC[e] = q < nq ? xq[R.idxC[i] + (int64_t)q * N] : zero<T>();
+    yC[e] = q < nq ? xq[R.idxC[i0 + i] + (int64_t)q * N] : zero<T>();
+  }
+  if (stage) {
+    for (int e = tid; e < rows * r; e += bs) {
+      const int i = e % rows, j = e / rows;
+      cp_async_el(Fs + i + (size_t)j * LDF, R.Ft + i0 + i + (size_t)j * c);
+    }
+    cp_async_wait_all();
   }
   __syncthreads();
-  for (int j = warp; j < r; j += nw) {            // y_R - F y_C
+  T* pp = part + ((box * nch_max + blockIdx.x) * rmax) * RC;
+  for (int j = tid; j < r; j += bs) {
     T acc[RC];
 #pragma unroll
     for (int q = 0; q < RC; ++q) acc[q] = zero<T>();
-    for (int i = lane; i < c; i += 32) {
-      const T fv = R.Ft[i + (size_t)j * c];
+    const T* Fj = stage ? Fs + (size_t)j * LDF : R.Ft + i0 + (size_t)j * c;
+#pragma unroll 4
+    for (int i = 0; i < rows; ++i) {
+      const T fv = Fj[i];
 #pragma unroll
       for (int q = 0; q < RC; ++q) acc[q] = mad(acc[q], fv, yC[i * RC + q]);
     }
 #pragma unroll
-    for (int q = 0; q < RC; ++q) acc[q] = warp_sum(acc[q]);
-    if (lane == 0) {
-      const int gj = R.idxR[j];
+    for (int q = 0; q < RC; ++q) pp[j * RC + q] = acc[q];
+  }
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) s_last = atomicAdd(cnt + box, 1) == nch - 1;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  T* z = yC;                    // r x RC (the shared buffers are free now)
+  T* yR = z + (size_t)r * RC;   // r x RC
+  T* Ms = yR + (size_t)r * RC;  // U^{-1} (r x r) and T (k x r, ld k|1)
+  const int ldt = k | 1;
+  const bool stage2 = (size_t)2 * r * RC + (size_t)r * r + (size_t)ldt * r <= (size_t)sm_cap;
+  T* Us = Ms;
+  T* Ts = Ms + (size_t)r * r;
+  for (int e = tid; e < r * RC; e += bs) {
+    const int j = e / RC, q = e % RC;
+    T sum = zero<T>();
+    for (int ch = 0; ch < nch; ++ch) sum = sum + ld_l2(part + ((box * nch_max + ch) * rmax + j) * RC + q);
+    z[e] = q < nq ? xq[R.idxR[j] + (int64_t)q * N] - sum : zero<T>();
+  }
+  if (stage2) {
+    for (int e = tid; e < r * r; e += bs) cp_async_el(Us + e, R.Ui + e);
+    for (int e = tid; e < k * r; e += bs) cp_async_el(Ts + (e / k) * ldt + e % k, R.Tm + e);
+    cp_async_wait_all();
+  }
+  __syncthreads();
+  const T* Usrc = stage2 ? Us : R.Ui;
+  for (int j = tid; j < r; j += bs) {    // y_R = U^{-1} z
+    T acc[RC];
 #pragma unroll
-      for (int q = 0; q < RC; ++q) t[j * RC + q] = q < nq ? xq[gj + (int64_t)q * N] - acc[q] : zero<T>();
+    for (int q = 0; q < RC; ++q) acc[q] = zero<T>();
+#pragma unroll 4
+    for (int l = j; l < r; ++l) {
+      const T uv = Usrc[j + (size_t)l * r];
+#pragma unroll
+      for (int q = 0; q < RC; ++q) acc[q] = mad(acc[q], uv, z[l * RC + q]);
+    }
+    const int gj = R.idxR[j];
+#pragma unroll
+    for (int q = 0; q < RC; ++q) {
+      yR[j * RC + q] = acc[q];
+      if (q < nq) xq[gj + (int64_t)q * N] = acc[q];
     }
   }
   __syncthreads();
-  for (int e = tid; e < r * RC; e += bs) {        // U_R^{-1} (y_R - F y_C)
+  const T* Tsrc = stage2 ? Ts : R.Tm;
+  const int tl = stage2 ? ldt : k;
+  for (int s2 = tid; s2 < k; s2 += bs) {   // y_S -= T y_R
+    T acc[RC];
+#pragma unroll
+    for (int q = 0; q < RC; ++q) acc[q] = zero<T>();
+#pragma unroll 4
+    for (int j = 0; j < r; ++j) {
+      const T tv = Tsrc[s2 + (size_t)j * tl];
+#pragma unroll
+      for (int q = 0; q < RC; ++q) acc[q] = mad(acc[q], tv, yR[j * RC + q]);
+    }
+    const int gs = R.idxC[s2];
+#pragma unroll
+    for (int q = 0; q < RC; ++q)
+      if (q < nq) xq[gs + (int64_t)q * N] = xq[gs + (int64_t)q * N] - acc[q];
+  }
+  if (tid == 0) cnt[box] = 0;   // ready for the next colour class
+}
+
+// Top block: x_top <- A_top^{-1} x_top with the inverse formed at factor time.
+template <typename T>
+__global__ void k_top_gather(const int* __restrict__ idx, int n, const T* __restrict__ x, int64_t N, int nrhs,
+                             T* __restrict__ z) {
+  const long long tot = (long long)n * nrhs;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(e % n);
+    const long long q = e / n;
+    z[e] = x[idx[i] + q * N];
+  }
+}
+
+template <typename T, int RC>
+__global__ void __launch_bounds__(SW_NT) k_top_gemv(const T* __restrict__ Ainv, const int* __restrict__ idx, int n,
+                                                    const T* __restrict__ z, T* __restrict__ x, int64_t N, int nrhs) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* zs = reinterpret_cast<T*>(smraw);   // n x RC
+  const int q0 = blockIdx.y * RC, nq = min(RC, nrhs - q0);
+  for (int e = threadIdx.x; e < n * RC; e += blockDim.x) {
     const int j = e / RC, q = e % RC;
-    T acc = zero<T>();
-    for (int l = j; l < r; ++l) acc = mad(acc, R.Ui[j + (size_t)l * r], t[l * RC + q]);
-    yR[e] = acc;
-    if (q < nq) xq[R.idxR[j] + (int64_t)q * N] = acc;
+    zs[e] = q < nq ? z[j + (int64_t)(q0 + q) * n] : zero<T>();
   }
   __syncthreads();
-  for (int e = tid; e < k * RC; e += bs) {        // y_S -= T y_R
-    const int s = e / RC, q = e % RC;
-    if (q >= nq) continue;
-    T acc = zero<T>();
-    for (int j = 0; j < r; ++j) acc = mad(acc, R.Tm[s + (size_t)j * k], yR[j * RC + q]);
-    const int gs = R.idxC[s];
-    xq[gs + (int64_t)q * N] = xq[gs + (int64_t)q * N] - acc;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  T acc[RC];
+#pragma unroll
+  for (int q = 0; q < RC; ++q) acc[q] = zero<T>();
+#pragma unroll 8
+  for (int j = 0; j < n; ++j) {
+    const T av = Ainv[i + (size_t)j * n];
+#pragma unroll
+    for (int q = 0; q < RC; ++q) acc[q] = mad(acc[q], av, zs[j * RC + q]);
   }
+#pragma unroll
+  for (int q = 0; q < RC; ++q)
+    if (q < nq) x[idx[i] + (int64_t)(q0 + q) * N] = acc[q];
 }
 
 // Dense top solve, blocked by 32: one warp solves each diagonal block (no
@@ -215,44 +378,133 @@ __global__ void __launch_bounds__(1024) k_top_solve(const T* __restrict__ LU, co
   }
 }
 
-template <typename T, int RC>
-rss_status sweeps(const rss_factorization* f, T* x, int64_t N, int nrhs, cudaStream_t st) {
-  const unsigned nchunk = cdiv(nrhs, RC);
-  RSS_CUDA(cudaFuncSetAttribute(k_solve_up<T, RC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-  RSS_CUDA(cudaFuncSetAttribute(k_solve_down<T, RC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+__global__ void k_iota(int* v, int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) v[i] = i;
+}
+template <typename T> __global__ void k_identity(T* A, int n) {
+  const long long tot = (long long)n * n;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x)
+    A[e] = (e % n == e / n) ? from_re<T>(1.0) : zero<T>();
+}
+
+// Workspace of the sweeps for nrhs right-hand sides in chunks of rc columns:
+// the downward sweep's partial sums, one counter per box, the gathered top block.
+struct SweepWs {
+  size_t cnt_off = 0, topz_off = 0, bytes = 0;
+};
+
+template <typename T> SweepWs sweep_ws(const rss_factorization* f, int64_t nrhs, int rc) {
+  const size_t nz = cdiv(nrhs, rc);
+  size_t part = 0, cnt = 0;
   for (const Batch& b : f->batches) {
-    const size_t smem = sizeof(T) * (size_t)(b.max_k + 2 * b.max_r) * RC;
-    k_solve_up<T, RC><<<dim3(b.nrec, nchunk), NT, smem, st>>>(static_cast<const BoxRec<T>*>(b.d_recs), x, N, nrhs);
+    part = std::max(part, (size_t)b.nrec * cdiv(b.max_c, SW_ROWS_D) * b.max_r);
+    cnt = std::max(cnt, (size_t)b.nrec);
+  }
+  auto al = [](size_t v) { return (v + 255) & ~size_t(255); };
+  SweepWs w;
+  w.cnt_off = al(sizeof(T) * part * nz * rc);
+  w.topz_off = w.cnt_off + al(sizeof(int) * cnt * nz);
+  w.bytes = w.topz_off + al(sizeof(T) * (size_t)f->ntop * nz * rc);
+  return w;
+}
+
+int rhs_chunk(int64_t nrhs) { return nrhs == 1 ? 1 : nrhs <= 4 ? 4 : 8; }
+
+template <typename T, int RC>
+rss_status sweeps(const rss_factorization* f, T* x, int64_t N, int nrhs, cudaStream_t st, void* ws) {
+  const unsigned nz = cdiv(nrhs, RC);
+  const SweepWs w = sweep_ws<T>(f, nrhs, RC);
+  char* wb = static_cast<char*>(ws);
+  T* part = reinterpret_cast<T*>(wb);
+  int* cnt = reinterpret_cast<int*>(wb + w.cnt_off);
+  T* topz = reinterpret_cast<T*>(wb + w.topz_off);
+  RSS_CUDA(cudaMemsetAsync(cnt, 0, w.topz_off - w.cnt_off, st));
+  RSS_CUDA(cudaFuncSetAttribute(k_up_r<T, RC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+  RSS_CUDA(cudaFuncSetAttribute(k_up_c<T, RC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+  RSS_CUDA(cudaFuncSetAttribute(k_down<T, RC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+  RSS_CUDA(cudaFuncSetAttribute(k_top_gemv<T, RC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+  for (const Batch& b : f->batches) {
+    const BoxRec<T>* recs = static_cast<const BoxRec<T>*>(b.d_recs);
+    const size_t want_r = sizeof(T) * ((size_t)(b.max_k + b.max_r) * RC + (size_t)(b.max_k | 1) * b.max_r +
+                                       (size_t)b.max_r * b.max_r);
+    const size_t sm_r = std::min<size_t>(want_r, 96 * 1024);
+    k_up_r<T, RC><<<dim3(b.nrec, 1, nz), SW_NT_R, sm_r, st>>>(recs, x, N, nrhs, (int)(sm_r / sizeof(T)));
+    RSS_LAUNCHED();
+    k_up_c<T, RC><<<dim3(cdiv(b.max_c, SW_ROWS), b.nrec, nz), SW_NT, sizeof(T) * (size_t)b.max_r * RC, st>>>(
+        recs, x, N, nrhs);
     RSS_LAUNCHED();
   }
-  constexpr int RT = 4;
-  const size_t tsm = sizeof(T) * (size_t)f->ntop * RT;
-  if (tsm > 200 * 1024) {
-    rss_set_error("rss_solve: top block too large for the on-chip solve");
-    return RSS_EINVAL;
-  }
-  RSS_CUDA(cudaFuncSetAttribute(k_top_solve<T, RT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
   if (f->ntop > 0) {
-    k_top_solve<T, RT><<<cdiv(nrhs, RT), 1024, tsm, st>>>(static_cast<const T*>(f->d_top_lu), f->d_top_piv,
-                                                         f->d_top_idx, f->ntop, x, N, nrhs);
+    const size_t tsm = sizeof(T) * (size_t)f->ntop * RC;
+    if (tsm > 200 * 1024) {
+      rss_set_error("rss_solve: top block too large for the on-chip solve");
+      return RSS_EINVAL;
+    }
+    const unsigned g = std::min<long long>(cdiv((long long)f->ntop * nz * RC, 256), 152LL * 8);
+    k_top_gather<T><<<g, 256, 0, st>>>(f->d_top_idx, f->ntop, x, N, nrhs, topz);
+    RSS_LAUNCHED();
+    k_top_gemv<T, RC><<<dim3(cdiv(f->ntop, SW_NT), nz), SW_NT, tsm, st>>>(static_cast<const T*>(f->d_top_inv),
+                                                                          f->d_top_idx, f->ntop, topz, x, N, nrhs);
     RSS_LAUNCHED();
   }
   for (auto it = f->batches.rbegin(); it != f->batches.rend(); ++it) {
-    const size_t smem = sizeof(T) * (size_t)(2 * it->max_r + it->max_c) * RC;
-    k_solve_down<T, RC><<<dim3(it->nrec, nchunk), NT, smem, st>>>(static_cast<const BoxRec<T>*>(it->d_recs), x, N,
-                                                                 nrhs);
+    const int nch = (int)cdiv(it->max_c, SW_ROWS_D);
+    const size_t want_d =
+        sizeof(T) * std::max((size_t)SW_ROWS_D * RC + (size_t)(SW_ROWS_D + 1) * it->max_r,
+                             (size_t)2 * it->max_r * RC + (size_t)it->max_r * it->max_r +
+                                 (size_t)(it->max_k | 1) * it->max_r);
+    const size_t sm_d = std::min<size_t>(want_d, 96 * 1024);
+    k_down<T, RC><<<dim3(nch, it->nrec, nz), SW_NT_R, sm_d, st>>>(static_cast<const BoxRec<T>*>(it->d_recs), x, N,
+                                                                nrhs, part, cnt, nch, it->max_r, (int)(sm_d / sizeof(T)));
     RSS_LAUNCHED();
   }
   return RSS_OK;
 }
 
+template <typename T>
+rss_status run_sweeps(const rss_factorization* f, T* x, int64_t N, int64_t nrhs, cudaStream_t st, void* ws) {
+  const int rc = rhs_chunk(nrhs);
+  return rc == 1 ? sweeps<T, 1>(f, x, N, (int)nrhs, st, ws)
+         : rc == 4 ? sweeps<T, 4>(f, x, N, (int)nrhs, st, ws)
+                   : sweeps<T, 8>(f, x, N, (int)nrhs, st, ws);
+}
+
 }  // namespace
+
+// A_top^{-1}, column by column from the LU (identity right-hand sides).
+template <typename T> rss_status top_inverse(const T* LU, const int* piv, int n, T* Ainv, cudaStream_t st) {
+  constexpr int RT = 4;
+  const size_t tsm = sizeof(T) * (size_t)n * RT;
+  if (tsm > 200 * 1024) {
+    rss_set_error("rss_factor: top block too large for the on-chip solve");
+    return RSS_EINVAL;
+  }
+  int* iota = nullptr;
+  RSS_CUDA(cudaMallocAsync(&iota, sizeof(int) * (size_t)n, st));
+  k_iota<<<cdiv(n, 256), 256, 0, st>>>(iota, n);
+  k_identity<T><<<std::min<long long>(cdiv((long long)n * n, 256), 152LL * 8), 256, 0, st>>>(Ainv, n);
+  RSS_CUDA(cudaFuncSetAttribute(k_top_solve<T, RT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+  k_top_solve<T, RT><<<cdiv(n, RT), 1024, tsm, st>>>(LU, piv, iota, n, Ainv, n, n);
+  const cudaError_t e = cudaGetLastError();
+  cudaFreeAsync(iota, st);
+  if (e != cudaSuccess) {
+    rss_set_error(std::string("rss_factor: top inverse launch failed: ") + cudaGetErrorString(e));
+    return RSS_ECUDA;
+  }
+  return RSS_OK;
+}
+
+template rss_status top_inverse<double>(const double*, const int*, int, double*, cudaStream_t);
+template rss_status top_inverse<zd>(const zd*, const int*, int, zd*, cudaStream_t);
 
 template <typename T>
 rss_status solve_impl(const rss_factorization* f, T* b, int64_t nrhs, int64_t ldb, cudaStream_t st) {
   const int64_t N = f->n;
-  T* x = nullptr;
-  RSS_CUDA(cudaMallocAsync(&x, sizeof(T) * (size_t)N * nrhs, st));
+  const SweepWs w = sweep_ws<T>(f, nrhs, rhs_chunk(nrhs));
+  const size_t xb = (sizeof(T) * (size_t)N * nrhs + 255) & ~size_t(255);
+  char* mem = nullptr;
+  RSS_CUDA(cudaMallocAsync(&mem, xb + w.bytes, st));
+  T* x = reinterpret_cast<T*>(mem);
   const unsigned grid = std::min<long long>(cdiv((long long)N * nrhs, NT), 152LL * 16);
   k_perm_in<T><<<grid, NT, 0, st>>>(b, ldb, x, N, (int)nrhs, f->d_user_to_tree);
   rss_status s = RSS_OK;
@@ -260,11 +512,7 @@ rss_status solve_impl(const rss_factorization* f, T* b, int64_t nrhs, int64_t ld
     rss_set_error("rss_solve: launch failed");
     s = RSS_ECUDA;
   }
-  if (s == RSS_OK) {
-    if (nrhs == 1) s = sweeps<T, 1>(f, x, N, (int)nrhs, st);
-    else if (nrhs <= 4) s = sweeps<T, 4>(f, x, N, (int)nrhs, st);
-    else s = sweeps<T, 8>(f, x, N, (int)nrhs, st);
-  }
+  if (s == RSS_OK) s = run_sweeps<T>(f, x, N, nrhs, st, mem + xb);
   if (s == RSS_OK) {
     k_perm_out<T><<<grid, NT, 0, st>>>(b, ldb, x, N, (int)nrhs, f->d_user_to_tree);
     if (cudaGetLastError() != cudaSuccess) {
@@ -272,7 +520,7 @@ rss_status solve_impl(const rss_factorization* f, T* b, int64_t nrhs, int64_t ld
       s = RSS_ECUDA;
     }
   }
-  cudaFreeAsync(x, st);
+  cudaFreeAsync(mem, st);
   return s;
 }
 
@@ -325,10 +573,8 @@ rss_status solve_in_scratch(const rss_factorization* f, T* b, int64_t nrhs, int6
   // every entry of x is written here, so nothing left from an earlier call is read
   k_perm_in<T><<<grid, NT, 0, st>>>(b, ldb, x, N, (int)nrhs, f->d_user_to_tree);
   RSS_LAUNCHED();
-  rss_status s;
-  if (nrhs == 1) s = sweeps<T, 1>(f, x, N, (int)nrhs, st);
-  else if (nrhs <= 4) s = sweeps<T, 4>(f, x, N, (int)nrhs, st);
-  else s = sweeps<T, 8>(f, x, N, (int)nrhs, st);
+  const size_t xb = (sizeof(T) * (size_t)N * nrhs + 255) & ~size_t(255);
+  const rss_status s = run_sweeps<T>(f, x, N, nrhs, st, reinterpret_cast<char*>(x) + xb);
   if (s != RSS_OK) return s;
   k_perm_out<T><<<grid, NT, 0, st>>>(b, ldb, x, N, (int)nrhs, f->d_user_to_tree);
   RSS_LAUNCHED();
@@ -348,9 +594,11 @@ extern "C" rss_status rss_solve_noalloc(const rss_factorization* f, void* b, int
     return RSS_EINVAL;
   }
   const size_t esz = f->is_complex ? 16 : 8;
-  const size_t need = esz * (size_t)f->n * (size_t)nrhs;
+  const size_t need = ((esz * (size_t)f->n * (size_t)nrhs + 255) & ~size_t(255)) +
+                      (f->is_complex ? sweep_ws<zd>(f, nrhs, rhs_chunk(nrhs)).bytes
+                                     : sweep_ws<double>(f, nrhs, rhs_chunk(nrhs)).bytes);
   if (need > kNoAllocScratchBytes) {
-    rss_set_error("rss_solve_noalloc: n * nrhs needs " + std::to_string(need) +
+    rss_set_error("rss_solve_noalloc: n * nrhs (with the sweep workspace) needs " + std::to_string(need) +
                   " bytes of scratch; the fixed maximum is " + std::to_string(kNoAllocScratchBytes) +
                   " bytes (use rss_solve, or fewer right-hand sides per call)");
     return RSS_EINVAL;
