@@ -891,6 +891,54 @@ __device__ void oz_split_row(const zd* __restrict__ src, int stride, int r, int 
     }
 }
 
+// LU with partial pivoting of the r x r matrix LU (ld r) by the whole CTA:
+// largest modulus, lowest row on ties; the exchanges go to piv.  Returns false
+// (after flagging RSS_ENUMERIC) on a zero pivot.
+template <typename T> __device__ bool lu_pp_block(T* LU, int r, int* piv, int* err) {
+  __shared__ int s_piv, s_zero;
+  const int tid = threadIdx.x, bs = blockDim.x, lane = tid & 31, warp = tid >> 5;
+  for (int j = 0; j < r; ++j) {
+    if (warp == 0) {
+      double mx = -1.0;
+      int mi = INT_MAX;
+      for (int i = j + lane; i < r; i += 32) {
+        const double v = abs2(LU[i + (size_t)j * r]);
+        if (v > mx) { mx = v; mi = i; }
+      }
+      for (int d = 16; d > 0; d >>= 1) {
+        const double om = __shfl_xor_sync(0xffffffffu, mx, d);
+        const int oi = __shfl_xor_sync(0xffffffffu, mi, d);
+        if (om > mx || (om == mx && oi < mi)) { mx = om; mi = oi; }
+      }
+      if (lane == 0) { s_piv = mi; s_zero = !(mx > 0.0); }
+    }
+    __syncthreads();
+    if (s_zero) {
+      if (tid == 0) atomicExch(err, (int)RSS_ENUMERIC);
+      return false;
+    }
+    const int p = s_piv;
+    if (p != j)
+      for (int col = tid; col < r; col += bs) {
+        const T t = LU[j + (size_t)col * r];
+        LU[j + (size_t)col * r] = LU[p + (size_t)col * r];
+        LU[p + (size_t)col * r] = t;
+      }
+    if (tid == 0) piv[j] = p;
+    __syncthreads();
+    const T d = dv(from_re<T>(1.0), LU[j + (size_t)j * r]);
+    for (int i = j + 1 + tid; i < r; i += bs) LU[i + (size_t)j * r] = LU[i + (size_t)j * r] * d;
+    __syncthreads();
+    const int w = r - j - 1;
+    for (int e = tid; e < w * w; e += bs) {
+      const int ii = j + 1 + e % w, jj = j + 1 + e / w;
+      LU[ii + (size_t)jj * r] = msb(LU[ii + (size_t)jj * r], LU[ii + (size_t)j * r], LU[j + (size_t)jj * r]);
+    }
+    __syncthreads();
+  }
+  return true;
+}
+
 // ------------------------------------------------------------------ sparsify + LU (Eqs. 7, 8)
 // k_elim_lu (one CTA per box): C map, X_SR, X_RR, P X_RR = L U, U^{-1}, L^{-1}
 // and L^{-1} P.  k_elim_panels (one CTA per 16-, 32- or 64-row panel of C): X_CR, X_RC and
@@ -914,7 +962,7 @@ template <typename T> __global__ void __launch_bounds__(NT, 4) k_elim_lu(ElimArg
   T* LU = onchip ? reinterpret_cast<T*>(smT) : R.LU;
   T* Ts = onchip ? LU + (size_t)r * r : R.Tm;
   T* Wb = onchip ? Ts : nullptr;
-  __shared__ int nb[9], coff[10], s_piv, s_zero, ord[9];
+  __shared__ int nb[9], coff[10], ord[9];
   if (tid == 0) {
     const int o9[9] = {4, 0, 1, 2, 3, 5, 6, 7, 8};
     int off = 0;
@@ -962,45 +1010,7 @@ template <typename T> __global__ void __launch_bounds__(NT, 4) k_elim_lu(ElimArg
   }
   __syncthreads();
   // P X_RR = L U, partial pivoting (largest modulus, lowest row on ties)   (Eq. 8)
-  for (int j = 0; j < r; ++j) {
-    if (warp == 0) {
-      double mx = -1.0;
-      int mi = INT_MAX;
-      for (int i = j + lane; i < r; i += 32) {
-        const double v = abs2(LU[i + (size_t)j * r]);
-        if (v > mx) { mx = v; mi = i; }
-      }
-      for (int d = 16; d > 0; d >>= 1) {
-        const double om = __shfl_xor_sync(0xffffffffu, mx, d);
-        const int oi = __shfl_xor_sync(0xffffffffu, mi, d);
-        if (om > mx || (om == mx && oi < mi)) { mx = om; mi = oi; }
-      }
-      if (lane == 0) { s_piv = mi; s_zero = !(mx > 0.0); }
-    }
-    __syncthreads();
-    if (s_zero) {
-      if (tid == 0) atomicExch(a.err, (int)RSS_ENUMERIC);
-      return;
-    }
-    const int p = s_piv;
-    if (p != j)
-      for (int col = tid; col < r; col += bs) {
-        const T t = LU[j + (size_t)col * r];
-        LU[j + (size_t)col * r] = LU[p + (size_t)col * r];
-        LU[p + (size_t)col * r] = t;
-      }
-    if (tid == 0) R.piv[j] = p;
-    __syncthreads();
-    const T d = dv(from_re<T>(1.0), LU[j + (size_t)j * r]);
-    for (int i = j + 1 + tid; i < r; i += bs) LU[i + (size_t)j * r] = LU[i + (size_t)j * r] * d;
-    __syncthreads();
-    const int w = r - j - 1;
-    for (int e = tid; e < w * w; e += bs) {
-      const int ii = j + 1 + e % w, jj = j + 1 + e / w;
-      LU[ii + (size_t)jj * r] = msb(LU[ii + (size_t)jj * r], LU[ii + (size_t)j * r], LU[j + (size_t)jj * r]);
-    }
-    __syncthreads();
-  }
+  if (!lu_pp_block(LU, r, R.piv, a.err)) return;
   // U^{-1} and L^{-1}, one column per thread (built in shared memory when it
   // fits, then copied out); L^{-1} P is L^{-1} with its columns permuted:
   // P e_j = e_{pos(j)} for pos the inverse of the exchange order sig (P v = v[sig])
@@ -1133,6 +1143,146 @@ template <typename T> __global__ void __launch_bounds__(NT, 4) k_elim_lu(ElimArg
 // the columns of A(B, u) for X_RC and F^T = (L^{-1} P_R X_RC)^T.  The right
 // operands (T, U^{-1}, L^{-1}) are staged from global memory in chunks, so any
 // rank fits.
+// On-chip k_elim_lu for boxes whose blocks fit in shared memory (and whose E
+// and F come from the panel kernels): the permuted diagonal block A_BB is
+// staged by cp.async, and X_SR, X_RR, the LU and both triangular inverses stay
+// on chip.  Every phase spreads its work over the whole CTA; U^{-1} and L^{-1}
+// are built by row sweeps (after row i is final it is subtracted from the
+// rows it feeds, one rank-1 update per row).
+template <typename T> __host__ __device__ inline size_t elim_lu_sm_bytes(int k, int r) {
+  const size_t n = (size_t)k + r;
+  const size_t ints = ((n + 2 * (size_t)r) * sizeof(int) + 15) & ~size_t(15);
+  const size_t kr = (size_t)k * r, rr = (size_t)r * r;
+  return ints + sizeof(T) * (n * n + kr + (kr > rr ? kr : rr) + rr);
+}
+
+template <typename T> __global__ void __launch_bounds__(NT, 2) k_elim_lu_sm(ElimArgs<T> a) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const LevelDev<T>& L = a.L;
+  const BoxRec<T> R = a.recs[blockIdx.x];
+  const int nmax = L.nmax, g = L.g, B = R.box, k = R.k, r = R.r, c = R.c, n = k + r;
+  const size_t nn = (size_t)nmax * nmax;
+  const int* perm_g = a.perm_in + (size_t)a.cls_idx[blockIdx.x] * nmax;
+  const T* Tw = a.T_ws + (size_t)a.cls_idx[blockIdx.x] * nn;
+  const int tid = threadIdx.x, bs = blockDim.x;
+  int* sp = reinterpret_cast<int*>(smraw);   // n: B's points in pivot order
+  int* sperm = sp + n;                      // 2 r: exchange order and its inverse
+  T* Ap = reinterpret_cast<T*>(smraw + (((size_t)(n + 2 * r) * sizeof(int) + 15) & ~size_t(15)));   // n x n
+  T* Ts = Ap + (size_t)n * n;                       // k x r
+  T* Xs = Ts + (size_t)k * r;                       // k x r: X_SR; later U^{-1} (r x r)
+  T* LU = Xs + (size_t)max(k * r, r * r);           // r x r
+  T* Ui = Xs;
+  T* Li = Ap;                                       // r x r, once A_BB is no longer needed
+  __shared__ int nb[9], coff[10], ord[9];
+  if (tid == 0) {
+    const int o9[9] = {4, 0, 1, 2, 3, 5, 6, 7, 8};
+    int off = 0;
+    for (int q = 0; q < 9; ++q) {
+      const int s = o9[q];
+      ord[q] = s;
+      nb[s] = nbr_box(B, g, s % 3 - 1, s / 3 - 1);
+      coff[q] = off;
+      off += s == 4 ? k : (nb[s] >= 0 ? L.nact[nb[s]] : 0);
+    }
+    coff[9] = off;
+  }
+  for (int i = tid; i < n; i += bs) sp[i] = perm_g[i];
+  __syncthreads();
+  const T* Abb = L.blk + ((size_t)B * 25 + 12) * nn;
+  for (int e = tid; e < n * n; e += bs) cp_async_el(Ap + e, Abb + (size_t)sp[e / n] * nmax + sp[e % n]);
+  for (int e = tid; e < k * r; e += bs) cp_async_el(Ts + e, Tw + (size_t)(e / k) * nmax + e % k);
+  for (int i = tid; i < c; i += bs) {
+    int q = 0;
+    while (coff[q + 1] <= i) ++q;
+    const int s = ord[q], ii = i - coff[q], u = nb[s];
+    const int pos = s == 4 ? sp[ii] : L.act[u * nmax + ii];
+    R.cmap[i] = (s << 16) | pos;
+    R.idxC[i] = L.pts[u * nmax + pos];
+  }
+  for (int j = tid; j < r; j += bs) R.idxR[j] = L.pts[B * nmax + sp[k + j]];
+  cp_async_wait_all();
+  __syncthreads();
+  for (int e = tid; e < k * r; e += bs) R.Tm[e] = Ts[e];
+  // X_SR = A_SR - A_SS T
+  for (int e = tid; e < k * r; e += bs) {
+    const int si = e % k, j = e / k;
+    T x = Ap[si + (size_t)(k + j) * n];
+    for (int q = 0; q < k; ++q) x = msb(x, Ap[si + (size_t)q * n], Ts[q + (size_t)j * k]);
+    Xs[e] = x;
+  }
+  __syncthreads();
+  // X_RR = A_RR - A_RS T - T^* X_SR
+  for (int e = tid; e < r * r; e += bs) {
+    const int ai = e % r, bj = e / r;
+    T x = Ap[(k + ai) + (size_t)(k + bj) * n];
+    for (int q = 0; q < k; ++q) x = msb(x, Ap[(k + ai) + (size_t)q * n], Ts[q + (size_t)bj * k]);
+    for (int q = 0; q < k; ++q) x = msbc(x, Ts[q + (size_t)ai * k], Xs[q + (size_t)bj * k]);
+    LU[e] = x;
+  }
+  __syncthreads();
+  if (!lu_pp_block(LU, r, R.piv, a.err)) return;
+  // U^{-1}: rows from the bottom
+  for (int e = tid; e < r * r; e += bs) Ui[e] = (e % r == e / r) ? from_re<T>(1.0) : zero<T>();
+  for (int e = tid; e < r * r; e += bs) Li[e] = (e % r == e / r) ? from_re<T>(1.0) : zero<T>();
+  __syncthreads();
+  for (int i = r - 1; i >= 0; --i) {
+    const T d = dv(from_re<T>(1.0), LU[i + (size_t)i * r]);
+    for (int j = i + tid; j < r; j += bs) Ui[i + (size_t)j * r] = Ui[i + (size_t)j * r] * d;
+    __syncthreads();
+    const int w = r - i;
+    for (int e = tid; e < i * w; e += bs) {
+      const int l = e % i, j = i + e / i;
+      Ui[l + (size_t)j * r] = msb(Ui[l + (size_t)j * r], LU[l + (size_t)i * r], Ui[i + (size_t)j * r]);
+    }
+    __syncthreads();
+  }
+  // L^{-1} (unit lower): rows from the top
+  for (int i = 0; i < r - 1; ++i) {
+    const int below = r - 1 - i;
+    for (int e = tid; e < below * (i + 1); e += bs) {
+      const int l = i + 1 + e % below, j = e / below;
+      Li[l + (size_t)j * r] = msb(Li[l + (size_t)j * r], LU[l + (size_t)i * r], Li[i + (size_t)j * r]);
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {   // exchange order sig (P v = v[sig]) and its inverse
+    for (int i = 0; i < r; ++i) sperm[i] = i;
+    for (int i = 0; i < r; ++i) {
+      const int p = R.piv[i], t = sperm[i];
+      sperm[i] = sperm[p];
+      sperm[p] = t;
+    }
+    for (int i = 0; i < r; ++i) sperm[r + sperm[i]] = i;
+  }
+  __syncthreads();
+  for (int e = tid; e < r * r; e += bs) {
+    R.LU[e] = LU[e];
+    R.Ui[e] = Ui[e];
+    R.Li[e] = Li[e];
+    R.LiP[e] = Li[e % r + (size_t)sperm[r + e / r] * r];
+  }
+  if (R.ozp) {   // W_E and W_F, as in k_elim_lu
+    for (int e = tid; e < n * r; e += bs) {
+      const int l = e % n, j = e / n;
+      T we, wf;
+      if (l < k) {
+        we = zero<T>();
+        for (int m = 0; m <= j; ++m) we = msb(we, Ts[l + (size_t)m * k], Ui[m + (size_t)j * r]);
+        wf = zero<T>();
+        for (int m = 0; m < r; ++m) wf = msb(wf, Li[j + (size_t)sperm[r + m] * r], cj(Ts[l + (size_t)m * k]));
+      } else {
+        we = l - k <= j ? Ui[(l - k) + (size_t)j * r] : zero<T>();
+        wf = Li[j + (size_t)sperm[r + l - k] * r];
+      }
+      R.We[e] = we;
+      R.Wf[e] = wf;
+    }
+  }
+  // B keeps only its skeleton
+  for (int q = tid; q < k; q += bs) L.act[B * nmax + q] = sp[q];
+  if (tid == 0) L.nact[B] = k;
+}
+
 template <typename T, int MA, int NBMAX>
 __device__ void elim_panel_body(const ElimArgs<T>& a, const BoxRec<T>& R, unsigned char* smraw, int p0, int rows) {
   constexpr int EPR = 16 * MA;
@@ -2361,10 +2511,23 @@ rss_status factor_impl(const rss_tree* tree, const rss_params* prm, cudaStream_t
           sizeof(T) * ((size_t)max_r * max_r + std::max((size_t)max_k * max_r, (size_t)max_r * max_r)) + ints;
       const size_t ecap = std::min<size_t>(want, 200 * 1024);
       ea.smem_cap = (int)((ecap - ints) / sizeof(T));
-      RSS_CUDA(cudaFuncSetAttribute(k_elim_lu<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ecap));
+      // the on-chip kernel when every box fits and takes E and F from the panel kernels
+      size_t sm_lu = 0;
+      bool lu_sm = true;
+      for (const BoxRec<T>& R : recs) {
+        sm_lu = std::max(sm_lu, elim_lu_sm_bytes<T>(R.k, R.r));
+        lu_sm = lu_sm && (R.panels || R.ozp);
+      }
+      lu_sm = lu_sm && sm_lu <= 200 * 1024;
       evs.emplace_back(1, std::make_unique<Ev>());
       evs.back().second->start(st);
-      k_elim_lu<T><<<nrec, NT, ecap, st>>>(ea);
+      if (lu_sm) {
+        RSS_CUDA(cudaFuncSetAttribute(k_elim_lu_sm<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_lu));
+        k_elim_lu_sm<T><<<nrec, NT, sm_lu, st>>>(ea);
+      } else {
+        RSS_CUDA(cudaFuncSetAttribute(k_elim_lu<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ecap));
+        k_elim_lu<T><<<nrec, NT, ecap, st>>>(ea);
+      }
       RSS_LAUNCHED();
       if (pan_max > 0) {
         auto launch_panels = [&](auto kern, int rows) -> cudaError_t {
