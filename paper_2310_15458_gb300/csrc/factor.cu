@@ -145,6 +145,7 @@ template <typename T, typename S = T> struct IdArgs {
   int P;              // proxy points
   double rho;         // proxy radius
   double Lbox;        // box side
+  int g_sm;           // 1: G (nmax x nmax) and row k of V are kept in shared memory
 };
 
 template <typename T, typename S> __device__ inline S id_store(T v) {
@@ -204,6 +205,9 @@ template <typename T, typename S = T> __global__ void __launch_bounds__(NT_ID, 4
   double* taus = ref + nmax;
   int* perm = reinterpret_cast<int*>(taus + nmax);
   int* flag = perm + nmax;
+  T* Gs = reinterpret_cast<T*>(reinterpret_cast<unsigned char*>(smraw) +
+                               ((reinterpret_cast<unsigned char*>(flag + nmax) - smraw + 15) & ~size_t(15)));
+  T* vrow = Gs + (size_t)nmax * nmax;             // row k of V (a.g_sm)
   __shared__ int Mbox[16], Moff[17], s_nM, s_piv, s_stop;
   __shared__ double s_thresh, s_y2max, s_redd[32];
   __shared__ T s_scale;
@@ -216,8 +220,8 @@ template <typename T, typename S = T> __global__ void __launch_bounds__(NT_ID, 4
   const T* Y = a.ws + (size_t)blockIdx.x * slot;
   T* Yw = a.ws + (size_t)blockIdx.x * slot;
   T* V = Yw + (size_t)ldY * nmax;
-  T* G = V + (size_t)ldY * nmax;        // G[l * nmax + c]
-  T* Rr = G + nn;                       // Rr[i * nmax + c]
+  T* G = a.g_sm ? Gs : V + (size_t)ldY * nmax;   // G[l * nmax + c]
+  T* Rr = V + (size_t)ldY * nmax + nn;            // Rr[i * nmax + c]
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
 
   if (tid == 0) {
@@ -371,6 +375,8 @@ template <typename T, typename S = T> __global__ void __launch_bounds__(NT_ID, 4
         else G[(size_t)k * nmax + perm[k + 1 + (w - k)]] = d;
       }
     }
+    if (a.g_sm)
+      for (int l = tid; l <= k; l += blockDim.x) vrow[l] = V[(size_t)l * ldY + k];
     __syncthreads();
     // g_c, row k of R, norm downdate
     const double tau = taus[k];
@@ -381,7 +387,10 @@ template <typename T, typename S = T> __global__ void __launch_bounds__(NT_ID, 4
       gc = scl(tau, gc);
       G[(size_t)k * nmax + c] = gc;
       T r = Y[(size_t)c * ldY + k];
-      for (int l = 0; l <= k; ++l) r = msb(r, V[(size_t)l * ldY + k], G[(size_t)l * nmax + c]);
+      if (a.g_sm)
+        for (int l = 0; l <= k; ++l) r = msb(r, vrow[l], G[(size_t)l * nmax + c]);
+      else
+        for (int l = 0; l <= k; ++l) r = msb(r, V[(size_t)l * ldY + k], G[(size_t)l * nmax + c]);
       Rr[(size_t)k * nmax + c] = r;
       const double nv = norms2[pos] - abs2(r);
       flag[pos] = nv < RECOMPUTE_REL * ref[pos];
@@ -462,6 +471,9 @@ template <typename T, typename S = T> __global__ void __launch_bounds__(NT_ID) k
   double* taus = ref + nmax;
   int* perm = reinterpret_cast<int*>(taus + nmax);
   int* flag = perm + nmax;
+  T* Gs = reinterpret_cast<T*>(reinterpret_cast<unsigned char*>(smraw) +
+                               ((reinterpret_cast<unsigned char*>(flag + nmax) - smraw + 15) & ~size_t(15)));
+  T* vrow = Gs + (size_t)nmax * nmax;              // row k of V (a.g_sm)
   __shared__ int Mbox[16], Moff[17], s_nM, s_stop;
   __shared__ double s_thresh, s_y2max;
   __shared__ T s_scale;
@@ -475,8 +487,8 @@ template <typename T, typename S = T> __global__ void __launch_bounds__(NT_ID) k
   T* Yw = a.ws + (size_t)box_local * slot;
   const T* Y = Yw;
   T* V = Yw + (size_t)ldY * nmax;
-  T* G = V + (size_t)ldY * nmax + 2 * nn * rank;   // this CTA's copy: G[l * nmax + c]
-  T* Rr = G + nn;                                   // Rr[i * nmax + c]
+  T* G = a.g_sm ? Gs : V + (size_t)ldY * nmax + 2 * nn * rank;   // this CTA's copy: G[l * nmax + c]
+  T* Rr = V + (size_t)ldY * nmax + 2 * nn * rank + nn;            // Rr[i * nmax + c]
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
   int pb = 0;                                       // partial-sum buffer in use
 
@@ -653,6 +665,8 @@ template <typename T, typename S = T> __global__ void __launch_bounds__(NT_ID) k
       const T d = warp_sum((d0 + d1) + (d2 + d3));
       if (lane == 0) part[pb * 2 * nmax + w] = d;
     }
+    if (a.g_sm)   // row k of V may belong to another CTA: read through L2
+      for (int l = tid; l <= k; l += blockDim.x) vrow[l] = ld_l2(V + (size_t)l * ldY + k);
     cluster_sum(k + nc, u);   // u[0..k): v^H V, u[k..k+nc): raw g for positions k+1..
     // g_c, row k of R, norm downdate (identical in every CTA; own copies of G, Rr)
     const double tau = taus[k];
@@ -663,7 +677,10 @@ template <typename T, typename S = T> __global__ void __launch_bounds__(NT_ID) k
       gc = scl(tau, gc);
       G[(size_t)k * nmax + c] = gc;
       T r = ld_l2(Y + (size_t)c * ldY + k);   // row k may belong to another CTA
-      for (int l = 0; l <= k; ++l) r = msb(r, ld_l2(V + (size_t)l * ldY + k), G[(size_t)l * nmax + c]);
+      if (a.g_sm)
+        for (int l = 0; l <= k; ++l) r = msb(r, vrow[l], G[(size_t)l * nmax + c]);
+      else
+        for (int l = 0; l <= k; ++l) r = msb(r, ld_l2(V + (size_t)l * ldY + k), G[(size_t)l * nmax + c]);
       Rr[(size_t)k * nmax + c] = r;
       const double nv = norms2[pos] - abs2(r);
       flag[pos] = nv < RECOMPUTE_REL * ref[pos];
@@ -2301,15 +2318,22 @@ rss_status factor_impl(const rss_tree* tree, const rss_params* prm, cudaStream_t
           return RSS_ENOMEM;
         }
         TC* d_Y = static_cast<TC*>(gb_Y.p);
-        const size_t smem_id =
+        size_t smem_id =
             sizeof(TC) * ((size_t)ldY + 2 * nmax) + (size_t)nmax * (3 * sizeof(double) + 2 * sizeof(int));
+        size_t smem_cl = sizeof(TC) * ((size_t)(ldY + Q - 1) / Q + 6 * (size_t)nmax) +
+                         (size_t)nmax * (3 * sizeof(double) + 2 * sizeof(int));
+        // G and row k of V on chip when they fit
+        const size_t gsm = 16 + sizeof(TC) * ((size_t)nmax * nmax + nmax);
+        const int g_sm = (Q > 1 ? smem_cl : smem_id) + gsm <= 200 * 1024 ? 1 : 0;
+        if (g_sm) {
+          smem_id += gsm;
+          smem_cl += gsm;
+        }
         if (smem_id > 220 * 1024) {
           rss_set_error("rss_factor: proxy stack of a box too tall for the on-chip reflector buffer");
           return RSS_EINVAL;
         }
         RSS_CUDA(cudaFuncSetAttribute(k_id<TC, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_id));
-        const size_t smem_cl = sizeof(TC) * ((size_t)(ldY + Q - 1) / Q + 6 * (size_t)nmax) +
-                               (size_t)nmax * (3 * sizeof(double) + 2 * sizeof(int));
         if (Q > 1)
           RSS_CUDA(cudaFuncSetAttribute(k_id_cl<TC, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cl));
         f->peak_transient = std::max(f->peak_transient, transient + slot * chunk);
@@ -2331,6 +2355,7 @@ rss_status factor_impl(const rss_tree* tree, const rss_params* prm, cudaStream_t
           a.P = P;
           a.rho = ratio * Lbox;
           a.Lbox = Lbox;
+          a.g_sm = g_sm;
           const int cnt = std::min(chunk, nb - c0);
           if (Q > 1) {
             cudaLaunchConfig_t cfg = {};
