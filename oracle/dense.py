@@ -13,7 +13,7 @@ from __future__ import annotations
 
 import numpy as np
 
-from .rss import KernelSpec, entries, grid_of, kernel_block
+from .rss import KernelSpec, entries, grid_of, kernel_block, ls_weights
 
 
 def dense_matrix(points: np.ndarray, spec: KernelSpec) -> np.ndarray:
@@ -32,7 +32,9 @@ def fft_matvec(points: np.ndarray, spec: KernelSpec, x: np.ndarray) -> np.ndarra
     d = np.arange(-(s - 1), s)
     DX, DY = np.meshgrid(d, d)                    # DY indexes rows, DX columns
     disp = np.stack([DX.ravel() * grid.hg, DY.ravel() * grid.hg], axis=1)
-    kv = kernel_block(spec, disp, np.zeros((1, 2)))[:, 0].reshape(2 * s - 1, 2 * s - 1)
+    base = KernelSpec("helmholtz", spec.h, spec.kappa) if spec.kind == "ls" else spec
+    with np.errstate(divide="ignore", invalid="ignore"):   # zero displacement: replaced below
+        kv = kernel_block(base, disp, np.zeros((1, 2)))[:, 0].reshape(2 * s - 1, 2 * s - 1)
     kv = kv.astype(spec.dtype)
     kv[s - 1, s - 1] = 0.0                        # the diagonal is added separately
     circ = np.zeros((2 * s, 2 * s), dtype=spec.dtype)
@@ -44,12 +46,18 @@ def fft_matvec(points: np.ndarray, spec: KernelSpec, x: np.ndarray) -> np.ndarra
     if squeeze:
         xv = xv[:, None]
     out = np.empty(xv.shape, dtype=np.result_type(xv, spec.dtype))
+    if spec.kind == "ls":   # A = I + W (T + diag I) W, W = diag(kappa sqrt(b))   (Eqs. 19, 20)
+        w = ls_weights(spec, np.asarray(points, np.float64))
+        dvec = 1.0 + w * w * spec.diag
+    else:
+        w = np.ones(xv.shape[0])
+        dvec = np.full(xv.shape[0], spec.diag)
     for j in range(xv.shape[1]):
         pad = np.zeros((2 * s, 2 * s), dtype=np.result_type(xv, spec.dtype))
-        pad[grid.iy, grid.ix] = xv[:, j]
+        pad[grid.iy, grid.ix] = w * xv[:, j]
         y = np.fft.ifft2(kf * np.fft.fft2(pad))[:s, :s]
         y = y if np.iscomplexobj(out) else y.real
-        out[:, j] = y[grid.iy, grid.ix] + spec.diag * xv[:, j]
+        out[:, j] = w * y[grid.iy, grid.ix] + dvec * xv[:, j]
     return out[:, 0] if squeeze else out
 
 

@@ -70,6 +70,10 @@ class KernelSpec:
     kind: 'laplace'   A_ij = -(h^2 / 2 pi) log |x_i - x_j|            (Eq. 15)
           'helmholtz' A_ij = h^2 (i/4) H0^(1)(kappa |x_i - x_j|)      (Eq. 18 with
                       the scaling of the dense-solver workloads: no kappa^2 b factor)
+          'ls'        Lippmann-Schwinger (Eq. 19): A_ij = w_i w_j h^2 (i/4) H0^(1)(kappa r)
+                      with w = kappa sqrt(b(x)), A_ii = 1 + w_i^2 diag (Eq. 20 when diag
+                      is the self-cell integral of (i/4) H0^(1)); proxy points (Eq. 6)
+                      take the weight kappa (sqrt(b) = 1)
           'poly'      A_ij = scale * conj(w_i) w_j sum_d coef[d] (z_i - z_j)^d, z = x + i y,
                       w = exp(i (phase[0] x + phase[1] y)): a test kernel whose far
                       field is exactly low rank, so that RS-S is exact up to
@@ -84,18 +88,62 @@ class KernelSpec:
     coef: tuple = ()
     scale: float = 1.0
     phase: tuple = (0.0, 0.0)
+    bump: tuple = (0.5, 0.5, 32.0)   # 'ls': b(x) = exp(-bump[2] |x - (bump[0], bump[1])|^2)
 
     @property
     def is_complex(self) -> bool:
-        return self.kind in ("helmholtz", "poly")
+        return self.kind in ("helmholtz", "poly", "ls")
 
     @property
     def dtype(self):
         return np.complex128 if self.is_complex else np.float64
 
 
-def kernel_block(spec: KernelSpec, X1: np.ndarray, X2: np.ndarray) -> np.ndarray:
-    """K(x_a, y_b) for all rows a of X1 and b of X2 (no diagonal rule)."""
+def ls_weights(spec: KernelSpec, X: np.ndarray) -> np.ndarray:
+    """w = kappa sqrt(b(x)) of the symmetrised Lippmann-Schwinger equation (Eq. 19)."""
+    cx, cy, a = spec.bump
+    return spec.kappa * np.exp(-0.5 * a * ((X[:, 0] - cx) ** 2 + (X[:, 1] - cy) ** 2))
+
+
+def self_integral(kind: str, h: float, kappa: float = 0.0) -> complex:
+    """Integral of the kernel over the self cell [-h/2, h/2]^2 (Eqs. 16 and 20).
+
+    By the cell's eight-fold symmetry the integral is 8 times the integral over
+    the triangle 0 <= theta <= pi/4, 0 <= rho <= a / cos(theta), a = h/2:
+      Laplace:   int_0^R rho log(rho) drho = R^2 log(R)/2 - R^2/4, integrated in
+                 theta in closed form: -(1/2pi) 2 a^2 (2 log a + log 2 - 3 + pi/2);
+      Helmholtz: int_0^R rho H0(kappa rho) drho = R H1(kappa R)/kappa + 2i/(pi kappa^2)
+                 (the limit at 0 from Y1(z) ~ -2/(pi z)), integrated in theta by
+                 adaptive quadrature.
+    """
+    a = 0.5 * h
+    if kind == "laplace":
+        return -(1.0 / (2.0 * np.pi)) * 2.0 * a * a * (2.0 * np.log(a) + np.log(2.0) - 3.0 + 0.5 * np.pi)
+    if kind in ("helmholtz", "ls"):
+        from scipy.integrate import quad
+
+        def f(t, part):
+            R = a / np.cos(t)
+            v = R * special.hankel1(1, kappa * R) / kappa + 2j / (np.pi * kappa * kappa)
+            return v.real if part == 0 else v.imag
+        re = quad(f, 0.0, 0.25 * np.pi, args=(0,), epsabs=0.0, epsrel=1e-13, limit=200)[0]
+        im = quad(f, 0.0, 0.25 * np.pi, args=(1,), epsabs=0.0, epsrel=1e-13, limit=200)[0]
+        return 8.0 * 0.25j * complex(re, im)
+    raise ValueError(f"no self integral for kernel kind {kind!r}")
+
+
+def kernel_block(spec: KernelSpec, X1: np.ndarray, X2: np.ndarray, proxy1: bool = False,
+                 proxy2: bool = False) -> np.ndarray:
+    """K(x_a, y_b) for all rows a of X1 and b of X2 (no diagonal rule).
+
+    proxy1 / proxy2: the points of X1 / X2 are proxy points (they take the
+    weight kappa for 'ls')."""
+    if spec.kind == "ls":
+        base = KernelSpec("helmholtz", spec.h, spec.kappa)
+        K = kernel_block(base, X1, X2)
+        w1 = np.full(X1.shape[0], spec.kappa) if proxy1 else ls_weights(spec, X1)
+        w2 = np.full(X2.shape[0], spec.kappa) if proxy2 else ls_weights(spec, X2)
+        return K * w1[:, None] * w2[None, :]
     dx = X1[:, None, 0] - X2[None, :, 0]
     dy = X1[:, None, 1] - X2[None, :, 1]
     if spec.kind == "laplace":
@@ -125,7 +173,11 @@ def entries(spec: KernelSpec, X: np.ndarray, I: np.ndarray, J: np.ndarray) -> np
     same = I[:, None] == J[None, :]
     if same.any():
         A = np.array(A, copy=True)
-        A[same] = spec.diag
+        if spec.kind == "ls":
+            w = ls_weights(spec, X[I])
+            A[same] = (1.0 + w * w * spec.diag)[np.nonzero(same)[0]]
+        else:
+            A[same] = spec.diag
     return A
 
 
@@ -377,9 +429,9 @@ def build_proxy_stack(spec, X, blocks, pts, B, g, centre, radius, nproxy):
     pB = pts[B]
     yp = proxy_points(centre, radius, nproxy)
     rows = [blocks[(m, B)] for m in Ms]
-    rows.append(kernel_block(spec, yp, X[pB]).astype(spec.dtype, copy=False))
+    rows.append(kernel_block(spec, yp, X[pB], proxy1=True).astype(spec.dtype, copy=False))
     rows += [blocks[(B, m)].conj().T for m in Ms]
-    rows.append(kernel_block(spec, X[pB], yp).astype(spec.dtype, copy=False).conj().T)
+    rows.append(kernel_block(spec, X[pB], yp, proxy2=True).astype(spec.dtype, copy=False).conj().T)
     return np.vstack(rows)
 
 
