@@ -51,10 +51,16 @@ typedef enum {
  *  RSS_TEST_POLY  A_ij = scale conj(w_i) w_j sum_d coef[d] (z_i - z_j)^d,
  *                 z = x + i y, w = exp(i (phase_x x + phase_y y)), complex.
  *  RSS_TEST_RPOLY the real part of sum_d coef[d] (z_i - z_j)^d times scale.
+ *  RSS_HELMHOLTZ_LS  the symmetrised Lippmann-Schwinger system of Eqs. 19-20:
+ *                 A_ij = w_i w_j h^2 (i/4) H0^(1)(kappa |x_i - x_j|) with
+ *                 w = kappa sqrt(b(x)), b(x) = exp(-bump_a |x - (bump_cx, bump_cy)|^2),
+ *                 and A_ii = 1 + w_i^2 d, d = diag_re + i diag_im (or, with
+ *                 diag_rule = 1, the self-cell integral of (i/4) H0^(1) of Eq. 20);
+ *                 complex.  Proxy points (Eq. 6) take the weight kappa.
  * The two test kinds have an exactly low-rank far field, so the whole
  * factorization is exact up to rounding; they exist to verify the elimination
  * bookkeeping against a dense solve and are not a workload of the paper. */
-enum { RSS_LAPLACE = 0, RSS_HELMHOLTZ = 1, RSS_TEST_POLY = 2, RSS_TEST_RPOLY = 3 };
+enum { RSS_LAPLACE = 0, RSS_HELMHOLTZ = 1, RSS_TEST_POLY = 2, RSS_TEST_RPOLY = 3, RSS_HELMHOLTZ_LS = 4 };
 
 #define RSS_MAX_COEF 8
 
@@ -85,6 +91,12 @@ typedef struct {
                                      0 spreads each box's ID over a thread-block cluster of
                                      up to 8 CTAs, > 0 caps the cluster size (1: one CTA per
                                      box), -1 is the same as 1 */
+  double bump_cx, bump_cy, bump_a;/* RSS_HELMHOLTZ_LS: b(x) = exp(-bump_a |x - c|^2); bump_a
+                                     <= 0 selects the paper's (0.5, 0.5) and 32 */
+  int diag_rule;                  /* 0: the diagonal is diag_re + i diag_im; 1: the paper's
+                                     quadrature, the integral of the kernel over the point's
+                                     own h x h cell (Eq. 16 for Laplace, Eq. 20 for Helmholtz
+                                     and Lippmann-Schwinger), see rss_self_integral */
 } rss_params;
 
 /* Build the quadtree of Section 2.1 for n points given as pts_xy[2*i],
@@ -169,6 +181,40 @@ rss_status rss_server_wait(rss_server* s, int64_t ticket, double timeout_s, doub
 
 /* JSON counters: requests, panels, columns, largest panel, memory in use. */
 rss_status rss_server_stats(rss_server* s, char* buf, size_t len);
+
+
+/* Integral of the kernel over one h x h cell centred on the singularity
+ * (paper Eqs. 16 and 20): kind RSS_LAPLACE gives the closed form
+ * -(1/2pi) 2 a^2 (2 log a + log 2 - 3 + pi/2), a = h/2; RSS_HELMHOLTZ and
+ * RSS_HELMHOLTZ_LS give the integral of (i/4) H0^(1)(kappa |x|), reduced by the
+ * cell's symmetry to 8 (i/4) int_0^{pi/4} [rho H1^(1)(kappa rho)/kappa + 2i/(pi kappa^2)]
+ * dtheta, rho = a / cos(theta), by Gauss-Legendre quadrature.  Host only, no
+ * GPU work.  EINVAL for other kinds, h <= 0, or kappa <= 0 where it is needed. */
+rss_status rss_self_integral(int kind, double h, double kappa, double* re, double* im);
+
+/* y = A x for the factored matrix (the exact A of Eq. 3, not its
+ * factorization), applied by FFT: on the uniform grid the off-diagonal part is
+ * a two-level Toeplitz convolution, embedded in a 2s x 2s circulant (s points
+ * per side); the diagonal and the Lippmann-Schwinger weights are applied
+ * pointwise.  x and y: device buffers of n x nrhs scalars, leading dimension
+ * ld >= n, in the caller's point order; x and y must not overlap.  The first
+ * call builds the circulant's spectrum (16 (2s)^2 bytes kept with the factor)
+ * and a cuFFT plan.  Asynchronous on stream. */
+rss_status rss_matvec(const rss_factorization* f, const void* x, void* y, int64_t nrhs, int64_t ld,
+                      void* stream);
+
+/* Solve A x = b to a relative residual ||b - A x|| / ||b|| <= tol with the
+ * factorization as preconditioner (Section 5): method 1 is preconditioned
+ * conjugate gradients (symmetric positive definite A: the Laplace kernel with
+ * the quadrature diagonal), method 2 right-preconditioned GMRES(restart)
+ * (restart <= 0: 20), method 0 picks PCG for real factors and GMRES for complex
+ * ones.  Both start from x0 = (factorization)^{-1} b.  b and x: device buffers
+ * of n scalars in the caller's order (one right-hand side).  *iters receives
+ * the iterations (GMRES: Arnoldi steps) and *relres the final relative residual
+ * of b - A x (either may be NULL).  At most maxit iterations (<= 0: 200); not
+ * reaching tol is not an error.  Synchronises stream. */
+rss_status rss_solve_iterative(const rss_factorization* f, const void* b, void* x, double tol, int maxit,
+                               int restart, int method, int* iters, double* relres, void* stream);
 
 /* Release a tree, a factor or a server (the handle is tagged; a server first
  * finishes its in-flight panels).  NULL is ignored. */

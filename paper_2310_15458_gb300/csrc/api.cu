@@ -114,7 +114,12 @@ rss_status rss_factor(const rss_tree* tree, const rss_params* p, void* stream, r
   if (!tree || tree->tag != RSS_TAG_TREE) return fail(RSS_EINVAL, "rss_factor: not a tree handle");
   if (!p) return fail(RSS_EINVAL, "rss_factor: params is NULL");
   if (!(p->eps >= 0) || p->eps >= 1) return fail(RSS_EINVAL, "rss_factor: eps must be in [0, 1)");
-  if (p->kind < RSS_LAPLACE || p->kind > RSS_TEST_RPOLY) return fail(RSS_EINVAL, "rss_factor: unknown kernel kind");
+  if (p->kind < RSS_LAPLACE || p->kind > RSS_HELMHOLTZ_LS) return fail(RSS_EINVAL, "rss_factor: unknown kernel kind");
+  if (p->diag_rule != 0 && p->diag_rule != 1) return fail(RSS_EINVAL, "rss_factor: diag_rule must be 0 or 1");
+  if ((p->kind == RSS_HELMHOLTZ || p->kind == RSS_HELMHOLTZ_LS) && !(p->kappa > 0))
+    return fail(RSS_EINVAL, "rss_factor: the Helmholtz kernels need kappa > 0");
+  if (p->diag_rule == 1 && (p->kind == RSS_TEST_POLY || p->kind == RSS_TEST_RPOLY))
+    return fail(RSS_EINVAL, "rss_factor: diag_rule 1 needs a Laplace or Helmholtz kernel");
   if (p->proxy_n < 0 || p->proxy_n > 4096) return fail(RSS_EINVAL, "rss_factor: proxy_n out of range");
   if (p->ncoef < 0 || p->ncoef > RSS_MAX_COEF) return fail(RSS_EINVAL, "rss_factor: ncoef out of range");
   if (p->proxy_radius_over_side < 0) return fail(RSS_EINVAL, "rss_factor: negative proxy radius");
@@ -137,7 +142,22 @@ rss_status rss_factor(const rss_tree* tree, const rss_params* p, void* stream, r
   f->kp.scale = p->scale;
   f->kp.phx = p->phase_x;
   f->kp.phy = p->phase_y;
-  f->is_complex = (p->kind == RSS_HELMHOLTZ || p->kind == RSS_TEST_POLY);
+  f->kp.w = nullptr;
+  if (f->params.bump_a <= 0) {
+    f->params.bump_cx = 0.5;
+    f->params.bump_cy = 0.5;
+    f->params.bump_a = 32.0;
+  }
+  if (p->diag_rule == 1) {   // the paper's self-cell quadrature (Eqs. 16, 20)
+    double re = 0, im = 0;
+    const rss_status si = self_integral(p->kind, h, p->kappa, &re, &im);
+    if (si != RSS_OK) { delete f; return si; }
+    f->kp.diag_re = re;
+    f->kp.diag_im = im;
+    f->params.diag_re = re;
+    f->params.diag_im = im;
+  }
+  f->is_complex = (p->kind == RSS_HELMHOLTZ || p->kind == RSS_TEST_POLY || p->kind == RSS_HELMHOLTZ_LS);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   rss_status s = f->is_complex ? factor_impl<zd>(tree, p, st, f) : factor_impl<double>(tree, p, st, f);
   if (s != RSS_OK) {
@@ -301,6 +321,7 @@ extern "C" rss_status rss_box_record(const rss_factorization* f, int side, int b
 void free_factor(rss_factorization* f) {
   if (!f) return;
   f->tag = 0;
+  free_matvec(f);
   f->arena.release();
   if (f->d_user_to_tree) cudaFree(f->d_user_to_tree);
   for (void* p : f->rec_host) std::free(p);

@@ -111,10 +111,11 @@ struct KParams {
   int kind;
   double h2;        // h^2
   double kappa;
-  double diag_re, diag_im;
+  double diag_re, diag_im;   // A_ii; Lippmann-Schwinger: d in A_ii = 1 + w_i^2 d
   int ncoef;
   double cre[RSS_MAX_COEF], cim[RSS_MAX_COEF];
   double scale, phx, phy;
+  const double* w;  // Lippmann-Schwinger: w = kappa sqrt(b) per grid point (iy * side + ix), device
 };
 
 // Grid geometry: point (ix, iy) sits at (x0 + ix hg, y0 + iy hg).
@@ -141,7 +142,7 @@ __device__ inline double kval(const KParams& kp, double x1, double y1, double x2
 }
 __device__ inline zd kval(const KParams& kp, double x1, double y1, double x2, double y2, zd) {
   double dx = x1 - x2, dy = y1 - y2;
-  if (kp.kind == RSS_HELMHOLTZ) {
+  if (kp.kind == RSS_HELMHOLTZ || kp.kind == RSS_HELMHOLTZ_LS) {   // (LS: before the weights)
     double kr = kp.kappa * sqrt(fma(dx, dx, dy * dy));
     // h^2 (i/4) (J0 + i Y0) = h^2 (-Y0/4 + i J0/4)
     return zd{-0.25 * kp.h2 * y0(kr), 0.25 * kp.h2 * j0(kr)};
@@ -153,24 +154,19 @@ __device__ inline zd kval(const KParams& kp, double x1, double y1, double x2, do
   return p * zd{c, s};
 }
 
-// Entry of A between grid points given as integer coordinates.
-template <typename T>
-__device__ inline T aval(const KParams& kp, const Geo& geo, int2 a, int2 b) {
-  if (a.x == b.x && a.y == b.y) {
-    T d;
-    if constexpr (sizeof(T) == sizeof(double)) d = from_re<T>(kp.diag_re);
-    else d = T{kp.diag_re, kp.diag_im};
-    return d;
-  }
-  return kval(kp, geo.x0 + a.x * geo.hg, geo.y0 + a.y * geo.hg, geo.x0 + b.x * geo.hg,
-              geo.y0 + b.y * geo.hg, T{});
-}
-
 // Kernel values by grid displacement.  Every kernel kind here depends only on
 // x_i - x_j (the test kernels' phase weights conj(w_i) w_j do too), so on a
 // uniform grid K(x_i, x_j) = tab[(iy_i - iy_j + s - 1) (2s - 1) + (ix_i - ix_j + s - 1)].
 template <typename T>
 __device__ inline T aval_tab(const KParams& kp, const T* __restrict__ tab, int side, int2 a, int2 b) {
+  if constexpr (sizeof(T) != sizeof(double)) {
+    if (kp.kind == RSS_HELMHOLTZ_LS) {   // A_ij = w_i w_j K_ij, A_ii = 1 + w_i^2 d   (Eqs. 19, 20)
+      const double wa = kp.w[a.y * side + a.x];
+      if (a.x == b.x && a.y == b.y) return T{1.0 + wa * wa * kp.diag_re, wa * wa * kp.diag_im};
+      const double wb = kp.w[b.y * side + b.x];
+      return (wa * wb) * tab[(size_t)(a.y - b.y + side - 1) * (2 * side - 1) + (a.x - b.x + side - 1)];
+    }
+  }
   if (a.x == b.x && a.y == b.y) {
     T d;
     if constexpr (sizeof(T) == sizeof(double)) d = from_re<T>(kp.diag_re);

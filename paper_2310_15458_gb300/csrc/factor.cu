@@ -94,6 +94,16 @@ template <typename T> __global__ void k_ktab(T* tab, int side, KParams kp, Geo g
   }
 }
 
+// Lippmann-Schwinger weights w = kappa sqrt(b(x)) = kappa exp(-bump_a |x - c|^2 / 2)
+// at each grid point (iy * side + ix)   (Eq. 19)
+__global__ void k_ls_weights(double* w, int side, Geo geo, double kappa, double cx, double cy, double a) {
+  const long long n = (long long)side * side;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    const double x = geo.x0 + (e % side) * geo.hg - cx, y = geo.y0 + (e / side) * geo.hg - cy;
+    w[e] = kappa * exp(-0.5 * a * (x * x + y * y));
+  }
+}
+
 // ------------------------------------------------------------------ leaf generation
 template <typename T>
 __global__ void __launch_bounds__(NT) k_gen_blocks(LevelDev<T> L, const int2* __restrict__ ixy,
@@ -188,6 +198,8 @@ __device__ __forceinline__ T id_entry(const IdArgs<T, S>& a, int B, int i, int j
     const int2 q = a.ixy[L.pts[B * nmax + j]];
     const double xj = a.geo.x0 + q.x * a.geo.hg, yj = a.geo.y0 + q.y * a.geo.hg;
     v = (!split && second) ? cj(kval(a.kp, xj, yj, px, py, S{})) : kval(a.kp, px, py, xj, yj, S{});
+    if (a.kp.kind == RSS_HELMHOLTZ_LS)   // proxy weight kappa, column weight w_j
+      v = (a.kp.kappa * a.kp.w[q.y * a.geo.side + q.x]) * v;
   }
   if constexpr (split) return second ? v.y : v.x;
   else return v;
@@ -2188,6 +2200,25 @@ rss_status factor_impl(const rss_tree* tree, const rss_params* prm, cudaStream_t
   if (!d_ixy || !d_err) { rss_set_error("rss_factor: device arena allocation failed"); return RSS_ENOMEM; }
   RSS_CUDA(cudaMemcpyAsync(d_ixy, hixy.data(), sizeof(int2) * N, cudaMemcpyHostToDevice, st));
   RSS_CUDA(cudaMemsetAsync(d_err, 0, sizeof(int), st));
+  {   // grid index (iy * side + ix) of each user point, for the FFT matvec
+    std::vector<int32_t> u2g(N);
+    for (int64_t i = 0; i < N; ++i) {
+      const int2 q = hixy[tree->user_to_tree[i]];
+      u2g[i] = q.y * tree->side + q.x;
+    }
+    f->d_user_to_grid = static_cast<int32_t*>(f->arena.get(sizeof(int32_t) * N));
+    if (!f->d_user_to_grid) { rss_set_error("rss_factor: device arena allocation failed"); return RSS_ENOMEM; }
+    RSS_CUDA(cudaMemcpy(f->d_user_to_grid, u2g.data(), sizeof(int32_t) * N, cudaMemcpyHostToDevice));
+  }
+  if (prm->kind == RSS_HELMHOLTZ_LS) {   // w = kappa sqrt(b) per grid point (Eq. 19)
+    f->d_w = static_cast<double*>(f->arena.get(sizeof(double) * N));
+    if (!f->d_w) { rss_set_error("rss_factor: device arena allocation failed"); return RSS_ENOMEM; }
+    k_ls_weights<<<cdiv(N, NT), NT, 0, st>>>(f->d_w, tree->side, f->geo, f->kp.kappa, f->params.bump_cx,
+                                             f->params.bump_cy, f->params.bump_a);
+    RSS_LAUNCHED();
+    f->kp.w = f->d_w;
+    f->launches += 1;
+  }
   // kernel values by displacement, for the leaf blocks and the never-modified far blocks
   const int side = tree->side;
   T* d_tab = nullptr;
@@ -2241,7 +2272,8 @@ rss_status factor_impl(const rss_tree* tree, const rss_params* prm, cudaStream_t
   const int half = (prm->id_rows == 0 && prm->kind == RSS_LAPLACE && prm->diag_im == 0.0) ? 1 : 0;
   // A complex symmetric kernel (Helmholtz): the ID of the real stack
   // [Re X; Im X], X = [A_MB; K_PB], which is the ID of the full stack (T real).
-  const bool split = std::is_same<T, zd>::value && prm->id_rows == 0 && prm->kind == RSS_HELMHOLTZ;
+  const bool split = std::is_same<T, zd>::value && prm->id_rows == 0 &&
+                     (prm->kind == RSS_HELMHOLTZ || prm->kind == RSS_HELMHOLTZ_LS);
   while (g >= 4) {
     const int nbox = g * g, nmax = cur.d.nmax;
     const size_t nn = (size_t)nmax * nmax;

@@ -92,6 +92,9 @@ struct rss_factorization {
   KParams kp{};
   Geo geo{};
   int32_t* d_user_to_tree = nullptr;   // n
+  int32_t* d_user_to_grid = nullptr;   // n: iy * side + ix of each user point (arena)
+  double* d_w = nullptr;               // Lippmann-Schwinger weights per grid point (arena)
+  void* mv = nullptr;                  // FFT matvec state (iterative.cu), built on first use
   std::vector<int32_t> tree_to_user;   // host copy, for inspection calls
   Arena arena;
   std::vector<Batch> batches;          // factor order
@@ -120,4 +123,6 @@ template <typename T> rss_status solve_impl(const rss_factorization* f, T* b_dev
                                             int64_t ldb, cudaStream_t st);
 template <typename T> rss_status top_inverse(const T* LU, const int* piv, int n, T* Ainv, cudaStream_t st);
 void free_factor(rss_factorization* f);
+void free_matvec(rss_factorization* f);
+rss_status self_integral(int kind, double h, double kappa, double* re, double* im);
 void free_server(rss_server* s);

@@ -14,7 +14,7 @@ import os
 
 import numpy as np
 
-LAPLACE, HELMHOLTZ, TEST_POLY, TEST_RPOLY = 0, 1, 2, 3
+LAPLACE, HELMHOLTZ, TEST_POLY, TEST_RPOLY, HELMHOLTZ_LS = 0, 1, 2, 3, 4
 MAX_COEF = 8
 _STATUS = {0: "RSS_OK", 1: "RSS_EINVAL", 2: "RSS_ENOMEM", 3: "RSS_ECUDA", 4: "RSS_ENUMERIC",
            5: "RSS_ETIMEOUT", 6: "RSS_EBUSY"}
@@ -40,7 +40,9 @@ class _Params(ctypes.Structure):
                 ("coef_re", ctypes.c_double * MAX_COEF), ("coef_im", ctypes.c_double * MAX_COEF),
                 ("scale", ctypes.c_double), ("phase_x", ctypes.c_double),
                 ("phase_y", ctypes.c_double), ("id_rows", ctypes.c_int),
-                ("schur_path", ctypes.c_int), ("id_cluster", ctypes.c_int)]
+                ("schur_path", ctypes.c_int), ("id_cluster", ctypes.c_int),
+                ("bump_cx", ctypes.c_double), ("bump_cy", ctypes.c_double),
+                ("bump_a", ctypes.c_double), ("diag_rule", ctypes.c_int)]
 
 
 _lib = None
@@ -71,9 +73,15 @@ def _load():
     lib.rss_info.argtypes = [vp, ctypes.c_char_p, ctypes.c_size_t]
     lib.rss_level_ranks.argtypes = [vp, ctypes.c_int, ctypes.POINTER(i32)]
     lib.rss_box_record.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(i32)] + [vp] * 8
+    dp = ctypes.POINTER(ctypes.c_double)
+    lib.rss_self_integral.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, dp, dp]
+    lib.rss_matvec.argtypes = [vp, vp, vp, i64, i64, vp]
+    lib.rss_solve_iterative.argtypes = [vp, vp, vp, ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                        ctypes.c_int, ctypes.POINTER(ctypes.c_int), dp, vp]
     for name in ("rss_build_tree", "rss_factor", "rss_solve", "rss_solve_noalloc", "rss_info",
                  "rss_level_ranks", "rss_box_record", "rss_server_create", "rss_server_add",
-                 "rss_server_submit", "rss_server_wait", "rss_server_stats"):
+                 "rss_server_submit", "rss_server_wait", "rss_server_stats", "rss_self_integral",
+                 "rss_matvec", "rss_solve_iterative"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -143,7 +151,8 @@ def rss_factor(tree: Tree, kind: int = LAPLACE, eps: float = 1e-6, h: float = 0.
                kappa: float = 0.0, diag: complex = 1.0, proxy_n: int = 64,
                proxy_radius_over_side: float = 1.25, coef=(), scale: float = 1.0,
                phase=(0.0, 0.0), full_stack: bool = False, schur_fp64: bool = False,
-               id_cluster: int = 0, stream=None) -> Factor:
+               id_cluster: int = 0, diag_rule: int = 0, bump=(0.5, 0.5, 32.0),
+               stream=None) -> Factor:
     lib = _load()
     p = _Params()
     p.kind, p.h, p.kappa = kind, h, kappa
@@ -159,9 +168,60 @@ def rss_factor(tree: Tree, kind: int = LAPLACE, eps: float = 1e-6, h: float = 0.
     p.id_rows = 1 if full_stack else 0
     p.schur_path = 1 if schur_fp64 else 0
     p.id_cluster = id_cluster
+    p.bump_cx, p.bump_cy, p.bump_a = bump
+    p.diag_rule = diag_rule
     out = ctypes.c_void_p()
     _check(lib.rss_factor(tree.handle, ctypes.byref(p), _stream_handle(stream), ctypes.byref(out)))
-    return Factor(out, tree.n, kind in (HELMHOLTZ, TEST_POLY), tree)
+    return Factor(out, tree.n, kind in (HELMHOLTZ, TEST_POLY, HELMHOLTZ_LS), tree)
+
+
+def rss_self_integral(kind: int, h: float, kappa: float = 0.0) -> complex:
+    """Integral of the kernel over one h x h cell (Eqs. 16 and 20)."""
+    lib = _load()
+    re, im = ctypes.c_double(), ctypes.c_double()
+    _check(lib.rss_self_integral(kind, h, kappa, ctypes.byref(re), ctypes.byref(im)))
+    return complex(re.value, im.value)
+
+
+def _dev_vector(f: Factor, t, name):
+    import torch
+    want = torch.complex128 if f.is_complex else torch.float64
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != want:
+        raise TypeError(f"{name} must be a CUDA tensor of {want}")
+    if t.shape[0] != f.n or t.stride(0) != 1:
+        raise ValueError(f"{name} must have n rows, contiguous down the column")
+    return t
+
+
+def rss_matvec(f: Factor, x, y=None, stream=None):
+    """y = A x by FFT (x: (n,) or (n, nrhs) column-major CUDA tensor); returns y."""
+    import torch
+    x = _dev_vector(f, x, "x")
+    if y is None:
+        y = torch.empty_like(x) if x.dim() == 1 else torch.empty(x.shape[1], x.shape[0], dtype=x.dtype,
+                                                                  device=x.device).T
+    y = _dev_vector(f, y, "y")
+    nrhs = 1 if x.dim() == 1 else x.shape[1]
+    ld = f.n if x.dim() == 1 else max(x.stride(1), f.n)
+    if x.dim() == 2 and max(y.stride(1), f.n) != ld:
+        raise ValueError("x and y must have the same leading dimension")
+    _check(_load().rss_matvec(f.handle, x.data_ptr(), y.data_ptr(), nrhs, ld, _stream_handle(stream)))
+    return y
+
+
+def rss_solve_iterative(f: Factor, b, tol: float = 1e-12, maxit: int = 200, restart: int = 20,
+                        method: int = 0, stream=None):
+    """x with ||b - A x|| <= tol ||b||, the factorization as preconditioner (PCG or
+    GMRES); returns (x, iterations, relative residual)."""
+    import torch
+    b = _dev_vector(f, b, "b")
+    if b.dim() != 1:
+        raise ValueError("b must be a single right-hand side")
+    x = torch.empty_like(b)
+    it, rel = ctypes.c_int(), ctypes.c_double()
+    _check(_load().rss_solve_iterative(f.handle, b.data_ptr(), x.data_ptr(), tol, maxit, restart, method,
+                                       ctypes.byref(it), ctypes.byref(rel), _stream_handle(stream)))
+    return x, it.value, rel.value
 
 
 def rss_solve(f: Factor, b, stream=None):

@@ -58,3 +58,18 @@ def test_binding_refuses_missing_library(monkeypatch, tmp_path):
     monkeypatch.setattr(R, "library_path", lambda: str(tmp_path / "missing.so"))
     with pytest.raises(ImportError):
         R._load()
+
+
+def test_self_integral_is_host_only_and_matches_oracle():
+    """rss_self_integral (Eqs. 16, 20) runs on the host: the Laplace closed form and
+    the Helmholtz Gauss-Legendre reduction against the oracle's adaptive quadrature."""
+    import paper_2310_15458_gb300 as P
+    from oracle.rss import self_integral
+    for h in (1 / 64, 1 / 1024):
+        assert abs(P.rss_self_integral(P.LAPLACE, h) - self_integral("laplace", h)) <= \
+            1e-13 * abs(self_integral("laplace", h))
+        for kappa in (25.0, 50.0):
+            o = self_integral("helmholtz", h, kappa)
+            assert abs(P.rss_self_integral(P.HELMHOLTZ, h, kappa) - o) <= 1e-12 * abs(o)
+    with pytest.raises(P.RSSError, match="EINVAL"):
+        P.rss_self_integral(P.HELMHOLTZ, 1 / 64, 0.0)
