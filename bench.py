@@ -51,6 +51,7 @@ def parse():
     ap.add_argument("--multi-rhs", type=int, default=256)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-paper", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=600)
     ap.add_argument("--serve-load", type=float, default=0.9)
     return ap.parse_args()
@@ -192,6 +193,62 @@ def reference_arm(args, w):
             "cpu_baseline": cb,
             "e2e": {"value": cb["value"], "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------- the paper's problems
+PAPER_SET = [("laplace_quadrature_2048x2048", W.LAPLACE, 2048, 0.0),
+             ("lippmann_schwinger_k25_1024x1024", W.HELMHOLTZ_LS, 1024, 25.0)]
+
+
+def paper_problems(P, torch):
+    """The paper's own discretisations (Section 5), run as the paper runs them:
+    Laplace with the self-cell quadrature diagonal (Eq. 16) and the symmetrised
+    Lippmann-Schwinger system at kappa = 25 (Eqs. 19-20, Gaussian bump), proxy
+    radius 2.5 L (Section 2.3), eps 1e-6, leaf 64, one right-hand side of
+    uniform random entries, refined to a relative residual of 1e-12 by PCG /
+    GMRES(20) with the factorization as preconditioner.  Reported beside the
+    paper's single-process rows (CPU, other hardware): context only."""
+    out = {}
+    for name, kind, side, kappa in PAPER_SET:
+        n = side * side
+        tree = P.rss_build_tree(W.grid_points(side), W.LEAF)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        f = P.rss_factor(tree, kind=kind, eps=1e-6, h=1.0 / side, kappa=kappa, diag_rule=1,
+                         proxy_radius_over_side=2.5)
+        torch.cuda.synchronize()
+        t_fact = time.perf_counter() - t0
+        rng = np.random.default_rng(2001)
+        if f.is_complex:
+            bh = rng.uniform(size=n) + 1j * rng.uniform(size=n)
+        else:
+            bh = rng.uniform(size=n)
+        b = torch.from_numpy(bh).cuda()
+        x = b.clone()
+        P.rss_solve(f, x)                      # warm-up (plans, workspaces)
+        P.rss_matvec(f, x)
+        x = b.clone()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        P.rss_solve(f, x)
+        torch.cuda.synchronize()
+        t_solve = time.perf_counter() - t0
+        r = P.rss_matvec(f, x) - b
+        direct = float(torch.linalg.vector_norm(r) / torch.linalg.vector_norm(b))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, it, rr = P.rss_solve_iterative(f, b, tol=1e-12)
+        torch.cuda.synchronize()
+        t_it = time.perf_counter() - t0
+        info = P.rss_info(f)
+        out[name] = {"n": n, "factor_s": t_fact, "solve_s": t_solve, "relres_direct": direct,
+                     "iterations": it, "relres_iterative": rr, "iterative_s": t_it,
+                     "method": "gmres20" if f.is_complex else "pcg",
+                     "ranks": [{"side": L["side"], "k_mean": L["k_mean"], "k_max": L["k_max"]}
+                               for L in info["levels"]]}
+        del f, tree
+        torch.cuda.empty_cache()
+    return out
 
 
 # ----------------------------------------------------------------------------- serving
@@ -430,6 +487,8 @@ def native_arm(args, w):
     }
     if not args.no_serve:
         line["serve"] = serve_run(P, torch, args)
+    if not args.no_paper and world == 1:
+        line["paper_problems"] = paper_problems(P, torch)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_block(w, run_oracle(w, 1))
     if rank == 0:

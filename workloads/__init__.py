@@ -14,6 +14,7 @@ import numpy as np
 
 LAPLACE = 0
 HELMHOLTZ = 1
+HELMHOLTZ_LS = 4   # symmetrised Lippmann-Schwinger (the paper's Helmholtz problem)
 
 
 def grid_points(side: int) -> np.ndarray:
