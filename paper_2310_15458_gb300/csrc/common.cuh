@@ -100,6 +100,84 @@ __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
 }
 
+// ------------------------------------------------------------------ tensor-core fragments
+// D += A B on one m16n8k16 tile, bf16 inputs, FP32 accumulators (mma.sync).
+__device__ __forceinline__ void mma_bf16(float* c, const uint32_t* a, const uint32_t* b) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+__device__ __forceinline__ void ldsm_x4(uint32_t* d, const void* smem_row) {
+  const unsigned addr = (unsigned)__cvta_generic_to_shared(smem_row);
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(d[0]), "=r"(d[1]), "=r"(d[2]), "=r"(d[3])
+               : "r"(addr));
+}
+
+// ------------------------------------------------------------------ digit slices, integer only
+// A vector x_0..x_{n-1} with max |x| = m 2^e (m in [0.5, 1)) is written as
+// x_l = 2^e sum_{p<8} d_{p,l} 2^{-7(p+1)} with signed 7-bit digits (|d_0| <= 128,
+// |d_p| <= 64), every digit exact in bf16.  These helpers do it with integer
+// operations on the bit patterns (no FP64 instruction).
+// |x| as an ordered integer key (non-negative doubles order like their bits)
+__device__ __forceinline__ unsigned long long oz_abs_bits(double x) {
+  return (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
+}
+// biased exponent field of the maximum (at least 1), from its key
+__device__ __forceinline__ int oz_emax_b(unsigned long long maxkey) {
+  const int eb = (int)(maxkey >> 52);
+  return eb > 0 ? eb : 1;
+}
+// x 2^(56 - e) rounded to an integer (ties away from zero), e = emax_b - 1022
+__device__ __forceinline__ long long oz_scaled_int(double x, int emax_b) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int eb = (int)((b >> 52) & 0x7FF);
+  unsigned long long m = b & 0xFFFFFFFFFFFFFull;
+  if (eb) m |= 1ull << 52;
+  const int sh = (eb > 0 ? eb : 1) - emax_b + 3;
+  long long X;
+  if (sh >= 0) X = (long long)(m << sh);
+  else if (sh > -63) X = (long long)((m + (1ull << (-sh - 1))) >> (-sh));
+  else X = 0;
+  return (b >> 63) ? -X : X;
+}
+// bf16 bit pattern of a small integer d, |d| <= 128 (exact)
+__device__ __forceinline__ unsigned oz_bf16_int(int d) {
+  if (d == 0) return 0u;
+  const unsigned a = d < 0 ? (unsigned)(-d) : (unsigned)d;
+  const int p = 31 - __clz(a);
+  return ((d < 0) ? 0x8000u : 0u) | ((unsigned)(p + 127) << 7) | ((a << (7 - p)) & 0x7Fu);
+}
+// the eight digits of X (|X| < 2^56), most significant first, packed for two
+// adjacent entries: out[p] = bf16(d_p(X0)) | bf16(d_p(X1)) << 16
+__device__ __forceinline__ void oz_digits2(long long X0, long long X1, uint32_t* out) {
+  int d0[8], d1[8];
+#pragma unroll
+  for (int p = 7; p >= 1; --p) {
+    d0[p] = (int)(((X0 + 64) & 127) - 64);
+    X0 = (X0 - d0[p]) >> 7;
+    d1[p] = (int)(((X1 + 64) & 127) - 64);
+    X1 = (X1 - d1[p]) >> 7;
+  }
+  d0[0] = (int)X0;
+  d1[0] = (int)X1;
+#pragma unroll
+  for (int p = 0; p < 8; ++p) out[p] = oz_bf16_int(d0[p]) | (oz_bf16_int(d1[p]) << 16);
+}
+// W 2^s as a double, W an exact integer (|W| < 2^63): one conversion, the
+// power of two added to the exponent field when the result stays normal
+__device__ __forceinline__ double oz_ldexp_int(long long W, int s) {
+  if (W == 0) return 0.0;
+  const double d = (double)W;
+  const long long b = __double_as_longlong(d);
+  const int eb = (int)((b >> 52) & 0x7FF) + s;
+  if (eb > 0 && eb < 2047) return __longlong_as_double(b + ((long long)s << 52));
+  return ldexp(d, s);
+}
+
 template <typename T> __device__ inline T warp_sum(T v) {
 #pragma unroll
   for (int d = 16; d > 0; d >>= 1) v = v + shfl_xor(v, d);

@@ -264,6 +264,220 @@ __global__ void __launch_bounds__(SW_NT_R) k_down(const BoxRec<T>* __restrict__ 
   if (tid == 0) cnt[box] = 0;   // ready for the next colour class
 }
 
+// ------------------------------------------------------------------ many right-hand sides on the tensor cores
+// Real factors with at least TCN right-hand sides: every product of a sweep is a
+// small GEMM (factor block) x (TCN columns of right-hand sides), formed exactly
+// from 7-bit digit slices as in the factorization's products: the rows of the
+// factor block and the columns of the right-hand sides are scaled by powers of
+// two and cut into eight digits (integer operations), the slice products are
+// summed exactly by bf16 MMAs with FP32 accumulation, gathered into one int64
+// per entry and per K chunk of TCK, and the chunks are added in FP64.  One CTA
+// owns one box and TCN columns, so each sweep is one launch per colour class
+// with no cross-CTA dependency.
+constexpr int TCN = 32, TCM = 64, TCK = 32, TSA = 8 * TCK + 8;   // TSA: bf16 per slice row (16-byte rows)
+constexpr int TC_NT = 256;
+
+// C(i, q) receives sum_l A(i, l) B(l, q) for i < M, q < TCN; A(i, l) = aval(i, l),
+// B(l, q) = bval(l, q) (FP64).  Every thread of the CTA calls it.
+template <typename AF, typename BF, typename OF>
+__device__ void tc_gemm32(int M, int K, AF aval, BF bval, OF cout, uint16_t* As, uint16_t* Bs, int* rexp,
+                          int* cexp) {
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, gq = lane >> 2, t4 = lane & 3;
+  const int m0 = (warp >> 1) * 16, n0 = (warp & 1) * 16;
+  const int a_row = lane & 15, a_k = (lane >> 4) * 8;
+  const int b_row = ((lane >> 4) << 3) + (lane & 7), b_k = ((lane >> 3) & 1) * 8;
+  for (int mt = 0; mt < M; mt += TCM) {
+    double acc[2][4];
+#pragma unroll
+    for (int ni = 0; ni < 2; ++ni)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) acc[ni][e] = 0.0;
+    for (int kc = 0; kc < K; kc += TCK) {
+      const int kl = min(TCK, K - kc);
+      __syncthreads();   // the previous chunk's slices are consumed
+      {   // rows of A: 64 rows x 4 lanes
+        const int row = tid >> 2, gl = tid & 3, i = mt + row;
+        const bool act = i < M;
+        unsigned long long mk = 0;
+        if (act)
+          for (int l = gl; l < kl; l += 4) mk = max(mk, oz_abs_bits(aval(i, kc + l)));
+        mk = max(mk, (unsigned long long)__shfl_xor_sync(0xffffffffu, (long long)mk, 1));
+        mk = max(mk, (unsigned long long)__shfl_xor_sync(0xffffffffu, (long long)mk, 2));
+        const int eb = oz_emax_b(mk);
+        if (gl == 0) rexp[row] = eb - 1022;
+        uint16_t* dst = As + row * TSA;
+        for (int l = 2 * gl; l < TCK; l += 8) {
+          const long long X0 = (act && l < kl) ? oz_scaled_int(aval(i, kc + l), eb) : 0;
+          const long long X1 = (act && l + 1 < kl) ? oz_scaled_int(aval(i, kc + l + 1), eb) : 0;
+          uint32_t dg[8];
+          oz_digits2(X0, X1, dg);
+#pragma unroll
+          for (int p = 0; p < 8; ++p) *reinterpret_cast<uint32_t*>(dst + p * TCK + l) = dg[p];
+        }
+      }
+      {   // columns of B: 32 columns x 8 lanes
+        const int col = tid >> 3, gl = tid & 7;
+        unsigned long long mk = 0;
+        for (int l = gl; l < kl; l += 8) mk = max(mk, oz_abs_bits(bval(kc + l, col)));
+#pragma unroll
+        for (int d = 1; d < 8; d <<= 1)
+          mk = max(mk, (unsigned long long)__shfl_xor_sync(0xffffffffu, (long long)mk, d));
+        const int eb = oz_emax_b(mk);
+        if (gl == 0) cexp[col] = eb - 1022;
+        uint16_t* dst = Bs + col * TSA;
+        for (int l = 2 * gl; l < TCK; l += 16) {
+          const long long X0 = l < kl ? oz_scaled_int(bval(kc + l, col), eb) : 0;
+          const long long X1 = l + 1 < kl ? oz_scaled_int(bval(kc + l + 1, col), eb) : 0;
+          uint32_t dg[8];
+          oz_digits2(X0, X1, dg);
+#pragma unroll
+          for (int p = 0; p < 8; ++p) *reinterpret_cast<uint32_t*>(dst + p * TCK + l) = dg[p];
+        }
+      }
+      __syncthreads();
+      long long W[2][4];
+#pragma unroll
+      for (int ni = 0; ni < 2; ++ni)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) W[ni][e] = 0;
+#pragma unroll 1
+      for (int u = 0; u < 8; ++u) {
+        float cf[2][4];
+#pragma unroll
+        for (int ni = 0; ni < 2; ++ni)
+#pragma unroll
+          for (int e = 0; e < 4; ++e) cf[ni][e] = 0.f;
+        for (int p = 0; p <= u; ++p) {
+          const uint16_t* Ab = As + p * TCK + (m0 + a_row) * TSA + a_k;
+          const uint16_t* Bb = Bs + (u - p) * TCK + (n0 + b_row) * TSA + b_k;
+#pragma unroll
+          for (int kk = 0; kk < TCK; kk += 16) {
+            uint32_t af[4], bq[4];
+            ldsm_x4(af, Ab + kk);
+            ldsm_x4(bq, Bb + kk);
+            mma_bf16(cf[0], af, bq);
+            mma_bf16(cf[1], af, bq + 2);
+          }
+        }
+        const int sh = 39 - 7 * u;
+#pragma unroll
+        for (int ni = 0; ni < 2; ++ni)
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const long long gv = (long long)__float2int_rn(cf[ni][e]);
+            W[ni][e] += sh >= 0 ? (gv << sh) : ((gv + (1LL << (-sh - 1))) >> (-sh));
+          }
+      }
+#pragma unroll
+      for (int ni = 0; ni < 2; ++ni)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int row = m0 + gq + (e >= 2 ? 8 : 0), col = n0 + ni * 8 + 2 * t4 + (e & 1);
+          acc[ni][e] += oz_ldexp_int(W[ni][e], rexp[row] + cexp[col] - 53);
+        }
+    }
+#pragma unroll
+    for (int ni = 0; ni < 2; ++ni)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int row = m0 + gq + (e >= 2 ? 8 : 0), col = n0 + ni * 8 + 2 * t4 + (e & 1);
+        if (mt + row < M) cout(mt + row, col, acc[ni][e]);
+      }
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ size_t tc_smem_head() {
+  return (size_t)(TCM + TCN) * TSA * sizeof(uint16_t);
+}
+
+// Upward sweep of one box for TCN right-hand-side columns:
+// t = b_R - T^* b_S, b_R = L^{-1} P t, b_C -= E b_R.
+__global__ void __launch_bounds__(TC_NT, 2) k_up_tc(const BoxRec<double>* __restrict__ recs, double* __restrict__ x,
+                                                    int64_t N, int nrhs) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const BoxRec<double> R = recs[blockIdx.x];
+  const int k = R.k, r = R.r, c = R.c;
+  const int q0 = blockIdx.y * TCN, nq = min(TCN, nrhs - q0);
+  uint16_t* As = reinterpret_cast<uint16_t*>(smraw);
+  uint16_t* Bs = As + TCM * TSA;
+  double* bS = reinterpret_cast<double*>(smraw + tc_smem_head());   // k x TCN
+  double* t = bS + (size_t)k * TCN;                                  // r x TCN
+  double* u = t + (size_t)r * TCN;                                   // r x TCN
+  __shared__ int rexp[TCM], cexp[TCN];
+  const int tid = threadIdx.x, bs = blockDim.x;
+  double* xq = x + (int64_t)q0 * N;
+  for (int e = tid; e < k * TCN; e += bs) {
+    const int s2 = e / TCN, q = e % TCN;
+    bS[e] = q < nq ? xq[R.idxC[s2] + (int64_t)q * N] : 0.0;
+  }
+  for (int e = tid; e < r * TCN; e += bs) {
+    const int j = e / TCN, q = e % TCN;
+    t[e] = q < nq ? xq[R.idxR[j] + (int64_t)q * N] : 0.0;
+  }
+  const double* __restrict__ Tm = R.Tm;
+  const double* __restrict__ LiP = R.LiP;
+  const double* __restrict__ E = R.E;
+  tc_gemm32(r, k, [&](int i, int l) { return Tm[l + (size_t)i * k]; }, [&](int l, int q) { return bS[l * TCN + q]; },
+            [&](int i, int q, double v) { t[i * TCN + q] -= v; }, As, Bs, rexp, cexp);
+  tc_gemm32(r, r, [&](int i, int l) { return LiP[i + (size_t)l * r]; }, [&](int l, int q) { return t[l * TCN + q]; },
+            [&](int i, int q, double v) { u[i * TCN + q] = v; }, As, Bs, rexp, cexp);
+  for (int e = tid; e < r * TCN; e += bs) {
+    const int j = e / TCN, q = e % TCN;
+    if (q < nq) xq[R.idxR[j] + (int64_t)q * N] = u[e];
+  }
+  tc_gemm32(c, r, [&](int i, int l) { return E[i + (size_t)l * c]; }, [&](int l, int q) { return u[l * TCN + q]; },
+            [&](int i, int q, double v) {
+              if (q < nq) {
+                const int64_t gi = R.idxC[i] + (int64_t)q * N;
+                xq[gi] = xq[gi] - v;
+              }
+            },
+            As, Bs, rexp, cexp);
+}
+
+// Downward sweep of one box for TCN columns: z = y_R - F y_C, y_R = U^{-1} z,
+// y_S -= T y_R.
+__global__ void __launch_bounds__(TC_NT, 2) k_down_tc(const BoxRec<double>* __restrict__ recs,
+                                                      double* __restrict__ x, int64_t N, int nrhs) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const BoxRec<double> R = recs[blockIdx.x];
+  const int k = R.k, r = R.r, c = R.c;
+  const int q0 = blockIdx.y * TCN, nq = min(TCN, nrhs - q0);
+  uint16_t* As = reinterpret_cast<uint16_t*>(smraw);
+  uint16_t* Bs = As + TCM * TSA;
+  double* z = reinterpret_cast<double*>(smraw + tc_smem_head());   // r x TCN
+  double* yR = z + (size_t)r * TCN;                                 // r x TCN
+  __shared__ int rexp[TCM], cexp[TCN];
+  const int tid = threadIdx.x, bs = blockDim.x;
+  double* xq = x + (int64_t)q0 * N;
+  for (int e = tid; e < r * TCN; e += bs) {
+    const int j = e / TCN, q = e % TCN;
+    z[e] = q < nq ? xq[R.idxR[j] + (int64_t)q * N] : 0.0;
+  }
+  const double* __restrict__ Ft = R.Ft;
+  const double* __restrict__ Ui = R.Ui;
+  const double* __restrict__ Tm = R.Tm;
+  const int* __restrict__ idxC = R.idxC;
+  tc_gemm32(r, c, [&](int j, int i) { return Ft[i + (size_t)j * c]; },
+            [&](int i, int q) { return q < nq ? xq[idxC[i] + (int64_t)q * N] : 0.0; },
+            [&](int j, int q, double v) { z[j * TCN + q] -= v; }, As, Bs, rexp, cexp);
+  tc_gemm32(r, r, [&](int j, int l) { return Ui[j + (size_t)l * r]; }, [&](int l, int q) { return z[l * TCN + q]; },
+            [&](int j, int q, double v) { yR[j * TCN + q] = v; }, As, Bs, rexp, cexp);
+  for (int e = tid; e < r * TCN; e += bs) {
+    const int j = e / TCN, q = e % TCN;
+    if (q < nq) xq[R.idxR[j] + (int64_t)q * N] = yR[e];
+  }
+  tc_gemm32(k, r, [&](int s2, int j) { return Tm[s2 + (size_t)j * k]; }, [&](int j, int q) { return yR[j * TCN + q]; },
+            [&](int s2, int q, double v) {
+              if (q < nq) {
+                const int64_t gs = idxC[s2] + (int64_t)q * N;
+                xq[gs] = xq[gs] - v;
+              }
+            },
+            As, Bs, rexp, cexp);
+}
+
 // Top block: x_top <- A_top^{-1} x_top with the inverse formed at factor time.
 template <typename T>
 __global__ void k_top_gather(const int* __restrict__ idx, int n, const T* __restrict__ x, int64_t N, int nrhs,
@@ -461,8 +675,56 @@ rss_status sweeps(const rss_factorization* f, T* x, int64_t N, int nrhs, cudaStr
   return RSS_OK;
 }
 
+// Real factors with at least TCN right-hand sides: the tensor-core sweeps; the
+// top block as in sweeps<double, 8>.
+rss_status sweeps_tc(const rss_factorization* f, double* x, int64_t N, int nrhs, cudaStream_t st, void* ws) {
+  constexpr int RC = 8;
+  const unsigned nz = cdiv(nrhs, TCN);
+  const SweepWs w = sweep_ws<double>(f, nrhs, RC);
+  double* topz = reinterpret_cast<double*>(static_cast<char*>(ws) + w.topz_off);
+  RSS_CUDA(cudaFuncSetAttribute(k_up_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
+  RSS_CUDA(cudaFuncSetAttribute(k_down_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
+  RSS_CUDA(cudaFuncSetAttribute(k_top_gemv<double, RC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+  const size_t head = (size_t)(TCM + TCN) * TSA * sizeof(uint16_t);
+  for (const Batch& b : f->batches) {
+    const size_t sm = head + sizeof(double) * (size_t)(b.max_k + 2 * b.max_r) * TCN;
+    if (sm > 220 * 1024) {
+      rss_set_error("rss_solve: box too large for the tensor-core sweep");
+      return RSS_EINVAL;
+    }
+    k_up_tc<<<dim3(b.nrec, nz), TC_NT, sm, st>>>(static_cast<const BoxRec<double>*>(b.d_recs), x, N, nrhs);
+    RSS_LAUNCHED();
+  }
+  if (f->ntop > 0) {
+    const unsigned nz8 = cdiv(nrhs, RC);
+    const size_t tsm = sizeof(double) * (size_t)f->ntop * RC;
+    if (tsm > 200 * 1024) {
+      rss_set_error("rss_solve: top block too large for the on-chip solve");
+      return RSS_EINVAL;
+    }
+    const unsigned g = std::min<long long>(cdiv((long long)f->ntop * nz8 * RC, 256), 152LL * 8);
+    k_top_gather<double><<<g, 256, 0, st>>>(f->d_top_idx, f->ntop, x, N, nrhs, topz);
+    RSS_LAUNCHED();
+    k_top_gemv<double, RC><<<dim3(cdiv(f->ntop, SW_NT), nz8), SW_NT, tsm, st>>>(
+        static_cast<const double*>(f->d_top_inv), f->d_top_idx, f->ntop, topz, x, N, nrhs);
+    RSS_LAUNCHED();
+  }
+  for (auto it = f->batches.rbegin(); it != f->batches.rend(); ++it) {
+    const size_t sm = head + sizeof(double) * (size_t)(2 * it->max_r) * TCN;
+    k_down_tc<<<dim3(it->nrec, nz), TC_NT, sm, st>>>(static_cast<const BoxRec<double>*>(it->d_recs), x, N, nrhs);
+    RSS_LAUNCHED();
+  }
+  return RSS_OK;
+}
+
+bool use_tc(const rss_factorization* f, int64_t nrhs) {
+  return !f->is_complex && nrhs >= TCN && f->params.schur_path == 0;
+}
+
 template <typename T>
 rss_status run_sweeps(const rss_factorization* f, T* x, int64_t N, int64_t nrhs, cudaStream_t st, void* ws) {
+  if constexpr (sizeof(T) == sizeof(double))
+    if (use_tc(f, nrhs)) return sweeps_tc(f, x, N, (int)nrhs, st, ws);
   const int rc = rhs_chunk(nrhs);
   return rc == 1 ? sweeps<T, 1>(f, x, N, (int)nrhs, st, ws)
          : rc == 4 ? sweeps<T, 4>(f, x, N, (int)nrhs, st, ws)

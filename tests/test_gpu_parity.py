@@ -157,6 +157,29 @@ def test_ragged_rhs_chunks_host_buffers_and_user_order(P):
     assert relres(pts, spec, x_dev, b) <= 10 * eps
 
 
+def test_tensor_core_sweeps_many_rhs(P):
+    """40 right-hand sides (a full chunk of 32 and a ragged one) take the tensor-core
+    sweeps: they agree with one-column FP64 solves to 1e-12, a column's result does
+    not depend on the other columns (bitwise), and the residual meets 10 eps."""
+    side, eps = 64, 1e-6
+    pts = W.grid_points(side)
+    spec = KernelSpec("laplace", h=1 / side)
+    f = gpu_factor(P, pts, spec, eps, 64)
+    b = W.gaussian_rhs(side * side, 40, False, 45)
+    x = gpu_solve(P, f, b)
+    for j in (0, 17, 31, 32, 39):
+        xj = gpu_solve(P, f, np.ascontiguousarray(b[:, j]))
+        assert np.linalg.norm(x[:, j] - xj) <= 1e-12 * np.linalg.norm(xj)
+    perm = np.random.default_rng(1).permutation(40)
+    xp = gpu_solve(P, f, np.asfortranarray(b[:, perm]))
+    assert np.array_equal(xp, x[:, perm])
+    x33 = gpu_solve(P, f, np.asfortranarray(b[:, :33]))
+    assert np.array_equal(x33, x[:, :33])
+    assert relres(pts, spec, x, b) <= 10 * eps
+    fac = orss.factor(pts, spec, eps)
+    assert rel(x, orss.solve(fac, b)) < 1e-9
+
+
 @pytest.mark.parametrize("side,leaf", [(8, 64), (16, 64), (32, 16)])
 def test_degenerate_trees(P, side, leaf):
     """One box, a 2 x 2 top only, and eps = 0 (no compression): all exact."""
