@@ -2,6 +2,7 @@
 // entries of A (paper Eqs. 3, 15, 18) and host error plumbing.
 #pragma once
 #include <cuda_runtime.h>
+#include <cuda_bf16.h>
 #include <cstdint>
 #include <cstdio>
 #include <string>
@@ -144,12 +145,9 @@ __device__ __forceinline__ long long oz_scaled_int(double x, int emax_b) {
   else X = 0;
   return (b >> 63) ? -X : X;
 }
-// bf16 bit pattern of a small integer d, |d| <= 128 (exact)
+// bf16 bit pattern of a small integer d, |d| <= 128 (exact: conversion instructions)
 __device__ __forceinline__ unsigned oz_bf16_int(int d) {
-  if (d == 0) return 0u;
-  const unsigned a = d < 0 ? (unsigned)(-d) : (unsigned)d;
-  const int p = 31 - __clz(a);
-  return ((d < 0) ? 0x8000u : 0u) | ((unsigned)(p + 127) << 7) | ((a << (7 - p)) & 0x7Fu);
+  return (unsigned)__bfloat16_as_ushort(__float2bfloat16_rn((float)d));
 }
 // the eight digits of X (|X| < 2^56), most significant first, packed for two
 // adjacent entries: out[p] = bf16(d_p(X0)) | bf16(d_p(X1)) << 16

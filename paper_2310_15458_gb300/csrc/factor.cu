@@ -741,10 +741,6 @@ template <typename T, typename S = T> __global__ void __launch_bounds__(NT_ID) k
 }
 
 // ------------------------------------------------------------------ tensor-core helpers
-// 2^e as a double for the normal range, from its bit pattern
-__device__ __forceinline__ double pow2(int e) {
-  return (e > -1023 && e < 1024) ? __longlong_as_double((long long)(e + 1023) << 52) : ldexp(1.0, e);
-}
 
 // ------------------------------------------------------------------ digit slices
 // A row x_0..x_{r-1} with max |x_l| = m 2^e (m in [0.5, 1)) is written as
@@ -1400,33 +1396,23 @@ template <typename T, int MA> __global__ void __launch_bounds__(NT, 2) k_elim_pa
 template <int G, typename VF>
 __device__ __forceinline__ void oz_split_vec(VF val, int len, int lenp, uint16_t* dst, int ldd, int* eout,
                                              bool store) {
+  // integer operations only (the FP64 pipe is the scarce unit)
   const int gl = threadIdx.x & (G - 1);
-  double mx = 0.0;
-  for (int l = gl; l < len; l += G) mx = fmax(mx, fabs(val(l)));
+  unsigned long long mk = 0;
+  for (int l = gl; l < len; l += G) mk = max(mk, oz_abs_bits(val(l)));
 #pragma unroll
-  for (int d = G / 2; d > 0; d >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, d));
+  for (int d = G / 2; d > 0; d >>= 1)
+    mk = max(mk, (unsigned long long)__shfl_xor_sync(0xffffffffu, (long long)mk, d));
   if (!store) return;
-  int e = 0;
-  if (mx > 0.0) frexp(mx, &e);
-  if (gl == 0) *eout = e;
-  const double scale = ldexp(1.0, 56 - e);
+  const int eb = oz_emax_b(mk);
+  if (gl == 0) *eout = mk ? eb - 1022 : 0;
   for (int l = 2 * gl; l < lenp; l += 2 * G) {
-    long long X0 = l < len ? llrint(val(l) * scale) : 0;
-    long long X1 = l + 1 < len ? llrint(val(l + 1) * scale) : 0;
-    int d0[OZ_S], d1[OZ_S];
+    const long long X0 = l < len ? oz_scaled_int(val(l), eb) : 0;
+    const long long X1 = l + 1 < len ? oz_scaled_int(val(l + 1), eb) : 0;
+    uint32_t dg[OZ_S];
+    oz_digits2(X0, X1, dg);
 #pragma unroll
-    for (int p = OZ_S - 1; p >= 1; --p) {
-      d0[p] = (int)(((X0 + 64) & 127) - 64);
-      X0 = (X0 - d0[p]) >> OZ_BITS;
-      d1[p] = (int)(((X1 + 64) & 127) - 64);
-      X1 = (X1 - d1[p]) >> OZ_BITS;
-    }
-    d0[0] = (int)X0;
-    d1[0] = (int)X1;
-#pragma unroll
-    for (int p = 0; p < OZ_S; ++p)
-      *reinterpret_cast<uint32_t*>(dst + (size_t)p * ldd + l) =
-          (uint32_t)bf16_of_small_int(d0[p]) | ((uint32_t)bf16_of_small_int(d1[p]) << 16);
+    for (int p = 0; p < OZ_S; ++p) *reinterpret_cast<uint32_t*>(dst + (size_t)p * ldd + l) = dg[p];
   }
 }
 
@@ -1526,7 +1512,7 @@ __global__ void __launch_bounds__(NT, 2) k_elim_oz(ElimArgs<double> a) {
           const int row = m0 + gq + (e >= 2 ? 8 : 0);
           const int col = n0 + ni * 8 + 2 * t4 + (e & 1), j = jc + col;
           if (row < rows && j < r)
-            out[(size_t)(p0 + row) + (size_t)j * c] = (double)W[ni][e] * pow2(rexp[row] + cexp[col] - 53);
+            out[(size_t)(p0 + row) + (size_t)j * c] = oz_ldexp_int(W[ni][e], rexp[row] + cexp[col] - 53);
         }
     }
     __syncthreads();
@@ -1712,7 +1698,7 @@ __global__ void __launch_bounds__(NT) k_schur_oz(LevelDev<double> L, const BoxRe
         const int row = m0 + mi * 16 + gq + (e >= 2 ? 8 : 0);
         const int col = n0 + ni * 8 + 2 * t4 + (e & 1);
         if (i0 + row < c && j0 + col < c) {
-          const double v = (double)W[mi][ni][e] * pow2(rexp[row] + cexp[col] - 53);
+          const double v = oz_ldexp_int(W[mi][ni][e], rexp[row] + cexp[col] - 53);
           double* ptr = L.blk + rowb[row] + colb[col];
           *ptr = *ptr - v;
         }
@@ -1834,10 +1820,10 @@ __global__ void __launch_bounds__(NT) k_schur_oz_c(LevelDev<zd> L, const BoxRec<
       const int row = m0 + gq + (e >= 2 ? 8 : 0);
       const int col = n0 + ni * 8 + 2 * t4 + (e & 1);
       if (i0 + row < c && j0 + col < c) {
-        const double s = pow2(rexp[row] + cexp[col] - 53);
+        const int sx = rexp[row] + cexp[col] - 53;
         zd* ptr = L.blk + rowb[row] + colb[col];
         const zd o = *ptr;
-        *ptr = zd{o.x - (double)Wr[ni][e] * s, o.y - (double)Wi[ni][e] * s};
+        *ptr = zd{o.x - oz_ldexp_int(Wr[ni][e], sx), o.y - oz_ldexp_int(Wi[ni][e], sx)};
       }
     }
 }
