@@ -118,6 +118,12 @@ __device__ __forceinline__ void ldsm_x4(uint32_t* d, const void* smem_row) {
                : "r"(addr));
 }
 
+// flip the sign of both bf16 values of every register of a fragment
+__device__ __forceinline__ void neg_bf16x2(uint32_t* a) {
+#pragma unroll
+  for (int i = 0; i < 4; ++i) a[i] ^= 0x80008000u;
+}
+
 // ------------------------------------------------------------------ digit slices, integer only
 // A vector x_0..x_{n-1} with max |x| = m 2^e (m in [0.5, 1)) is written as
 // x_l = 2^e sum_{p<8} d_{p,l} 2^{-7(p+1)} with signed 7-bit digits (|d_0| <= 128,

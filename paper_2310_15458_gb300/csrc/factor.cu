@@ -1528,6 +1528,211 @@ __global__ void __launch_bounds__(NT, 2) k_elim_oz(ElimArgs<double> a) {
   }
 }
 
+// ------------------------------------------------------------------ complex E and F on the tensor cores
+// C(i, q) = sum_l A(i, l) B(l, q) for complex A (M x K) and B (K x 32): every row
+// of A and column of B is scaled by one power of two for its real and imaginary
+// parts and cut into eight 7-bit digit slices each (slices 0-7 real, 8-15
+// imaginary); Re = Ar Br - Ai Bi and Im = Ar Bi + Ai Br are summed exactly per
+// K chunk of 32 (bf16 MMAs, FP32 accumulators, the sign of Ai flipped on the
+// fragment bits), gathered in int64 and added over the chunks in FP64.  Rows in
+// tiles of 64; every thread of the CTA calls it.
+constexpr int ZCN = 32, ZCM = 64, ZCK = 32, ZSA = 16 * ZCK + 8;
+
+template <typename AF, typename BF, typename OF>
+__device__ void tc_gemm_c(int M, int K, AF aval, BF bval, OF cout, uint16_t* As, uint16_t* Bs, int* rexp, int* cexp) {
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, gq = lane >> 2, t4 = lane & 3;
+  const int m0 = (warp >> 1) * 16, n0 = (warp & 1) * 16;
+  const int a_row = lane & 15, a_k = (lane >> 4) * 8;
+  const int b_row = ((lane >> 4) << 3) + (lane & 7), b_k = ((lane >> 3) & 1) * 8;
+  for (int mt = 0; mt < M; mt += ZCM) {
+    double accr[2][4], acci[2][4];
+#pragma unroll
+    for (int ni = 0; ni < 2; ++ni)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) accr[ni][e] = acci[ni][e] = 0.0;
+    for (int kc = 0; kc < K; kc += ZCK) {
+      const int kl = min(ZCK, K - kc);
+      __syncthreads();
+      {   // rows of A: 64 rows x 4 lanes
+        const int row = tid >> 2, gl = tid & 3, i = mt + row;
+        const bool act = i < M;
+        unsigned long long mk = 0;
+        if (act)
+          for (int l = gl; l < kl; l += 4) {
+            const zd v = aval(i, kc + l);
+            mk = max(mk, max(oz_abs_bits(v.x), oz_abs_bits(v.y)));
+          }
+        mk = max(mk, (unsigned long long)__shfl_xor_sync(0xffffffffu, (long long)mk, 1));
+        mk = max(mk, (unsigned long long)__shfl_xor_sync(0xffffffffu, (long long)mk, 2));
+        const int eb = oz_emax_b(mk);
+        if (gl == 0) rexp[row] = eb - 1022;
+        uint16_t* dst = As + row * ZSA;
+        for (int l = 2 * gl; l < ZCK; l += 8) {
+          const zd v0 = (act && l < kl) ? aval(i, kc + l) : zd{0.0, 0.0};
+          const zd v1 = (act && l + 1 < kl) ? aval(i, kc + l + 1) : zd{0.0, 0.0};
+          uint32_t dr[8], di[8];
+          oz_digits2(oz_scaled_int(v0.x, eb), oz_scaled_int(v1.x, eb), dr);
+          oz_digits2(oz_scaled_int(v0.y, eb), oz_scaled_int(v1.y, eb), di);
+#pragma unroll
+          for (int p = 0; p < 8; ++p) {
+            *reinterpret_cast<uint32_t*>(dst + p * ZCK + l) = dr[p];
+            *reinterpret_cast<uint32_t*>(dst + (8 + p) * ZCK + l) = di[p];
+          }
+        }
+      }
+      {   // columns of B: 32 columns x 8 lanes
+        const int col = tid >> 3, gl = tid & 7;
+        unsigned long long mk = 0;
+        for (int l = gl; l < kl; l += 8) {
+          const zd b = bval(kc + l, col);
+          mk = max(mk, max(oz_abs_bits(b.x), oz_abs_bits(b.y)));
+        }
+#pragma unroll
+        for (int d = 1; d < 8; d <<= 1)
+          mk = max(mk, (unsigned long long)__shfl_xor_sync(0xffffffffu, (long long)mk, d));
+        const int eb = oz_emax_b(mk);
+        if (gl == 0) cexp[col] = eb - 1022;
+        uint16_t* dst = Bs + col * ZSA;
+        for (int l = 2 * gl; l < ZCK; l += 16) {
+          const zd v0 = l < kl ? bval(kc + l, col) : zd{0.0, 0.0};
+          const zd v1 = l + 1 < kl ? bval(kc + l + 1, col) : zd{0.0, 0.0};
+          uint32_t dr[8], di[8];
+          oz_digits2(oz_scaled_int(v0.x, eb), oz_scaled_int(v1.x, eb), dr);
+          oz_digits2(oz_scaled_int(v0.y, eb), oz_scaled_int(v1.y, eb), di);
+#pragma unroll
+          for (int p = 0; p < 8; ++p) {
+            *reinterpret_cast<uint32_t*>(dst + p * ZCK + l) = dr[p];
+            *reinterpret_cast<uint32_t*>(dst + (8 + p) * ZCK + l) = di[p];
+          }
+        }
+      }
+      __syncthreads();
+      long long Wr[2][4], Wi[2][4];
+#pragma unroll
+      for (int ni = 0; ni < 2; ++ni)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) Wr[ni][e] = Wi[ni][e] = 0;
+#pragma unroll 1
+      for (int u = 0; u < 8; ++u) {
+        float cr[2][4], ci[2][4];
+#pragma unroll
+        for (int ni = 0; ni < 2; ++ni)
+#pragma unroll
+          for (int e = 0; e < 4; ++e) cr[ni][e] = ci[ni][e] = 0.f;
+        for (int p = 0; p <= u; ++p) {
+          const uint16_t* Ar = As + p * ZCK + (m0 + a_row) * ZSA + a_k;
+          const uint16_t* Ai = As + (8 + p) * ZCK + (m0 + a_row) * ZSA + a_k;
+          const uint16_t* Br = Bs + (u - p) * ZCK + (n0 + b_row) * ZSA + b_k;
+          const uint16_t* Bi = Bs + (8 + u - p) * ZCK + (n0 + b_row) * ZSA + b_k;
+#pragma unroll
+          for (int kk = 0; kk < ZCK; kk += 16) {
+            uint32_t ar[4], ai[4], br[4], bi[4];
+            ldsm_x4(ar, Ar + kk);
+            ldsm_x4(ai, Ai + kk);
+            ldsm_x4(br, Br + kk);
+            ldsm_x4(bi, Bi + kk);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              mma_bf16(cr[h], ar, br + 2 * h);
+              mma_bf16(ci[h], ar, bi + 2 * h);
+              mma_bf16(ci[h], ai, br + 2 * h);
+            }
+            neg_bf16x2(ai);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) mma_bf16(cr[h], ai, bi + 2 * h);
+          }
+        }
+        const int sh = 39 - 7 * u;
+#pragma unroll
+        for (int ni = 0; ni < 2; ++ni)
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const long long gr = (long long)__float2int_rn(cr[ni][e]), gi = (long long)__float2int_rn(ci[ni][e]);
+            Wr[ni][e] += sh >= 0 ? (gr << sh) : ((gr + (1LL << (-sh - 1))) >> (-sh));
+            Wi[ni][e] += sh >= 0 ? (gi << sh) : ((gi + (1LL << (-sh - 1))) >> (-sh));
+          }
+      }
+#pragma unroll
+      for (int ni = 0; ni < 2; ++ni)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int row = m0 + gq + (e >= 2 ? 8 : 0), col = n0 + ni * 8 + 2 * t4 + (e & 1);
+          const int sx = rexp[row] + cexp[col] - 53;
+          accr[ni][e] += oz_ldexp_int(Wr[ni][e], sx);
+          acci[ni][e] += oz_ldexp_int(Wi[ni][e], sx);
+        }
+    }
+#pragma unroll
+    for (int ni = 0; ni < 2; ++ni)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int row = m0 + gq + (e >= 2 ? 8 : 0), col = n0 + ni * 8 + 2 * t4 + (e & 1);
+        if (mt + row < M) cout(mt + row, col, zd{accr[ni][e], acci[ni][e]});
+      }
+  }
+  __syncthreads();
+}
+
+// Complex factors: E = A_CB W_E and F^T = A_BC^T W_F for one 64-row panel of C
+// (any n_B: K is taken in chunks), then the rows' digit slices for the Schur
+// update.
+__global__ void __launch_bounds__(NT, 2) k_elim_ozc(ElimArgs<zd> a) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const BoxRec<zd> R = a.recs[blockIdx.y];
+  if (!R.ozp) return;
+  const int p0 = blockIdx.x * ZCM;
+  if (p0 >= R.c) return;
+  const LevelDev<zd>& L = a.L;
+  const int nmax = L.nmax, g = L.g, B = R.box, k = R.k, r = R.r, c = R.c, n = k + r;
+  const size_t nn = (size_t)nmax * nmax;
+  const int* perm = a.perm_in + (size_t)a.cls_idx[blockIdx.y] * nmax;
+  uint16_t* As = reinterpret_cast<uint16_t*>(smraw);
+  uint16_t* Bs = As + ZCM * ZSA;
+  __shared__ int rexp[ZCM], cexp[ZCN], ru[ZCM], rpos[ZCM], sperm[256];
+  const int tid = threadIdx.x, rows = min(ZCM, c - p0);
+  if (tid < ZCM) {
+    ru[tid] = -1;
+    rpos[tid] = 0;
+    if (tid < rows) {
+      const int cm = R.cmap[p0 + tid], s = cm >> 16;
+      ru[tid] = nbr_box(B, g, s % 3 - 1, s / 3 - 1);
+      rpos[tid] = cm & 0xffff;
+    }
+  }
+  const bool pin = n <= 256;
+  if (pin)
+    for (int i = tid; i < n; i += blockDim.x) sperm[i] = perm[i];
+  __syncthreads();
+  auto pm = [&](int l) { return pin ? sperm[l] : perm[l]; };
+  for (int pass = 0; pass < 2; ++pass) {
+    const zd* __restrict__ Wm = pass == 0 ? R.We : R.Wf;
+    zd* out = pass == 0 ? R.E : R.Ft;
+    for (int jc = 0; jc < r; jc += ZCN) {
+      auto aval = [&](int i, int l) -> zd {
+        const int u = ru[i], pos = rpos[i];
+        return pass == 0 ? L.blk[((size_t)u * 25 + off_index(u, B, g)) * nn + (size_t)pm(l) * nmax + pos]
+                         : L.blk[((size_t)B * 25 + off_index(B, u, g)) * nn + (size_t)pos * nmax + pm(l)];
+      };
+      auto bval = [&](int l, int q) -> zd {
+        const int j = jc + q;
+        return j < r ? Wm[(size_t)l + (size_t)j * n] : zd{0.0, 0.0};
+      };
+      tc_gemm_c(rows, n, aval, bval,
+                [&](int i, int q, zd v) {
+                  const int j = jc + q;
+                  if (j < r) out[(size_t)(p0 + i) + (size_t)j * c] = v;
+                },
+                As, Bs, rexp, cexp);
+    }
+    if (R.Esl != nullptr) {   // digit slices of this panel's rows for the Schur update
+      for (int e = tid; e < rows; e += blockDim.x)
+        oz_split_row(out + p0 + e, c, r, R.kp, (pass == 0 ? R.Esl : R.Fsl) + (size_t)(p0 + e) * 2 * OZ_S * R.kp,
+                     (pass == 0 ? R.Eexp : R.Fexp) + p0 + e);
+      __syncthreads();
+    }
+  }
+}
+
 // ------------------------------------------------------------------ Schur update A_CC -= E F
 template <typename T> __global__ void __launch_bounds__(NT) k_schur(LevelDev<T> L, const BoxRec<T>* recs) {
   constexpr int TM = 64, KC = 16;
@@ -1709,10 +1914,6 @@ __global__ void __launch_bounds__(NT) k_schur_oz(LevelDev<double> L, const BoxRe
 // (F^T rows split as Fr, Fi), each group sum exact as in the real case; the
 // sign of -Ei is flipped on the bf16 fragment bits.  64 x 32 tile per CTA,
 // 8 warps of 16 x 16.
-__device__ __forceinline__ void neg_bf16x2(uint32_t* a) {
-#pragma unroll
-  for (int i = 0; i < 4; ++i) a[i] ^= 0x80008000u;
-}
 
 __global__ void __launch_bounds__(NT) k_schur_oz_c(LevelDev<zd> L, const BoxRec<zd>* recs) {
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -2466,11 +2667,13 @@ rss_status factor_impl(const rss_tree* tree, const rss_params* prm, cudaStream_t
       // E = A_CB W_E and F^T = A_BC^T W_F on the tensor cores: real factors,
       // n <= 128 (the slices of a 64-row panel and of 32 columns of W fit in
       // shared memory)
+      // (complex factors: any n_B, K taken in chunks by k_elim_ozc)
       int ozp_np = 0;
-      if (sizeof(T) == sizeof(double) && prm->schur_path == 0) {
+      const int ozp_nmax = sizeof(T) == sizeof(double) ? 128 : (1 << 30);
+      if (prm->schur_path == 0) {
         size_t bytes = 0;
         for (const BoxRec<T>& R : recs)
-          if (R.k + R.r <= 128) bytes += 2 * (((size_t)(R.k + R.r) * R.r * sizeof(T) + 255) & ~size_t(255));
+          if (R.k + R.r <= ozp_nmax) bytes += 2 * (((size_t)(R.k + R.r) * R.r * sizeof(T) + 255) & ~size_t(255));
         if (bytes > 0) {
           if (!gb_w.ensure(bytes)) {
             rss_set_error("rss_factor: device workspace allocation failed");
@@ -2478,7 +2681,7 @@ rss_status factor_impl(const rss_tree* tree, const rss_params* prm, cudaStream_t
           }
           char* p = static_cast<char*>(gb_w.p);
           for (BoxRec<T>& R : recs) {
-            if (R.k + R.r > 128) continue;
+            if (R.k + R.r > ozp_nmax) continue;
             const size_t b = ((size_t)(R.k + R.r) * R.r * sizeof(T) + 255) & ~size_t(255);
             R.We = reinterpret_cast<T*>(p);
             R.Wf = reinterpret_cast<T*>(p + b);
@@ -2575,6 +2778,14 @@ rss_status factor_impl(const rss_tree* tree, const rss_params* prm, cudaStream_t
           const int smem = (64 + OZ_NCH) * (OZ_S * ozp_np + 8) * (int)sizeof(uint16_t);
           RSS_CUDA(cudaFuncSetAttribute(k_elim_oz, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
           k_elim_oz<<<dim3((max_c + 63) / 64, nrec), NT, smem, st>>>(ea);
+          RSS_LAUNCHED();
+          f->launches += 1;
+        }
+      } else {
+        if (ozp_np > 0) {
+          const int smem = (ZCM + ZCN) * ZSA * (int)sizeof(uint16_t);
+          RSS_CUDA(cudaFuncSetAttribute(k_elim_ozc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+          k_elim_ozc<<<dim3((max_c + ZCM - 1) / ZCM, nrec), NT, smem, st>>>(ea);
           RSS_LAUNCHED();
           f->launches += 1;
         }
