@@ -81,9 +81,10 @@ typedef struct {
                                      stack [A_MB; K_PB; A_BM^*; K_BP^*] */
   int schur_path;                 /* 0: the dense products of the elimination on the tensor
                                      cores where they apply: the Schur update A_CC -= E F
-                                     (real factors with r <= 96, complex with r <= 64) and,
-                                     for real factors with n_B <= 128, E = A_CB W_E and
-                                     F^T = A_BC^T W_F; operands split into eight 7-bit
+                                     (real factors with r <= 96, complex with any r) and
+                                     E = A_CB W_E and
+                                     F^T = A_BC^T W_F (real factors with n_B <= 128,
+                                     complex with any n_B); operands split into eight 7-bit
                                      slices with row and column scales, exact integer
                                      products, FP64 recombination (accuracy of an FP64
                                      product); 1: FP64 FMA kernels everywhere */

@@ -1913,7 +1913,10 @@ __global__ void __launch_bounds__(NT) k_schur_oz(LevelDev<double> L, const BoxRe
 // Complex factors: Re(E F) = Er Fr^T - Ei Fi^T and Im(E F) = Er Fi^T + Ei Fr^T
 // (F^T rows split as Fr, Fi), each group sum exact as in the real case; the
 // sign of -Ei is flipped on the bf16 fragment bits.  64 x 32 tile per CTA,
-// 8 warps of 16 x 16.
+// 8 warps of 16 x 16; K (the slices' length kp) in chunks of 32.  Row and
+// column scales are fixed per row, so the int64 sums of the chunks add exactly
+// (|W| <= kp 2^53).
+constexpr int SCK = 32, SCSA = 2 * OZ_S * SCK + 8;
 
 __global__ void __launch_bounds__(NT) k_schur_oz_c(LevelDev<zd> L, const BoxRec<zd>* recs) {
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -1922,7 +1925,7 @@ __global__ void __launch_bounds__(NT) k_schur_oz_c(LevelDev<zd> L, const BoxRec<
   const int ntr = (c + 63) / 64, ntc = (c + 31) / 32;
   if ((int)blockIdx.x >= ntr * ntc) return;
   const int i0 = (blockIdx.x % ntr) * 64, j0 = (blockIdx.x / ntr) * 32;
-  const int SA = 2 * OZ_S * kp + 8;             // row: 8 real then 8 imaginary slices
+  const int SA = SCSA;                          // row: 8 real then 8 imaginary slices of one chunk
   uint16_t* As = reinterpret_cast<uint16_t*>(smraw);
   uint16_t* Bs = As + 64 * SA;
   __shared__ long long rowb[64], colb[32];
@@ -1930,20 +1933,6 @@ __global__ void __launch_bounds__(NT) k_schur_oz_c(LevelDev<zd> L, const BoxRec<
   const int nmax = L.nmax, g = L.g;
   const long long nn = (long long)nmax * nmax;
   const int tid = threadIdx.x;
-  const int chunks = 2 * kp;                    // 16-byte chunks per row
-  for (int e = tid; e < 64 * chunks; e += NT) {
-    const int row = e / chunks, ch = e % chunks;
-    uint16_t* da = As + row * SA + ch * 8;
-    if (i0 + row < c) cp_async16(da, R.Esl + (size_t)(i0 + row) * 2 * OZ_S * kp + ch * 8);
-    else *reinterpret_cast<uint4*>(da) = make_uint4(0, 0, 0, 0);
-  }
-  for (int e = tid; e < 32 * chunks; e += NT) {
-    const int row = e / chunks, ch = e % chunks;
-    uint16_t* db = Bs + row * SA + ch * 8;
-    if (j0 + row < c) cp_async16(db, R.Fsl + (size_t)(j0 + row) * 2 * OZ_S * kp + ch * 8);
-    else *reinterpret_cast<uint4*>(db) = make_uint4(0, 0, 0, 0);
-  }
-  cp_async_wait_all();
   if (tid < 64) {
     const int i = i0 + tid;
     if (i < c) {
@@ -1960,7 +1949,6 @@ __global__ void __launch_bounds__(NT) k_schur_oz_c(LevelDev<zd> L, const BoxRec<
       cexp[tid - 64] = R.Fexp[j];
     }
   }
-  __syncthreads();
   const int warp = tid >> 5, lane = tid & 31, gq = lane >> 2, t4 = lane & 3;
   const int m0 = (warp >> 1) * 16, n0 = (warp & 1) * 16;
   const int a_row = lane & 15, a_k = (lane >> 4) * 8;
@@ -1970,49 +1958,66 @@ __global__ void __launch_bounds__(NT) k_schur_oz_c(LevelDev<zd> L, const BoxRec<
   for (int ni = 0; ni < 2; ++ni)
 #pragma unroll
     for (int e = 0; e < 4; ++e) { Wr[ni][e] = 0; Wi[ni][e] = 0; }
-  for (int u = 0; u < OZ_S; ++u) {
-    float cr[2][4], ci[2][4];
-#pragma unroll
-    for (int ni = 0; ni < 2; ++ni)
-#pragma unroll
-      for (int e = 0; e < 4; ++e) { cr[ni][e] = 0.f; ci[ni][e] = 0.f; }
-    for (int p = 0; p <= u; ++p) {
-      const uint16_t* Ar = As + p * kp;
-      const uint16_t* Ai = As + (OZ_S + p) * kp;
-      const uint16_t* Br = Bs + (u - p) * kp;
-      const uint16_t* Bi = Bs + (OZ_S + u - p) * kp;
-      for (int kk = 0; kk < kp; kk += 16) {
-        uint32_t ar[4], ai[4], br[4], bi[4];
-        ldsm_x4(ar, Ar + (m0 + a_row) * SA + kk + a_k);
-        ldsm_x4(ai, Ai + (m0 + a_row) * SA + kk + a_k);
-        ldsm_x4(br, Br + (n0 + b_row) * SA + kk + b_k);
-        ldsm_x4(bi, Bi + (n0 + b_row) * SA + kk + b_k);
-#pragma unroll
-        for (int ni = 0; ni < 2; ++ni) {
-          mma_bf16(cr[ni], ar, br + 2 * ni);
-          mma_bf16(ci[ni], ar, bi + 2 * ni);
-          mma_bf16(ci[ni], ai, br + 2 * ni);
-        }
-        neg_bf16x2(ai);
-#pragma unroll
-        for (int ni = 0; ni < 2; ++ni) mma_bf16(cr[ni], ai, bi + 2 * ni);
-      }
+  for (int kc = 0; kc < kp; kc += SCK) {
+    const int kl = min(SCK, kp - kc), cpr = 2 * OZ_S * (kl / 8);   // 16-byte chunks per row
+    __syncthreads();
+    for (int e = tid; e < 96 * cpr; e += NT) {
+      const int row = e / cpr, rem = e % cpr, sl = rem / (kl / 8), ch = rem % (kl / 8);
+      const bool isA = row < 64;
+      const int rr = isA ? row : row - 64;
+      uint16_t* d = (isA ? As : Bs) + rr * SA + sl * SCK + ch * 8;
+      const int gi = (isA ? i0 : j0) + rr;
+      if (gi < c)
+        cp_async16(d, (isA ? R.Esl : R.Fsl) + (size_t)gi * 2 * OZ_S * kp + (size_t)sl * kp + kc + ch * 8);
+      else
+        *reinterpret_cast<uint4*>(d) = make_uint4(0, 0, 0, 0);
     }
-    const int sh = 39 - OZ_BITS * u;
+    cp_async_wait_all();
+    __syncthreads();
+    for (int u = 0; u < OZ_S; ++u) {
+      float cr[2][4], ci[2][4];
 #pragma unroll
-    for (int ni = 0; ni < 2; ++ni)
+      for (int ni = 0; ni < 2; ++ni)
 #pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const long long gr = (long long)__float2int_rn(cr[ni][e]);
-        const long long gi = (long long)__float2int_rn(ci[ni][e]);
-        if (sh >= 0) {
-          Wr[ni][e] += gr << sh;
-          Wi[ni][e] += gi << sh;
-        } else {
-          Wr[ni][e] += (gr + (1LL << (-sh - 1))) >> (-sh);
-          Wi[ni][e] += (gi + (1LL << (-sh - 1))) >> (-sh);
+        for (int e = 0; e < 4; ++e) { cr[ni][e] = 0.f; ci[ni][e] = 0.f; }
+      for (int p = 0; p <= u; ++p) {
+        const uint16_t* Ar = As + p * SCK;
+        const uint16_t* Ai = As + (OZ_S + p) * SCK;
+        const uint16_t* Br = Bs + (u - p) * SCK;
+        const uint16_t* Bi = Bs + (OZ_S + u - p) * SCK;
+        for (int kk = 0; kk < kl; kk += 16) {
+          uint32_t ar[4], ai[4], br[4], bi[4];
+          ldsm_x4(ar, Ar + (m0 + a_row) * SA + kk + a_k);
+          ldsm_x4(ai, Ai + (m0 + a_row) * SA + kk + a_k);
+          ldsm_x4(br, Br + (n0 + b_row) * SA + kk + b_k);
+          ldsm_x4(bi, Bi + (n0 + b_row) * SA + kk + b_k);
+#pragma unroll
+          for (int ni = 0; ni < 2; ++ni) {
+            mma_bf16(cr[ni], ar, br + 2 * ni);
+            mma_bf16(ci[ni], ar, bi + 2 * ni);
+            mma_bf16(ci[ni], ai, br + 2 * ni);
+          }
+          neg_bf16x2(ai);
+#pragma unroll
+          for (int ni = 0; ni < 2; ++ni) mma_bf16(cr[ni], ai, bi + 2 * ni);
         }
       }
+      const int sh = 39 - OZ_BITS * u;
+#pragma unroll
+      for (int ni = 0; ni < 2; ++ni)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const long long gr = (long long)__float2int_rn(cr[ni][e]);
+          const long long gi = (long long)__float2int_rn(ci[ni][e]);
+          if (sh >= 0) {
+            Wr[ni][e] += gr << sh;
+            Wi[ni][e] += gi << sh;
+          } else {
+            Wr[ni][e] += (gr + (1LL << (-sh - 1))) >> (-sh);
+            Wi[ni][e] += (gi + (1LL << (-sh - 1))) >> (-sh);
+          }
+        }
+    }
   }
 #pragma unroll
   for (int ni = 0; ni < 2; ++ni)
@@ -2695,8 +2700,9 @@ rss_status factor_impl(const rss_tree* tree, const rss_params* prm, cudaStream_t
       for (const BoxRec<T>& R : recs)
         if (R.panels && !R.ozp) pan_max = std::max(pan_max, panel_smem_bytes<T>(pan_ma, R.k + R.r, R.r));
       // tensor-core Schur update: real factors with r <= 96 (the slices of a
-      // 64-row tile of E and of F^T must fit in shared memory)
-      const bool oz = prm->schur_path == 0 && max_r <= (sizeof(T) == sizeof(double) ? 96 : 64);
+      // 64-row tile of E and of F^T must fit in shared memory), complex factors
+      // with any r (K taken in chunks)
+      const bool oz = prm->schur_path == 0 && (sizeof(T) != sizeof(double) || max_r <= 96);
       const int ns = sizeof(T) == sizeof(double) ? OZ_S : 2 * OZ_S;   // slices per row
       int kp_max = 0;
       if (oz) {
@@ -2800,7 +2806,7 @@ rss_status factor_impl(const rss_tree* tree, const rss_params* prm, cudaStream_t
           RSS_CUDA(cudaFuncSetAttribute(k_schur_oz, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
           k_schur_oz<<<dim3(ntile * ntile, nrec), NT, smem, st>>>(cur.d, d_recs);
         } else {
-          const size_t smem = (64 + 32) * (size_t)(2 * OZ_S * kp_max + 8) * sizeof(uint16_t);
+          const size_t smem = (64 + 32) * (size_t)SCSA * sizeof(uint16_t);
           RSS_CUDA(cudaFuncSetAttribute(k_schur_oz_c, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
           const int ntc = (max_c + 31) / 32;
           k_schur_oz_c<<<dim3(ntile * ntc, nrec), NT, smem, st>>>(cur.d, d_recs);
