@@ -81,7 +81,7 @@ typedef struct {
                                      stack [A_MB; K_PB; A_BM^*; K_BP^*] */
   int schur_path;                 /* 0: the dense products of the elimination on the tensor
                                      cores where they apply: the Schur update A_CC -= E F
-                                     (real factors with r <= 96, complex with any r) and
+                                     (any rank) and
                                      E = A_CB W_E and
                                      F^T = A_BC^T W_F (real factors with n_B <= 128,
                                      complex with any n_B); operands split into eight 7-bit

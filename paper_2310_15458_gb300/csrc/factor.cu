@@ -1805,14 +1805,18 @@ template <typename T> __global__ void __launch_bounds__(NT) k_schur(LevelDev<T> 
 // The groups are gathered in one int64 W = sum_u G_u 2^(39-7u) (the last two by
 // rounding right shifts, an error below 2^-53 of the scale), so
 // (E F)_ij = W 2^(e_i + f_j - 53): one conversion and one scaling per entry.
-// 64 x 64 tile per CTA, 8 warps of 32 x 16, fragments loaded with ldmatrix.
+// 64 x 64 tile per CTA, 8 warps of 32 x 16, fragments loaded with ldmatrix; K
+// (the slices' length kp) in chunks of 32 whose int64 sums add exactly under the
+// per-row scales (|W| <= kp 2^53).
+constexpr int SRK = 32, SRSA = OZ_S * SRK + 8;   // real Schur: K chunk and slice-row stride
+
 __global__ void __launch_bounds__(NT) k_schur_oz(LevelDev<double> L, const BoxRec<double>* recs) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const BoxRec<double> R = recs[blockIdx.y];
   const int c = R.c, kp = R.kp, nt = (c + 63) / 64;
   if ((int)blockIdx.x >= nt * nt) return;
   const int i0 = (blockIdx.x % nt) * 64, j0 = (blockIdx.x / nt) * 64;
-  const int SA = OZ_S * kp + 8;                 // smem row stride in bf16 elements (16-byte rows)
+  const int SA = SRSA;                          // one K chunk of the eight slices per row
   uint16_t* As = reinterpret_cast<uint16_t*>(smraw);
   uint16_t* Bs = As + 64 * SA;
   __shared__ long long rowb[64], colb[64];
@@ -1820,16 +1824,6 @@ __global__ void __launch_bounds__(NT) k_schur_oz(LevelDev<double> L, const BoxRe
   const int nmax = L.nmax, g = L.g;
   const long long nn = (long long)nmax * nmax;
   const int tid = threadIdx.x;
-  for (int e = tid; e < 64 * kp; e += NT) {     // kp 16-byte chunks per row (OZ_S * 2 = 16)
-    const int row = e / kp, ch = e % kp;
-    uint16_t* da = As + row * SA + ch * 8;
-    uint16_t* db = Bs + row * SA + ch * 8;
-    if (i0 + row < c) cp_async16(da, R.Esl + (size_t)(i0 + row) * OZ_S * kp + ch * 8);
-    else *reinterpret_cast<uint4*>(da) = make_uint4(0, 0, 0, 0);
-    if (j0 + row < c) cp_async16(db, R.Fsl + (size_t)(j0 + row) * OZ_S * kp + ch * 8);
-    else *reinterpret_cast<uint4*>(db) = make_uint4(0, 0, 0, 0);
-  }
-  cp_async_wait_all();
   if (tid < 64) {
     const int i = i0 + tid;
     if (i < c) {
@@ -1846,7 +1840,6 @@ __global__ void __launch_bounds__(NT) k_schur_oz(LevelDev<double> L, const BoxRe
       cexp[tid - 64] = R.Fexp[j];
     }
   }
-  __syncthreads();
   const int warp = tid >> 5, lane = tid & 31, gq = lane >> 2, t4 = lane & 3;
   const int m0 = (warp >> 2) * 32, n0 = (warp & 3) * 16;
   // ldmatrix row addresses: A tiles (rows m0 + mi*16 + lane%16, k + 8*(lane/16)),
@@ -1860,39 +1853,56 @@ __global__ void __launch_bounds__(NT) k_schur_oz(LevelDev<double> L, const BoxRe
     for (int ni = 0; ni < 2; ++ni)
 #pragma unroll
       for (int e = 0; e < 4; ++e) W[mi][ni][e] = 0;
-  for (int u = 0; u < OZ_S; ++u) {
-    float cf[2][2][4];
+  for (int kc = 0; kc < kp; kc += SRK) {
+    const int kl = min(SRK, kp - kc), cpr = OZ_S * (kl / 8);   // 16-byte chunks per row
+    __syncthreads();
+    for (int e = tid; e < 128 * cpr; e += NT) {
+      const int row = e / cpr, rem = e % cpr, sl = rem / (kl / 8), ch = rem % (kl / 8);
+      const bool isA = row < 64;
+      const int rr = isA ? row : row - 64;
+      uint16_t* d = (isA ? As : Bs) + rr * SA + sl * SRK + ch * 8;
+      const int gi = (isA ? i0 : j0) + rr;
+      if (gi < c)
+        cp_async16(d, (isA ? R.Esl : R.Fsl) + (size_t)gi * OZ_S * kp + (size_t)sl * kp + kc + ch * 8);
+      else
+        *reinterpret_cast<uint4*>(d) = make_uint4(0, 0, 0, 0);
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    for (int u = 0; u < OZ_S; ++u) {
+      float cf[2][2][4];
 #pragma unroll
-    for (int mi = 0; mi < 2; ++mi)
+      for (int mi = 0; mi < 2; ++mi)
 #pragma unroll
-      for (int ni = 0; ni < 2; ++ni)
+        for (int ni = 0; ni < 2; ++ni)
 #pragma unroll
-        for (int e = 0; e < 4; ++e) cf[mi][ni][e] = 0.f;
-    for (int p = 0; p <= u; ++p) {
-      const uint16_t* Ab = As + p * kp;
-      const uint16_t* Bb = Bs + (u - p) * kp;
-      for (int kk = 0; kk < kp; kk += 16) {
-        uint32_t af[2][4], bq[4];
+          for (int e = 0; e < 4; ++e) cf[mi][ni][e] = 0.f;
+      for (int p = 0; p <= u; ++p) {
+        const uint16_t* Ab = As + p * SRK;
+        const uint16_t* Bb = Bs + (u - p) * SRK;
+        for (int kk = 0; kk < kl; kk += 16) {
+          uint32_t af[2][4], bq[4];
 #pragma unroll
-        for (int mi = 0; mi < 2; ++mi) ldsm_x4(af[mi], Ab + (m0 + mi * 16 + a_row) * SA + kk + a_k);
-        ldsm_x4(bq, Bb + (n0 + b_row) * SA + kk + b_k);
+          for (int mi = 0; mi < 2; ++mi) ldsm_x4(af[mi], Ab + (m0 + mi * 16 + a_row) * SA + kk + a_k);
+          ldsm_x4(bq, Bb + (n0 + b_row) * SA + kk + b_k);
 #pragma unroll
-        for (int mi = 0; mi < 2; ++mi) {
-          mma_bf16(cf[mi][0], af[mi], bq);
-          mma_bf16(cf[mi][1], af[mi], bq + 2);
+          for (int mi = 0; mi < 2; ++mi) {
+            mma_bf16(cf[mi][0], af[mi], bq);
+            mma_bf16(cf[mi][1], af[mi], bq + 2);
+          }
         }
       }
+      const int sh = 39 - OZ_BITS * u;
+#pragma unroll
+      for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+        for (int ni = 0; ni < 2; ++ni)
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const long long gv = (long long)__float2int_rn(cf[mi][ni][e]);
+            W[mi][ni][e] += sh >= 0 ? (gv << sh) : ((gv + (1LL << (-sh - 1))) >> (-sh));
+          }
     }
-    const int sh = 39 - OZ_BITS * u;
-#pragma unroll
-    for (int mi = 0; mi < 2; ++mi)
-#pragma unroll
-      for (int ni = 0; ni < 2; ++ni)
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          const long long gv = (long long)__float2int_rn(cf[mi][ni][e]);
-          W[mi][ni][e] += sh >= 0 ? (gv << sh) : ((gv + (1LL << (-sh - 1))) >> (-sh));
-        }
   }
 #pragma unroll
   for (int mi = 0; mi < 2; ++mi)
@@ -2699,10 +2709,8 @@ rss_status factor_impl(const rss_tree* tree, const rss_params* prm, cudaStream_t
       }
       for (const BoxRec<T>& R : recs)
         if (R.panels && !R.ozp) pan_max = std::max(pan_max, panel_smem_bytes<T>(pan_ma, R.k + R.r, R.r));
-      // tensor-core Schur update: real factors with r <= 96 (the slices of a
-      // 64-row tile of E and of F^T must fit in shared memory), complex factors
-      // with any r (K taken in chunks)
-      const bool oz = prm->schur_path == 0 && (sizeof(T) != sizeof(double) || max_r <= 96);
+      // tensor-core Schur update for any r (K taken in chunks of 32)
+      const bool oz = prm->schur_path == 0;
       const int ns = sizeof(T) == sizeof(double) ? OZ_S : 2 * OZ_S;   // slices per row
       int kp_max = 0;
       if (oz) {
@@ -2802,7 +2810,7 @@ rss_status factor_impl(const rss_tree* tree, const rss_params* prm, cudaStream_t
       evs.back().second->start(st);
       if (oz) {
         if constexpr (sizeof(T) == sizeof(double)) {
-          const size_t smem = 2 * 64 * (size_t)(OZ_S * kp_max + 8) * sizeof(uint16_t);
+          const size_t smem = 2 * 64 * (size_t)SRSA * sizeof(uint16_t);
           RSS_CUDA(cudaFuncSetAttribute(k_schur_oz, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
           k_schur_oz<<<dim3(ntile * ntile, nrec), NT, smem, st>>>(cur.d, d_recs);
         } else {
