@@ -171,6 +171,12 @@ __device__ __forceinline__ void oz_digits2(long long X0, long long X1, uint32_t*
 #pragma unroll
   for (int p = 0; p < 8; ++p) out[p] = oz_bf16_int(d0[p]) | (oz_bf16_int(d1[p]) << 16);
 }
+// An FP32 value holding an integer |g| < 2^22 as an int32, by adding 1.5 2^23 and
+// reading the mantissa (one FP32 add and one integer add)
+__device__ __forceinline__ int oz_fint(float g) {
+  return __float_as_int(g + 12582912.0f) - 0x4B400000;
+}
+
 // W 2^s as a double, W an exact integer (|W| < 2^63): one conversion, the
 // power of two added to the exponent field when the result stays normal
 __device__ __forceinline__ double oz_ldexp_int(long long W, int s) {

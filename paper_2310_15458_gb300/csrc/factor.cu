@@ -1810,7 +1810,7 @@ template <typename T> __global__ void __launch_bounds__(NT) k_schur(LevelDev<T> 
 // per-row scales (|W| <= kp 2^53).
 constexpr int SRK = 32, SRSA = OZ_S * SRK + 8;   // real Schur: K chunk and slice-row stride
 
-__global__ void __launch_bounds__(NT) k_schur_oz(LevelDev<double> L, const BoxRec<double>* recs) {
+__global__ void __launch_bounds__(NT, 3) k_schur_oz(LevelDev<double> L, const BoxRec<double>* recs) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const BoxRec<double> R = recs[blockIdx.y];
   const int c = R.c, kp = R.kp, nt = (c + 63) / 64;
@@ -1869,37 +1869,50 @@ __global__ void __launch_bounds__(NT) k_schur_oz(LevelDev<double> L, const BoxRe
     }
     cp_async_wait_all();
     __syncthreads();
-    for (int u = 0; u < OZ_S; ++u) {
-      float cf[2][2][4];
+    // groups u and u + 1 together: G_u 2^(39-7u) + G_{u+1} 2^(32-7u) =
+    // (G_u 2^7 + G_{u+1}) 2^(32-7u), the bracket exact in int32 (|G| < 2^21)
+#pragma unroll 1
+    for (int u = 0; u < OZ_S; u += 2) {
+      float ca[2][2][4], cb[2][2][4];
 #pragma unroll
       for (int mi = 0; mi < 2; ++mi)
 #pragma unroll
         for (int ni = 0; ni < 2; ++ni)
 #pragma unroll
-          for (int e = 0; e < 4; ++e) cf[mi][ni][e] = 0.f;
-      for (int p = 0; p <= u; ++p) {
+          for (int e = 0; e < 4; ++e) ca[mi][ni][e] = cb[mi][ni][e] = 0.f;
+      for (int p = 0; p <= u + 1; ++p) {
         const uint16_t* Ab = As + p * SRK;
-        const uint16_t* Bb = Bs + (u - p) * SRK;
+        const uint16_t* Bb1 = Bs + (u + 1 - p) * SRK;
+        const uint16_t* Bb0 = Bs + (u - p) * SRK;
         for (int kk = 0; kk < kl; kk += 16) {
-          uint32_t af[2][4], bq[4];
+          uint32_t af[2][4], b1[4];
 #pragma unroll
           for (int mi = 0; mi < 2; ++mi) ldsm_x4(af[mi], Ab + (m0 + mi * 16 + a_row) * SA + kk + a_k);
-          ldsm_x4(bq, Bb + (n0 + b_row) * SA + kk + b_k);
+          ldsm_x4(b1, Bb1 + (n0 + b_row) * SA + kk + b_k);
 #pragma unroll
           for (int mi = 0; mi < 2; ++mi) {
-            mma_bf16(cf[mi][0], af[mi], bq);
-            mma_bf16(cf[mi][1], af[mi], bq + 2);
+            mma_bf16(cb[mi][0], af[mi], b1);
+            mma_bf16(cb[mi][1], af[mi], b1 + 2);
+          }
+          if (p <= u) {
+            uint32_t b0[4];
+            ldsm_x4(b0, Bb0 + (n0 + b_row) * SA + kk + b_k);
+#pragma unroll
+            for (int mi = 0; mi < 2; ++mi) {
+              mma_bf16(ca[mi][0], af[mi], b0);
+              mma_bf16(ca[mi][1], af[mi], b0 + 2);
+            }
           }
         }
       }
-      const int sh = 39 - OZ_BITS * u;
+      const int sh = 32 - OZ_BITS * u;
 #pragma unroll
       for (int mi = 0; mi < 2; ++mi)
 #pragma unroll
         for (int ni = 0; ni < 2; ++ni)
 #pragma unroll
           for (int e = 0; e < 4; ++e) {
-            const long long gv = (long long)__float2int_rn(cf[mi][ni][e]);
+            const long long gv = (long long)(oz_fint(ca[mi][ni][e]) * 128 + oz_fint(cb[mi][ni][e]));
             W[mi][ni][e] += sh >= 0 ? (gv << sh) : ((gv + (1LL << (-sh - 1))) >> (-sh));
           }
     }
