@@ -1613,41 +1613,51 @@ __device__ void tc_gemm_c(int M, int K, AF aval, BF bval, OF cout, uint16_t* As,
 #pragma unroll
         for (int e = 0; e < 4; ++e) Wr[ni][e] = Wi[ni][e] = 0;
 #pragma unroll 1
-      for (int u = 0; u < 8; ++u) {
-        float cr[2][4], ci[2][4];
+      for (int u = 0; u < 8; u += 2) {   // groups u, u + 1 together (|G| < 2^22)
+        float cr0[2][4], ci0[2][4], cr1[2][4], ci1[2][4];
 #pragma unroll
         for (int ni = 0; ni < 2; ++ni)
 #pragma unroll
-          for (int e = 0; e < 4; ++e) cr[ni][e] = ci[ni][e] = 0.f;
-        for (int p = 0; p <= u; ++p) {
+          for (int e = 0; e < 4; ++e) cr0[ni][e] = ci0[ni][e] = cr1[ni][e] = ci1[ni][e] = 0.f;
+        for (int p = 0; p <= u + 1; ++p) {
           const uint16_t* Ar = As + p * ZCK + (m0 + a_row) * ZSA + a_k;
           const uint16_t* Ai = As + (8 + p) * ZCK + (m0 + a_row) * ZSA + a_k;
-          const uint16_t* Br = Bs + (u - p) * ZCK + (n0 + b_row) * ZSA + b_k;
-          const uint16_t* Bi = Bs + (8 + u - p) * ZCK + (n0 + b_row) * ZSA + b_k;
 #pragma unroll
           for (int kk = 0; kk < ZCK; kk += 16) {
-            uint32_t ar[4], ai[4], br[4], bi[4];
+            uint32_t ar[4], ai[4], ain[4], br[4], bi[4];
             ldsm_x4(ar, Ar + kk);
             ldsm_x4(ai, Ai + kk);
-            ldsm_x4(br, Br + kk);
-            ldsm_x4(bi, Bi + kk);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) ain[i] = ai[i] ^ 0x80008000u;
+            ldsm_x4(br, Bs + (u + 1 - p) * ZCK + (n0 + b_row) * ZSA + b_k + kk);
+            ldsm_x4(bi, Bs + (8 + u + 1 - p) * ZCK + (n0 + b_row) * ZSA + b_k + kk);
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
-              mma_bf16(cr[h], ar, br + 2 * h);
-              mma_bf16(ci[h], ar, bi + 2 * h);
-              mma_bf16(ci[h], ai, br + 2 * h);
+              mma_bf16(cr1[h], ar, br + 2 * h);
+              mma_bf16(cr1[h], ain, bi + 2 * h);
+              mma_bf16(ci1[h], ar, bi + 2 * h);
+              mma_bf16(ci1[h], ai, br + 2 * h);
             }
-            neg_bf16x2(ai);
+            if (p <= u) {
+              ldsm_x4(br, Bs + (u - p) * ZCK + (n0 + b_row) * ZSA + b_k + kk);
+              ldsm_x4(bi, Bs + (8 + u - p) * ZCK + (n0 + b_row) * ZSA + b_k + kk);
 #pragma unroll
-            for (int h = 0; h < 2; ++h) mma_bf16(cr[h], ai, bi + 2 * h);
+              for (int h = 0; h < 2; ++h) {
+                mma_bf16(cr0[h], ar, br + 2 * h);
+                mma_bf16(cr0[h], ain, bi + 2 * h);
+                mma_bf16(ci0[h], ar, bi + 2 * h);
+                mma_bf16(ci0[h], ai, br + 2 * h);
+              }
+            }
           }
         }
-        const int sh = 39 - 7 * u;
+        const int sh = 32 - 7 * u;
 #pragma unroll
         for (int ni = 0; ni < 2; ++ni)
 #pragma unroll
           for (int e = 0; e < 4; ++e) {
-            const long long gr = (long long)__float2int_rn(cr[ni][e]), gi = (long long)__float2int_rn(ci[ni][e]);
+            const long long gr = (long long)(oz_fint(cr0[ni][e]) * 128 + oz_fint(cr1[ni][e]));
+            const long long gi = (long long)(oz_fint(ci0[ni][e]) * 128 + oz_fint(ci1[ni][e]));
             Wr[ni][e] += sh >= 0 ? (gr << sh) : ((gr + (1LL << (-sh - 1))) >> (-sh));
             Wi[ni][e] += sh >= 0 ? (gi << sh) : ((gi + (1LL << (-sh - 1))) >> (-sh));
           }
@@ -1997,41 +2007,52 @@ __global__ void __launch_bounds__(NT) k_schur_oz_c(LevelDev<zd> L, const BoxRec<
     }
     cp_async_wait_all();
     __syncthreads();
-    for (int u = 0; u < OZ_S; ++u) {
-      float cr[2][4], ci[2][4];
+    // groups u and u + 1 together, combined exactly in int32 (|G| < 2^22)
+#pragma unroll 1
+    for (int u = 0; u < OZ_S; u += 2) {
+      float cr0[2][4], ci0[2][4], cr1[2][4], ci1[2][4];
 #pragma unroll
       for (int ni = 0; ni < 2; ++ni)
 #pragma unroll
-        for (int e = 0; e < 4; ++e) { cr[ni][e] = 0.f; ci[ni][e] = 0.f; }
-      for (int p = 0; p <= u; ++p) {
+        for (int e = 0; e < 4; ++e) cr0[ni][e] = ci0[ni][e] = cr1[ni][e] = ci1[ni][e] = 0.f;
+      for (int p = 0; p <= u + 1; ++p) {
         const uint16_t* Ar = As + p * SCK;
         const uint16_t* Ai = As + (OZ_S + p) * SCK;
-        const uint16_t* Br = Bs + (u - p) * SCK;
-        const uint16_t* Bi = Bs + (OZ_S + u - p) * SCK;
         for (int kk = 0; kk < kl; kk += 16) {
-          uint32_t ar[4], ai[4], br[4], bi[4];
+          uint32_t ar[4], ai[4], ain[4], br[4], bi[4];
           ldsm_x4(ar, Ar + (m0 + a_row) * SA + kk + a_k);
           ldsm_x4(ai, Ai + (m0 + a_row) * SA + kk + a_k);
-          ldsm_x4(br, Br + (n0 + b_row) * SA + kk + b_k);
-          ldsm_x4(bi, Bi + (n0 + b_row) * SA + kk + b_k);
+#pragma unroll
+          for (int i = 0; i < 4; ++i) ain[i] = ai[i] ^ 0x80008000u;
+          ldsm_x4(br, Bs + (u + 1 - p) * SCK + (n0 + b_row) * SA + kk + b_k);
+          ldsm_x4(bi, Bs + (OZ_S + u + 1 - p) * SCK + (n0 + b_row) * SA + kk + b_k);
 #pragma unroll
           for (int ni = 0; ni < 2; ++ni) {
-            mma_bf16(cr[ni], ar, br + 2 * ni);
-            mma_bf16(ci[ni], ar, bi + 2 * ni);
-            mma_bf16(ci[ni], ai, br + 2 * ni);
+            mma_bf16(cr1[ni], ar, br + 2 * ni);
+            mma_bf16(cr1[ni], ain, bi + 2 * ni);
+            mma_bf16(ci1[ni], ar, bi + 2 * ni);
+            mma_bf16(ci1[ni], ai, br + 2 * ni);
           }
-          neg_bf16x2(ai);
+          if (p <= u) {
+            ldsm_x4(br, Bs + (u - p) * SCK + (n0 + b_row) * SA + kk + b_k);
+            ldsm_x4(bi, Bs + (OZ_S + u - p) * SCK + (n0 + b_row) * SA + kk + b_k);
 #pragma unroll
-          for (int ni = 0; ni < 2; ++ni) mma_bf16(cr[ni], ai, bi + 2 * ni);
+            for (int ni = 0; ni < 2; ++ni) {
+              mma_bf16(cr0[ni], ar, br + 2 * ni);
+              mma_bf16(cr0[ni], ain, bi + 2 * ni);
+              mma_bf16(ci0[ni], ar, bi + 2 * ni);
+              mma_bf16(ci0[ni], ai, br + 2 * ni);
+            }
+          }
         }
       }
-      const int sh = 39 - OZ_BITS * u;
+      const int sh = 32 - OZ_BITS * u;
 #pragma unroll
       for (int ni = 0; ni < 2; ++ni)
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
-          const long long gr = (long long)__float2int_rn(cr[ni][e]);
-          const long long gi = (long long)__float2int_rn(ci[ni][e]);
+          const long long gr = (long long)(oz_fint(cr0[ni][e]) * 128 + oz_fint(cr1[ni][e]));
+          const long long gi = (long long)(oz_fint(ci0[ni][e]) * 128 + oz_fint(ci1[ni][e]));
           if (sh >= 0) {
             Wr[ni][e] += gr << sh;
             Wi[ni][e] += gi << sh;

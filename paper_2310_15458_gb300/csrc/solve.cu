@@ -341,30 +341,34 @@ __device__ void tc_gemm32(int M, int K, AF aval, BF bval, OF cout, uint16_t* As,
 #pragma unroll
         for (int e = 0; e < 4; ++e) W[ni][e] = 0;
 #pragma unroll 1
-      for (int u = 0; u < 8; ++u) {
-        float cf[2][4];
+      for (int u = 0; u < 8; u += 2) {   // groups u, u + 1 together (|G| < 2^22)
+        float c0[2][4], c1[2][4];
 #pragma unroll
         for (int ni = 0; ni < 2; ++ni)
 #pragma unroll
-          for (int e = 0; e < 4; ++e) cf[ni][e] = 0.f;
-        for (int p = 0; p <= u; ++p) {
+          for (int e = 0; e < 4; ++e) c0[ni][e] = c1[ni][e] = 0.f;
+        for (int p = 0; p <= u + 1; ++p) {
           const uint16_t* Ab = As + p * TCK + (m0 + a_row) * TSA + a_k;
-          const uint16_t* Bb = Bs + (u - p) * TCK + (n0 + b_row) * TSA + b_k;
 #pragma unroll
           for (int kk = 0; kk < TCK; kk += 16) {
             uint32_t af[4], bq[4];
             ldsm_x4(af, Ab + kk);
-            ldsm_x4(bq, Bb + kk);
-            mma_bf16(cf[0], af, bq);
-            mma_bf16(cf[1], af, bq + 2);
+            ldsm_x4(bq, Bs + (u + 1 - p) * TCK + (n0 + b_row) * TSA + b_k + kk);
+            mma_bf16(c1[0], af, bq);
+            mma_bf16(c1[1], af, bq + 2);
+            if (p <= u) {
+              ldsm_x4(bq, Bs + (u - p) * TCK + (n0 + b_row) * TSA + b_k + kk);
+              mma_bf16(c0[0], af, bq);
+              mma_bf16(c0[1], af, bq + 2);
+            }
           }
         }
-        const int sh = 39 - 7 * u;
+        const int sh = 32 - 7 * u;
 #pragma unroll
         for (int ni = 0; ni < 2; ++ni)
 #pragma unroll
           for (int e = 0; e < 4; ++e) {
-            const long long gv = (long long)__float2int_rn(cf[ni][e]);
+            const long long gv = (long long)(oz_fint(c0[ni][e]) * 128 + oz_fint(c1[ni][e]));
             W[ni][e] += sh >= 0 ? (gv << sh) : ((gv + (1LL << (-sh - 1))) >> (-sh));
           }
       }
