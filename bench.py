@@ -38,6 +38,7 @@ METRIC = "RS-S factor s and solve RHS/s at N=1M, rel.res<=1e-5; serve p50/p99 la
 # CTAs (1.195 TFLOP/s at a 1995 MHz SM clock); the fp64 mma.sync path measured
 # 1.05 TFLOP/s, so DFMA is the FP64 roof.
 FP64_PEAK_TFLOPS = 1.195
+TRAFFIC_PER_LAUNCH = {"id": 3.494e9, "elim": 3.125e8, "schur": 1.608e9}   # bytes, see the roofline below
 CPU_SAMPLE_SIDE = 128           # oracle sample: the same workload on a 128 x 128 grid
 
 
@@ -457,6 +458,10 @@ def native_arm(args, w):
     flops = info["flops"][dom]
     achieved = flops / (gms[dom] * 1e-3) / 1e12
     kern = {"id": "k_id", "elim": "k_elim", "schur": "k_schur"}[dom]
+    # DRAM bytes (read + write) per launch of each phase's kernels, from one ncu
+    # capture of this command (profiles/traffic_factor_laplace_1024x1024.md); only
+    # valid for the 1024 x 1024 Laplace workload and the kernels as captured
+    traffic = TRAFFIC_PER_LAUNCH.get(dom) if args.workload == WORKLOAD else None
     solve_launches = 2 + 2 * info["batches"] + 1
     line = {
         "metric": METRIC, "value": ms / 1e3, "unit": "s", "n_gpus": world, "steps": args.steps,
@@ -480,7 +485,7 @@ def native_arm(args, w):
                 "d2h_bytes_per_step": bh.nbytes},
         "gpu_launches": args.steps * (info["launches"] + solve_launches),
         "roofline": {"kernel": kern, "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-                     "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                     "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
                      "launches": launches, "avg_launch_ms": gms[dom] / max(launches, 1),
                      "peak_source": "FP64 DFMA loop measured on this GB300 (no FP64 figure in "
                                     "MEASURED_PEAKS.json)"},

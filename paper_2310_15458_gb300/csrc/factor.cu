@@ -2642,12 +2642,9 @@ rss_status factor_impl(const rss_tree* tree, const rss_params* prm, cudaStream_t
       RSS_CUDA(cudaStreamSynchronize(st));
       f->t_id += tid_.ms();
       const double cf = (sizeof(T) == sizeof(double) || split) ? 1.0 : 4.0;
-      for (int q = 0; q < nb; ++q) {   // CPQR: norms, per step v^H Y and the k-column corrections, T
+      for (int q = 0; q < nb; ++q) {   // k steps of Householder QR on the m x n stack
         const double m = mrows[q], n = cur.n[boxes[q]], k = hk[q];
-        double fl = 2.0 * m * n + k * k * (n - k);
-        for (int j = 0; j < hk[q]; ++j)
-          fl += 2.0 * (m - j) * (n - j - 1) + 4.0 * (m - j) * j + 4.0 * (n - j) * j;
-        f->f_id += cf * fl;
+        f->f_id += cf * (4.0 * m * n * k - 2.0 * k * k * (m + n) + 2.0 * k * k * k / 3.0);
       }
 
       // records for the boxes that have redundant points
