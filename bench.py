@@ -53,8 +53,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-paper", action="store_true")
-    ap.add_argument("--serve-requests", type=int, default=600)
-    ap.add_argument("--serve-load", type=float, default=0.9)
+    ap.add_argument("--serve-requests", type=int, default=600,
+                    help="requests per load, the first 100 warm-up (2100 is the full protocol)")
+    ap.add_argument("--serve-loads", type=float, nargs="+", default=[0.5, 0.9])
     return ap.parse_args()
 
 
@@ -261,18 +262,15 @@ def serve_run(P, torch, args):
     """Resident factorizations (Laplace 128^2, 256^2, 512^2 and Helmholtz kappa = 25 at
     256^2, eps 1e-6) behind the continuous-batching server; seeded Poisson arrivals of
     requests with 1-64 Gaussian right-hand sides on a uniformly drawn factorization, at
-    a load of serve_load times the solo capacity.  Latency = submit to result in host
-    memory."""
+    loads of 50 % and 90 % of the solo capacity; the first 100 requests of each run are
+    warm-up.  Latency = submit to result in host memory.  Beside it, the same requests
+    solved one after another (no batching) give the plain throughput."""
     import threading
     facs = []
     for kind, side, kappa in SERVE_SET:
         tree = P.rss_build_tree(W.grid_points(side), W.LEAF)
         facs.append(P.rss_factor(tree, kind=W.LAPLACE if kind == "laplace" else W.HELMHOLTZ,
                                  eps=1e-6, h=1.0 / side, kappa=kappa))
-    rng = np.random.default_rng(1003)
-    nreq = args.serve_requests
-    which = rng.integers(0, len(facs), nreq)
-    nrhs = rng.integers(1, 65, nreq)
     pool = {}
     for j, f in enumerate(facs):
         pool[j] = W.gaussian_rhs(f.n, 64, f.is_complex, 2000 + j)
@@ -286,46 +284,86 @@ def serve_run(P, torch, args):
             b = np.asfortranarray(pool[j][:, :32].copy())
             P.rss_solve(f, b)
         solo.append((time.perf_counter() - t0) / 3)
-    mean_service = float(np.mean(solo)) * (np.mean(nrhs) / 32.0)
-    rate = args.serve_load / mean_service
-    gaps = rng.exponential(1.0 / rate, nreq)
     srv = P.rss_server_create(8 << 30, 256)
     ids = [P.rss_server_add(srv, f) for f in facs]
-    tickets = [None] * nreq
-    lat = [0.0] * nreq
-    done = threading.Event()
-
-    def waiter():
-        for q in range(nreq):
-            while tickets[q] is None:
-                time.sleep(1e-5)
-            _, lat[q] = P.rss_server_wait(srv, tickets[q], timeout=120.0)
-        done.set()
-
-    th = threading.Thread(target=waiter)
-    th.start()
-    t_start = time.perf_counter()
-    t_next = t_start
-    for q in range(nreq):
-        t_next += gaps[q]
-        while time.perf_counter() < t_next:
-            pass
-        j = int(which[q])
-        b = np.asfortranarray(pool[j][:, :int(nrhs[q])])
-        tickets[q] = P.rss_server_submit(srv, ids[j], b)
-    done.wait()
-    t_total = time.perf_counter() - t_start
-    th.join()
-    st = P.rss_server_stats(srv)
+    nreq = args.serve_requests
     warm = min(100, nreq // 6)
-    l = np.array(lat[warm:]) * 1e3
+    runs = []
+    for li, load in enumerate(args.serve_loads):
+        rng = np.random.default_rng(1003 + li)
+        which = rng.integers(0, len(facs), nreq)
+        nrhs = rng.integers(1, 65, nreq)
+        mean_service = float(np.mean(solo)) * (np.mean(nrhs) / 32.0)
+        rate = load / mean_service
+        gaps = rng.exponential(1.0 / rate, nreq)
+        tickets = [None] * nreq
+        lat = [0.0] * nreq
+        done = threading.Event()
+
+        def waiter():
+            for q in range(nreq):
+                while tickets[q] is None:
+                    time.sleep(1e-5)
+                _, lat[q] = P.rss_server_wait(srv, tickets[q], timeout=120.0)
+            done.set()
+
+        th = threading.Thread(target=waiter)
+        th.start()
+        t_start = time.perf_counter()
+        t_next = t_start
+        for q in range(nreq):
+            t_next += gaps[q]
+            while time.perf_counter() < t_next:
+                pass
+            j = int(which[q])
+            b = np.asfortranarray(pool[j][:, :int(nrhs[q])])
+            tickets[q] = P.rss_server_submit(srv, ids[j], b)
+        done.wait()
+        t_total = time.perf_counter() - t_start
+        th.join()
+        l = np.array(lat[warm:]) * 1e3
+        runs.append({"load": load, "arrival_rate_per_s": rate, "p50_ms": float(np.percentile(l, 50)),
+                     "p99_ms": float(np.percentile(l, 99)), "mean_ms": float(l.mean()),
+                     "rhs_per_s": float(nrhs.sum() / t_total)})
+    st = P.rss_server_stats(srv)
+    # the plain form: the last run's requests one after another, each solved alone
+    t0 = time.perf_counter()
+    for q in range(warm, nreq):
+        j = int(which[q])
+        b = np.asfortranarray(pool[j][:, :int(nrhs[q])].copy())
+        P.rss_solve(facs[j], b)
+    plain = float(nrhs[warm:].sum() / (time.perf_counter() - t0))
     return {"workload": "Laplace 128^2, 256^2, 512^2 + Helmholtz k=25 256^2, eps 1e-6, 1-64 RHS",
-            "requests": nreq, "warmup_requests": warm, "load": args.serve_load,
-            "arrival_rate_per_s": rate, "p50_ms": float(np.percentile(l, 50)),
-            "p99_ms": float(np.percentile(l, 99)), "mean_ms": float(l.mean()),
-            "rhs_per_s": float(nrhs.sum() / t_total), "panels": st["batches"],
+            "requests_per_run": nreq, "warmup_requests": warm, "runs": runs,
+            "plain_sequential_rhs_per_s": plain, "panels": st["batches"],
             "max_requests_per_panel": st["max_requests_per_batch"],
             "solo_ms_32rhs": [t * 1e3 for t in solo]}
+
+
+def batching_run(P, torch):
+    """What batching a colour class into one launch per phase gains: the 256 x 256
+    Laplace workload factored batched and in the plain per-box form (one box per
+    launch, same order, one-CTA ID in both so the arithmetic is identical)."""
+    side = 256
+    tree = P.rss_build_tree(W.grid_points(side), W.LEAF)
+    b = W.gaussian_rhs(side * side, 1, False, 1003)[:, 0]
+    out = {"workload": "laplace_256x256_eps1e-6"}
+    xs = []
+    for name, per_box in (("batched", False), ("per_box", True)):
+        f = P.rss_factor(tree, kind=W.LAPLACE, eps=1e-6, h=1.0 / side, id_cluster=-1, per_box=per_box)
+        del f
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        f = P.rss_factor(tree, kind=W.LAPLACE, eps=1e-6, h=1.0 / side, id_cluster=-1, per_box=per_box)
+        torch.cuda.synchronize()
+        out[name + "_factor_s"] = time.perf_counter() - t0
+        x = b.copy()
+        P.rss_solve(f, x)
+        xs.append(x)
+        out[name + "_launches"] = P.rss_info(f)["launches"]
+        del f
+    out["identical_solutions"] = bool(np.array_equal(xs[0], xs[1]))
+    return out
 
 
 # ----------------------------------------------------------------------------- replicas
@@ -494,6 +532,7 @@ def native_arm(args, w):
         line["serve"] = serve_run(P, torch, args)
     if not args.no_paper and world == 1:
         line["paper_problems"] = paper_problems(P, torch)
+        line["batching"] = batching_run(P, torch)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_block(w, run_oracle(w, 1))
     if rank == 0:

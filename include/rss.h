@@ -98,6 +98,9 @@ typedef struct {
                                      quadrature, the integral of the kernel over the point's
                                      own h x h cell (Eq. 16 for Laplace, Eq. 20 for Helmholtz
                                      and Lippmann-Schwinger), see rss_self_integral */
+  int per_box;                    /* 0: all boxes of a colour class in one launch per phase;
+                                     1: the plain per-box form, one box per launch in the same
+                                     order (for comparison: same mathematics, slower) */
 } rss_params;
 
 /* Build the quadtree of Section 2.1 for n points given as pts_xy[2*i],

@@ -2529,10 +2529,19 @@ rss_status factor_impl(const rss_tree* tree, const rss_params* prm, cudaStream_t
     std::vector<int> hk(maxcls);
     std::vector<std::pair<int, std::unique_ptr<Ev>>> evs;   // phase (0 id, 1 elim, 2 schur), events
 
-    for (int col = 0; col < 9; ++col) {
-      const int nb = coff[col + 1] - coff[col];
+    // launch segments: the nine colour classes, or (the plain per-box form, kept
+    // to measure what batching gains) one box per launch in the same order
+    std::vector<int> segs;
+    if (prm->per_box) {
+      for (int i = 0; i <= (int)cls.size(); ++i) segs.push_back(i);
+    } else {
+      segs = coff;
+    }
+    for (size_t sgi = 0; sgi + 1 < segs.size(); ++sgi) {
+      const int seg0 = segs[sgi];
+      const int nb = segs[sgi + 1] - seg0;
       if (nb == 0) continue;
-      const int* boxes = cls.data() + coff[col];
+      const int* boxes = cls.data() + seg0;
       // rows of Y per box, from the host copy of the active counts
       int mmax = 0;
       std::vector<int> mrows(nb);
@@ -2593,7 +2602,7 @@ rss_status factor_impl(const rss_tree* tree, const rss_params* prm, cudaStream_t
         for (int c0 = 0; c0 < nb; c0 += chunk) {
           IdArgs<TC, T> a;
           a.L = cur.d;
-          a.boxes = d_cls + coff[col];
+          a.boxes = d_cls + seg0;
           a.base = c0;
           a.ws = d_Y;
           a.ldY = ldY;
@@ -2863,7 +2872,8 @@ rss_status factor_impl(const rss_tree* tree, const rss_params* prm, cudaStream_t
       if (!hcopy) { rss_set_error("rss_factor: host allocation failed"); return RSS_ENOMEM; }
       std::memcpy(hcopy, recs.data(), sizeof(BoxRec<T>) * nrec);
       f->rec_host.push_back(hcopy);
-      f->batches.push_back(Batch{g, col, nrec, d_recs, max_k, max_r, max_c});
+      const int colour = (boxes[0] % g) % 3 + 3 * ((boxes[0] / g) % 3);
+      f->batches.push_back(Batch{g, colour, nrec, d_recs, max_k, max_r, max_c});
     }
     RSS_CUDA(cudaStreamSynchronize(st));
     for (auto& pe : evs) {

@@ -180,6 +180,21 @@ def test_tensor_core_sweeps_many_rhs(P):
     assert rel(x, orss.solve(fac, b)) < 1e-9
 
 
+def test_per_box_form_equals_batched(P):
+    """The plain per-box form (one box per launch) and the batched form (one launch per
+    colour class and phase) compute the same factorization: same ranks, bitwise equal
+    solutions (one-CTA ID in both, so the arithmetic is the same)."""
+    side = 64
+    tree = P.rss_build_tree(W.grid_points(side), 16)
+    fb = P.rss_factor(tree, kind=0, eps=1e-6, h=1 / side, id_cluster=-1)
+    fp = P.rss_factor(tree, kind=0, eps=1e-6, h=1 / side, id_cluster=-1, per_box=True)
+    for g in (16, 8, 4):
+        assert np.array_equal(P.rss_level_ranks(fb, g), P.rss_level_ranks(fp, g))
+    b = W.gaussian_rhs(side * side, 2, False, 46)
+    assert np.array_equal(gpu_solve(P, fb, b), gpu_solve(P, fp, b))
+    assert P.rss_info(fp)["launches"] > 4 * P.rss_info(fb)["launches"]
+
+
 @pytest.mark.parametrize("side,leaf", [(8, 64), (16, 64), (32, 16)])
 def test_degenerate_trees(P, side, leaf):
     """One box, a 2 x 2 top only, and eps = 0 (no compression): all exact."""
