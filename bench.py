@@ -513,7 +513,12 @@ def native_arm(args, w):
         "solve_1rhs_ms": t1,
         "solve_rhs_per_s": {"1": r1, str(args.multi_rhs): rm},
         "relres": relres,
-        "phase_gpu_ms": gms,
+        "phase_gpu_ms": {k: v for k, v in gms.items() if k != "span"},
+        # device time from the first to the last kernel of the factor, and the part of
+        # it in which no phase kernel ran (host work between launches)
+        "factor_gpu_span_ms": gms.get("span"),
+        "factor_gpu_idle_ms": gms["span"] - sum(v for k, v in gms.items() if k != "span")
+        if gms.get("span") else None,
         "phase_tflops": {k: info["flops"][k] / (gms[k] * 1e-3) / 1e12 for k in ("id", "elim", "schur", "top")
                          if gms.get(k)},
         "ranks": [{"side": L["side"], "k_mean": L["k_mean"], "k_max": L["k_max"]} for L in info["levels"]],

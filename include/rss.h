@@ -224,6 +224,16 @@ rss_status rss_solve_iterative(const rss_factorization* f, const void* b, void* 
  * finishes its in-flight panels).  NULL is ignored. */
 void rss_free(void* handle);
 
+/* Device memory.  Every device allocation of the library (factor storage,
+ * per-level stencil slabs and workspaces, solve and server panels) comes from
+ * one stream-ordered pool per device, owned by the library.  Freed blocks stay
+ * reserved for the next factorization or solve instead of going back to the
+ * driver, so repeated calls do not map and unmap memory.  rss_trim_memory
+ * waits for the current device, then returns reserved but unused memory of
+ * its pool to the driver until at most keep_bytes stay reserved.  Errors:
+ * RSS_ECUDA if the device cannot be queried or synchronised. */
+rss_status rss_trim_memory(size_t keep_bytes);
+
 /* Message for the last non-OK status returned on this thread. */
 const char* rss_last_error(void);
 

@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <sstream>
 
@@ -18,16 +19,85 @@ static rss_status fail(rss_status s, const std::string& msg) {
   return s;
 }
 
+// One pool per device, created on first use.
+static std::mutex g_pool_mu;
+static cudaMemPool_t g_pools[64] = {};
+
+static cudaError_t get_pool(cudaMemPool_t* out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  if (!g_pools[dev]) {
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.handleTypes = cudaMemHandleTypeNone;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pool = nullptr;
+    e = cudaMemPoolCreate(&pool, &props);
+    if (e != cudaSuccess) return e;
+    uint64_t keep = UINT64_MAX;
+    e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    if (e != cudaSuccess) {
+      cudaMemPoolDestroy(pool);
+      return e;
+    }
+    g_pools[dev] = pool;
+  }
+  *out = g_pools[dev];
+  return cudaSuccess;
+}
+
+cudaError_t pool_malloc(void** p, size_t bytes, cudaStream_t st) {
+  *p = nullptr;
+  cudaMemPool_t pool = nullptr;
+  cudaError_t e = get_pool(&pool);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return e;
+  }
+  if (bytes == 0) bytes = 256;
+  e = cudaMallocFromPoolAsync(p, bytes, pool, st);
+  if (e == cudaErrorMemoryAllocation) {
+    // blocks freed on other streams may not be reusable yet: let them
+    // complete, hand idle memory back to the driver, and try once more
+    cudaGetLastError();
+    cudaDeviceSynchronize();
+    cudaMemPoolTrimTo(pool, 0);
+    e = cudaMallocFromPoolAsync(p, bytes, pool, st);
+  }
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+  }
+  return e;
+}
+
+void pool_free(void* p, cudaStream_t st) {
+  if (p) cudaFreeAsync(p, st);
+}
+
+size_t pool_idle_bytes() {
+  cudaMemPool_t pool = nullptr;
+  if (get_pool(&pool) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  uint64_t reserved = 0, used = 0;
+  cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemCurrent, &reserved);
+  cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &used);
+  return reserved > used ? (size_t)(reserved - used) : 0;
+}
+
 void* Arena::get(size_t bytes) {
   bytes = (bytes + 255) & ~size_t(255);
   if (bytes == 0) bytes = 256;
   if (bytes > left) {
     size_t sz = std::max(bytes, chunk_min);
     void* p = nullptr;
-    if (cudaMalloc(&p, sz) != cudaSuccess) {
-      cudaGetLastError();
-      return nullptr;
-    }
+    if (pool_malloc(&p, sz, st) != cudaSuccess) return nullptr;
     chunks.push_back(p);
     cur = static_cast<char*>(p);
     left = sz;
@@ -40,7 +110,8 @@ void* Arena::get(size_t bytes) {
 }
 
 void Arena::release() {
-  for (void* p : chunks) cudaFree(p);
+  if (!chunks.empty()) cudaDeviceSynchronize();   // solves on any stream may still read the chunks
+  for (void* p : chunks) pool_free(p, 0);
   chunks.clear();
   cur = nullptr;
   left = 0;
@@ -50,6 +121,18 @@ void Arena::release() {
 extern "C" {
 
 const char* rss_last_error(void) { return g_last_error.c_str(); }
+
+rss_status rss_trim_memory(size_t keep_bytes) {
+  cudaMemPool_t pool = nullptr;
+  cudaError_t e = get_pool(&pool);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemPoolTrimTo(pool, keep_bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(RSS_ECUDA, std::string("rss_trim_memory: ") + cudaGetErrorString(e));
+  }
+  return RSS_OK;
+}
 
 rss_status rss_build_tree(const double* pts, int64_t n, int leaf, rss_tree** out) {
   if (!out) return fail(RSS_EINVAL, "rss_build_tree: out is NULL");
@@ -192,7 +275,7 @@ rss_status rss_solve(const rss_factorization* f, void* b, int64_t nrhs, int64_t 
   // host buffer: stage through the device (copies inside this call)
   void* d = nullptr;
   size_t bytes = esz * (size_t)f->n * (size_t)nrhs;
-  RSS_CUDA(cudaMallocAsync(&d, bytes, st));
+  RSS_CUDA(pool_malloc(&d, bytes, st));
   rss_status s = RSS_OK;
   cudaError_t e = cudaMemcpy2DAsync(d, esz * f->n, b, esz * ldb, esz * f->n, nrhs,
                                     cudaMemcpyHostToDevice, st);
@@ -202,7 +285,7 @@ rss_status rss_solve(const rss_factorization* f, void* b, int64_t nrhs, int64_t 
     if (s == RSS_OK)
       e = cudaMemcpy2DAsync(b, esz * ldb, d, esz * f->n, esz * f->n, nrhs, cudaMemcpyDeviceToHost, st);
   }
-  cudaFreeAsync(d, st);
+  pool_free(d, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return fail(RSS_ECUDA, std::string("rss_solve: ") + cudaGetErrorString(e));
   return s;
@@ -233,7 +316,7 @@ rss_status rss_info(const rss_factorization* f, char* buf, size_t len) {
     << ", \"schur\": " << f->t_schur << ", \"merge\": " << f->t_merge << ", \"top\": " << f->t_top
     << ", \"total\": " << f->t_total << "}, \"gpu_ms\": {\"gen\": " << f->g_gen << ", \"id\": " << f->g_id
     << ", \"elim\": " << f->g_elim << ", \"schur\": " << f->g_schur << ", \"merge\": " << f->g_merge
-    << ", \"top\": " << f->g_top << "}, \"flops\": {\"id\": " << f->f_id << ", \"elim\": " << f->f_elim
+    << ", \"top\": " << f->g_top << ", \"span\": " << f->g_span << "}, \"flops\": {\"id\": " << f->f_id << ", \"elim\": " << f->f_elim
     << ", \"schur\": " << f->f_schur << ", \"top\": " << f->f_top << "}, \"phase_launches\": {\"id\": "
     << f->n_id << ", \"elim\": " << f->n_elim << ", \"schur\": " << f->n_schur << "}, \"levels\": [";
   for (size_t l = 0; l < f->levels.size(); ++l) {
@@ -323,7 +406,6 @@ void free_factor(rss_factorization* f) {
   f->tag = 0;
   free_matvec(f);
   f->arena.release();
-  if (f->d_user_to_tree) cudaFree(f->d_user_to_tree);
   for (void* p : f->rec_host) std::free(p);
   delete f;
 }

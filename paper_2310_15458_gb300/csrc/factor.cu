@@ -2319,24 +2319,26 @@ template <typename T> struct HostLevel {
   std::vector<int32_t> n, nact;
 };
 
-template <typename T> void free_level(HostLevel<T>& L) {
-  cudaFree(L.d.pts); cudaFree(L.d.n); cudaFree(L.d.act); cudaFree(L.d.nact); cudaFree(L.d.blk);
+// Level memory is stream-ordered: freeing it needs no device synchronisation.
+template <typename T> void free_level(HostLevel<T>& L, cudaStream_t st) {
+  pool_free(L.d.pts, st); pool_free(L.d.n, st); pool_free(L.d.act, st); pool_free(L.d.nact, st);
+  pool_free(L.d.blk, st);
   L.d = LevelDev<T>{};
 }
 
-template <typename T> rss_status alloc_level(HostLevel<T>& L, int g, int nmax, size_t& transient) {
+template <typename T>
+rss_status alloc_level(HostLevel<T>& L, int g, int nmax, size_t& transient, cudaStream_t st) {
+  L.d = LevelDev<T>{};
   L.d.g = g;
   L.d.nbox = g * g;
   L.d.nmax = nmax;
   const size_t nb = (size_t)g * g;
-  RSS_CUDA(cudaMalloc(&L.d.pts, sizeof(int) * nb * nmax));
-  RSS_CUDA(cudaMalloc(&L.d.n, sizeof(int) * nb));
-  RSS_CUDA(cudaMalloc(&L.d.act, sizeof(int) * nb * nmax));
-  RSS_CUDA(cudaMalloc(&L.d.nact, sizeof(int) * nb));
+  auto get = [&](auto** p, size_t bytes) { return pool_malloc(reinterpret_cast<void**>(p), bytes, st); };
   const size_t bytes = sizeof(T) * nb * 25 * (size_t)nmax * nmax;
-  if (cudaMalloc(&L.d.blk, bytes) != cudaSuccess) {
-    cudaGetLastError();
-    L.d.blk = nullptr;
+  if (get(&L.d.pts, sizeof(int) * nb * nmax) != cudaSuccess || get(&L.d.n, sizeof(int) * nb) != cudaSuccess ||
+      get(&L.d.act, sizeof(int) * nb * nmax) != cudaSuccess || get(&L.d.nact, sizeof(int) * nb) != cudaSuccess ||
+      get(&L.d.blk, bytes) != cudaSuccess) {
+    free_level(L, st);
     rss_set_error("rss_factor: out of device memory for the stencil blocks of the " + std::to_string(g) + " x " +
                   std::to_string(g) + " level (" + std::to_string(bytes >> 20) + " MiB, " + std::to_string(nmax) +
                   " points per box)");
@@ -2345,6 +2347,13 @@ template <typename T> rss_status alloc_level(HostLevel<T>& L, int g, int nmax, s
   transient += bytes;
   return RSS_OK;
 }
+
+// Frees the level it watches when the factorization returns early.
+template <typename T> struct LevelGuard {
+  HostLevel<T>& L;
+  cudaStream_t st;
+  ~LevelGuard() { free_level(L, st); }
+};
 
 // Device time of a phase: events recorded on the factor's stream around it.
 struct Ev {
@@ -2360,28 +2369,24 @@ struct Ev {
   }
 };
 
-// Grow-only device buffer (freed with the factorization's host frame).
+// Grow-only device buffer (freed with the factorization's host frame), in the
+// order of the factor's stream: the old buffer is released after the launches
+// already queued that read it.
 struct GrowBuf {
+  cudaStream_t st;
   void* p = nullptr;
   size_t cap = 0;
+  explicit GrowBuf(cudaStream_t s) : st(s) {}
   bool ensure(size_t bytes) {
     if (bytes <= cap) return true;
-    if (p) {
-      cudaDeviceSynchronize();   // earlier launches may still read the old buffer
-      cudaFree(p);
-    }
+    pool_free(p, st);
     p = nullptr;
     cap = 0;
-    if (cudaMalloc(&p, bytes) != cudaSuccess) {
-      cudaGetLastError();
-      return false;
-    }
+    if (pool_malloc(&p, bytes, st) != cudaSuccess) return false;
     cap = bytes;
     return true;
   }
-  ~GrowBuf() {
-    if (p) cudaFree(p);
-  }
+  ~GrowBuf() { pool_free(p, st); }
 };
 
 struct Timer {
@@ -2407,7 +2412,9 @@ rss_status factor_impl(const rss_tree* tree, const rss_params* prm, cudaStream_t
   const double extent = tree->side * tree->geo.hg;
   const int64_t N = tree->n;
 
-  RSS_CUDA(cudaMalloc(&f->d_user_to_tree, sizeof(int32_t) * N));
+  f->arena.st = st;
+  f->d_user_to_tree = static_cast<int32_t*>(f->arena.get(sizeof(int32_t) * N));
+  if (!f->d_user_to_tree) { rss_set_error("rss_factor: device arena allocation failed"); return RSS_ENOMEM; }
   RSS_CUDA(cudaMemcpyAsync(f->d_user_to_tree, tree->user_to_tree.data(), sizeof(int32_t) * N,
                            cudaMemcpyHostToDevice, st));
   // integer grid coordinates of each tree index
@@ -2443,23 +2450,27 @@ rss_status factor_impl(const rss_tree* tree, const rss_params* prm, cudaStream_t
   // kernel values by displacement, for the leaf blocks and the never-modified far blocks
   const int side = tree->side;
   T* d_tab = nullptr;
-  RSS_CUDA(cudaMalloc(&d_tab, sizeof(T) * (size_t)(2 * side - 1) * (2 * side - 1)));
+  RSS_CUDA(pool_malloc(reinterpret_cast<void**>(&d_tab), sizeof(T) * (size_t)(2 * side - 1) * (2 * side - 1), st));
   struct TabFree {
     T* p;
-    ~TabFree() { cudaFree(p); }
-  } tab_free{d_tab};
+    cudaStream_t st;
+    ~TabFree() { pool_free(p, st); }
+  } tab_free{d_tab, st};
+  Ev span;
+  span.start(st);
   k_ktab<T><<<152 * 8, NT, 0, st>>>(d_tab, side, f->kp, f->geo);
   RSS_LAUNCHED();
   f->launches += 1;
 
   // workspaces reused across colour classes and levels
-  GrowBuf gb_cls, gb_k, gb_perm, gb_clsidx, gb_Tws, gb_Y, gb_oz, gb_w;
+  GrowBuf gb_cls(st), gb_k(st), gb_perm(st), gb_clsidx(st), gb_Tws(st), gb_Y(st), gb_oz(st), gb_w(st);
   // leaf level
   size_t transient = 0;
   HostLevel<T> cur;
+  LevelGuard<T> cur_guard{cur, st};
   int g = tree->gL;
   {
-    rss_status s = alloc_level(cur, g, tree->leaf, transient);
+    rss_status s = alloc_level(cur, g, tree->leaf, transient, st);
     if (s != RSS_OK) return s;
     const int nbox = g * g, leaf = tree->leaf;
     std::vector<int> hp((size_t)nbox * leaf), hn(nbox, leaf);
@@ -2906,6 +2917,7 @@ rss_status factor_impl(const rss_tree* tree, const rss_params* prm, cudaStream_t
       // child's active entries (all the merge reads) and free the rest first
       size_t fr = 0, tot = 0;
       RSS_CUDA(cudaMemGetInfo(&fr, &tot));
+      fr += pool_idle_bytes();
       const size_t pbytes = sizeof(T) * (size_t)gp * gp * 25 * (size_t)pmax * pmax;
       if (pbytes + (size_t(4) << 30) > fr) {
         int kmax = 1;
@@ -2913,18 +2925,22 @@ rss_status factor_impl(const rss_tree* tree, const rss_params* prm, cudaStream_t
         const size_t cbytes = sizeof(T) * (size_t)nbox * 25 * (size_t)kmax * kmax;
         T* cblk = nullptr;
         int *cpts = nullptr, *cact = nullptr;
-        RSS_CUDA(cudaMalloc(&cblk, cbytes));
-        RSS_CUDA(cudaMalloc(&cpts, sizeof(int) * (size_t)nbox * kmax));
-        RSS_CUDA(cudaMalloc(&cact, sizeof(int) * (size_t)nbox * kmax));
+        if (pool_malloc(reinterpret_cast<void**>(&cblk), cbytes, st) != cudaSuccess ||
+            pool_malloc(reinterpret_cast<void**>(&cpts), sizeof(int) * (size_t)nbox * kmax, st) != cudaSuccess ||
+            pool_malloc(reinterpret_cast<void**>(&cact), sizeof(int) * (size_t)nbox * kmax, st) != cudaSuccess) {
+          pool_free(cblk, st); pool_free(cpts, st); pool_free(cact, st);
+          rss_set_error("rss_factor: out of device memory for the compacted child blocks");
+          return RSS_ENOMEM;
+        }
         k_compact_blk<T><<<nbox * 25, NT, 0, st>>>(cur.d, cblk, cpts, kmax);
         RSS_LAUNCHED();
         k_iota_rows<<<1024, NT, 0, st>>>(cact, nbox, kmax);
         RSS_LAUNCHED();
         RSS_CUDA(cudaStreamSynchronize(st));
         f->launches += 2;
-        cudaFree(cur.d.blk);
-        cudaFree(cur.d.pts);
-        cudaFree(cur.d.act);
+        pool_free(cur.d.blk, st);
+        pool_free(cur.d.pts, st);
+        pool_free(cur.d.act, st);
         transient -= sizeof(T) * (size_t)nbox * 25 * nn;
         transient += cbytes;
         cur.d.blk = cblk;
@@ -2933,8 +2949,9 @@ rss_status factor_impl(const rss_tree* tree, const rss_params* prm, cudaStream_t
         cur.d.nmax = kmax;
       }
     }
+    LevelGuard<T> par_guard{par, st};
     {
-      rss_status s = alloc_level(par, gp, pmax, transient);
+      rss_status s = alloc_level(par, gp, pmax, transient, st);
       if (s != RSS_OK) return s;
     }
     f->peak_transient = std::max(f->peak_transient, transient);
@@ -2949,8 +2966,9 @@ rss_status factor_impl(const rss_tree* tree, const rss_params* prm, cudaStream_t
     f->g_merge += evm.ms();
     f->launches += 2;
     transient -= sizeof(T) * (size_t)nbox * 25 * (size_t)cur.d.nmax * cur.d.nmax;
-    free_level(cur);
+    free_level(cur, st);
     cur = par;
+    par.d = LevelDev<T>{};   // owned by cur from here
     g = gp;
     f->t_merge += tm.ms();
   }
@@ -3001,11 +3019,13 @@ rss_status factor_impl(const rss_tree* tree, const rss_params* prm, cudaStream_t
       f->launches += 3;
     }
     evt.stop(st);
+    span.stop(st);
     f->launches += 1;
     RSS_CUDA(cudaStreamSynchronize(st));
     f->g_top += evt.ms();
+    f->g_span = span.ms();
     f->f_top += (sizeof(T) == sizeof(double) ? 1.0 : 4.0) * (2.0 / 3.0 + 2.0) * (double)ntop * ntop * ntop;
-    free_level(cur);
+    free_level(cur, st);
     int herr = 0;
     RSS_CUDA(cudaMemcpy(&herr, d_err, sizeof(int), cudaMemcpyDeviceToHost));
     if (herr) { rss_set_error("rss_factor: zero pivot in the dense top LU"); return RSS_ENUMERIC; }

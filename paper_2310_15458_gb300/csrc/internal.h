@@ -72,15 +72,25 @@ struct LevelInfo {
   std::vector<int32_t> k;   // skeleton rank per box
 };
 
-// Device memory arena: big chunks, bump allocation, freed together.
+// Stream-ordered device memory from the library's pool of the current device.
+// Freed blocks stay reserved by the pool (release threshold: unlimited) until
+// rss_trim_memory.  pool_malloc retries once after returning idle memory to the
+// driver; it leaves *p null and the CUDA error state clear on failure.
+cudaError_t pool_malloc(void** p, size_t bytes, cudaStream_t st);
+void pool_free(void* p, cudaStream_t st);   // stream-ordered; null is ignored
+size_t pool_idle_bytes();                   // reserved by the pool but not in use
+
+// Device memory arena: big chunks, bump allocation, freed together.  Chunks
+// come from the pool in the order of stream `st` (the factor's stream).
 struct Arena {
   std::vector<void*> chunks;
   char* cur = nullptr;
   size_t left = 0;
   size_t total = 0;
   size_t chunk_min = size_t(256) << 20;
+  cudaStream_t st = nullptr;
   void* get(size_t bytes);   // nullptr on failure
-  void release();
+  void release();            // waits for the device first
 };
 
 struct rss_factorization {
@@ -111,6 +121,7 @@ struct rss_factorization {
   // device times (ms, CUDA events on the factor's stream), algorithmic real
   // flops (a complex multiply-add counts 8) and launch counts per phase
   double g_gen = 0, g_id = 0, g_elim = 0, g_schur = 0, g_merge = 0, g_top = 0;
+  double g_span = 0;   // device time from the first kernel to the end of the top inverse
   double f_id = 0, f_elim = 0, f_schur = 0, f_top = 0;
   long long n_id = 0, n_elim = 0, n_schur = 0;
   long long launches = 0;

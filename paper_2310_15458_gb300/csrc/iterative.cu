@@ -231,7 +231,7 @@ rss_status matvec_impl(const rss_factorization* f, const T* x, T* y, int64_t nrh
   const int s = m->s;
   const size_t tot = (size_t)4 * s * s;
   cufftDoubleComplex* pad = nullptr;
-  RSS_CUDA(cudaMallocAsync(&pad, sizeof(cufftDoubleComplex) * tot, st));
+  RSS_CUDA(pool_malloc(reinterpret_cast<void**>(&pad), sizeof(cufftDoubleComplex) * tot, st));
   std::lock_guard<std::mutex> lk(m->mu);   // one plan: calls on the same factor are serialised
   rss_status res = RSS_OK;
   const unsigned g1 = std::min<long long>(cdiv(f->n, NTI), 152LL * 8), g2 = 152 * 8;
@@ -247,7 +247,7 @@ rss_status matvec_impl(const rss_factorization* f, const T* x, T* y, int64_t nrh
     k_extract<T><<<g1, NTI, 0, st>>>(pad, x + q * ld, y + q * ld, f->n, f->d_user_to_grid, s, f->d_w, f->kp);
     if (cudaGetLastError() != cudaSuccess) res = RSS_ECUDA;
   }
-  cudaFreeAsync(pad, st);
+  pool_free(pad, st);
   if (res != RSS_OK) rss_set_error("rss_matvec: FFT or launch failure");
   return res;
 }
@@ -483,13 +483,13 @@ rss_status iterative_impl(const rss_factorization* f, const T* b, T* x, double t
   const size_t nvec = use_cg ? 4 : 3 + (size_t)m + 1;
   char* mem = nullptr;
   const size_t vb = (sizeof(T) * (size_t)n + 255) & ~size_t(255);
-  RSS_CUDA(cudaMallocAsync(&mem, vb * nvec + sizeof(double2) * (RED_BLOCKS + 1), st));
+  RSS_CUDA(pool_malloc(reinterpret_cast<void**>(&mem), vb * nvec + sizeof(double2) * (RED_BLOCKS + 1), st));
   T* w0 = reinterpret_cast<T*>(mem);
   auto vec = [&](size_t i) { return reinterpret_cast<T*>(mem + i * vb); };
   Vec<T> v{f, st, reinterpret_cast<double2*>(mem + vb * nvec), reinterpret_cast<double2*>(mem + vb * nvec) + RED_BLOCKS, n};
   rss_status s = use_cg ? pcg<T>(v, b, x, w0, vec(1), vec(2), vec(3), tol, maxit, iters, relres)
                         : gmres<T>(v, b, x, w0, vec(1), vec(2), vec(3), m, tol, maxit, iters, relres);
-  cudaFreeAsync(mem, st);
+  pool_free(mem, st);
   cudaStreamSynchronize(st);
   return s;
 }

@@ -112,11 +112,10 @@ bool launch_panel(rss_server* S, Slot& s) {
     S->cv_done.notify_all();
   };
   if (s.d_cap < bytes) {
-    if (s.d_panel) cudaFree(s.d_panel);
+    pool_free(s.d_panel, s.stream);   // ordered after the panels already queued on this stream
     s.d_panel = nullptr;
     s.d_cap = 0;
-    if (cudaMalloc(&s.d_panel, bytes) != cudaSuccess) {
-      cudaGetLastError();
+    if (pool_malloc(&s.d_panel, bytes, s.stream) != cudaSuccess) {
       fail_batch("panel allocation failed");
       return true;
     }
@@ -317,7 +316,8 @@ void free_server(rss_server* S) {
   if (S->worker.joinable()) S->worker.join();
   for (auto& sp : S->slots) {
     if (sp->stream) cudaStreamSynchronize(sp->stream);
-    if (sp->d_panel) cudaFree(sp->d_panel);
+    pool_free(sp->d_panel, sp->stream);
+    if (sp->stream) cudaStreamSynchronize(sp->stream);
     if (sp->h_panel) cudaFreeHost(sp->h_panel);
     if (sp->done) cudaEventDestroy(sp->done);
     if (sp->stream) cudaStreamDestroy(sp->stream);

@@ -746,13 +746,13 @@ template <typename T> rss_status top_inverse(const T* LU, const int* piv, int n,
     return RSS_EINVAL;
   }
   int* iota = nullptr;
-  RSS_CUDA(cudaMallocAsync(&iota, sizeof(int) * (size_t)n, st));
+  RSS_CUDA(pool_malloc(reinterpret_cast<void**>(&iota), sizeof(int) * (size_t)n, st));
   k_iota<<<cdiv(n, 256), 256, 0, st>>>(iota, n);
   k_identity<T><<<std::min<long long>(cdiv((long long)n * n, 256), 152LL * 8), 256, 0, st>>>(Ainv, n);
   RSS_CUDA(cudaFuncSetAttribute(k_top_solve<T, RT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
   k_top_solve<T, RT><<<cdiv(n, RT), 1024, tsm, st>>>(LU, piv, iota, n, Ainv, n, n);
   const cudaError_t e = cudaGetLastError();
-  cudaFreeAsync(iota, st);
+  pool_free(iota, st);
   if (e != cudaSuccess) {
     rss_set_error(std::string("rss_factor: top inverse launch failed: ") + cudaGetErrorString(e));
     return RSS_ECUDA;
@@ -769,7 +769,7 @@ rss_status solve_impl(const rss_factorization* f, T* b, int64_t nrhs, int64_t ld
   const SweepWs w = sweep_ws<T>(f, nrhs, rhs_chunk(nrhs));
   const size_t xb = (sizeof(T) * (size_t)N * nrhs + 255) & ~size_t(255);
   char* mem = nullptr;
-  RSS_CUDA(cudaMallocAsync(&mem, xb + w.bytes, st));
+  RSS_CUDA(pool_malloc(reinterpret_cast<void**>(&mem), xb + w.bytes, st));
   T* x = reinterpret_cast<T*>(mem);
   const unsigned grid = std::min<long long>(cdiv((long long)N * nrhs, NT), 152LL * 16);
   k_perm_in<T><<<grid, NT, 0, st>>>(b, ldb, x, N, (int)nrhs, f->d_user_to_tree);
@@ -786,7 +786,7 @@ rss_status solve_impl(const rss_factorization* f, T* b, int64_t nrhs, int64_t ld
       s = RSS_ECUDA;
     }
   }
-  cudaFreeAsync(mem, st);
+  pool_free(mem, st);
   return s;
 }
 

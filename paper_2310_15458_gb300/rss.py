@@ -78,10 +78,11 @@ def _load():
     lib.rss_matvec.argtypes = [vp, vp, vp, i64, i64, vp]
     lib.rss_solve_iterative.argtypes = [vp, vp, vp, ctypes.c_double, ctypes.c_int, ctypes.c_int,
                                         ctypes.c_int, ctypes.POINTER(ctypes.c_int), dp, vp]
+    lib.rss_trim_memory.argtypes = [ctypes.c_size_t]
     for name in ("rss_build_tree", "rss_factor", "rss_solve", "rss_solve_noalloc", "rss_info",
                  "rss_level_ranks", "rss_box_record", "rss_server_create", "rss_server_add",
                  "rss_server_submit", "rss_server_wait", "rss_server_stats", "rss_self_integral",
-                 "rss_matvec", "rss_solve_iterative"):
+                 "rss_matvec", "rss_solve_iterative", "rss_trim_memory"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -290,6 +291,12 @@ def rss_free(obj):
     if obj is not None and getattr(obj, "_h", None):
         _load().rss_free(obj._h)
         obj._h = None
+
+
+def rss_trim_memory(keep_bytes: int = 0):
+    """Return reserved but unused memory of the library's device pool to the
+    driver, keeping at most ``keep_bytes`` reserved (waits for the device)."""
+    _check(_load().rss_trim_memory(int(keep_bytes)))
 
 
 def rss_info(f: Factor) -> dict:
