@@ -788,6 +788,7 @@ template <typename T> struct ElimArgs {
   const T* T_ws;
   int* err;
   int smem_cap;             // scalars of dynamic shared memory available
+  int sym;                  // A is symmetric (real Laplace): A_BC^T = A_CB
 };
 
 constexpr int PKC = 16;     // rows of a panel product's right operand staged per chunk
@@ -1416,12 +1417,28 @@ __device__ __forceinline__ void oz_split_vec(VF val, int len, int lenp, uint16_t
   }
 }
 
+// Real factors: the columns of W_E and W_F cut into digit slices once per box
+// (every panel CTA of the box reads them).  One CTA per box, eight threads per
+// column.
+__global__ void __launch_bounds__(NT) k_w_split(ElimArgs<double> a) {
+  const BoxRec<double> R = a.recs[blockIdx.x];
+  if (!R.ozp) return;
+  const int r = R.r, n = R.k + r, np = (n + 15) & ~15, rp = (r + 31) & ~31;
+  for (int c0 = 0; c0 < 2 * rp; c0 += NT / 8) {
+    const int col = c0 + (int)threadIdx.x / 8, pass = col / rp, j = col % rp;
+    const double* w = (pass ? R.Wf : R.We) + (size_t)j * n;
+    oz_split_vec<8>([&](int l) { return w[l]; }, j < r ? n : 0, np, R.Wsl + (size_t)col * OZ_S * np, np,
+                    &R.Wexp[col], true);
+  }
+}
+
 // Real factors: E = A_CB W_E and F^T = A_BC^T W_F for one 64-row panel of C,
 // with the panel rows and the columns of W cut into digit slices (row and
 // column scales) and the slice products summed exactly on the tensor cores as
 // in the Schur update; E (F^T) = W 2^(e_i + f_j - 53) from one int64 per entry.
-// W is taken 32 columns at a time.  The rows of E and F^T are then sliced for
-// the Schur update.
+// W is taken 32 columns at a time from its precomputed slices.  A symmetric A
+// gives A_BC^T = A_CB, so the panel is cut once for both products.  The rows of
+// E and F^T are then sliced for the Schur update.
 constexpr int OZ_NCH = 32;
 
 __global__ void __launch_bounds__(NT, 2) k_elim_oz(ElimArgs<double> a) {
@@ -1432,7 +1449,7 @@ __global__ void __launch_bounds__(NT, 2) k_elim_oz(ElimArgs<double> a) {
   if (p0 >= R.c) return;
   const LevelDev<double>& L = a.L;
   const int nmax = L.nmax, g = L.g, B = R.box, k = R.k, r = R.r, c = R.c, n = k + r;
-  const int np = (n + 15) & ~15, SA = OZ_S * np + 8;
+  const int np = (n + 15) & ~15, SA = OZ_S * np + 8, rp = (r + 31) & ~31, cpc = OZ_S * np / 8;
   const size_t nn = (size_t)nmax * nmax;
   const int* perm = a.perm_in + (size_t)a.cls_idx[blockIdx.y] * nmax;
   uint16_t* As = reinterpret_cast<uint16_t*>(smraw);   // 64 x SA: panel rows
@@ -1453,9 +1470,8 @@ __global__ void __launch_bounds__(NT, 2) k_elim_oz(ElimArgs<double> a) {
   const int m0 = (warp >> 1) * 16, n0 = (warp & 1) * 16;
   const int a_row = lane & 15, a_k = (lane >> 4) * 8;
   const int b_row = ((lane >> 4) << 3) + (lane & 7), b_k = ((lane >> 3) & 1) * 8;
-  for (int pass = 0; pass < 2; ++pass) {
-    const double* __restrict__ Wm = pass == 0 ? R.We : R.Wf;
-    double* out = pass == 0 ? R.E : R.Ft;
+  const int npass = a.sym ? 1 : 2;
+  for (int pass = 0; pass < npass; ++pass) {
     {   // panel rows: A(u, B)[pos, perm[l]] (pass 0) or A(B, u)[perm[l], pos] (pass 1)
       const int row = tid >> 2, u = ru[row], pos = rpos[row];
       const double* base = nullptr;
@@ -1466,65 +1482,82 @@ __global__ void __launch_bounds__(NT, 2) k_elim_oz(ElimArgs<double> a) {
       oz_split_vec<4>([&](int l) { return base[(size_t)perm[l] * ls]; }, u >= 0 ? n : 0, np, As + row * SA, np,
                       &rexp[row], true);
     }
-    for (int jc = 0; jc < r; jc += OZ_NCH) {
+    // columns of [W_E W_F] (symmetric A) or of the pass's W
+    const int c_lo = a.sym ? 0 : pass * rp, c_hi = a.sym ? 2 * rp : (pass + 1) * rp;
+    for (int cc = c_lo; cc < c_hi; cc += OZ_NCH) {
+      const int j0 = cc % rp;
+      if (j0 >= r) continue;   // padding columns only
       __syncthreads();
-      {   // columns jc .. jc + 31 of W
-        const int col = tid >> 3, j = jc + col;
-        const double* wc = Wm + (size_t)j * n;
-        oz_split_vec<8>([&](int l) { return wc[l]; }, j < r ? n : 0, np, Bs + col * SA, np, &cexp[col], true);
+      for (int e = tid; e < OZ_NCH * cpc; e += NT) {
+        const int col = e / cpc, ch = e % cpc, sl = ch / (np / 8), q = ch % (np / 8);
+        cp_async16(Bs + col * SA + sl * np + q * 8, R.Wsl + (size_t)(cc + col) * OZ_S * np + (size_t)sl * np + q * 8);
       }
+      if (tid < OZ_NCH) cexp[tid] = R.Wexp[cc + tid];
+      cp_async_wait_all();
       __syncthreads();
       long long W[2][4];
 #pragma unroll
       for (int ni = 0; ni < 2; ++ni)
 #pragma unroll
         for (int e = 0; e < 4; ++e) W[ni][e] = 0;
-      for (int u = 0; u < OZ_S; ++u) {
-        float cf[2][4];
+      // groups u and u + 1 together: (G_u 2^7 + G_{u+1}) 2^(32-7u), exact in
+      // int32 for K <= 128 (|G| < 2^23)
+#pragma unroll 1
+      for (int u = 0; u < OZ_S; u += 2) {
+        float ca[2][4], cb[2][4];
 #pragma unroll
         for (int ni = 0; ni < 2; ++ni)
 #pragma unroll
-          for (int e = 0; e < 4; ++e) cf[ni][e] = 0.f;
-        for (int p = 0; p <= u; ++p) {
+          for (int e = 0; e < 4; ++e) ca[ni][e] = cb[ni][e] = 0.f;
+        for (int p = 0; p <= u + 1; ++p) {
           const uint16_t* Ab = As + p * np + (m0 + a_row) * SA + a_k;
-          const uint16_t* Bb = Bs + (u - p) * np + (n0 + b_row) * SA + b_k;
+          const uint16_t* Bb1 = Bs + (u + 1 - p) * np + (n0 + b_row) * SA + b_k;
+          const uint16_t* Bb0 = Bs + (u - p) * np + (n0 + b_row) * SA + b_k;
           for (int kk = 0; kk < np; kk += 16) {
-            uint32_t af[4], bq[4];
+            uint32_t af[4], b1[4];
             ldsm_x4(af, Ab + kk);
-            ldsm_x4(bq, Bb + kk);
-            mma_bf16(cf[0], af, bq);
-            mma_bf16(cf[1], af, bq + 2);
+            ldsm_x4(b1, Bb1 + kk);
+            mma_bf16(cb[0], af, b1);
+            mma_bf16(cb[1], af, b1 + 2);
+            if (p <= u) {
+              uint32_t b0[4];
+              ldsm_x4(b0, Bb0 + kk);
+              mma_bf16(ca[0], af, b0);
+              mma_bf16(ca[1], af, b0 + 2);
+            }
           }
         }
-        const int sh = 39 - OZ_BITS * u;
+        const int sh = 32 - OZ_BITS * u;
 #pragma unroll
         for (int ni = 0; ni < 2; ++ni)
 #pragma unroll
           for (int e = 0; e < 4; ++e) {
-            const long long gv = (long long)__float2int_rn(cf[ni][e]);
+            const long long gv = (long long)(oz_fint(ca[ni][e]) * 128 + oz_fint(cb[ni][e]));
             W[ni][e] += sh >= 0 ? (gv << sh) : ((gv + (1LL << (-sh - 1))) >> (-sh));
           }
       }
+      double* out = cc < rp ? R.E : R.Ft;
 #pragma unroll
       for (int ni = 0; ni < 2; ++ni)
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
           const int row = m0 + gq + (e >= 2 ? 8 : 0);
-          const int col = n0 + ni * 8 + 2 * t4 + (e & 1), j = jc + col;
+          const int col = n0 + ni * 8 + 2 * t4 + (e & 1), j = j0 + col;
           if (row < rows && j < r)
             out[(size_t)(p0 + row) + (size_t)j * c] = oz_ldexp_int(W[ni][e], rexp[row] + cexp[col] - 53);
         }
     }
     __syncthreads();
-    if (R.Esl != nullptr) {   // digit slices of this panel's rows of E (F^T) for the Schur update
-      const int row = tid >> 2;
-      const bool act = row < rows;
-      const double* src = out + (size_t)(p0 + row);
-      uint16_t* dst = (pass == 0 ? R.Esl : R.Fsl) + (size_t)(p0 + (act ? row : 0)) * OZ_S * R.kp;
-      int* ex = (pass == 0 ? R.Eexp : R.Fexp) + p0 + (act ? row : 0);
+  }
+  if (R.Esl != nullptr) {   // digit slices of this panel's rows of E and F^T for the Schur update
+    const int row = tid >> 2;
+    const bool act = row < rows;
+    for (int q = 0; q < 2; ++q) {
+      const double* src = (q == 0 ? R.E : R.Ft) + (size_t)(p0 + row);
+      uint16_t* dst = (q == 0 ? R.Esl : R.Fsl) + (size_t)(p0 + (act ? row : 0)) * OZ_S * R.kp;
+      int* ex = (q == 0 ? R.Eexp : R.Fexp) + p0 + (act ? row : 0);
       oz_split_vec<4>([&](int l) { return src[(size_t)l * c]; }, act ? r : 0, R.kp, dst, R.kp, ex, act);
     }
-    __syncthreads();
   }
 }
 
@@ -2164,6 +2197,32 @@ __global__ void __launch_bounds__(NT) k_compact_blk(LevelDev<T> C, T* __restrict
   }
 }
 
+// Grid coordinates of every tree index (box-major, row-major inside a leaf box)
+// and the grid index iy * side + ix of every user point.
+__global__ void k_grid_coords(int2* ixy, int32_t* u2g, const int32_t* u2t, long long n, int gL, int ls,
+                              int side) {
+  const int leaf = ls * ls;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    const int b = (int)(t / leaf), l = (int)(t % leaf);
+    ixy[t] = make_int2((b % gL) * ls + l % ls, (b / gL) * ls + l / ls);
+  }
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const long long t = u2t[i];
+    const int b = (int)(t / leaf), l = (int)(t % leaf);
+    u2g[i] = ((b / gL) * ls + l / ls) * side + (b % gL) * ls + l % ls;
+  }
+}
+
+// Leaf level: box b holds tree indices b * leaf + i, all active.
+__global__ void k_leaf_init(int* pts, int* act, int* n, int* nact, int nbox, int leaf) {
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < (long long)nbox * leaf;
+       e += (long long)gridDim.x * blockDim.x) {
+    pts[e] = (int)e;
+    act[e] = (int)(e % leaf);
+    if (e % leaf == 0) n[e / leaf] = nact[e / leaf] = leaf;
+  }
+}
+
 __global__ void k_iota_rows(int* act, int nbox, int kmax) {
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < (long long)nbox * kmax;
        e += (long long)gridDim.x * blockDim.x)
@@ -2417,27 +2476,18 @@ rss_status factor_impl(const rss_tree* tree, const rss_params* prm, cudaStream_t
   if (!f->d_user_to_tree) { rss_set_error("rss_factor: device arena allocation failed"); return RSS_ENOMEM; }
   RSS_CUDA(cudaMemcpyAsync(f->d_user_to_tree, tree->user_to_tree.data(), sizeof(int32_t) * N,
                            cudaMemcpyHostToDevice, st));
-  // integer grid coordinates of each tree index
-  std::vector<int2> hixy(N);
-  for (int64_t t = 0; t < N; ++t) {
-    const int b = (int)(t / tree->leaf), l = (int)(t % tree->leaf);
-    hixy[t] = make_int2((b % tree->gL) * tree->ls + l % tree->ls, (b / tree->gL) * tree->ls + l / tree->ls);
-  }
   int2* d_ixy = static_cast<int2*>(f->arena.get(sizeof(int2) * N));
   int* d_err = static_cast<int*>(f->arena.get(sizeof(int)));
-  if (!d_ixy || !d_err) { rss_set_error("rss_factor: device arena allocation failed"); return RSS_ENOMEM; }
-  RSS_CUDA(cudaMemcpyAsync(d_ixy, hixy.data(), sizeof(int2) * N, cudaMemcpyHostToDevice, st));
-  RSS_CUDA(cudaMemsetAsync(d_err, 0, sizeof(int), st));
-  {   // grid index (iy * side + ix) of each user point, for the FFT matvec
-    std::vector<int32_t> u2g(N);
-    for (int64_t i = 0; i < N; ++i) {
-      const int2 q = hixy[tree->user_to_tree[i]];
-      u2g[i] = q.y * tree->side + q.x;
-    }
-    f->d_user_to_grid = static_cast<int32_t*>(f->arena.get(sizeof(int32_t) * N));
-    if (!f->d_user_to_grid) { rss_set_error("rss_factor: device arena allocation failed"); return RSS_ENOMEM; }
-    RSS_CUDA(cudaMemcpy(f->d_user_to_grid, u2g.data(), sizeof(int32_t) * N, cudaMemcpyHostToDevice));
+  f->d_user_to_grid = static_cast<int32_t*>(f->arena.get(sizeof(int32_t) * N));
+  if (!d_ixy || !d_err || !f->d_user_to_grid) {
+    rss_set_error("rss_factor: device arena allocation failed");
+    return RSS_ENOMEM;
   }
+  RSS_CUDA(cudaMemsetAsync(d_err, 0, sizeof(int), st));
+  k_grid_coords<<<152 * 8, NT, 0, st>>>(d_ixy, f->d_user_to_grid, f->d_user_to_tree, N, tree->gL, tree->ls,
+                                        tree->side);
+  RSS_LAUNCHED();
+  f->launches += 1;
   if (prm->kind == RSS_HELMHOLTZ_LS) {   // w = kappa sqrt(b) per grid point (Eq. 19)
     f->d_w = static_cast<double*>(f->arena.get(sizeof(double) * N));
     if (!f->d_w) { rss_set_error("rss_factor: device arena allocation failed"); return RSS_ENOMEM; }
@@ -2473,17 +2523,10 @@ rss_status factor_impl(const rss_tree* tree, const rss_params* prm, cudaStream_t
     rss_status s = alloc_level(cur, g, tree->leaf, transient, st);
     if (s != RSS_OK) return s;
     const int nbox = g * g, leaf = tree->leaf;
-    std::vector<int> hp((size_t)nbox * leaf), hn(nbox, leaf);
-    for (int b = 0; b < nbox; ++b)
-      for (int i = 0; i < leaf; ++i) hp[(size_t)b * leaf + i] = b * leaf + i;
-    std::vector<int> ha((size_t)nbox * leaf);
-    for (int b = 0; b < nbox; ++b)
-      for (int i = 0; i < leaf; ++i) ha[(size_t)b * leaf + i] = i;
-    RSS_CUDA(cudaMemcpyAsync(cur.d.pts, hp.data(), sizeof(int) * hp.size(), cudaMemcpyHostToDevice, st));
-    RSS_CUDA(cudaMemcpyAsync(cur.d.act, ha.data(), sizeof(int) * ha.size(), cudaMemcpyHostToDevice, st));
-    RSS_CUDA(cudaMemcpyAsync(cur.d.n, hn.data(), sizeof(int) * nbox, cudaMemcpyHostToDevice, st));
-    RSS_CUDA(cudaMemcpyAsync(cur.d.nact, hn.data(), sizeof(int) * nbox, cudaMemcpyHostToDevice, st));
-    RSS_CUDA(cudaStreamSynchronize(st));
+    std::vector<int> hn(nbox, leaf);
+    k_leaf_init<<<152 * 8, NT, 0, st>>>(cur.d.pts, cur.d.act, cur.d.n, cur.d.nact, nbox, leaf);
+    RSS_LAUNCHED();
+    f->launches += 1;
     cur.n = hn;
     cur.nact = hn;
     Timer tg;
@@ -2736,10 +2779,17 @@ rss_status factor_impl(const rss_tree* tree, const rss_params* prm, cudaStream_t
       // (complex factors: any n_B, K taken in chunks by k_elim_ozc)
       int ozp_np = 0;
       const int ozp_nmax = sizeof(T) == sizeof(double) ? 128 : (1 << 30);
+      // (real factors also keep the digit slices of the columns of W_E and W_F)
+      auto wsl_bytes = [&](const BoxRec<T>& R) -> size_t {
+        if (sizeof(T) != sizeof(double)) return 0;
+        const size_t np = (R.k + R.r + 15) & ~15, rp = (R.r + 31) & ~31;
+        return ((2 * rp * OZ_S * np * sizeof(uint16_t) + 255) & ~size_t(255)) + ((2 * rp * sizeof(int) + 255) & ~size_t(255));
+      };
       if (prm->schur_path == 0) {
         size_t bytes = 0;
         for (const BoxRec<T>& R : recs)
-          if (R.k + R.r <= ozp_nmax) bytes += 2 * (((size_t)(R.k + R.r) * R.r * sizeof(T) + 255) & ~size_t(255));
+          if (R.k + R.r <= ozp_nmax)
+            bytes += 2 * (((size_t)(R.k + R.r) * R.r * sizeof(T) + 255) & ~size_t(255)) + wsl_bytes(R);
         if (bytes > 0) {
           if (!gb_w.ensure(bytes)) {
             rss_set_error("rss_factor: device workspace allocation failed");
@@ -2752,6 +2802,13 @@ rss_status factor_impl(const rss_tree* tree, const rss_params* prm, cudaStream_t
             R.We = reinterpret_cast<T*>(p);
             R.Wf = reinterpret_cast<T*>(p + b);
             p += 2 * b;
+            if (sizeof(T) == sizeof(double)) {
+              const size_t np = (R.k + R.r + 15) & ~15, rp = (R.r + 31) & ~31;
+              const size_t bs = (2 * rp * OZ_S * np * sizeof(uint16_t) + 255) & ~size_t(255);
+              R.Wsl = reinterpret_cast<uint16_t*>(p);
+              R.Wexp = reinterpret_cast<int*>(p + bs);
+              p += wsl_bytes(R);
+            }
             R.ozp = 1;
             ozp_np = std::max(ozp_np, (R.k + R.r + 15) & ~15);
           }
@@ -2801,6 +2858,7 @@ rss_status factor_impl(const rss_tree* tree, const rss_params* prm, cudaStream_t
       ea.perm_in = d_perm;
       ea.T_ws = d_Tws;
       ea.err = d_err;
+      ea.sym = (sizeof(T) == sizeof(double) && prm->kind == RSS_LAPLACE) ? 1 : 0;
       // shared memory of the per-box kernel: T and the LU of the largest box that fits
       const size_t ints = (2 * (size_t)max_r * sizeof(int) + 15) & ~size_t(15);
       const size_t want =
@@ -2840,11 +2898,13 @@ rss_status factor_impl(const rss_tree* tree, const rss_params* prm, cudaStream_t
       }
       if constexpr (sizeof(T) == sizeof(double)) {
         if (ozp_np > 0) {
+          k_w_split<<<nrec, NT, 0, st>>>(ea);
+          RSS_LAUNCHED();
           const int smem = (64 + OZ_NCH) * (OZ_S * ozp_np + 8) * (int)sizeof(uint16_t);
           RSS_CUDA(cudaFuncSetAttribute(k_elim_oz, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
           k_elim_oz<<<dim3((max_c + 63) / 64, nrec), NT, smem, st>>>(ea);
           RSS_LAUNCHED();
-          f->launches += 1;
+          f->launches += 2;
         }
       } else {
         if (ozp_np > 0) {

@@ -52,6 +52,12 @@ template <typename T> struct BoxRec {
   // W_E = [-T U^{-1}; U^{-1}] and W_F = [-(L^{-1} P T^*)^T; (L^{-1} P)^T]
   T* We;
   T* Wf;
+  // the columns of W_E then W_F (2 rp columns, rp = r rounded up to 32, the
+  // padding columns zero), each cut into OZ_S bf16 digit slices of np = n
+  // rounded up to 16 entries: column j at Wsl + j * OZ_S * np, slice p at
+  // + p * np; Wexp[j] its power-of-two scale
+  uint16_t* Wsl;
+  int* Wexp;
   int ozp;
 };
 
