@@ -100,6 +100,12 @@ template <typename T> __device__ __forceinline__ void cp_async_el(T* smem, const
 __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
 }
+// close the group of this thread's copies issued since the last commit
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+// wait until at most N of this thread's committed groups are still in flight
+template <int N> __device__ __forceinline__ void cp_async_wait_group() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
 
 // ------------------------------------------------------------------ tensor-core fragments
 // D += A B on one m16n8k16 tile, bf16 inputs, FP32 accumulators (mma.sync).

@@ -1848,26 +1848,32 @@ template <typename T> __global__ void __launch_bounds__(NT) k_schur(LevelDev<T> 
 // The groups are gathered in one int64 W = sum_u G_u 2^(39-7u) (the last two by
 // rounding right shifts, an error below 2^-53 of the scale), so
 // (E F)_ij = W 2^(e_i + f_j - 53): one conversion and one scaling per entry.
-// 64 x 64 tile per CTA, 8 warps of 32 x 16, fragments loaded with ldmatrix; K
-// (the slices' length kp) in chunks of 32 whose int64 sums add exactly under the
-// per-row scales (|W| <= kp 2^53).
+// 64 x 32 tile per CTA, 8 warps of 16 x 16.  All eight group sums of a warp's
+// tile stay in FP32 registers over the whole K: each is an integer below
+// 10 2^12 K, exact for K <= 384, so the groups are combined into W once per
+// tile (and once per 384 entries of K beyond that) instead of once per chunk.
+// Per K step of 16 the B fragments are loaded once, four slices at a time, and
+// the A slices that pair with them, for the 36 products p + q <= 7.  K is staged in chunks of
+// 32, double-buffered with cp.async.
 constexpr int SRK = 32, SRSA = OZ_S * SRK + 8;   // real Schur: K chunk and slice-row stride
+constexpr int SR_M = 64, SR_N = 32;              // CTA tile
+constexpr int SR_BUF = (SR_M + SR_N) * SRSA;     // one stage of slices (uint16)
+constexpr int SR_FLUSH = 12;                     // chunks between int64 gathers (12 x 32 = 384)
 
-__global__ void __launch_bounds__(NT, 3) k_schur_oz(LevelDev<double> L, const BoxRec<double>* recs) {
+__global__ void __launch_bounds__(NT, 2) k_schur_oz(LevelDev<double> L, const BoxRec<double>* recs) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const BoxRec<double> R = recs[blockIdx.y];
-  const int c = R.c, kp = R.kp, nt = (c + 63) / 64;
-  if ((int)blockIdx.x >= nt * nt) return;
-  const int i0 = (blockIdx.x % nt) * 64, j0 = (blockIdx.x / nt) * 64;
-  const int SA = SRSA;                          // one K chunk of the eight slices per row
-  uint16_t* As = reinterpret_cast<uint16_t*>(smraw);
-  uint16_t* Bs = As + 64 * SA;
-  __shared__ long long rowb[64], colb[64];
-  __shared__ int rexp[64], cexp[64];
+  const int c = R.c, kp = R.kp, ntr = (c + SR_M - 1) / SR_M, ntc = (c + SR_N - 1) / SR_N;
+  if ((int)blockIdx.x >= ntr * ntc) return;
+  const int i0 = (blockIdx.x % ntr) * SR_M, j0 = (blockIdx.x / ntr) * SR_N;
+  const int SA = SRSA;
+  uint16_t* stage = reinterpret_cast<uint16_t*>(smraw);   // two stages: A rows then B rows
+  __shared__ long long rowb[SR_M], colb[SR_N];
+  __shared__ int rexp[SR_M], cexp[SR_N];
   const int nmax = L.nmax, g = L.g;
   const long long nn = (long long)nmax * nmax;
   const int tid = threadIdx.x;
-  if (tid < 64) {
+  if (tid < SR_M) {
     const int i = i0 + tid;
     if (i < c) {
       const int cm = R.cmap[i], s = cm >> 16, pos = cm & 0xffff;
@@ -1875,105 +1881,118 @@ __global__ void __launch_bounds__(NT, 3) k_schur_oz(LevelDev<double> L, const Bo
       rowb[tid] = (long long)u * 25 * nn + pos - (long long)((s / 3) * 5 + s % 3) * nn;
       rexp[tid] = R.Eexp[i];
     }
-  } else if (tid < 128) {
-    const int j = j0 + tid - 64;
+  } else if (tid < SR_M + SR_N) {
+    const int j = j0 + tid - SR_M;
     if (j < c) {
       const int cm = R.cmap[j], s = cm >> 16, pos = cm & 0xffff;
-      colb[tid - 64] = (long long)((s / 3) * 5 + s % 3 + 12) * nn + (long long)pos * nmax;
-      cexp[tid - 64] = R.Fexp[j];
+      colb[tid - SR_M] = (long long)((s / 3) * 5 + s % 3 + 12) * nn + (long long)pos * nmax;
+      cexp[tid - SR_M] = R.Fexp[j];
     }
   }
   const int warp = tid >> 5, lane = tid & 31, gq = lane >> 2, t4 = lane & 3;
-  const int m0 = (warp >> 2) * 32, n0 = (warp & 3) * 16;
-  // ldmatrix row addresses: A tiles (rows m0 + mi*16 + lane%16, k + 8*(lane/16)),
-  // B pair of n8 tiles (rows n0 + 8*(lane/16) + lane%8, k + 8*((lane/8)%2))
+  const int m0 = (warp >> 1) * 16, n0 = (warp & 1) * 16;
   const int a_row = lane & 15, a_k = (lane >> 4) * 8;
   const int b_row = ((lane >> 4) << 3) + (lane & 7), b_k = ((lane >> 3) & 1) * 8;
-  long long W[2][2][4];
-#pragma unroll
-  for (int mi = 0; mi < 2; ++mi)
-#pragma unroll
-    for (int ni = 0; ni < 2; ++ni)
-#pragma unroll
-      for (int e = 0; e < 4; ++e) W[mi][ni][e] = 0;
-  for (int kc = 0; kc < kp; kc += SRK) {
+  // slices of rows i0.. of E and j0.. of F^T, entries kc .. kc + kl of K
+  auto load = [&](int buf, int kc) {
     const int kl = min(SRK, kp - kc), cpr = OZ_S * (kl / 8);   // 16-byte chunks per row
-    __syncthreads();
-    for (int e = tid; e < 128 * cpr; e += NT) {
+    uint16_t* As = stage + buf * SR_BUF;
+    for (int e = tid; e < (SR_M + SR_N) * cpr; e += NT) {
       const int row = e / cpr, rem = e % cpr, sl = rem / (kl / 8), ch = rem % (kl / 8);
-      const bool isA = row < 64;
-      const int rr = isA ? row : row - 64;
-      uint16_t* d = (isA ? As : Bs) + rr * SA + sl * SRK + ch * 8;
-      const int gi = (isA ? i0 : j0) + rr;
+      const bool isA = row < SR_M;
+      const int gi = isA ? i0 + row : j0 + row - SR_M;
+      uint16_t* d = As + row * SA + sl * SRK + ch * 8;
       if (gi < c)
         cp_async16(d, (isA ? R.Esl : R.Fsl) + (size_t)gi * OZ_S * kp + (size_t)sl * kp + kc + ch * 8);
       else
         *reinterpret_cast<uint4*>(d) = make_uint4(0, 0, 0, 0);
     }
-    cp_async_wait_all();
-    __syncthreads();
-    // groups u and u + 1 together: G_u 2^(39-7u) + G_{u+1} 2^(32-7u) =
-    // (G_u 2^7 + G_{u+1}) 2^(32-7u), the bracket exact in int32 (|G| < 2^21)
-#pragma unroll 1
-    for (int u = 0; u < OZ_S; u += 2) {
-      float ca[2][2][4], cb[2][2][4];
+    cp_async_commit();
+  };
+  float acc[OZ_S][2][4];
+  long long W[2][4];
 #pragma unroll
-      for (int mi = 0; mi < 2; ++mi)
+  for (int ni = 0; ni < 2; ++ni)
 #pragma unroll
-        for (int ni = 0; ni < 2; ++ni)
+    for (int e = 0; e < 4; ++e) {
+      W[ni][e] = 0;
 #pragma unroll
-          for (int e = 0; e < 4; ++e) ca[mi][ni][e] = cb[mi][ni][e] = 0.f;
-      for (int p = 0; p <= u + 1; ++p) {
-        const uint16_t* Ab = As + p * SRK;
-        const uint16_t* Bb1 = Bs + (u + 1 - p) * SRK;
-        const uint16_t* Bb0 = Bs + (u - p) * SRK;
-        for (int kk = 0; kk < kl; kk += 16) {
-          uint32_t af[2][4], b1[4];
-#pragma unroll
-          for (int mi = 0; mi < 2; ++mi) ldsm_x4(af[mi], Ab + (m0 + mi * 16 + a_row) * SA + kk + a_k);
-          ldsm_x4(b1, Bb1 + (n0 + b_row) * SA + kk + b_k);
-#pragma unroll
-          for (int mi = 0; mi < 2; ++mi) {
-            mma_bf16(cb[mi][0], af[mi], b1);
-            mma_bf16(cb[mi][1], af[mi], b1 + 2);
-          }
-          if (p <= u) {
-            uint32_t b0[4];
-            ldsm_x4(b0, Bb0 + (n0 + b_row) * SA + kk + b_k);
-#pragma unroll
-            for (int mi = 0; mi < 2; ++mi) {
-              mma_bf16(ca[mi][0], af[mi], b0);
-              mma_bf16(ca[mi][1], af[mi], b0 + 2);
-            }
-          }
-        }
-      }
-      const int sh = 32 - OZ_BITS * u;
-#pragma unroll
-      for (int mi = 0; mi < 2; ++mi)
-#pragma unroll
-        for (int ni = 0; ni < 2; ++ni)
-#pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            const long long gv = (long long)(oz_fint(ca[mi][ni][e]) * 128 + oz_fint(cb[mi][ni][e]));
-            W[mi][ni][e] += sh >= 0 ? (gv << sh) : ((gv + (1LL << (-sh - 1))) >> (-sh));
-          }
+      for (int u = 0; u < OZ_S; ++u) acc[u][ni][e] = 0.f;
     }
-  }
-#pragma unroll
-  for (int mi = 0; mi < 2; ++mi)
+  // W += sum_u G_u 2^(39-7u), groups u and u + 1 as (G_u 2^7 + G_{u+1}) 2^(32-7u)
+  // (exact in int32: |G| < 2^23); then the FP32 sums restart from zero
+  auto gather = [&]() {
 #pragma unroll
     for (int ni = 0; ni < 2; ++ni)
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
-        const int row = m0 + mi * 16 + gq + (e >= 2 ? 8 : 0);
-        const int col = n0 + ni * 8 + 2 * t4 + (e & 1);
-        if (i0 + row < c && j0 + col < c) {
-          const double v = oz_ldexp_int(W[mi][ni][e], rexp[row] + cexp[col] - 53);
-          double* ptr = L.blk + rowb[row] + colb[col];
-          *ptr = *ptr - v;
+        long long w = W[ni][e];
+#pragma unroll
+        for (int u = 0; u < OZ_S; u += 2) {
+          const long long gv = (long long)(oz_fint(acc[u][ni][e]) * 128 + oz_fint(acc[u + 1][ni][e]));
+          const int sh = 32 - OZ_BITS * u;
+          w += sh >= 0 ? (gv << sh) : ((gv + (1LL << (-sh - 1))) >> (-sh));
+          acc[u][ni][e] = acc[u + 1][ni][e] = 0.f;
+        }
+        W[ni][e] = w;
+      }
+  };
+  const int nch = (kp + SRK - 1) / SRK;
+  // the tile of A_CC, prefetched into the idle stage while the last chunk is multiplied
+  double* Cs = reinterpret_cast<double*>(stage + (nch & 1) * SR_BUF);   // SR_M x SR_N, ld SR_M
+  load(0, 0);
+  for (int ci = 0; ci < nch; ++ci) {
+    if (ci + 1 < nch) {
+      load((ci + 1) & 1, (ci + 1) * SRK);
+    } else {
+      if (ci == 0) __syncthreads();   // rowb and colb
+      for (int e = tid; e < SR_M * SR_N; e += NT) {
+        const int row = e % SR_M, col = e / SR_M;
+        if (i0 + row < c && j0 + col < c) cp_async8(Cs + e, L.blk + rowb[row] + colb[col]);
+      }
+      cp_async_commit();
+    }
+    cp_async_wait_group<1>();
+    __syncthreads();
+    const uint16_t* As = stage + (ci & 1) * SR_BUF;
+    const uint16_t* Bs = As + SR_M * SA;
+    const int kl = min(SRK, kp - ci * SRK);
+    for (int kk = 0; kk < kl; kk += 16) {
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {   // slices q = 4h .. 4h + 3 of B, then every A slice p <= 7 - q
+        uint32_t bq[4][4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) ldsm_x4(bq[q], Bs + (n0 + b_row) * SA + (4 * h + q) * SRK + kk + b_k);
+#pragma unroll
+        for (int p = 0; p + 4 * h < OZ_S; ++p) {
+          uint32_t af[4];
+          ldsm_x4(af, As + (m0 + a_row) * SA + p * SRK + kk + a_k);
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+            if (p + 4 * h + q < OZ_S) {
+              mma_bf16(acc[p + 4 * h + q][0], af, bq[q]);
+              mma_bf16(acc[p + 4 * h + q][1], af, bq[q] + 2);
+            }
         }
       }
+    }
+    if ((ci + 1) % SR_FLUSH == 0 && ci + 1 < nch) gather();
+    __syncthreads();   // the stage read here is refilled by the next iteration's load
+  }
+  gather();
+  cp_async_wait_group<0>();
+  __syncthreads();
+#pragma unroll
+  for (int ni = 0; ni < 2; ++ni)
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int row = m0 + gq + (e >= 2 ? 8 : 0);
+      const int col = n0 + ni * 8 + 2 * t4 + (e & 1);
+      if (i0 + row < c && j0 + col < c) {
+        const double v = oz_ldexp_int(W[ni][e], rexp[row] + cexp[col] - 53);
+        L.blk[rowb[row] + colb[col]] = Cs[row + col * SR_M] - v;
+      }
+    }
 }
 
 // Complex factors: Re(E F) = Er Fr^T - Ei Fi^T and Im(E F) = Er Fi^T + Ei Fr^T
@@ -2921,9 +2940,10 @@ rss_status factor_impl(const rss_tree* tree, const rss_params* prm, cudaStream_t
       evs.back().second->start(st);
       if (oz) {
         if constexpr (sizeof(T) == sizeof(double)) {
-          const size_t smem = 2 * 64 * (size_t)SRSA * sizeof(uint16_t);
+          const size_t smem = 2 * (size_t)SR_BUF * sizeof(uint16_t);
           RSS_CUDA(cudaFuncSetAttribute(k_schur_oz, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-          k_schur_oz<<<dim3(ntile * ntile, nrec), NT, smem, st>>>(cur.d, d_recs);
+          const int ntr = (max_c + SR_M - 1) / SR_M, ntc = (max_c + SR_N - 1) / SR_N;
+          k_schur_oz<<<dim3(ntr * ntc, nrec), NT, smem, st>>>(cur.d, d_recs);
         } else {
           const size_t smem = (64 + 32) * (size_t)SCSA * sizeof(uint16_t);
           RSS_CUDA(cudaFuncSetAttribute(k_schur_oz_c, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
