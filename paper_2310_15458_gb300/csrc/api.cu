@@ -330,7 +330,8 @@ rss_status rss_info(const rss_factorization* f, char* buf, size_t len) {
     }
     o << (l ? ", " : "") << "{\"side\": " << L.side << ", \"k_mean\": " << (double)sk / L.k.size()
       << ", \"k_min\": " << kmin << ", \"k_max\": " << kmax << ", \"n_mean\": "
-      << (double)sn / L.n.size() << ", \"n_max\": " << nmax << "}";
+      << (double)sn / L.n.size() << ", \"n_max\": " << nmax << ", \"gpu_ms\": {\"id\": " << L.g_id
+      << ", \"elim\": " << L.g_elim << ", \"schur\": " << L.g_schur << "}}";
   }
   o << "]}";
   std::string s = o.str();

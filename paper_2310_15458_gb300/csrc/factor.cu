@@ -349,14 +349,14 @@ template <typename T, typename S = T> __global__ void __launch_bounds__(NT_ID, 4
         if (ax0 != 0.0) phase = scl(1.0 / ax0, x0);
         const T bt = scl(-alpha, phase);
         beta[k] = bt;
-        s_scale = x0 - bt;
+        s_scale = dv(from_re<T>(1.0), x0 - bt);   // 1 / (x0 - beta), one division
         taus[k] = (alpha + ax0) / alpha;
       }
     }
     __syncthreads();
     if (s_stop) break;
     {
-      const T d = dv(from_re<T>(1.0), s_scale);
+      const T d = s_scale;
       for (int i = k + 1 + tid; i < m; i += blockDim.x) {
         const T v = vbuf[i] * d;
         vbuf[i] = v;
@@ -508,8 +508,14 @@ template <typename T, typename S = T> __global__ void __launch_bounds__(NT_ID) k
   auto cluster_sum = [&](int len, T* out) {
     cl.sync();
     for (int e = tid; e < len; e += blockDim.x) {
+      T v[8];   // the Q (<= 8) remote loads issued together, then added in rank order
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+        if (q < Q) v[q] = cl.map_shared_rank(part + pb * 2 * nmax, q)[e];
       T s = zero<T>();
-      for (int q = 0; q < Q; ++q) s = s + cl.map_shared_rank(part + pb * 2 * nmax, q)[e];
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+        if (q < Q) s = s + v[q];
       out[e] = s;
     }
     pb ^= 1;
@@ -641,14 +647,14 @@ template <typename T, typename S = T> __global__ void __launch_bounds__(NT_ID) k
         if (ax0 != 0.0) phase = scl(1.0 / ax0, x0);
         const T bt = scl(-alpha, phase);
         beta[k] = bt;
-        s_scale = x0 - bt;
+        s_scale = dv(from_re<T>(1.0), x0 - bt);   // 1 / (x0 - beta), one division
         taus[k] = (alpha + ax0) / alpha;
       }
     }
     __syncthreads();
     if (s_stop) break;
     {
-      const T d = dv(from_re<T>(1.0), s_scale);
+      const T d = s_scale;
       for (int i = max(k + 1, r0) + tid; i < r1; i += blockDim.x) {
         const T v = vbuf[i - r0] * d;
         vbuf[i - r0] = v;
@@ -682,6 +688,7 @@ template <typename T, typename S = T> __global__ void __launch_bounds__(NT_ID) k
     cluster_sum(k + nc, u);   // u[0..k): v^H V, u[k..k+nc): raw g for positions k+1..
     // g_c, row k of R, norm downdate (identical in every CTA; own copies of G, Rr)
     const double tau = taus[k];
+    int anyf = 0;
     for (int pos = k + 1 + tid; pos < n; pos += blockDim.x) {
       const int c = perm[pos];
       T gc = u[k + (pos - k - 1)];
@@ -696,9 +703,15 @@ template <typename T, typename S = T> __global__ void __launch_bounds__(NT_ID) k
       Rr[(size_t)k * nmax + c] = r;
       const double nv = norms2[pos] - abs2(r);
       flag[pos] = nv < RECOMPUTE_REL * ref[pos];
+      anyf |= flag[pos];
       norms2[pos] = nv;
     }
-    __syncthreads();
+    // the flags are the same in every CTA of the cluster (same data, same
+    // operations), so all of them skip the re-accumulation together
+    if (!__syncthreads_or(anyf)) {
+      ++k;
+      continue;
+    }
     // re-accumulation of flagged norms: partials over owned rows
     for (int pos = k + 1 + warp; pos < n; pos += nwarp) {
       double t = 0.0;
@@ -907,6 +920,7 @@ __device__ void oz_split_row(const zd* __restrict__ src, int stride, int r, int 
 // (after flagging RSS_ENUMERIC) on a zero pivot.
 template <typename T> __device__ bool lu_pp_block(T* LU, int r, int* piv, int* err) {
   __shared__ int s_piv, s_zero;
+  __shared__ __align__(16) double s_dinv[2];   // 1 / pivot, computed once per step (T = double or zd)
   const int tid = threadIdx.x, bs = blockDim.x, lane = tid & 31, warp = tid >> 5;
   for (int j = 0; j < r; ++j) {
     if (warp == 0) {
@@ -921,7 +935,11 @@ template <typename T> __device__ bool lu_pp_block(T* LU, int r, int* piv, int* e
         const int oi = __shfl_xor_sync(0xffffffffu, mi, d);
         if (om > mx || (om == mx && oi < mi)) { mx = om; mi = oi; }
       }
-      if (lane == 0) { s_piv = mi; s_zero = !(mx > 0.0); }
+      if (lane == 0) {
+        s_piv = mi;
+        s_zero = !(mx > 0.0);
+        if (mx > 0.0) *reinterpret_cast<T*>(s_dinv) = dv(from_re<T>(1.0), LU[mi + (size_t)j * r]);
+      }
     }
     __syncthreads();
     if (s_zero) {
@@ -937,7 +955,7 @@ template <typename T> __device__ bool lu_pp_block(T* LU, int r, int* piv, int* e
       }
     if (tid == 0) piv[j] = p;
     __syncthreads();
-    const T d = dv(from_re<T>(1.0), LU[j + (size_t)j * r]);
+    const T d = *reinterpret_cast<const T*>(s_dinv);
     for (int i = j + 1 + tid; i < r; i += bs) LU[i + (size_t)j * r] = LU[i + (size_t)j * r] * d;
     __syncthreads();
     const int w = r - j - 1;
@@ -1164,7 +1182,7 @@ template <typename T> __host__ __device__ inline size_t elim_lu_sm_bytes(int k, 
   const size_t n = (size_t)k + r;
   const size_t ints = ((n + 2 * (size_t)r) * sizeof(int) + 15) & ~size_t(15);
   const size_t kr = (size_t)k * r, rr = (size_t)r * r;
-  return ints + sizeof(T) * (n * n + kr + (kr > rr ? kr : rr) + rr);
+  return ints + sizeof(T) * (n * n + kr + (kr > rr ? kr : rr) + rr + r);
 }
 
 template <typename T> __global__ void __launch_bounds__(NT, 2) k_elim_lu_sm(ElimArgs<T> a) {
@@ -1181,7 +1199,7 @@ template <typename T> __global__ void __launch_bounds__(NT, 2) k_elim_lu_sm(Elim
   T* Ap = reinterpret_cast<T*>(smraw + (((size_t)(n + 2 * r) * sizeof(int) + 15) & ~size_t(15)));   // n x n
   T* Ts = Ap + (size_t)n * n;                       // k x r
   T* Xs = Ts + (size_t)k * r;                       // k x r: X_SR; later U^{-1} (r x r)
-  T* LU = Xs + (size_t)max(k * r, r * r);           // r x r
+  T* LU = Xs + (size_t)max(k * r, r * r);           // r x r, then r reciprocals of U's diagonal
   T* Ui = Xs;
   T* Li = Ap;                                       // r x r, once A_BB is no longer needed
   __shared__ int nb[9], coff[10], ord[9];
@@ -1235,9 +1253,11 @@ template <typename T> __global__ void __launch_bounds__(NT, 2) k_elim_lu_sm(Elim
   // U^{-1}: rows from the bottom
   for (int e = tid; e < r * r; e += bs) Ui[e] = (e % r == e / r) ? from_re<T>(1.0) : zero<T>();
   for (int e = tid; e < r * r; e += bs) Li[e] = (e % r == e / r) ? from_re<T>(1.0) : zero<T>();
+  T* Dr = LU + (size_t)r * r;   // r reciprocals of the diagonal of U, one division each
+  for (int i = tid; i < r; i += bs) Dr[i] = dv(from_re<T>(1.0), LU[i + (size_t)i * r]);
   __syncthreads();
   for (int i = r - 1; i >= 0; --i) {
-    const T d = dv(from_re<T>(1.0), LU[i + (size_t)i * r]);
+    const T d = Dr[i];
     for (int j = i + tid; j < r; j += bs) Ui[i + (size_t)j * r] = Ui[i + (size_t)j * r] * d;
     __syncthreads();
     const int w = r - i;
@@ -2274,6 +2294,7 @@ constexpr int LB = 32;
 template <typename T> __global__ void __launch_bounds__(1024) k_lu_panel(T* A, int n, int jb, int* piv, int* err) {
   __shared__ double s_mx[32];
   __shared__ int s_mi[32], s_piv, s_zero;
+  __shared__ __align__(16) double s_dinv[2];   // 1 / pivot, one division per step
   const int tid = threadIdx.x, bs = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = bs >> 5;
   const int je = min(n, jb + LB);
   for (int j = jb; j < je; ++j) {
@@ -2298,7 +2319,11 @@ template <typename T> __global__ void __launch_bounds__(1024) k_lu_panel(T* A, i
         const int oi = __shfl_xor_sync(0xffffffffu, mi, d);
         if (om > mx || (om == mx && oi < mi)) { mx = om; mi = oi; }
       }
-      if (lane == 0) { s_piv = mi; s_zero = !(mx > 0.0); }
+      if (lane == 0) {
+        s_piv = mi;
+        s_zero = !(mx > 0.0);
+        if (mx > 0.0) *reinterpret_cast<T*>(s_dinv) = dv(from_re<T>(1.0), A[mi + (size_t)j * n]);
+      }
     }
     __syncthreads();
     if (s_zero) {
@@ -2314,7 +2339,7 @@ template <typename T> __global__ void __launch_bounds__(1024) k_lu_panel(T* A, i
     }
     if (tid == 0) piv[j] = p;
     __syncthreads();
-    const T d = dv(from_re<T>(1.0), A[j + (size_t)j * n]);
+    const T d = *reinterpret_cast<const T*>(s_dinv);
     for (int i = j + 1 + tid; i < n; i += bs) A[i + (size_t)j * n] = A[i + (size_t)j * n] * d;
     __syncthreads();
     const int w = je - j - 1;
@@ -2970,6 +2995,7 @@ rss_status factor_impl(const rss_tree* tree, const rss_params* prm, cudaStream_t
     for (auto& pe : evs) {
       const double ms = pe.second->ms();
       (pe.first == 0 ? f->g_id : pe.first == 1 ? f->g_elim : f->g_schur) += ms;
+      (pe.first == 0 ? info.g_id : pe.first == 1 ? info.g_elim : info.g_schur) += ms;
       (pe.first == 1 ? f->t_elim : pe.first == 2 ? f->t_schur : f->t_gen) += pe.first ? ms : 0.0;
     }
     int herr = 0;

@@ -76,6 +76,7 @@ struct LevelInfo {
   int side;
   std::vector<int32_t> n;   // points per box at level start
   std::vector<int32_t> k;   // skeleton rank per box
+  double g_id = 0, g_elim = 0, g_schur = 0;   // device ms of the level's phases
 };
 
 // Stream-ordered device memory from the library's pool of the current device.
