@@ -406,7 +406,8 @@ void free_factor(rss_factorization* f) {
   if (!f) return;
   f->tag = 0;
   free_matvec(f);
-  f->arena.release();
+  f->arena.release();   // waits for the device
+  pool_free(f->d_slice_mem, 0);
   for (void* p : f->rec_host) std::free(p);
   delete f;
 }

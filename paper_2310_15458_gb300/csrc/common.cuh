@@ -131,6 +131,9 @@ __device__ __forceinline__ void neg_bf16x2(uint32_t* a) {
 }
 
 // ------------------------------------------------------------------ digit slices, integer only
+constexpr int OZ_S = 8;      // digit slices per operand
+constexpr int OZ_BITS = 7;   // bits per slice
+
 // A vector x_0..x_{n-1} with max |x| = m 2^e (m in [0.5, 1)) is written as
 // x_l = 2^e sum_{p<8} d_{p,l} 2^{-7(p+1)} with signed 7-bit digits (|d_0| <= 128,
 // |d_p| <= 64), every digit exact in bf16.  These helpers do it with integer
@@ -181,6 +184,36 @@ __device__ __forceinline__ void oz_digits2(long long X0, long long X1, uint32_t*
 // reading the mantissa (one FP32 add and one integer add)
 __device__ __forceinline__ int oz_fint(float g) {
   return __float_as_int(g + 12582912.0f) - 0x4B400000;
+}
+
+// ------------------------------------------------------------------ E and F on the tensor cores
+// One vector x_0..x_{len-1} (x_l = val(l)) shared by G consecutive lanes, cut
+// into OZ_S signed 7-bit digit slices as oz_split_row does: 2^e with e the
+// exponent of max |x_l|, x_l 2^(56-e) rounded to an integer, digits stored at
+// dst[p * ldd + l] for l < lenp (zeros past len).  Every lane of the warp calls
+// it (the maximum is a shuffle reduction); inactive groups pass len = 0 and
+// store = false.
+template <int G, typename VF>
+__device__ __forceinline__ void oz_split_vec(VF val, int len, int lenp, uint16_t* dst, int ldd, int* eout,
+                                             bool store) {
+  // integer operations only (the FP64 pipe is the scarce unit)
+  const int gl = threadIdx.x & (G - 1);
+  unsigned long long mk = 0;
+  for (int l = gl; l < len; l += G) mk = max(mk, oz_abs_bits(val(l)));
+#pragma unroll
+  for (int d = G / 2; d > 0; d >>= 1)
+    mk = max(mk, (unsigned long long)__shfl_xor_sync(0xffffffffu, (long long)mk, d));
+  if (!store) return;
+  const int eb = oz_emax_b(mk);
+  if (gl == 0) *eout = mk ? eb - 1022 : 0;
+  for (int l = 2 * gl; l < lenp; l += 2 * G) {
+    const long long X0 = l < len ? oz_scaled_int(val(l), eb) : 0;
+    const long long X1 = l + 1 < len ? oz_scaled_int(val(l + 1), eb) : 0;
+    uint32_t dg[OZ_S];
+    oz_digits2(X0, X1, dg);
+#pragma unroll
+    for (int p = 0; p < OZ_S; ++p) *reinterpret_cast<uint32_t*>(dst + (size_t)p * ldd + l) = dg[p];
+  }
 }
 
 // W 2^s as a double, W an exact integer (|W| < 2^63): one conversion, the

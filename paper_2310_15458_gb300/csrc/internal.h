@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -61,8 +62,18 @@ template <typename T> struct BoxRec {
   int ozp;
 };
 
-constexpr int OZ_S = 8;      // digit slices per operand
-constexpr int OZ_BITS = 7;   // bits per slice
+
+// Digit slices of the two large blocks of a real box record, for the
+// tensor-core sweeps with many right-hand sides (built on first use): the rows
+// of E (c rows, K = r) and the rows of F = (F^T)^T (r rows, K = c), each row cut
+// into OZ_S bf16 digit slices under one power-of-two scale over its K entries.
+struct SliceRec {
+  uint16_t* Esl;   // c x OZ_S x kp: row i at Esl + i * OZ_S * kp, slice p at + p * kp
+  int* Eexp;       // c row scales
+  uint16_t* Fsl;   // r x OZ_S x cp
+  int* Fexp;       // r row scales
+  int kp, cp;      // r and c rounded up to 16 (zero padding)
+};
 
 struct Batch {
   int side;       // box grid side of the level
@@ -123,6 +134,12 @@ struct rss_factorization {
   int* d_top_piv = nullptr;
   int* d_top_idx = nullptr;            // tree indices
   void* d_top_inv = nullptr;           // ntop x ntop: A_top^{-1}, applied by the solve
+  // slices of E and F for the tensor-core sweeps (real factors), built by the
+  // first solve that uses them: one pool block, one SliceRec array per batch
+  std::mutex slice_mu;
+  bool slices_ready = false;
+  void* d_slice_mem = nullptr;
+  std::vector<SliceRec*> d_slices;
   // wall times (ms, host clock around each synchronised phase) for rss_info
   double t_gen = 0, t_id = 0, t_elim = 0, t_schur = 0, t_merge = 0, t_top = 0, t_total = 0;
   // device times (ms, CUDA events on the factor's stream), algorithmic real

@@ -395,9 +395,150 @@ __device__ __forceinline__ size_t tc_smem_head() {
   return (size_t)(TCM + TCN) * TSA * sizeof(uint16_t);
 }
 
+// Slices of the rows of E (K = r), 64 rows per CTA, four lanes per row.
+__global__ void __launch_bounds__(TC_NT) k_slice_e(const BoxRec<double>* __restrict__ recs,
+                                                   const SliceRec* __restrict__ sl) {
+  const BoxRec<double> R = recs[blockIdx.x];
+  const SliceRec S = sl[blockIdx.x];
+  const int i = blockIdx.y * 64 + (int)threadIdx.x / 4, c = R.c, r = R.r;
+  if (blockIdx.y * 64 >= c) return;
+  const bool act = i < c;
+  const double* E = R.E;
+  oz_split_vec<4>([&](int l) { return E[i + (size_t)l * c]; }, act ? r : 0, S.kp,
+                  S.Esl + (size_t)(act ? i : 0) * OZ_S * S.kp, S.kp, S.Eexp + (act ? i : 0), act);
+}
+
+// Slices of the rows of F (columns of F^T, K = c), one warp per row.
+__global__ void __launch_bounds__(TC_NT) k_slice_f(const BoxRec<double>* __restrict__ recs,
+                                                   const SliceRec* __restrict__ sl) {
+  const BoxRec<double> R = recs[blockIdx.x];
+  const SliceRec S = sl[blockIdx.x];
+  const int j = blockIdx.y * (TC_NT / 32) + (int)threadIdx.x / 32, c = R.c, r = R.r;
+  if (blockIdx.y * (TC_NT / 32) >= r) return;
+  const bool act = j < r;
+  const double* Fc = R.Ft + (size_t)(act ? j : 0) * c;
+  oz_split_vec<32>([&](int l) { return Fc[l]; }, act ? c : 0, S.cp, S.Fsl + (size_t)(act ? j : 0) * OZ_S * S.cp,
+                   S.cp, S.Fexp + (act ? j : 0), act);
+}
+
+// C(i, q) receives sum_l A(i, l) B(l, q) for i < M, q < TCN, with the rows of A
+// given as precomputed slices (row i at Asl + i * OZ_S * ka, scale 2^Aexp[i],
+// zero past K) and B(l, q) = bval(l, q) in FP64, cut here under one scale per
+// column over the whole K.  With both scales fixed along K, the eight group
+// sums stay exact in FP32 for 384 entries of K and are gathered into one int64
+// per entry (|W| <= K 2^53, K < 1024); K is staged in chunks of TCK.  Every
+// thread of the CTA calls it.
+template <typename BF, typename OF>
+__device__ void tc_gemm_sl(int M, int ka, const uint16_t* __restrict__ Asl, const int* __restrict__ Aexp, BF bval,
+                           OF cout, uint16_t* As, uint16_t* Bs, int* rexp, int* cexp, int* ceb) {
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, gq = lane >> 2, t4 = lane & 3;
+  const int m0 = (warp >> 1) * 16, n0 = (warp & 1) * 16;
+  const int a_row = lane & 15, a_k = (lane >> 4) * 8;
+  const int b_row = ((lane >> 4) << 3) + (lane & 7), b_k = ((lane >> 3) & 1) * 8;
+  {   // column scales of B over the whole K (zero past it)
+    const int col = tid >> 3, gl = tid & 7;
+    unsigned long long mk = 0;
+    for (int l = gl; l < ka; l += 8) mk = max(mk, oz_abs_bits(bval(l, col)));
+#pragma unroll
+    for (int d = 1; d < 8; d <<= 1)
+      mk = max(mk, (unsigned long long)__shfl_xor_sync(0xffffffffu, (long long)mk, d));
+    const int eb = oz_emax_b(mk);
+    if (gl == 0) {
+      ceb[col] = eb;
+      cexp[col] = mk ? eb - 1022 : 0;
+    }
+  }
+  for (int mt = 0; mt < M; mt += TCM) {
+    float acc[OZ_S][2][4];
+    long long W[2][4];
+#pragma unroll
+    for (int ni = 0; ni < 2; ++ni)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        W[ni][e] = 0;
+#pragma unroll
+        for (int u = 0; u < OZ_S; ++u) acc[u][ni][e] = 0.f;
+      }
+    auto gather = [&]() {
+#pragma unroll
+      for (int ni = 0; ni < 2; ++ni)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          long long w = W[ni][e];
+#pragma unroll
+          for (int u = 0; u < OZ_S; u += 2) {
+            const long long gv = (long long)(oz_fint(acc[u][ni][e]) * 128 + oz_fint(acc[u + 1][ni][e]));
+            const int sh = 32 - OZ_BITS * u;
+            w += sh >= 0 ? (gv << sh) : ((gv + (1LL << (-sh - 1))) >> (-sh));
+            acc[u][ni][e] = acc[u + 1][ni][e] = 0.f;
+          }
+          W[ni][e] = w;
+        }
+    };
+    for (int kc = 0; kc < ka; kc += TCK) {
+      const int kl = min(TCK, ka - kc), cpr = OZ_S * (kl / 8);   // ka is a multiple of 16
+      __syncthreads();   // the previous chunk is consumed (and the column scales are visible)
+      for (int e = tid; e < TCM * cpr; e += TC_NT) {   // rows of A: slices p, entries kc .. kc + kl
+        const int row = e / cpr, rem = e % cpr, p = rem / (kl / 8), ch = rem % (kl / 8);
+        uint16_t* d = As + row * TSA + p * TCK + ch * 8;
+        if (mt + row < M)
+          cp_async16(d, Asl + (size_t)(mt + row) * OZ_S * ka + (size_t)p * ka + kc + ch * 8);
+        else
+          *reinterpret_cast<uint4*>(d) = make_uint4(0, 0, 0, 0);
+      }
+      {   // columns of B: 32 columns x 8 lanes, two entries per lane and step
+        const int col = tid >> 3, gl = tid & 7, eb = ceb[col];
+        uint16_t* dst = Bs + col * TSA;
+        for (int l = 2 * gl; l < TCK; l += 16) {
+          const long long X0 = l < kl ? oz_scaled_int(bval(kc + l, col), eb) : 0;
+          const long long X1 = l + 1 < kl ? oz_scaled_int(bval(kc + l + 1, col), eb) : 0;
+          uint32_t dg[8];
+          oz_digits2(X0, X1, dg);
+#pragma unroll
+          for (int p = 0; p < 8; ++p) *reinterpret_cast<uint32_t*>(dst + p * TCK + l) = dg[p];
+        }
+      }
+      cp_async_wait_all();
+      __syncthreads();
+      for (int kk = 0; kk < kl; kk += 16) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {   // slices q = 4h .. 4h + 3 of B, then every A slice p <= 7 - q
+          uint32_t bq[4][4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) ldsm_x4(bq[q], Bs + (n0 + b_row) * TSA + (4 * h + q) * TCK + kk + b_k);
+#pragma unroll
+          for (int p = 0; p + 4 * h < OZ_S; ++p) {
+            uint32_t af[4];
+            ldsm_x4(af, As + (m0 + a_row) * TSA + p * TCK + kk + a_k);
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+              if (p + 4 * h + q < OZ_S) {
+                mma_bf16(acc[p + 4 * h + q][0], af, bq[q]);
+                mma_bf16(acc[p + 4 * h + q][1], af, bq[q] + 2);
+              }
+          }
+        }
+      }
+      if ((kc / TCK + 1) % 12 == 0 && kc + TCK < ka) gather();   // 12 chunks: 384 entries of K
+    }
+    gather();
+    if (tid < TCM) rexp[tid] = mt + tid < M ? Aexp[mt + tid] : 0;
+    __syncthreads();
+#pragma unroll
+    for (int ni = 0; ni < 2; ++ni)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int row = m0 + gq + (e >= 2 ? 8 : 0), col = n0 + ni * 8 + 2 * t4 + (e & 1);
+        if (mt + row < M) cout(mt + row, col, oz_ldexp_int(W[ni][e], rexp[row] + cexp[col] - 53));
+      }
+  }
+  __syncthreads();
+}
+
 // Upward sweep of one box for TCN right-hand-side columns:
 // t = b_R - T^* b_S, b_R = L^{-1} P t, b_C -= E b_R.
-__global__ void __launch_bounds__(TC_NT, 2) k_up_tc(const BoxRec<double>* __restrict__ recs, double* __restrict__ x,
+__global__ void __launch_bounds__(TC_NT, 2) k_up_tc(const BoxRec<double>* __restrict__ recs,
+                                                    const SliceRec* __restrict__ sl, double* __restrict__ x,
                                                     int64_t N, int nrhs) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const BoxRec<double> R = recs[blockIdx.x];
@@ -408,7 +549,7 @@ __global__ void __launch_bounds__(TC_NT, 2) k_up_tc(const BoxRec<double>* __rest
   double* bS = reinterpret_cast<double*>(smraw + tc_smem_head());   // k x TCN
   double* t = bS + (size_t)k * TCN;                                  // r x TCN
   double* u = t + (size_t)r * TCN;                                   // r x TCN
-  __shared__ int rexp[TCM], cexp[TCN];
+  __shared__ int rexp[TCM], cexp[TCN], ceb[TCN];
   const int tid = threadIdx.x, bs = blockDim.x;
   double* xq = x + (int64_t)q0 * N;
   for (int e = tid; e < k * TCN; e += bs) {
@@ -430,20 +571,27 @@ __global__ void __launch_bounds__(TC_NT, 2) k_up_tc(const BoxRec<double>* __rest
     const int j = e / TCN, q = e % TCN;
     if (q < nq) xq[R.idxR[j] + (int64_t)q * N] = u[e];
   }
-  tc_gemm32(c, r, [&](int i, int l) { return E[i + (size_t)l * c]; }, [&](int l, int q) { return u[l * TCN + q]; },
-            [&](int i, int q, double v) {
-              if (q < nq) {
-                const int64_t gi = R.idxC[i] + (int64_t)q * N;
-                xq[gi] = xq[gi] - v;
-              }
-            },
-            As, Bs, rexp, cexp);
+  auto sub_c = [&](int i, int q, double v) {
+    if (q < nq) {
+      const int64_t gi = R.idxC[i] + (int64_t)q * N;
+      xq[gi] = xq[gi] - v;
+    }
+  };
+  if (sl != nullptr) {
+    const SliceRec S = sl[blockIdx.x];
+    tc_gemm_sl(c, S.kp, S.Esl, S.Eexp, [&](int l, int q) { return l < r ? u[l * TCN + q] : 0.0; }, sub_c, As, Bs,
+               rexp, cexp, ceb);
+  } else {
+    tc_gemm32(c, r, [&](int i, int l) { return E[i + (size_t)l * c]; }, [&](int l, int q) { return u[l * TCN + q]; },
+              sub_c, As, Bs, rexp, cexp);
+  }
 }
 
 // Downward sweep of one box for TCN columns: z = y_R - F y_C, y_R = U^{-1} z,
 // y_S -= T y_R.
 __global__ void __launch_bounds__(TC_NT, 2) k_down_tc(const BoxRec<double>* __restrict__ recs,
-                                                      double* __restrict__ x, int64_t N, int nrhs) {
+                                                      const SliceRec* __restrict__ sl, double* __restrict__ x,
+                                                      int64_t N, int nrhs) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const BoxRec<double> R = recs[blockIdx.x];
   const int k = R.k, r = R.r, c = R.c;
@@ -452,7 +600,7 @@ __global__ void __launch_bounds__(TC_NT, 2) k_down_tc(const BoxRec<double>* __re
   uint16_t* Bs = As + TCM * TSA;
   double* z = reinterpret_cast<double*>(smraw + tc_smem_head());   // r x TCN
   double* yR = z + (size_t)r * TCN;                                 // r x TCN
-  __shared__ int rexp[TCM], cexp[TCN];
+  __shared__ int rexp[TCM], cexp[TCN], ceb[TCN];
   const int tid = threadIdx.x, bs = blockDim.x;
   double* xq = x + (int64_t)q0 * N;
   for (int e = tid; e < r * TCN; e += bs) {
@@ -463,9 +611,16 @@ __global__ void __launch_bounds__(TC_NT, 2) k_down_tc(const BoxRec<double>* __re
   const double* __restrict__ Ui = R.Ui;
   const double* __restrict__ Tm = R.Tm;
   const int* __restrict__ idxC = R.idxC;
-  tc_gemm32(r, c, [&](int j, int i) { return Ft[i + (size_t)j * c]; },
-            [&](int i, int q) { return q < nq ? xq[idxC[i] + (int64_t)q * N] : 0.0; },
-            [&](int j, int q, double v) { z[j * TCN + q] -= v; }, As, Bs, rexp, cexp);
+  if (sl != nullptr) {
+    const SliceRec S = sl[blockIdx.x];
+    tc_gemm_sl(r, S.cp, S.Fsl, S.Fexp,
+               [&](int i, int q) { return (i < c && q < nq) ? xq[idxC[i] + (int64_t)q * N] : 0.0; },
+               [&](int j, int q, double v) { z[j * TCN + q] -= v; }, As, Bs, rexp, cexp, ceb);
+  } else {
+    tc_gemm32(r, c, [&](int j, int i) { return Ft[i + (size_t)j * c]; },
+              [&](int i, int q) { return q < nq ? xq[idxC[i] + (int64_t)q * N] : 0.0; },
+              [&](int j, int q, double v) { z[j * TCN + q] -= v; }, As, Bs, rexp, cexp);
+  }
   tc_gemm32(r, r, [&](int j, int l) { return Ui[j + (size_t)l * r]; }, [&](int l, int q) { return z[l * TCN + q]; },
             [&](int j, int q, double v) { yR[j * TCN + q] = v; }, As, Bs, rexp, cexp);
   for (int e = tid; e < r * TCN; e += bs) {
@@ -681,8 +836,90 @@ rss_status sweeps(const rss_factorization* f, T* x, int64_t N, int nrhs, cudaStr
 
 // Real factors with at least TCN right-hand sides: the tensor-core sweeps; the
 // top block as in sweeps<double, 8>.
-rss_status sweeps_tc(const rss_factorization* f, double* x, int64_t N, int nrhs, cudaStream_t st, void* ws) {
+// The digit slices of E and F for the tensor-core sweeps: built once per factor
+// by the first solve that needs them (on its stream, which it then waits for),
+// kept until the factor is freed.  Boxes with c >= 1024 keep the per-chunk
+// products (the int64 sums of tc_gemm_sl need K < 1024).
+bool slices_fit(const rss_factorization* f) {
+  for (const Batch& b : f->batches)
+    if (b.max_c >= 1024) return false;
+  return true;
+}
+
+rss_status ensure_slices(rss_factorization* f, cudaStream_t st) {
+  std::lock_guard<std::mutex> lk(f->slice_mu);
+  if (f->slices_ready) return RSS_OK;
+  auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
+  size_t total = 0;
+  for (size_t bi = 0; bi < f->batches.size(); ++bi) {
+    const Batch& b = f->batches[bi];
+    const BoxRec<double>* hr = static_cast<const BoxRec<double>*>(f->rec_host[bi]);
+    total += al(sizeof(SliceRec) * b.nrec);
+    for (int q = 0; q < b.nrec; ++q) {
+      const size_t kp = (hr[q].r + 15) & ~15, cp = (hr[q].c + 15) & ~15;
+      total += al(sizeof(uint16_t) * hr[q].c * OZ_S * kp) + al(sizeof(int) * hr[q].c) +
+               al(sizeof(uint16_t) * hr[q].r * OZ_S * cp) + al(sizeof(int) * hr[q].r);
+    }
+  }
+  char* base = nullptr;
+  RSS_CUDA(pool_malloc(reinterpret_cast<void**>(&base), total, st));
+  char* p = base;
+  auto take = [&](size_t b) {
+    char* q = p;
+    p += al(b);
+    return q;
+  };
+  std::vector<SliceRec*> recs(f->batches.size());
+  std::vector<SliceRec> hs;
+  for (size_t bi = 0; bi < f->batches.size(); ++bi) {
+    const Batch& b = f->batches[bi];
+    const BoxRec<double>* hr = static_cast<const BoxRec<double>*>(f->rec_host[bi]);
+    recs[bi] = reinterpret_cast<SliceRec*>(take(sizeof(SliceRec) * b.nrec));
+    hs.assign(b.nrec, SliceRec{});
+    for (int q = 0; q < b.nrec; ++q) {
+      SliceRec& S = hs[q];
+      S.kp = (hr[q].r + 15) & ~15;
+      S.cp = (hr[q].c + 15) & ~15;
+      S.Esl = reinterpret_cast<uint16_t*>(take(sizeof(uint16_t) * hr[q].c * OZ_S * S.kp));
+      S.Eexp = reinterpret_cast<int*>(take(sizeof(int) * hr[q].c));
+      S.Fsl = reinterpret_cast<uint16_t*>(take(sizeof(uint16_t) * hr[q].r * OZ_S * S.cp));
+      S.Fexp = reinterpret_cast<int*>(take(sizeof(int) * hr[q].r));
+    }
+    cudaError_t e = cudaMemcpyAsync(recs[bi], hs.data(), sizeof(SliceRec) * b.nrec, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);   // hs is reused for the next batch
+    if (e == cudaSuccess) {
+      const BoxRec<double>* dr = static_cast<const BoxRec<double>*>(b.d_recs);
+      k_slice_e<<<dim3(b.nrec, cdiv(b.max_c, 64)), TC_NT, 0, st>>>(dr, recs[bi]);
+      k_slice_f<<<dim3(b.nrec, cdiv(b.max_r, TC_NT / 32)), TC_NT, 0, st>>>(dr, recs[bi]);
+      e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) {
+      cudaStreamSynchronize(st);
+      pool_free(base, st);
+      rss_set_error(std::string("rss_solve: slice cache: ") + cudaGetErrorString(e));
+      return RSS_ECUDA;
+    }
+  }
+  RSS_CUDA(cudaStreamSynchronize(st));   // other streams may use the slices from here on
+  f->d_slice_mem = base;
+  f->d_slices = recs;
+  f->slices_ready = true;
+  return RSS_OK;
+}
+
+// may_build: the caller allows the one-time allocation of the slice cache
+// (rss_solve_noalloc does not; it uses the cache only when it already exists).
+rss_status sweeps_tc(const rss_factorization* f, double* x, int64_t N, int nrhs, cudaStream_t st, void* ws,
+                     bool may_build) {
   constexpr int RC = 8;
+  bool sl = slices_fit(f);
+  if (sl && may_build) {
+    const rss_status s = ensure_slices(const_cast<rss_factorization*>(f), st);
+    if (s != RSS_OK) return s;
+  } else if (sl) {
+    std::lock_guard<std::mutex> lk(const_cast<rss_factorization*>(f)->slice_mu);
+    sl = f->slices_ready;
+  }
   const unsigned nz = cdiv(nrhs, TCN);
   const SweepWs w = sweep_ws<double>(f, nrhs, RC);
   double* topz = reinterpret_cast<double*>(static_cast<char*>(ws) + w.topz_off);
@@ -690,13 +927,15 @@ rss_status sweeps_tc(const rss_factorization* f, double* x, int64_t N, int nrhs,
   RSS_CUDA(cudaFuncSetAttribute(k_down_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
   RSS_CUDA(cudaFuncSetAttribute(k_top_gemv<double, RC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
   const size_t head = (size_t)(TCM + TCN) * TSA * sizeof(uint16_t);
-  for (const Batch& b : f->batches) {
+  for (size_t bi = 0; bi < f->batches.size(); ++bi) {
+    const Batch& b = f->batches[bi];
     const size_t sm = head + sizeof(double) * (size_t)(b.max_k + 2 * b.max_r) * TCN;
     if (sm > 220 * 1024) {
       rss_set_error("rss_solve: box too large for the tensor-core sweep");
       return RSS_EINVAL;
     }
-    k_up_tc<<<dim3(b.nrec, nz), TC_NT, sm, st>>>(static_cast<const BoxRec<double>*>(b.d_recs), x, N, nrhs);
+    k_up_tc<<<dim3(b.nrec, nz), TC_NT, sm, st>>>(static_cast<const BoxRec<double>*>(b.d_recs),
+                                                  sl ? f->d_slices[bi] : nullptr, x, N, nrhs);
     RSS_LAUNCHED();
   }
   if (f->ntop > 0) {
@@ -713,9 +952,11 @@ rss_status sweeps_tc(const rss_factorization* f, double* x, int64_t N, int nrhs,
         static_cast<const double*>(f->d_top_inv), f->d_top_idx, f->ntop, topz, x, N, nrhs);
     RSS_LAUNCHED();
   }
-  for (auto it = f->batches.rbegin(); it != f->batches.rend(); ++it) {
-    const size_t sm = head + sizeof(double) * (size_t)(2 * it->max_r) * TCN;
-    k_down_tc<<<dim3(it->nrec, nz), TC_NT, sm, st>>>(static_cast<const BoxRec<double>*>(it->d_recs), x, N, nrhs);
+  for (size_t bi = f->batches.size(); bi-- > 0;) {
+    const Batch& b = f->batches[bi];
+    const size_t sm = head + sizeof(double) * (size_t)(2 * b.max_r) * TCN;
+    k_down_tc<<<dim3(b.nrec, nz), TC_NT, sm, st>>>(static_cast<const BoxRec<double>*>(b.d_recs),
+                                                    sl ? f->d_slices[bi] : nullptr, x, N, nrhs);
     RSS_LAUNCHED();
   }
   return RSS_OK;
@@ -726,9 +967,10 @@ bool use_tc(const rss_factorization* f, int64_t nrhs) {
 }
 
 template <typename T>
-rss_status run_sweeps(const rss_factorization* f, T* x, int64_t N, int64_t nrhs, cudaStream_t st, void* ws) {
+rss_status run_sweeps(const rss_factorization* f, T* x, int64_t N, int64_t nrhs, cudaStream_t st, void* ws,
+                      bool may_build = true) {
   if constexpr (sizeof(T) == sizeof(double))
-    if (use_tc(f, nrhs)) return sweeps_tc(f, x, N, (int)nrhs, st, ws);
+    if (use_tc(f, nrhs)) return sweeps_tc(f, x, N, (int)nrhs, st, ws, may_build);
   const int rc = rhs_chunk(nrhs);
   return rc == 1 ? sweeps<T, 1>(f, x, N, (int)nrhs, st, ws)
          : rc == 4 ? sweeps<T, 4>(f, x, N, (int)nrhs, st, ws)
@@ -840,7 +1082,7 @@ rss_status solve_in_scratch(const rss_factorization* f, T* b, int64_t nrhs, int6
   k_perm_in<T><<<grid, NT, 0, st>>>(b, ldb, x, N, (int)nrhs, f->d_user_to_tree);
   RSS_LAUNCHED();
   const size_t xb = (sizeof(T) * (size_t)N * nrhs + 255) & ~size_t(255);
-  const rss_status s = run_sweeps<T>(f, x, N, nrhs, st, reinterpret_cast<char*>(x) + xb);
+  const rss_status s = run_sweeps<T>(f, x, N, nrhs, st, reinterpret_cast<char*>(x) + xb, false);
   if (s != RSS_OK) return s;
   k_perm_out<T><<<grid, NT, 0, st>>>(b, ldb, x, N, (int)nrhs, f->d_user_to_tree);
   RSS_LAUNCHED();

@@ -59,3 +59,30 @@ def test_noalloc_rejects_what_it_cannot_hold(P):
     assert bool(torch.all(b == 1.0))
     with pytest.raises(TypeError):
         P.rss_solve_noalloc(f, np.ones(side * side))
+
+
+def test_many_rhs_before_and_after_the_slice_cache(P):
+    """With 32 or more right-hand sides the sweeps run on the tensor cores.  The
+    digit slices of E and F are cached by the first rss_solve that needs them;
+    rss_solve_noalloc never builds that cache, so before it exists it cuts the
+    factor blocks chunk by chunk, and afterwards it reads the cache.  Both forms
+    agree with one-column FP64 solves to 1e-12 and with each other."""
+    side = 64
+    tree = P.rss_build_tree(W.grid_points(side), 64)
+    f = P.rss_factor(tree, kind=0, eps=1e-6, h=1.0 / side)
+    b = W.gaussian_rhs(side * side, 36, False, 12)
+    before = _cols(b)
+    P.rss_solve_noalloc(f, before)           # no cache yet: per-chunk products
+    after = _cols(b)
+    P.rss_solve(f, after)                    # builds the cache, then uses it
+    again = _cols(b)
+    P.rss_solve_noalloc(f, again)            # the cache now exists
+    torch.cuda.synchronize()
+    before, after, again = before.cpu().numpy(), after.cpu().numpy(), again.cpu().numpy()
+    assert np.array_equal(after, again)
+    assert np.linalg.norm(before - after) <= 1e-12 * np.linalg.norm(after)
+    for j in (0, 31, 35):
+        xj = torch.from_numpy(b[:, j].copy()).cuda()
+        P.rss_solve(f, xj)
+        xj = xj.cpu().numpy()
+        assert np.linalg.norm(after[:, j] - xj) <= 1e-12 * np.linalg.norm(xj)
