@@ -199,6 +199,7 @@ rss_status rss_factor(const rss_tree* tree, const rss_params* p, void* stream, r
   if (!(p->eps >= 0) || p->eps >= 1) return fail(RSS_EINVAL, "rss_factor: eps must be in [0, 1)");
   if (p->kind < RSS_LAPLACE || p->kind > RSS_HELMHOLTZ_LS) return fail(RSS_EINVAL, "rss_factor: unknown kernel kind");
   if (p->diag_rule != 0 && p->diag_rule != 1) return fail(RSS_EINVAL, "rss_factor: diag_rule must be 0 or 1");
+  if (p->schur_path < 0 || p->schur_path > 2) return fail(RSS_EINVAL, "rss_factor: schur_path must be 0, 1 or 2");
   if ((p->kind == RSS_HELMHOLTZ || p->kind == RSS_HELMHOLTZ_LS) && !(p->kappa > 0))
     return fail(RSS_EINVAL, "rss_factor: the Helmholtz kernels need kappa > 0");
   if (p->diag_rule == 1 && (p->kind == RSS_TEST_POLY || p->kind == RSS_TEST_RPOLY))

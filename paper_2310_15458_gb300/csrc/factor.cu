@@ -1986,6 +1986,148 @@ __global__ void __launch_bounds__(NT, 2) k_schur_oz(LevelDev<double> L, const Bo
     }
 }
 
+// The same update on the 5th-generation tensor cores (tcgen05): one thread
+// issues the slice products into tensor memory.  A CTA of 256 threads owns 128
+// rows (of E) x 32 columns (rows of F^T) of A_CC; group sum G_u (u = p + q)
+// accumulates in TMEM columns 32u .. 32u + 31 (256 columns, two CTAs per SM) in
+// FP32 over the whole K (exact for kp <= 384, checked by the host); per K step
+// of 16 it takes eight products, A slice p against the stacked B slices
+// 0 .. 7 - p (N = 32 (8 - p)).  K is staged
+// in chunks of 32 in the no-swizzle K-major layout of 8-row x 16-byte core
+// matrices: slice p, row m, entries 8g .. 8g + 7 of the chunk at
+// p * rows * 64 + ((m / 8) * 4 + g) * 128 + (m % 8) * 16 bytes (LBO 128, SBO 512).
+// After the last chunk every thread reads the eight groups of 16 columns of its
+// row (warps w and w + 4 share TMEM lanes 32 (w % 4) ..) with
+// tcgen05.ld, gathers each entry into one int64 as k_schur_oz does (same integer
+// arithmetic, same result) and subtracts it from the entries of A_CC, which it
+// loaded while the last products ran.  A barrier wait that runs out sets
+// RSS_ETIMEOUT in *err; the CTA then frees its tensor memory and returns.
+constexpr int ST_M = 128, ST_N = 32, ST_KC = 32, ST_NT = 256;
+constexpr int ST_A = OZ_S * ST_M * ST_KC * 2;   // bytes of one chunk of A slices (64 KB)
+constexpr int ST_B = OZ_S * ST_N * ST_KC * 2;   // 16 KB
+constexpr uint32_t ST_TMEM_COLS = OZ_S * ST_N;  // 256
+constexpr long long ST_POLLS = 1LL << 22;
+
+__global__ void __launch_bounds__(ST_NT, 2) k_schur_tc(LevelDev<double> L, const BoxRec<double>* recs, int* err) {
+  extern __shared__ __align__(1024) unsigned char smraw[];
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t s_tmem;
+  __shared__ long long colb[ST_N];
+  __shared__ int cexp[ST_N];
+  const BoxRec<double> R = recs[blockIdx.y];
+  const int c = R.c, kp = R.kp, ntr = (c + ST_M - 1) / ST_M, ntc = (c + ST_N - 1) / ST_N;
+  if ((int)blockIdx.x >= ntr * ntc) return;
+  const int i0 = (blockIdx.x % ntr) * ST_M, j0 = (blockIdx.x / ntr) * ST_N;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int quarter = warp & 3, half = warp >> 2;   // TMEM lanes 32 quarter .., columns 16 half ..
+  unsigned char* As = smraw;
+  unsigned char* Bs = smraw + ST_A;
+  const int nmax = L.nmax, g = L.g;
+  const long long nn = (long long)nmax * nmax;
+  const int i = i0 + 32 * quarter + lane;   // this thread's row of the tile (TMEM lane)
+  long long rowb = 0;
+  int rexp = 0;
+  if (i < c) {
+    const int cm = R.cmap[i], s = cm >> 16, pos = cm & 0xffff;
+    const int u = nbr_box(R.box, g, s % 3 - 1, s / 3 - 1);
+    rowb = (long long)u * 25 * nn + pos - (long long)((s / 3) * 5 + s % 3) * nn;
+    rexp = R.Eexp[i];
+  }
+  if (tid < ST_N) {
+    const int j = j0 + tid;
+    colb[tid] = 0;
+    cexp[tid] = 0;
+    if (j < c) {
+      const int cm = R.cmap[j], s = cm >> 16, pos = cm & 0xffff;
+      colb[tid] = (long long)((s / 3) * 5 + s % 3 + 12) * nn + (long long)pos * nmax;
+      cexp[tid] = R.Fexp[j];
+    }
+  }
+  if (tid == 0) mbar_init(&mbar, 1);
+  if (warp == 0) tmem_alloc(&s_tmem, ST_TMEM_COLS);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = s_tmem;
+  const int nch = (kp + ST_KC - 1) / ST_KC;
+  constexpr int CH = ST_N / 2;   // columns of the tile per thread
+  double cv[CH];
+#pragma unroll
+  for (int j = 0; j < CH; ++j) cv[j] = 0.0;
+  int ok = 1;
+  uint32_t parity = 0;   // phase of the barrier for the chunk in flight
+  for (int ci = 0; ci < nch && ok; ++ci) {
+    parity = ci & 1;
+    const int kc = ci * ST_KC, kl = min(ST_KC, kp - kc), ng = kl / 8;   // 16-byte pieces per slice row
+    for (int e = tid; e < (ST_M + ST_N) * OZ_S * ng; e += ST_NT) {
+      const int row = e / (OZ_S * ng), rem = e % (OZ_S * ng), p = rem / ng, gg = rem % ng;
+      const bool isA = row < ST_M;
+      const int rr = isA ? row : row - ST_M, gi = (isA ? i0 : j0) + rr;
+      unsigned char* d = (isA ? As + p * (ST_M * ST_KC * 2) : Bs + p * (ST_N * ST_KC * 2)) +
+                         ((rr / 8) * 4 + gg) * 128 + (rr % 8) * 16;
+      if (gi < c)
+        cp_async16(d, (isA ? R.Esl : R.Fsl) + (size_t)gi * OZ_S * kp + (size_t)p * kp + kc + gg * 8);
+      else
+        *reinterpret_cast<uint4*>(d) = make_uint4(0, 0, 0, 0);
+    }
+    if (ci + 1 == nch && i < c) {   // the entries of A_CC this thread updates, loaded under the last products
+#pragma unroll
+      for (int j = 0; j < CH; ++j)
+        if (j0 + CH * half + j < c) cv[j] = L.blk[rowb + colb[CH * half + j]];
+    }
+    cp_async_wait_all();
+    fence_async_smem();
+    __syncthreads();
+    if (tid == 0) {
+      // the B slices are stacked along N (slice q = rows 32q .. 32q + 31, SBO 512
+      // throughout), so one product of A slice p with slices 0 .. 7 - p written at
+      // TMEM column 32p puts A_p B_q^T into the columns of group p + q
+      tc_fence_after();
+      for (int s = 0; s < kl / 16; ++s) {
+        const uint64_t bd = umma_desc(smem_u32(Bs + s * 256), 128, 512);
+#pragma unroll
+        for (int p = 0; p < OZ_S; ++p) {
+          const uint64_t ad = umma_desc(smem_u32(As + p * (ST_M * ST_KC * 2) + s * 256), 128, 512);
+          umma_bf16(tmem + ST_N * p, ad, bd, umma_idesc_bf16(ST_M, ST_N * (OZ_S - p)),
+                    (ci > 0 || s > 0 || p > 0) ? 1u : 0u);
+        }
+      }
+      umma_commit(&mbar);
+    }
+    ok = __syncthreads_and(mbar_wait(&mbar, parity, ST_POLLS) ? 1 : 0);
+  }
+  tc_fence_after();
+  if (ok) {
+    const uint32_t lane_base = tmem + ((uint32_t)(32 * quarter) << 16) + CH * half;
+#pragma unroll
+    for (int c0 = 0; c0 < CH; c0 += 8) {
+      uint32_t gr[OZ_S][8];
+#pragma unroll
+      for (int u = 0; u < OZ_S; ++u) tmem_ld8(gr[u], lane_base + ST_N * u + c0);
+      tmem_ld_wait();
+#pragma unroll
+      for (int jj = 0; jj < 8; ++jj) {
+        long long w = 0;
+#pragma unroll
+        for (int u = 0; u < OZ_S; u += 2) {
+          const long long gv = (long long)(oz_fint(__uint_as_float(gr[u][jj])) * 128 +
+                                           oz_fint(__uint_as_float(gr[u + 1][jj])));
+          const int sh = 32 - OZ_BITS * u;
+          w += sh >= 0 ? (gv << sh) : ((gv + (1LL << (-sh - 1))) >> (-sh));
+        }
+        const int j = CH * half + c0 + jj;
+        if (i < c && j0 + j < c) L.blk[rowb + colb[j]] = cv[c0 + jj] - oz_ldexp_int(w, rexp + cexp[j] - 53);
+      }
+    }
+  } else {
+    if (tid == 0) atomicExch(err, (int)RSS_ETIMEOUT);
+    mbar_wait(&mbar, parity, ST_POLLS);   // products still in flight must finish before the TMEM is freed
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_free(tmem, ST_TMEM_COLS);
+}
+
 // Complex factors: Re(E F) = Er Fr^T - Ei Fi^T and Im(E F) = Er Fi^T + Ei Fr^T
 // (F^T rows split as Fr, Fi), each group sum exact as in the real case; the
 // sign of -Ei is flipped on the bf16 fragment bits.  64 x 32 tile per CTA,
@@ -2800,7 +2942,7 @@ rss_status factor_impl(const rss_tree* tree, const rss_params* prm, cudaStream_t
         const size_t np = (R.k + R.r + 15) & ~15, rp = (R.r + 31) & ~31;
         return ((2 * rp * OZ_S * np * sizeof(uint16_t) + 255) & ~size_t(255)) + ((2 * rp * sizeof(int) + 255) & ~size_t(255));
       };
-      if (prm->schur_path == 0) {
+      if (prm->schur_path == 0 || prm->schur_path == 2) {
         size_t bytes = 0;
         for (const BoxRec<T>& R : recs)
           if (R.k + R.r <= ozp_nmax)
@@ -2833,7 +2975,7 @@ rss_status factor_impl(const rss_tree* tree, const rss_params* prm, cudaStream_t
       for (const BoxRec<T>& R : recs)
         if (R.panels && !R.ozp) pan_max = std::max(pan_max, panel_smem_bytes<T>(pan_ma, R.k + R.r, R.r));
       // tensor-core Schur update for any r (K taken in chunks of 32)
-      const bool oz = prm->schur_path == 0;
+      const bool oz = prm->schur_path == 0 || prm->schur_path == 2;
       const int ns = sizeof(T) == sizeof(double) ? OZ_S : 2 * OZ_S;   // slices per row
       int kp_max = 0;
       if (oz) {
@@ -2936,10 +3078,17 @@ rss_status factor_impl(const rss_tree* tree, const rss_params* prm, cudaStream_t
       evs.back().second->start(st);
       if (oz) {
         if constexpr (sizeof(T) == sizeof(double)) {
-          const size_t smem = 2 * (size_t)SR_BUF * sizeof(uint16_t);
-          RSS_CUDA(cudaFuncSetAttribute(k_schur_oz, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-          const int ntr = (max_c + SR_M - 1) / SR_M, ntc = (max_c + SR_N - 1) / SR_N;
-          k_schur_oz<<<dim3(ntr * ntc, nrec), NT, smem, st>>>(cur.d, d_recs);
+          if (prm->schur_path == 0 && kp_max <= 384) {   // tcgen05: FP32 group sums over the whole K
+            const int smem = ST_A + ST_B;
+            RSS_CUDA(cudaFuncSetAttribute(k_schur_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+            const int ntr = (max_c + ST_M - 1) / ST_M, ntc = (max_c + ST_N - 1) / ST_N;
+            k_schur_tc<<<dim3(ntr * ntc, nrec), ST_NT, smem, st>>>(cur.d, d_recs, d_err);
+          } else {
+            const size_t smem = 2 * (size_t)SR_BUF * sizeof(uint16_t);
+            RSS_CUDA(cudaFuncSetAttribute(k_schur_oz, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            const int ntr = (max_c + SR_M - 1) / SR_M, ntc = (max_c + SR_N - 1) / SR_N;
+            k_schur_oz<<<dim3(ntr * ntc, nrec), NT, smem, st>>>(cur.d, d_recs);
+          }
         } else {
           const size_t smem = (64 + 32) * (size_t)SCSA * sizeof(uint16_t);
           RSS_CUDA(cudaFuncSetAttribute(k_schur_oz_c, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -2971,6 +3120,10 @@ rss_status factor_impl(const rss_tree* tree, const rss_params* prm, cudaStream_t
     }
     int herr = 0;
     RSS_CUDA(cudaMemcpy(&herr, d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (herr == RSS_ETIMEOUT) {
+      rss_set_error("rss_factor: a tensor-core barrier wait of the Schur update ran out");
+      return RSS_ETIMEOUT;
+    }
     if (herr) { rss_set_error("rss_factor: zero pivot in the LU of a redundant block"); return RSS_ENUMERIC; }
     f->levels.push_back(info);
 

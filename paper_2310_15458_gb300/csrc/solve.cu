@@ -963,7 +963,7 @@ rss_status sweeps_tc(const rss_factorization* f, double* x, int64_t N, int nrhs,
 }
 
 bool use_tc(const rss_factorization* f, int64_t nrhs) {
-  return !f->is_complex && nrhs >= TCN && f->params.schur_path == 0;
+  return !f->is_complex && nrhs >= TCN && (f->params.schur_path == 0 || f->params.schur_path == 2);
 }
 
 template <typename T>

@@ -153,7 +153,7 @@ def rss_factor(tree: Tree, kind: int = LAPLACE, eps: float = 1e-6, h: float = 0.
                proxy_radius_over_side: float = 1.25, coef=(), scale: float = 1.0,
                phase=(0.0, 0.0), full_stack: bool = False, schur_fp64: bool = False,
                id_cluster: int = 0, diag_rule: int = 0, bump=(0.5, 0.5, 32.0),
-               per_box: bool = False, stream=None) -> Factor:
+               per_box: bool = False, schur_mma_sync: bool = False, stream=None) -> Factor:
     lib = _load()
     p = _Params()
     p.kind, p.h, p.kappa = kind, h, kappa
@@ -167,7 +167,7 @@ def rss_factor(tree: Tree, kind: int = LAPLACE, eps: float = 1e-6, h: float = 0.
         p.coef_re[i], p.coef_im[i] = complex(c).real, complex(c).imag
     p.scale, p.phase_x, p.phase_y = scale, phase[0], phase[1]
     p.id_rows = 1 if full_stack else 0
-    p.schur_path = 1 if schur_fp64 else 0
+    p.schur_path = 1 if schur_fp64 else (2 if schur_mma_sync else 0)
     p.id_cluster = id_cluster
     p.bump_cx, p.bump_cy, p.bump_a = bump
     p.diag_rule = diag_rule

@@ -345,3 +345,21 @@ def test_tensor_core_schur_complex_matches_fp64_schur(P):
     assert rel(x_tc, x_64) < 1e-12
     spec = KernelSpec("helmholtz", h=1 / side, kappa=25.0)
     assert relres(pts, spec, x_tc, bvec) <= 10 * eps
+
+
+def test_tcgen05_schur_equals_mma_sync_schur(P):
+    """The real Schur update issued as tcgen05 products into tensor memory and the
+    one on warp-level MMAs form the same exact digit-group sums and gather them
+    with the same integer arithmetic, so the two factorizations agree bit for bit."""
+    side, eps = 128, 1e-6
+    tree = P.rss_build_tree(W.grid_points(side), 64)
+    f_tc = P.rss_factor(tree, kind=0, eps=eps, h=1 / side)
+    f_ms = P.rss_factor(tree, kind=0, eps=eps, h=1 / side, schur_mma_sync=True)
+    for g in (16, 8, 4):
+        assert np.array_equal(P.rss_level_ranks(f_tc, g), P.rss_level_ranks(f_ms, g))
+    for g, box in ((16, 0), (16, 137), (8, 27), (4, 5)):
+        a, b = P.rss_box_record(f_tc, g, box), P.rss_box_record(f_ms, g, box)
+        for key in ("S", "C", "T", "E", "F", "LU", "piv"):
+            assert np.array_equal(a[key], b[key]), (g, box, key)
+    bvec = W.gaussian_rhs(side * side, 2, False, 24)
+    assert np.array_equal(gpu_solve(P, f_tc, bvec), gpu_solve(P, f_ms, bvec))
