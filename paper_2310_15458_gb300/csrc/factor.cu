@@ -2059,8 +2059,9 @@ __global__ void __launch_bounds__(ST_NT, 2) k_schur_tc(LevelDev<double> L, const
   for (int ci = 0; ci < nch && ok; ++ci) {
     parity = ci & 1;
     const int kc = ci * ST_KC, kl = min(ST_KC, kp - kc), ng = kl / 8;   // 16-byte pieces per slice row
+    const int lg = ng == 4 ? 2 : 1;                                        // kl is 16 or 32
     for (int e = tid; e < (ST_M + ST_N) * OZ_S * ng; e += ST_NT) {
-      const int row = e / (OZ_S * ng), rem = e % (OZ_S * ng), p = rem / ng, gg = rem % ng;
+      const int row = e >> (3 + lg), rem = e & (OZ_S * ng - 1), p = rem >> lg, gg = rem & (ng - 1);
       const bool isA = row < ST_M;
       const int rr = isA ? row : row - ST_M, gi = (isA ? i0 : j0) + rr;
       unsigned char* d = (isA ? As + p * (ST_M * ST_KC * 2) : Bs + p * (ST_N * ST_KC * 2)) +
@@ -2094,7 +2095,10 @@ __global__ void __launch_bounds__(ST_NT, 2) k_schur_tc(LevelDev<double> L, const
       }
       umma_commit(&mbar);
     }
-    ok = __syncthreads_and(mbar_wait(&mbar, parity, ST_POLLS) ? 1 : 0);
+    // one warp polls the barrier; the others wait at the block barrier without issuing
+    int got = 1;
+    if (warp == 0) got = mbar_wait(&mbar, parity, ST_POLLS) ? 1 : 0;
+    ok = __syncthreads_and(got);
   }
   tc_fence_after();
   if (ok) {
@@ -2121,7 +2125,7 @@ __global__ void __launch_bounds__(ST_NT, 2) k_schur_tc(LevelDev<double> L, const
     }
   } else {
     if (tid == 0) atomicExch(err, (int)RSS_ETIMEOUT);
-    mbar_wait(&mbar, parity, ST_POLLS);   // products still in flight must finish before the TMEM is freed
+    if (warp == 0) mbar_wait(&mbar, parity, ST_POLLS);   // products in flight finish before the TMEM is freed
   }
   tc_fence_before();
   __syncthreads();
