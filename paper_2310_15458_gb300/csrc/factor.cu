@@ -1440,7 +1440,7 @@ __global__ void __launch_bounds__(NT, 2) k_elim_oz(ElimArgs<double> a) {
   if (p0 >= R.c) return;
   const LevelDev<double>& L = a.L;
   const int nmax = L.nmax, g = L.g, B = R.box, k = R.k, r = R.r, c = R.c, n = k + r;
-  const int np = (n + 15) & ~15, SA = OZ_S * np + 8, rp = (r + 31) & ~31, cpc = OZ_S * np / 8;
+  const int np = (n + 15) & ~15, SA = OZ_S * np + 8, rp = (r + 31) & ~31;
   const size_t nn = (size_t)nmax * nmax;
   const int* perm = a.perm_in + (size_t)a.cls_idx[blockIdx.y] * nmax;
   uint16_t* As = reinterpret_cast<uint16_t*>(smraw);   // 64 x SA: panel rows
@@ -1479,54 +1479,58 @@ __global__ void __launch_bounds__(NT, 2) k_elim_oz(ElimArgs<double> a) {
       const int j0 = cc % rp;
       if (j0 >= r) continue;   // padding columns only
       __syncthreads();
-      for (int e = tid; e < OZ_NCH * cpc; e += NT) {
-        const int col = e / cpc, ch = e % cpc, sl = ch / (np / 8), q = ch % (np / 8);
-        cp_async16(Bs + col * SA + sl * np + q * 8, R.Wsl + (size_t)(cc + col) * OZ_S * np + (size_t)sl * np + q * 8);
+      {   // one (column, slice) row of the chunk's W slices per thread
+        const int col = tid >> 3, sl = tid & 7;
+        const uint16_t* src = R.Wsl + (size_t)(cc + col) * OZ_S * np + (size_t)sl * np;
+        uint16_t* dst = Bs + col * SA + sl * np;
+        for (int q = 0; q < np; q += 8) cp_async16(dst + q, src + q);
       }
       if (tid < OZ_NCH) cexp[tid] = R.Wexp[cc + tid];
       cp_async_wait_all();
       __syncthreads();
+      // all eight group sums in FP32 over the whole K (K <= 128: exact), B slices
+      // loaded four at a time with the A slices that pair with them
+      float acc[OZ_S][2][4];
+#pragma unroll
+      for (int u = 0; u < OZ_S; ++u)
+#pragma unroll
+        for (int ni = 0; ni < 2; ++ni)
+#pragma unroll
+          for (int e = 0; e < 4; ++e) acc[u][ni][e] = 0.f;
+      for (int kk = 0; kk < np; kk += 16) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          uint32_t bq[4][4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) ldsm_x4(bq[q], Bs + (4 * h + q) * np + (n0 + b_row) * SA + kk + b_k);
+#pragma unroll
+          for (int p = 0; p + 4 * h < OZ_S; ++p) {
+            uint32_t af[4];
+            ldsm_x4(af, As + p * np + (m0 + a_row) * SA + kk + a_k);
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+              if (p + 4 * h + q < OZ_S) {
+                mma_bf16(acc[p + 4 * h + q][0], af, bq[q]);
+                mma_bf16(acc[p + 4 * h + q][1], af, bq[q] + 2);
+              }
+          }
+        }
+      }
+      // W = sum_u G_u 2^(39-7u), groups u and u + 1 as (G_u 2^7 + G_{u+1}) 2^(32-7u)
       long long W[2][4];
 #pragma unroll
       for (int ni = 0; ni < 2; ++ni)
 #pragma unroll
-        for (int e = 0; e < 4; ++e) W[ni][e] = 0;
-      // groups u and u + 1 together: (G_u 2^7 + G_{u+1}) 2^(32-7u), exact in
-      // int32 for K <= 128 (|G| < 2^23)
-#pragma unroll 1
-      for (int u = 0; u < OZ_S; u += 2) {
-        float ca[2][4], cb[2][4];
+        for (int e = 0; e < 4; ++e) {
+          long long w = 0;
 #pragma unroll
-        for (int ni = 0; ni < 2; ++ni)
-#pragma unroll
-          for (int e = 0; e < 4; ++e) ca[ni][e] = cb[ni][e] = 0.f;
-        for (int p = 0; p <= u + 1; ++p) {
-          const uint16_t* Ab = As + p * np + (m0 + a_row) * SA + a_k;
-          const uint16_t* Bb1 = Bs + (u + 1 - p) * np + (n0 + b_row) * SA + b_k;
-          const uint16_t* Bb0 = Bs + (u - p) * np + (n0 + b_row) * SA + b_k;
-          for (int kk = 0; kk < np; kk += 16) {
-            uint32_t af[4], b1[4];
-            ldsm_x4(af, Ab + kk);
-            ldsm_x4(b1, Bb1 + kk);
-            mma_bf16(cb[0], af, b1);
-            mma_bf16(cb[1], af, b1 + 2);
-            if (p <= u) {
-              uint32_t b0[4];
-              ldsm_x4(b0, Bb0 + kk);
-              mma_bf16(ca[0], af, b0);
-              mma_bf16(ca[1], af, b0 + 2);
-            }
+          for (int u = 0; u < OZ_S; u += 2) {
+            const long long gv = (long long)(oz_fint(acc[u][ni][e]) * 128 + oz_fint(acc[u + 1][ni][e]));
+            const int sh = 32 - OZ_BITS * u;
+            w += sh >= 0 ? (gv << sh) : ((gv + (1LL << (-sh - 1))) >> (-sh));
           }
+          W[ni][e] = w;
         }
-        const int sh = 32 - OZ_BITS * u;
-#pragma unroll
-        for (int ni = 0; ni < 2; ++ni)
-#pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            const long long gv = (long long)(oz_fint(ca[ni][e]) * 128 + oz_fint(cb[ni][e]));
-            W[ni][e] += sh >= 0 ? (gv << sh) : ((gv + (1LL << (-sh - 1))) >> (-sh));
-          }
-      }
       double* out = cc < rp ? R.E : R.Ft;
 #pragma unroll
       for (int ni = 0; ni < 2; ++ni)
