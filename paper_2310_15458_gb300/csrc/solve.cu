@@ -8,8 +8,10 @@
 // launch; the right-hand sides are split into chunks of RC columns.
 #include <algorithm>
 #include <mutex>
+#include <type_traits>
 
 #include "internal.h"
+#include "tc_gemm.cuh"
 
 namespace {
 
@@ -637,6 +639,101 @@ __global__ void __launch_bounds__(TC_NT, 2) k_down_tc(const BoxRec<double>* __re
             As, Bs, rexp, cexp);
 }
 
+// Complex factors with at least ZCN right-hand sides: the products of both sweeps
+// as complex digit-slice GEMMs on the tensor cores (tc_gemm_c), one CTA per box
+// and ZCN columns; the vectors of the box stay in shared memory between them.
+__device__ __forceinline__ size_t tcz_head() { return (size_t)(ZCM + ZCN) * ZSA * sizeof(uint16_t); }
+inline size_t tcz_smem_up(int k, int r) { return (size_t)(ZCM + ZCN) * ZSA * 2 + sizeof(zd) * (size_t)(k + 2 * r) * ZCN; }
+inline size_t tcz_smem_down(int r) { return (size_t)(ZCM + ZCN) * ZSA * 2 + sizeof(zd) * (size_t)(2 * r) * ZCN; }
+constexpr size_t TCZ_SMEM_MAX = 220 * 1024;
+
+// t = b_R - T^* b_S, b_R = L^{-1} P t, b_C -= E b_R.
+__global__ void __launch_bounds__(TC_NT) k_up_tcz(const BoxRec<zd>* __restrict__ recs, zd* __restrict__ x,
+                                                  int64_t N, int nrhs) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const BoxRec<zd> R = recs[blockIdx.x];
+  const int k = R.k, r = R.r, c = R.c;
+  const int q0 = blockIdx.y * ZCN, nq = min(ZCN, nrhs - q0);
+  uint16_t* As = reinterpret_cast<uint16_t*>(smraw);
+  uint16_t* Bs = As + ZCM * ZSA;
+  zd* bS = reinterpret_cast<zd*>(smraw + tcz_head());   // k x ZCN
+  zd* t = bS + (size_t)k * ZCN;                           // r x ZCN
+  zd* u = t + (size_t)r * ZCN;                            // r x ZCN
+  __shared__ int rexp[ZCM], cexp[ZCN];
+  const int tid = threadIdx.x, bs = blockDim.x;
+  zd* xq = x + (int64_t)q0 * N;
+  for (int e = tid; e < k * ZCN; e += bs) {
+    const int s2 = e / ZCN, q = e % ZCN;
+    bS[e] = q < nq ? xq[R.idxC[s2] + (int64_t)q * N] : zero<zd>();
+  }
+  for (int e = tid; e < r * ZCN; e += bs) {
+    const int j = e / ZCN, q = e % ZCN;
+    t[e] = q < nq ? xq[R.idxR[j] + (int64_t)q * N] : zero<zd>();
+  }
+  __syncthreads();   // (tc_gemm_c synchronises per K chunk; K = k may be 0)
+  const zd* __restrict__ Tm = R.Tm;
+  const zd* __restrict__ LiP = R.LiP;
+  const zd* __restrict__ E = R.E;
+  tc_gemm_c(r, k, [&](int i, int l) { return cj(Tm[l + (size_t)i * k]); }, [&](int l, int q) { return bS[l * ZCN + q]; },
+            [&](int i, int q, zd v) { t[i * ZCN + q] = t[i * ZCN + q] - v; }, As, Bs, rexp, cexp);
+  tc_gemm_c(r, r, [&](int i, int l) { return LiP[i + (size_t)l * r]; }, [&](int l, int q) { return t[l * ZCN + q]; },
+            [&](int i, int q, zd v) { u[i * ZCN + q] = v; }, As, Bs, rexp, cexp);
+  for (int e = tid; e < r * ZCN; e += bs) {
+    const int j = e / ZCN, q = e % ZCN;
+    if (q < nq) xq[R.idxR[j] + (int64_t)q * N] = u[e];
+  }
+  tc_gemm_c(c, r, [&](int i, int l) { return E[i + (size_t)l * c]; }, [&](int l, int q) { return u[l * ZCN + q]; },
+            [&](int i, int q, zd v) {
+              if (q < nq) {
+                const int64_t gi = R.idxC[i] + (int64_t)q * N;
+                xq[gi] = xq[gi] - v;
+              }
+            },
+            As, Bs, rexp, cexp);
+}
+
+// z = y_R - F y_C, y_R = U^{-1} z, y_S -= T y_R.
+__global__ void __launch_bounds__(TC_NT) k_down_tcz(const BoxRec<zd>* __restrict__ recs, zd* __restrict__ x,
+                                                    int64_t N, int nrhs) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const BoxRec<zd> R = recs[blockIdx.x];
+  const int k = R.k, r = R.r, c = R.c;
+  const int q0 = blockIdx.y * ZCN, nq = min(ZCN, nrhs - q0);
+  uint16_t* As = reinterpret_cast<uint16_t*>(smraw);
+  uint16_t* Bs = As + ZCM * ZSA;
+  zd* z = reinterpret_cast<zd*>(smraw + tcz_head());   // r x ZCN
+  zd* yR = z + (size_t)r * ZCN;                          // r x ZCN
+  __shared__ int rexp[ZCM], cexp[ZCN];
+  const int tid = threadIdx.x, bs = blockDim.x;
+  zd* xq = x + (int64_t)q0 * N;
+  for (int e = tid; e < r * ZCN; e += bs) {
+    const int j = e / ZCN, q = e % ZCN;
+    z[e] = q < nq ? xq[R.idxR[j] + (int64_t)q * N] : zero<zd>();
+  }
+  __syncthreads();
+  const zd* __restrict__ Ft = R.Ft;
+  const zd* __restrict__ Ui = R.Ui;
+  const zd* __restrict__ Tm = R.Tm;
+  const int* __restrict__ idxC = R.idxC;
+  tc_gemm_c(r, c, [&](int j, int i) { return Ft[i + (size_t)j * c]; },
+            [&](int i, int q) { return q < nq ? xq[idxC[i] + (int64_t)q * N] : zero<zd>(); },
+            [&](int j, int q, zd v) { z[j * ZCN + q] = z[j * ZCN + q] - v; }, As, Bs, rexp, cexp);
+  tc_gemm_c(r, r, [&](int j, int l) { return Ui[j + (size_t)l * r]; }, [&](int l, int q) { return z[l * ZCN + q]; },
+            [&](int j, int q, zd v) { yR[j * ZCN + q] = v; }, As, Bs, rexp, cexp);
+  for (int e = tid; e < r * ZCN; e += bs) {
+    const int j = e / ZCN, q = e % ZCN;
+    if (q < nq) xq[R.idxR[j] + (int64_t)q * N] = yR[e];
+  }
+  tc_gemm_c(k, r, [&](int s2, int j) { return Tm[s2 + (size_t)j * k]; }, [&](int j, int q) { return yR[j * ZCN + q]; },
+            [&](int s2, int q, zd v) {
+              if (q < nq) {
+                const int64_t gs = idxC[s2] + (int64_t)q * N;
+                xq[gs] = xq[gs] - v;
+              }
+            },
+            As, Bs, rexp, cexp);
+}
+
 // Top block: x_top <- A_top^{-1} x_top with the inverse formed at factor time.
 template <typename T>
 __global__ void k_top_gather(const int* __restrict__ idx, int n, const T* __restrict__ x, int64_t N, int nrhs,
@@ -783,9 +880,20 @@ template <typename T> SweepWs sweep_ws(const rss_factorization* f, int64_t nrhs,
 
 int rhs_chunk(int64_t nrhs) { return nrhs == 1 ? 1 : nrhs <= 4 ? 4 : 8; }
 
+// tcz: complex factors with at least ZCN right-hand sides take the tensor-core
+// sweeps (k_up_tcz, k_down_tcz) for every colour class whose boxes fit their
+// shared memory, and these FP64 kernels for the others.
 template <typename T, int RC>
-rss_status sweeps(const rss_factorization* f, T* x, int64_t N, int nrhs, cudaStream_t st, void* ws) {
+rss_status sweeps(const rss_factorization* f, T* x, int64_t N, int nrhs, cudaStream_t st, void* ws,
+                  bool tcz = false) {
   const unsigned nz = cdiv(nrhs, RC);
+  const unsigned nzc = cdiv(nrhs, ZCN);
+  if constexpr (std::is_same<T, zd>::value) {
+    if (tcz) {
+      RSS_CUDA(cudaFuncSetAttribute(k_up_tcz, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TCZ_SMEM_MAX));
+      RSS_CUDA(cudaFuncSetAttribute(k_down_tcz, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TCZ_SMEM_MAX));
+    }
+  }
   const SweepWs w = sweep_ws<T>(f, nrhs, RC);
   char* wb = static_cast<char*>(ws);
   T* part = reinterpret_cast<T*>(wb);
@@ -798,6 +906,14 @@ rss_status sweeps(const rss_factorization* f, T* x, int64_t N, int nrhs, cudaStr
   RSS_CUDA(cudaFuncSetAttribute(k_top_gemv<T, RC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
   for (const Batch& b : f->batches) {
     const BoxRec<T>* recs = static_cast<const BoxRec<T>*>(b.d_recs);
+    if constexpr (std::is_same<T, zd>::value) {
+      const size_t sm = tcz_smem_up(b.max_k, b.max_r);
+      if (tcz && sm <= TCZ_SMEM_MAX) {
+        k_up_tcz<<<dim3(b.nrec, nzc), TC_NT, sm, st>>>(recs, x, N, nrhs);
+        RSS_LAUNCHED();
+        continue;
+      }
+    }
     const size_t want_r = sizeof(T) * ((size_t)(b.max_k + b.max_r) * RC + (size_t)(b.max_k | 1) * b.max_r +
                                        (size_t)b.max_r * b.max_r);
     const size_t sm_r = std::min<size_t>(want_r, 96 * 1024);
@@ -821,6 +937,14 @@ rss_status sweeps(const rss_factorization* f, T* x, int64_t N, int nrhs, cudaStr
     RSS_LAUNCHED();
   }
   for (auto it = f->batches.rbegin(); it != f->batches.rend(); ++it) {
+    if constexpr (std::is_same<T, zd>::value) {
+      const size_t sm = tcz_smem_down(it->max_r);
+      if (tcz && tcz_smem_up(it->max_k, it->max_r) <= TCZ_SMEM_MAX) {   // the same classes as upward
+        k_down_tcz<<<dim3(it->nrec, nzc), TC_NT, sm, st>>>(static_cast<const BoxRec<T>*>(it->d_recs), x, N, nrhs);
+        RSS_LAUNCHED();
+        continue;
+      }
+    }
     const int nch = (int)cdiv(it->max_c, SW_ROWS_D);
     const size_t want_d =
         sizeof(T) * std::max((size_t)SW_ROWS_D * RC + (size_t)(SW_ROWS_D + 1) * it->max_r,
@@ -834,8 +958,6 @@ rss_status sweeps(const rss_factorization* f, T* x, int64_t N, int nrhs, cudaStr
   return RSS_OK;
 }
 
-// Real factors with at least TCN right-hand sides: the tensor-core sweeps; the
-// top block as in sweeps<double, 8>.
 // The digit slices of E and F for the tensor-core sweeps: built once per factor
 // by the first solve that needs them (on its stream, which it then waits for),
 // kept until the factor is freed.  Boxes with c >= 1024 keep the per-chunk
@@ -907,6 +1029,8 @@ rss_status ensure_slices(rss_factorization* f, cudaStream_t st) {
   return RSS_OK;
 }
 
+// Real factors with at least TCN right-hand sides: the tensor-core sweeps; the
+// top block as in sweeps<double, 8>.
 // may_build: the caller allows the one-time allocation of the slice cache
 // (rss_solve_noalloc does not; it uses the cache only when it already exists).
 rss_status sweeps_tc(const rss_factorization* f, double* x, int64_t N, int nrhs, cudaStream_t st, void* ws,
@@ -972,9 +1096,10 @@ rss_status run_sweeps(const rss_factorization* f, T* x, int64_t N, int64_t nrhs,
   if constexpr (sizeof(T) == sizeof(double))
     if (use_tc(f, nrhs)) return sweeps_tc(f, x, N, (int)nrhs, st, ws, may_build);
   const int rc = rhs_chunk(nrhs);
-  return rc == 1 ? sweeps<T, 1>(f, x, N, (int)nrhs, st, ws)
-         : rc == 4 ? sweeps<T, 4>(f, x, N, (int)nrhs, st, ws)
-                   : sweeps<T, 8>(f, x, N, (int)nrhs, st, ws);
+  const bool tcz = f->is_complex && nrhs >= ZCN && (f->params.schur_path == 0 || f->params.schur_path == 2);
+  return rc == 1 ? sweeps<T, 1>(f, x, N, (int)nrhs, st, ws, tcz)
+         : rc == 4 ? sweeps<T, 4>(f, x, N, (int)nrhs, st, ws, tcz)
+                   : sweeps<T, 8>(f, x, N, (int)nrhs, st, ws, tcz);
 }
 
 }  // namespace

@@ -363,3 +363,23 @@ def test_tcgen05_schur_equals_mma_sync_schur(P):
             assert np.array_equal(a[key], b[key]), (g, box, key)
     bvec = W.gaussian_rhs(side * side, 2, False, 24)
     assert np.array_equal(gpu_solve(P, f_tc, bvec), gpu_solve(P, f_ms, bvec))
+
+
+def test_tensor_core_sweeps_many_rhs_complex(P):
+    """Complex factors with 32 or more right-hand sides take the complex tensor-core
+    sweeps (digit-slice products with shared real/imaginary scales): they agree with
+    one-column FP64 solves to 1e-12, a column's result does not depend on the other
+    columns, and the residual meets 10 eps."""
+    side, eps = 64, 1e-6
+    pts = W.grid_points(side)
+    spec = KernelSpec("helmholtz", h=1 / side, kappa=25.0)
+    f = gpu_factor(P, pts, spec, eps, 64)
+    b = W.gaussian_rhs(side * side, 40, True, 47)
+    x = gpu_solve(P, f, b)
+    for j in (0, 17, 31, 32, 39):
+        xj = gpu_solve(P, f, np.ascontiguousarray(b[:, j]))
+        assert np.linalg.norm(x[:, j] - xj) <= 1e-12 * np.linalg.norm(xj)
+    perm = np.random.default_rng(2).permutation(40)
+    xp = gpu_solve(P, f, np.asfortranarray(b[:, perm]))
+    assert np.array_equal(xp, x[:, perm])
+    assert relres(pts, spec, x, b) <= 10 * eps
