@@ -87,11 +87,13 @@ typedef struct {
                                      complex with any n_B); operands split into eight 7-bit
                                      slices with row and column scales, exact integer
                                      products, FP64 recombination (accuracy of an FP64
-                                     product); the real Schur update runs on tcgen05
-                                     (tensor memory accumulators) when every r <= 384;
+                                     product); the Schur update runs on tcgen05
+                                     (tensor memory accumulators) when every r <= 384
+                                     (real) or r <= 192 (complex);
                                      1: FP64 FMA kernels everywhere; 2: as 0 with the real
                                      Schur update on warp-level MMAs (mma.sync), the same
-                                     integer arithmetic and the same result */
+                                     integer arithmetic and, for real factors, the same
+                                     result */
   int id_cluster;                 /* colour classes with fewer boxes than the GPU has room for:
                                      0 spreads each box's ID over a thread-block cluster of
                                      up to 8 CTAs, > 0 caps the cluster size (1: one CTA per

@@ -1985,6 +1985,168 @@ __global__ void __launch_bounds__(ST_NT, 2) k_schur_tc(LevelDev<double> L, const
   if (warp == 0) tmem_free(tmem, ST_TMEM_COLS);
 }
 
+// Complex factors on tcgen05: Re(E F) = Er Fr^T + Ei (-Fi)^T and
+// Im(E F) = Er Fi^T + Ei Fr^T, the slices of E and F^T sharing one scale per row
+// for the real and imaginary parts.  The eight Re group sums occupy TMEM columns
+// 32u .. 32u + 31 and the eight Im group sums columns 256 + 32u .. (512 columns,
+// one CTA per SM); per K step of 16 each A slice p (real and imaginary) takes
+// four products against the stacked B slices (Fr, Fi, and -Fi, a sign-flipped
+// copy made in shared memory).  A Re or Im group sum adds twice as many products
+// as a real one, so it is exact in FP32 for kp <= 192 (checked by the host).  Tile,
+// staging, barrier handling and gathering as in k_schur_tc.
+constexpr int SZ_A = 2 * OZ_S * ST_M * ST_KC * 2;   // Er and Ei slices of one chunk (128 KB)
+constexpr int SZ_B = OZ_S * ST_N * ST_KC * 2;       // one kind of B slices (16 KB): Fr, Fi, -Fi
+constexpr uint32_t SZ_TMEM_COLS = 2 * OZ_S * ST_N;  // 512
+
+__global__ void __launch_bounds__(ST_NT, 1) k_schur_tc_c(LevelDev<zd> L, const BoxRec<zd>* recs, int* err) {
+  extern __shared__ __align__(1024) unsigned char smraw[];
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t s_tmem;
+  __shared__ long long colb[ST_N];
+  __shared__ int cexp[ST_N];
+  const BoxRec<zd> R = recs[blockIdx.y];
+  const int c = R.c, kp = R.kp, ntr = (c + ST_M - 1) / ST_M, ntc = (c + ST_N - 1) / ST_N;
+  if ((int)blockIdx.x >= ntr * ntc) return;
+  const int i0 = (blockIdx.x % ntr) * ST_M, j0 = (blockIdx.x / ntr) * ST_N;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int quarter = warp & 3, half = warp >> 2;   // TMEM lanes 32 quarter .., columns 16 half ..
+  unsigned char* As = smraw;
+  unsigned char* Br = smraw + SZ_A;
+  unsigned char* Bi = Br + SZ_B;
+  unsigned char* Bn = Bi + SZ_B;
+  const int nmax = L.nmax, g = L.g;
+  const long long nn = (long long)nmax * nmax;
+  const int i = i0 + 32 * quarter + lane;
+  long long rowb = 0;
+  int rexp = 0;
+  if (i < c) {
+    const int cm = R.cmap[i], s = cm >> 16, pos = cm & 0xffff;
+    const int u = nbr_box(R.box, g, s % 3 - 1, s / 3 - 1);
+    rowb = (long long)u * 25 * nn + pos - (long long)((s / 3) * 5 + s % 3) * nn;
+    rexp = R.Eexp[i];
+  }
+  if (tid < ST_N) {
+    const int j = j0 + tid;
+    colb[tid] = 0;
+    cexp[tid] = 0;
+    if (j < c) {
+      const int cm = R.cmap[j], s = cm >> 16, pos = cm & 0xffff;
+      colb[tid] = (long long)((s / 3) * 5 + s % 3 + 12) * nn + (long long)pos * nmax;
+      cexp[tid] = R.Fexp[j];
+    }
+  }
+  if (tid == 0) mbar_init(&mbar, 1);
+  if (warp == 0) tmem_alloc(&s_tmem, SZ_TMEM_COLS);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = s_tmem;
+  const int nch = (kp + ST_KC - 1) / ST_KC;
+  constexpr int CH = ST_N / 2;
+  zd cv[CH];
+#pragma unroll
+  for (int j = 0; j < CH; ++j) cv[j] = zd{0.0, 0.0};
+  int ok = 1;
+  uint32_t parity = 0;
+  for (int ci = 0; ci < nch && ok; ++ci) {
+    parity = ci & 1;
+    const int kc = ci * ST_KC, kl = min(ST_KC, kp - kc), ng = kl / 8;
+    const int lg = ng == 4 ? 2 : 1;
+    // 16 slices per row (8 real, 8 imaginary): rows of E into As, rows of F^T into Br / Bi
+    for (int e = tid; e < (ST_M + ST_N) * 2 * OZ_S * ng; e += ST_NT) {
+      const int row = e >> (4 + lg), rem = e & (2 * OZ_S * ng - 1), sl = rem >> lg, gg = rem & (ng - 1);
+      const bool isA = row < ST_M;
+      const int rr = isA ? row : row - ST_M, gi = (isA ? i0 : j0) + rr;
+      unsigned char* base = isA ? As + sl * (ST_M * ST_KC * 2)
+                                : (sl < OZ_S ? Br + sl * (ST_N * ST_KC * 2) : Bi + (sl - OZ_S) * (ST_N * ST_KC * 2));
+      unsigned char* d = base + ((rr / 8) * 4 + gg) * 128 + (rr % 8) * 16;
+      if (gi < c)
+        cp_async16(d, (isA ? R.Esl : R.Fsl) + (size_t)gi * 2 * OZ_S * kp + (size_t)sl * kp + kc + gg * 8);
+      else
+        *reinterpret_cast<uint4*>(d) = make_uint4(0, 0, 0, 0);
+    }
+    if (ci + 1 == nch && i < c) {
+#pragma unroll
+      for (int j = 0; j < CH; ++j)
+        if (j0 + CH * half + j < c) cv[j] = L.blk[rowb + colb[CH * half + j]];
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    for (int e = tid; e < SZ_B / 16; e += ST_NT) {   // -Fi: flip the sign bit of every bf16
+      uint4 v = reinterpret_cast<const uint4*>(Bi)[e];
+      v.x ^= 0x80008000u; v.y ^= 0x80008000u; v.z ^= 0x80008000u; v.w ^= 0x80008000u;
+      reinterpret_cast<uint4*>(Bn)[e] = v;
+    }
+    fence_async_smem();
+    __syncthreads();
+    if (tid == 0) {
+      tc_fence_after();
+      for (int s = 0; s < kl / 16; ++s) {
+        const uint64_t br = umma_desc(smem_u32(Br + s * 256), 128, 512);
+        const uint64_t bi = umma_desc(smem_u32(Bi + s * 256), 128, 512);
+        const uint64_t bn = umma_desc(smem_u32(Bn + s * 256), 128, 512);
+#pragma unroll
+        for (int p = 0; p < OZ_S; ++p) {
+          const uint64_t ar = umma_desc(smem_u32(As + p * (ST_M * ST_KC * 2) + s * 256), 128, 512);
+          const uint64_t ai = umma_desc(smem_u32(As + (OZ_S + p) * (ST_M * ST_KC * 2) + s * 256), 128, 512);
+          const uint32_t idesc = umma_idesc_bf16(ST_M, ST_N * (OZ_S - p));
+          const uint32_t acc = (ci > 0 || s > 0 || p > 0) ? 1u : 0u;
+          umma_bf16(tmem + ST_N * p, ar, br, idesc, acc);                        // Re += Er Fr^T
+          umma_bf16(tmem + ST_N * p, ai, bn, idesc, 1u);                         // Re += Ei (-Fi)^T
+          umma_bf16(tmem + OZ_S * ST_N + ST_N * p, ar, bi, idesc, acc);          // Im += Er Fi^T
+          umma_bf16(tmem + OZ_S * ST_N + ST_N * p, ai, br, idesc, 1u);           // Im += Ei Fr^T
+        }
+      }
+      umma_commit(&mbar);
+    }
+    int got = 1;
+    if (warp == 0) got = mbar_wait(&mbar, parity, ST_POLLS) ? 1 : 0;
+    ok = __syncthreads_and(got);
+  }
+  tc_fence_after();
+  if (ok) {
+    const uint32_t lane_base = tmem + ((uint32_t)(32 * quarter) << 16) + CH * half;
+#pragma unroll
+    for (int c0 = 0; c0 < CH; c0 += 8) {
+      long long w[2][8];
+#pragma unroll
+      for (int part = 0; part < 2; ++part) {   // Re, then Im
+        uint32_t gr[OZ_S][8];
+#pragma unroll
+        for (int u = 0; u < OZ_S; ++u) tmem_ld8(gr[u], lane_base + part * OZ_S * ST_N + ST_N * u + c0);
+        tmem_ld_wait();
+#pragma unroll
+        for (int jj = 0; jj < 8; ++jj) {
+          long long acc = 0;
+#pragma unroll
+          for (int u = 0; u < OZ_S; u += 2) {
+            const long long gv = (long long)(oz_fint(__uint_as_float(gr[u][jj])) * 128 +
+                                             oz_fint(__uint_as_float(gr[u + 1][jj])));
+            const int sh = 32 - OZ_BITS * u;
+            acc += sh >= 0 ? (gv << sh) : ((gv + (1LL << (-sh - 1))) >> (-sh));
+          }
+          w[part][jj] = acc;
+        }
+      }
+#pragma unroll
+      for (int jj = 0; jj < 8; ++jj) {
+        const int j = CH * half + c0 + jj;
+        if (i < c && j0 + j < c) {
+          const int sx = rexp + cexp[j] - 53;
+          const zd o = cv[c0 + jj];
+          L.blk[rowb + colb[j]] = zd{o.x - oz_ldexp_int(w[0][jj], sx), o.y - oz_ldexp_int(w[1][jj], sx)};
+        }
+      }
+    }
+  } else {
+    if (tid == 0) atomicExch(err, (int)RSS_ETIMEOUT);
+    if (warp == 0) mbar_wait(&mbar, parity, ST_POLLS);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_free(tmem, SZ_TMEM_COLS);
+}
+
 // Complex factors: Re(E F) = Er Fr^T - Ei Fi^T and Im(E F) = Er Fi^T + Ei Fr^T
 // (F^T rows split as Fr, Fi), each group sum exact as in the real case; the
 // sign of -Ei is flipped on the bf16 fragment bits.  64 x 32 tile per CTA,
@@ -2947,10 +3109,17 @@ rss_status factor_impl(const rss_tree* tree, const rss_params* prm, cudaStream_t
             k_schur_oz<<<dim3(ntr * ntc, nrec), NT, smem, st>>>(cur.d, d_recs);
           }
         } else {
-          const size_t smem = (64 + 32) * (size_t)SCSA * sizeof(uint16_t);
-          RSS_CUDA(cudaFuncSetAttribute(k_schur_oz_c, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-          const int ntc = (max_c + 31) / 32;
-          k_schur_oz_c<<<dim3(ntile * ntc, nrec), NT, smem, st>>>(cur.d, d_recs);
+          if (prm->schur_path == 0 && kp_max <= 192) {   // tcgen05: Re/Im group sums exact for kp <= 192
+            const int smem = SZ_A + 3 * SZ_B;
+            RSS_CUDA(cudaFuncSetAttribute(k_schur_tc_c, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+            const int ntr = (max_c + ST_M - 1) / ST_M, ntc = (max_c + ST_N - 1) / ST_N;
+            k_schur_tc_c<<<dim3(ntr * ntc, nrec), ST_NT, smem, st>>>(cur.d, d_recs, d_err);
+          } else {
+            const size_t smem = (64 + 32) * (size_t)SCSA * sizeof(uint16_t);
+            RSS_CUDA(cudaFuncSetAttribute(k_schur_oz_c, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            const int ntc = (max_c + 31) / 32;
+            k_schur_oz_c<<<dim3(ntile * ntc, nrec), NT, smem, st>>>(cur.d, d_recs);
+          }
         }
       } else {
         k_schur<T><<<dim3(ntile * ntile, nrec), NT, 0, st>>>(cur.d, d_recs);
