@@ -882,7 +882,9 @@ int rhs_chunk(int64_t nrhs) { return nrhs == 1 ? 1 : nrhs <= 4 ? 4 : 8; }
 
 // tcz: complex factors with at least ZCN right-hand sides take the tensor-core
 // sweeps (k_up_tcz, k_down_tcz) for every colour class whose boxes fit their
-// shared memory, and these FP64 kernels for the others.
+// shared memory and that gives at least one CTA per SM (boxes x column chunks);
+// smaller classes, whose one-CTA-per-box chain of products would be latency
+// bound, keep these FP64 kernels, which spread the rows of C over CTAs.
 template <typename T, int RC>
 rss_status sweeps(const rss_factorization* f, T* x, int64_t N, int nrhs, cudaStream_t st, void* ws,
                   bool tcz = false) {
@@ -908,7 +910,7 @@ rss_status sweeps(const rss_factorization* f, T* x, int64_t N, int nrhs, cudaStr
     const BoxRec<T>* recs = static_cast<const BoxRec<T>*>(b.d_recs);
     if constexpr (std::is_same<T, zd>::value) {
       const size_t sm = tcz_smem_up(b.max_k, b.max_r);
-      if (tcz && sm <= TCZ_SMEM_MAX) {
+      if (tcz && sm <= TCZ_SMEM_MAX && (long long)b.nrec * nzc >= 152) {
         k_up_tcz<<<dim3(b.nrec, nzc), TC_NT, sm, st>>>(recs, x, N, nrhs);
         RSS_LAUNCHED();
         continue;
@@ -939,7 +941,8 @@ rss_status sweeps(const rss_factorization* f, T* x, int64_t N, int nrhs, cudaStr
   for (auto it = f->batches.rbegin(); it != f->batches.rend(); ++it) {
     if constexpr (std::is_same<T, zd>::value) {
       const size_t sm = tcz_smem_down(it->max_r);
-      if (tcz && tcz_smem_up(it->max_k, it->max_r) <= TCZ_SMEM_MAX) {   // the same classes as upward
+      if (tcz && tcz_smem_up(it->max_k, it->max_r) <= TCZ_SMEM_MAX &&
+          (long long)it->nrec * nzc >= 152) {   // the same classes as upward
         k_down_tcz<<<dim3(it->nrec, nzc), TC_NT, sm, st>>>(static_cast<const BoxRec<T>*>(it->d_recs), x, N, nrhs);
         RSS_LAUNCHED();
         continue;

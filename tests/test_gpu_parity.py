@@ -369,8 +369,10 @@ def test_tensor_core_sweeps_many_rhs_complex(P):
     """Complex factors with 32 or more right-hand sides take the complex tensor-core
     sweeps (digit-slice products with shared real/imaginary scales): they agree with
     one-column FP64 solves to 1e-12, a column's result does not depend on the other
-    columns, and the residual meets 10 eps."""
-    side, eps = 64, 1e-6
+    columns, and the residual meets 10 eps.  At 256 x 256 the leaf colour classes
+    (114 boxes, two column chunks) take the tensor-core sweeps, the coarser ones the
+    FP64 kernels."""
+    side, eps = 256, 1e-6
     pts = W.grid_points(side)
     spec = KernelSpec("helmholtz", h=1 / side, kappa=25.0)
     f = gpu_factor(P, pts, spec, eps, 64)
