@@ -107,6 +107,10 @@ typedef struct {
   int per_box;                    /* 0: all boxes of a colour class in one launch per phase;
                                      1: the plain per-box form, one box per launch in the same
                                      order (for comparison: same mathematics, slower) */
+  int class_order;                /* 0: the boxes of a colour class in row-major order; any
+                                     other value: a permutation of each class drawn from this
+                                     seed (same-colour boxes are independent, Algorithm 1 with
+                                     nine colours, so the factorization must not change) */
 } rss_params;
 
 /* Build the quadtree of Section 2.1 for n points given as pts_xy[2*i],

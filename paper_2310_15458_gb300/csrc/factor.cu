@@ -2742,6 +2742,15 @@ rss_status factor_impl(const rss_tree* tree, const rss_params* prm, cudaStream_t
         for (int bx = col % 3; bx < g; bx += 3) cls.push_back(by * g + bx);
     }
     coff[9] = (int)cls.size();
+    if (prm->class_order != 0) {   // a seeded permutation of every class (Fisher-Yates, 64-bit LCG)
+      uint64_t st64 = (uint64_t)(uint32_t)prm->class_order * 0x9E3779B97F4A7C15ull + (uint64_t)g;
+      for (int col = 0; col < 9; ++col)
+        for (int i = coff[col + 1] - 1; i > coff[col]; --i) {
+          st64 = st64 * 6364136223846793005ull + 1442695040888963407ull;
+          const int j = coff[col] + (int)((st64 >> 33) % (uint64_t)(i - coff[col] + 1));
+          std::swap(cls[i], cls[j]);
+        }
+    }
     int maxcls = 0;
     for (int col = 0; col < 9; ++col) maxcls = std::max(maxcls, coff[col + 1] - coff[col]);
     if (!gb_cls.ensure(sizeof(int) * cls.size()) || !gb_k.ensure(sizeof(int) * maxcls) ||

@@ -42,7 +42,8 @@ class _Params(ctypes.Structure):
                 ("phase_y", ctypes.c_double), ("id_rows", ctypes.c_int),
                 ("schur_path", ctypes.c_int), ("id_cluster", ctypes.c_int),
                 ("bump_cx", ctypes.c_double), ("bump_cy", ctypes.c_double),
-                ("bump_a", ctypes.c_double), ("diag_rule", ctypes.c_int), ("per_box", ctypes.c_int)]
+                ("bump_a", ctypes.c_double), ("diag_rule", ctypes.c_int), ("per_box", ctypes.c_int),
+                ("class_order", ctypes.c_int)]
 
 
 _lib = None
@@ -153,7 +154,8 @@ def rss_factor(tree: Tree, kind: int = LAPLACE, eps: float = 1e-6, h: float = 0.
                proxy_radius_over_side: float = 1.25, coef=(), scale: float = 1.0,
                phase=(0.0, 0.0), full_stack: bool = False, schur_fp64: bool = False,
                id_cluster: int = 0, diag_rule: int = 0, bump=(0.5, 0.5, 32.0),
-               per_box: bool = False, schur_mma_sync: bool = False, stream=None) -> Factor:
+               per_box: bool = False, schur_mma_sync: bool = False, class_order: int = 0,
+               stream=None) -> Factor:
     lib = _load()
     p = _Params()
     p.kind, p.h, p.kappa = kind, h, kappa
@@ -172,6 +174,7 @@ def rss_factor(tree: Tree, kind: int = LAPLACE, eps: float = 1e-6, h: float = 0.
     p.bump_cx, p.bump_cy, p.bump_a = bump
     p.diag_rule = diag_rule
     p.per_box = 1 if per_box else 0
+    p.class_order = int(class_order)
     out = ctypes.c_void_p()
     _check(lib.rss_factor(tree.handle, ctypes.byref(p), _stream_handle(stream), ctypes.byref(out)))
     return Factor(out, tree.n, kind in (HELMHOLTZ, TEST_POLY, HELMHOLTZ_LS), tree)
