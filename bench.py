@@ -38,7 +38,7 @@ METRIC = "RS-S factor s and solve RHS/s at N=1M, rel.res<=1e-5; serve p50/p99 la
 # CTAs (1.195 TFLOP/s at a 1995 MHz SM clock); the fp64 mma.sync path measured
 # 1.05 TFLOP/s, so DFMA is the FP64 roof.
 FP64_PEAK_TFLOPS = 1.195
-TRAFFIC_PER_LAUNCH = {"id": 3.498e9, "elim": 6.37e8, "schur": 1.603e9}   # bytes, see the roofline below
+TRAFFIC_PER_LAUNCH = {"id": 3.482e9, "elim": 6.37e8, "schur": 1.603e9}   # bytes, see the roofline below
 CPU_SAMPLE_SIDE = 128           # oracle sample: the same workload on a 128 x 128 grid
 
 
