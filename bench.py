@@ -191,7 +191,8 @@ def reference_arm(args, w):
             "ms_per_step": cb["value"] * 1e3, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": args.workload, "n": w["side"] ** 2, "eps": w["eps"], "leaf": W.LEAF,
-                       "rhs": 1, "parallelism": "replicas"},
+                       "proxy_n": W.PROXY_N, "rhs": 1,
+                       "parallelism": "replicas" if args.gpus > 1 else "single"},
             "cpu_baseline": cb,
             "e2e": {"value": cb["value"], "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
