@@ -18,7 +18,8 @@
  *  - Input errors (bad sizes, points that are not a complete uniform grid,
  *    unsupported parameters) return RSS_EINVAL before any GPU work.
  *  - CUDA failures return RSS_ECUDA; device memory exhaustion RSS_ENOMEM; a
- *    zero pivot in an LU returns RSS_ENUMERIC.
+ *    zero pivot in an LU returns RSS_ENUMERIC (Eq. 8 supposes X_RR non-singular);
+ *    a bounded device wait that runs out returns RSS_ETIMEOUT.
  */
 #ifndef RSS_GB300_H
 #define RSS_GB300_H
@@ -40,7 +41,8 @@ typedef enum {
   RSS_ENOMEM = 2,   /* device or host allocation failed */
   RSS_ECUDA = 3,    /* a CUDA runtime call or kernel launch failed */
   RSS_ENUMERIC = 4, /* exact zero pivot in an LU factorization */
-  RSS_ETIMEOUT = 5, /* reserved: a bounded device wait expired */
+  RSS_ETIMEOUT = 5, /* a bounded device wait expired (the tensor-core barrier of
+                       the Schur update; see rss_params.wait_polls) */
   RSS_EBUSY = 6     /* reserved */
 } rss_status;
 
@@ -111,6 +113,13 @@ typedef struct {
                                      other value: a permutation of each class drawn from this
                                      seed (same-colour boxes are independent, Algorithm 1 with
                                      nine colours, so the factorization must not change) */
+  int wait_polls;                 /* device waits are bounded: a CTA of the tensor-core Schur
+                                     update polls its barrier at most this many times before it
+                                     gives up, and rss_factor then returns RSS_ETIMEOUT (after
+                                     the products already issued have finished, so nothing is
+                                     left running).  0: the default limit (2^22 polls); n > 0:
+                                     n polls; -1: give up without polling, which exercises the
+                                     timeout path on purpose (for tests) */
 } rss_params;
 
 /* Build the quadtree of Section 2.1 for n points given as pts_xy[2*i],
@@ -174,11 +183,17 @@ rss_status rss_solve_noalloc(const rss_factorization* f, void* b, int64_t nrhs, 
  * against several resident factorizations); the paper has no counterpart. */
 
 /* Start a server that may hold at most device_bytes of device memory for
- * panels and solve workspaces (2 * n * columns * scalar bytes per panel), with
- * at most max_batch_rhs columns per panel. */
+ * panels and solve workspaces, with at most max_batch_rhs columns per panel.
+ * A panel of c columns is charged n * c scalars for itself plus what the solve
+ * allocates for it (its working copy of the panel and the sweep workspace). */
 rss_status rss_server_create(size_t device_bytes, int64_t max_batch_rhs, rss_server** out);
 
-/* Register a factorization (it must outlive the server); *factor_id names it. */
+/* Register a factorization (it must outlive the server); *factor_id names it.
+ * Caches that the factorization's solves would build on first use (the digit
+ * slices of E and F that real factors use for 32 or more columns) are built
+ * here, on the server's stream for this factorization, and charged to the
+ * budget for the server's lifetime; RSS_ENOMEM if they and a one-column panel
+ * do not fit. */
 rss_status rss_server_add(rss_server* s, const rss_factorization* f, int32_t* factor_id);
 
 /* Queue a solve: b and x are host arrays of n x nrhs scalars, column-major with

@@ -207,6 +207,7 @@ rss_status rss_factor(const rss_tree* tree, const rss_params* p, void* stream, r
   if (p->proxy_n < 0 || p->proxy_n > 4096) return fail(RSS_EINVAL, "rss_factor: proxy_n out of range");
   if (p->ncoef < 0 || p->ncoef > RSS_MAX_COEF) return fail(RSS_EINVAL, "rss_factor: ncoef out of range");
   if (p->proxy_radius_over_side < 0) return fail(RSS_EINVAL, "rss_factor: negative proxy radius");
+  if (p->wait_polls < -1) return fail(RSS_EINVAL, "rss_factor: wait_polls must be >= -1");
   rss_factorization* f = new (std::nothrow) rss_factorization();
   if (!f) return fail(RSS_ENOMEM, "rss_factor: host allocation failed");
   f->params = *p;

@@ -944,7 +944,8 @@ __device__ void oz_split_row(const zd* __restrict__ src, int stride, int r, int 
 
 // LU with partial pivoting of the r x r matrix LU (ld r) by the whole CTA:
 // largest modulus, lowest row on ties; the exchanges go to piv.  Returns false
-// (after flagging RSS_ENUMERIC) on a zero pivot.
+// (after flagging RSS_ENUMERIC) on a zero pivot; piv then holds no exchange for
+// the remaining steps, so kernels that still read it index within 0 .. r-1.
 template <typename T> __device__ bool lu_pp_block(T* LU, int r, int* piv, int* err) {
   __shared__ int s_piv, s_zero;
   __shared__ __align__(16) double s_dinv[2];   // 1 / pivot, computed once per step (T = double or zd)
@@ -971,6 +972,8 @@ template <typename T> __device__ bool lu_pp_block(T* LU, int r, int* piv, int* e
     __syncthreads();
     if (s_zero) {
       if (tid == 0) atomicExch(err, (int)RSS_ENUMERIC);
+      for (int i = j + tid; i < r; i += bs) piv[i] = i;
+      __syncthreads();
       return false;
     }
     const int p = s_piv;
@@ -1879,15 +1882,19 @@ __global__ void __launch_bounds__(NT, 2) k_schur_oz(LevelDev<double> L, const Bo
 // row (warps w and w + 4 share TMEM lanes 32 (w % 4) ..) with
 // tcgen05.ld, gathers each entry into one int64 as k_schur_oz does (same integer
 // arithmetic, same result) and subtracts it from the entries of A_CC, which it
-// loaded while the last products ran.  A barrier wait that runs out sets
-// RSS_ETIMEOUT in *err; the CTA then frees its tensor memory and returns.
+// loaded while the last products ran.  A barrier wait that runs out (after
+// `polls` polls) sets RSS_ETIMEOUT in *err; the CTA then waits, with the much
+// longer limit ST_DRAIN_POLLS, for the products it already issued to finish
+// (they write its tensor memory), frees its tensor memory and returns.
 constexpr int ST_M = 128, ST_N = 32, ST_KC = 32, ST_NT = 256;
 constexpr int ST_A = OZ_S * ST_M * ST_KC * 2;   // bytes of one chunk of A slices (64 KB)
 constexpr int ST_B = OZ_S * ST_N * ST_KC * 2;   // 16 KB
 constexpr uint32_t ST_TMEM_COLS = OZ_S * ST_N;  // 256
 constexpr long long ST_POLLS = 1LL << 22;
+constexpr long long ST_DRAIN_POLLS = 1LL << 26;
 
-__global__ void __launch_bounds__(ST_NT, 2) k_schur_tc(LevelDev<double> L, const BoxRec<double>* recs, int* err) {
+__global__ void __launch_bounds__(ST_NT, 2) k_schur_tc(LevelDev<double> L, const BoxRec<double>* recs, int* err,
+                                                        long long polls) {
   extern __shared__ __align__(1024) unsigned char smraw[];
   __shared__ __align__(8) uint64_t mbar;
   __shared__ uint32_t s_tmem;
@@ -1976,7 +1983,7 @@ __global__ void __launch_bounds__(ST_NT, 2) k_schur_tc(LevelDev<double> L, const
     }
     // one warp polls the barrier; the others wait at the block barrier without issuing
     int got = 1;
-    if (warp == 0) got = mbar_wait(&mbar, parity, ST_POLLS) ? 1 : 0;
+    if (warp == 0) got = mbar_wait(&mbar, parity, polls) ? 1 : 0;
     ok = __syncthreads_and(got);
   }
   tc_fence_after();
@@ -2004,7 +2011,7 @@ __global__ void __launch_bounds__(ST_NT, 2) k_schur_tc(LevelDev<double> L, const
     }
   } else {
     if (tid == 0) atomicExch(err, (int)RSS_ETIMEOUT);
-    if (warp == 0) mbar_wait(&mbar, parity, ST_POLLS);   // products in flight finish before the TMEM is freed
+    if (warp == 0) mbar_wait(&mbar, parity, ST_DRAIN_POLLS);   // products in flight finish before the TMEM is freed
   }
   tc_fence_before();
   __syncthreads();
@@ -2024,7 +2031,8 @@ constexpr int SZ_A = 2 * OZ_S * ST_M * ST_KC * 2;   // Er and Ei slices of one c
 constexpr int SZ_B = OZ_S * ST_N * ST_KC * 2;       // one kind of B slices (16 KB): Fr, Fi, -Fi
 constexpr uint32_t SZ_TMEM_COLS = 2 * OZ_S * ST_N;  // 512
 
-__global__ void __launch_bounds__(ST_NT, 1) k_schur_tc_c(LevelDev<zd> L, const BoxRec<zd>* recs, int* err) {
+__global__ void __launch_bounds__(ST_NT, 1) k_schur_tc_c(LevelDev<zd> L, const BoxRec<zd>* recs, int* err,
+                                                          long long polls) {
   extern __shared__ __align__(1024) unsigned char smraw[];
   __shared__ __align__(8) uint64_t mbar;
   __shared__ uint32_t s_tmem;
@@ -2126,7 +2134,7 @@ __global__ void __launch_bounds__(ST_NT, 1) k_schur_tc_c(LevelDev<zd> L, const B
       umma_commit(&mbar);
     }
     int got = 1;
-    if (warp == 0) got = mbar_wait(&mbar, parity, ST_POLLS) ? 1 : 0;
+    if (warp == 0) got = mbar_wait(&mbar, parity, polls) ? 1 : 0;
     ok = __syncthreads_and(got);
   }
   tc_fence_after();
@@ -2166,7 +2174,7 @@ __global__ void __launch_bounds__(ST_NT, 1) k_schur_tc_c(LevelDev<zd> L, const B
     }
   } else {
     if (tid == 0) atomicExch(err, (int)RSS_ETIMEOUT);
-    if (warp == 0) mbar_wait(&mbar, parity, ST_POLLS);
+    if (warp == 0) mbar_wait(&mbar, parity, ST_DRAIN_POLLS);
   }
   tc_fence_before();
   __syncthreads();
@@ -2484,8 +2492,9 @@ template <typename T> __global__ void __launch_bounds__(1024) k_lu_panel(T* A, i
       }
     }
     __syncthreads();
-    if (s_zero) {
+    if (s_zero) {   // no exchange for the remaining steps: later launches index within 0 .. n-1
       if (tid == 0) atomicExch(err, (int)RSS_ENUMERIC);
+      for (int i = j + tid; i < n; i += bs) piv[i] = i;
       return;
     }
     const int p = s_piv;
@@ -2747,6 +2756,8 @@ rss_status factor_impl(const rss_tree* tree, const rss_params* prm, cudaStream_t
   // eliminations, so the conjugate half of the proxy stack repeats the first half
   // and the ID of [A_MB; K_PB] alone is the same ID.
   const int half = (prm->id_rows == 0 && prm->kind == RSS_LAPLACE && prm->diag_im == 0.0) ? 1 : 0;
+  // poll limit of the first barrier wait of the tensor-core Schur updates
+  const long long polls = prm->wait_polls == 0 ? ST_POLLS : prm->wait_polls < 0 ? 0 : (long long)prm->wait_polls;
   // A complex symmetric kernel (Helmholtz): the ID of the real stack
   // [Re X; Im X], X = [A_MB; K_PB], which is the ID of the full stack (T real).
   const bool split = std::is_same<T, zd>::value && prm->id_rows == 0 &&
@@ -3136,7 +3147,7 @@ rss_status factor_impl(const rss_tree* tree, const rss_params* prm, cudaStream_t
             const int smem = ST_A + ST_B;
             RSS_CUDA(cudaFuncSetAttribute(k_schur_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
             const int ntr = (max_c + ST_M - 1) / ST_M, ntc = (max_c + ST_N - 1) / ST_N;
-            k_schur_tc<<<dim3(ntr * ntc, nrec), ST_NT, smem, st>>>(cur.d, d_recs, d_err);
+            k_schur_tc<<<dim3(ntr * ntc, nrec), ST_NT, smem, st>>>(cur.d, d_recs, d_err, polls);
           } else {
             const size_t smem = 2 * (size_t)SR_BUF * sizeof(uint16_t);
             RSS_CUDA(cudaFuncSetAttribute(k_schur_oz, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -3148,7 +3159,7 @@ rss_status factor_impl(const rss_tree* tree, const rss_params* prm, cudaStream_t
             const int smem = SZ_A + 3 * SZ_B;
             RSS_CUDA(cudaFuncSetAttribute(k_schur_tc_c, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
             const int ntr = (max_c + ST_M - 1) / ST_M, ntc = (max_c + ST_N - 1) / ST_N;
-            k_schur_tc_c<<<dim3(ntr * ntc, nrec), ST_NT, smem, st>>>(cur.d, d_recs, d_err);
+            k_schur_tc_c<<<dim3(ntr * ntc, nrec), ST_NT, smem, st>>>(cur.d, d_recs, d_err, polls);
           } else {
             const size_t smem = (64 + 32) * (size_t)SCSA * sizeof(uint16_t);
             RSS_CUDA(cudaFuncSetAttribute(k_schur_oz_c, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));

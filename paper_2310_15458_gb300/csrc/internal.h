@@ -139,6 +139,7 @@ struct rss_factorization {
   std::mutex slice_mu;
   bool slices_ready = false;
   void* d_slice_mem = nullptr;
+  size_t slice_bytes = 0;
   std::vector<SliceRec*> d_slices;
   // wall times (ms, host clock around each synchronised phase) for rss_info
   double t_gen = 0, t_id = 0, t_elim = 0, t_schur = 0, t_merge = 0, t_top = 0, t_total = 0;
@@ -157,6 +158,14 @@ template <typename T> rss_status factor_impl(const rss_tree* tree, const rss_par
 template <typename T> rss_status solve_impl(const rss_factorization* f, T* b_dev, int64_t nrhs,
                                             int64_t ldb, cudaStream_t st);
 template <typename T> rss_status top_inverse(const T* LU, const int* piv, int n, T* Ainv, cudaStream_t st);
+// device bytes one solve of nrhs columns allocates (working copy plus sweep
+// workspace), beside the caller's b
+size_t solve_device_bytes(const rss_factorization* f, int64_t nrhs);
+// device bytes of the factor-owned caches that solves with up to max_nrhs
+// columns build on first use (the digit slices of E and F of a real factor;
+// 0 when none applies), and the call that builds them now, on st
+size_t solve_cache_bytes(const rss_factorization* f, int64_t max_nrhs);
+rss_status prepare_solve_caches(const rss_factorization* f, int64_t max_nrhs, cudaStream_t st);
 void free_factor(rss_factorization* f);
 void free_matvec(rss_factorization* f);
 rss_status self_integral(int kind, double h, double kappa, double* re, double* im);

@@ -19,6 +19,7 @@
 #include <mutex>
 #include <new>
 #include <sstream>
+#include <string>
 #include <thread>
 #include <unordered_map>
 #include <vector>
@@ -62,6 +63,7 @@ struct rss_server {
   std::thread worker;
   bool stop = false;
   size_t budget = 0, in_use = 0;
+  size_t reserved = 0;   // factor caches built for the server's panels (held for its lifetime)
   int64_t max_cols = 256;
   int device = 0;
   std::vector<std::unique_ptr<Slot>> slots;
@@ -84,9 +86,13 @@ bool launch_panel(rss_server* S, Slot& s) {
   std::vector<Request*> batch;
   int64_t cols = 0;
   bool acted = false;
+  // device bytes of a panel of c columns: the panel itself plus what the solve
+  // allocates for it (working copy and sweep workspace)
+  auto need_of = [&](int64_t c) { return esz * (size_t)n * (size_t)c + solve_device_bytes(s.f, c); };
+  size_t need = 0;
   while (!s.pending.empty()) {
     Request* r = s.pending.front();
-    if (2 * esz * (size_t)n * (size_t)r->nrhs > S->budget) {   // can never fit: refuse it
+    if (need_of(r->nrhs) > S->budget - S->reserved) {   // can never fit: refuse it
       s.pending.pop_front();
       r->status = RSS_ENOMEM;
       r->t_done = Clock::now();
@@ -94,9 +100,10 @@ bool launch_panel(rss_server* S, Slot& s) {
       acted = true;
       continue;
     }
-    const size_t need = 2 * esz * (size_t)n * (size_t)(cols + r->nrhs);   // panel + solve workspace
     if (cols + r->nrhs > S->max_cols && !batch.empty()) break;
-    if (S->in_use + need > S->budget) break;   // wait for memory to free up
+    const size_t need_next = need_of(cols + r->nrhs);
+    if (S->in_use + S->reserved + need_next > S->budget) break;   // wait for memory to free up
+    need = need_next;
     batch.push_back(r);
     cols += r->nrhs;
     s.pending.pop_front();
@@ -152,7 +159,7 @@ bool launch_panel(rss_server* S, Slot& s) {
   }
   s.inflight = std::move(batch);
   s.inflight_cols = cols;
-  s.inflight_bytes = 2 * bytes;
+  s.inflight_bytes = need;
   S->in_use += s.inflight_bytes;
   S->n_batch += 1;
   S->n_cols += cols;
@@ -242,8 +249,34 @@ rss_status rss_server_add(rss_server* S, const rss_factorization* f, int32_t* fa
     return fail(RSS_EINVAL, "rss_server_add: bad arguments");
   auto s = std::make_unique<Slot>();
   s->f = f;
-  RSS_CUDA(cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking));
-  RSS_CUDA(cudaEventCreateWithFlags(&s->done, cudaEventDisableTiming));
+  // the factor caches the panels' solves would build on first use (outside any
+  // budget) are built here and charged to the budget for the server's lifetime
+  const size_t cache = solve_cache_bytes(f, S->max_cols);
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    if (S->reserved + cache + solve_device_bytes(f, 1) + (f->is_complex ? 16 : 8) * (size_t)f->n > S->budget)
+      return fail(RSS_ENOMEM, "rss_server_add: the factorization's solve caches (" + std::to_string(cache) +
+                                  " bytes) and one column do not fit the server's device budget");
+    S->reserved += cache;
+  }
+  auto unreserve = [&] {
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->reserved -= cache;
+  };
+  if (cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&s->done, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    if (s->stream) cudaStreamDestroy(s->stream);
+    unreserve();
+    return fail(RSS_ECUDA, "rss_server_add: stream or event creation failed");
+  }
+  const rss_status cs = prepare_solve_caches(f, S->max_cols, s->stream);
+  if (cs != RSS_OK) {
+    cudaEventDestroy(s->done);
+    cudaStreamDestroy(s->stream);
+    unreserve();
+    return cs;
+  }
   std::lock_guard<std::mutex> lk(S->mu);
   *factor_id = (int32_t)S->slots.size();
   S->slots.push_back(std::move(s));
@@ -297,7 +330,8 @@ rss_status rss_server_stats(rss_server* S, char* buf, size_t len) {
     std::lock_guard<std::mutex> lk(S->mu);
     o << "{\"requests\": " << S->n_req << ", \"batches\": " << S->n_batch << ", \"columns\": " << S->n_cols
       << ", \"max_requests_per_batch\": " << S->max_batch_seen << ", \"factors\": " << S->slots.size()
-      << ", \"device_bytes_in_use\": " << S->in_use << ", \"budget\": " << S->budget << "}";
+      << ", \"device_bytes_in_use\": " << S->in_use << ", \"device_bytes_reserved\": " << S->reserved
+      << ", \"budget\": " << S->budget << "}";
   }
   const std::string s = o.str();
   if (s.size() + 1 > len) return fail(RSS_EINVAL, "rss_server_stats: buffer too small");

@@ -971,9 +971,7 @@ bool slices_fit(const rss_factorization* f) {
   return true;
 }
 
-rss_status ensure_slices(rss_factorization* f, cudaStream_t st) {
-  std::lock_guard<std::mutex> lk(f->slice_mu);
-  if (f->slices_ready) return RSS_OK;
+size_t slice_total(const rss_factorization* f) {
   auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
   size_t total = 0;
   for (size_t bi = 0; bi < f->batches.size(); ++bi) {
@@ -986,6 +984,14 @@ rss_status ensure_slices(rss_factorization* f, cudaStream_t st) {
                al(sizeof(uint16_t) * hr[q].r * OZ_S * cp) + al(sizeof(int) * hr[q].r);
     }
   }
+  return total;
+}
+
+rss_status ensure_slices(rss_factorization* f, cudaStream_t st) {
+  std::lock_guard<std::mutex> lk(f->slice_mu);
+  if (f->slices_ready) return RSS_OK;
+  auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
+  const size_t total = slice_total(f);
   char* base = nullptr;
   RSS_CUDA(pool_malloc(reinterpret_cast<void**>(&base), total, st));
   char* p = base;
@@ -1026,6 +1032,7 @@ rss_status ensure_slices(rss_factorization* f, cudaStream_t st) {
     }
   }
   RSS_CUDA(cudaStreamSynchronize(st));   // other streams may use the slices from here on
+  f->slice_bytes = total;
   f->d_slice_mem = base;
   f->d_slices = recs;
   f->slices_ready = true;
@@ -1161,6 +1168,22 @@ rss_status solve_impl(const rss_factorization* f, T* b, int64_t nrhs, int64_t ld
 }
 
 template rss_status solve_impl<double>(const rss_factorization*, double*, int64_t, int64_t, cudaStream_t);
+
+size_t solve_device_bytes(const rss_factorization* f, int64_t nrhs) {
+  const size_t esz = f->is_complex ? 16 : 8;
+  const size_t xb = (esz * (size_t)f->n * (size_t)nrhs + 255) & ~size_t(255);
+  return xb + (f->is_complex ? sweep_ws<zd>(f, nrhs, rhs_chunk(nrhs)).bytes
+                             : sweep_ws<double>(f, nrhs, rhs_chunk(nrhs)).bytes);
+}
+
+size_t solve_cache_bytes(const rss_factorization* f, int64_t max_nrhs) {
+  return use_tc(f, max_nrhs) && slices_fit(f) ? slice_total(f) : 0;
+}
+
+rss_status prepare_solve_caches(const rss_factorization* f, int64_t max_nrhs, cudaStream_t st) {
+  if (!use_tc(f, max_nrhs) || !slices_fit(f)) return RSS_OK;
+  return ensure_slices(const_cast<rss_factorization*>(f), st);
+}
 template rss_status solve_impl<zd>(const rss_factorization*, zd*, int64_t, int64_t, cudaStream_t);
 
 // ---------------------------------------------------------------------------

@@ -43,7 +43,7 @@ class _Params(ctypes.Structure):
                 ("schur_path", ctypes.c_int), ("id_cluster", ctypes.c_int),
                 ("bump_cx", ctypes.c_double), ("bump_cy", ctypes.c_double),
                 ("bump_a", ctypes.c_double), ("diag_rule", ctypes.c_int), ("per_box", ctypes.c_int),
-                ("class_order", ctypes.c_int)]
+                ("class_order", ctypes.c_int), ("wait_polls", ctypes.c_int)]
 
 
 _lib = None
@@ -155,7 +155,7 @@ def rss_factor(tree: Tree, kind: int = LAPLACE, eps: float = 1e-6, h: float = 0.
                phase=(0.0, 0.0), full_stack: bool = False, schur_fp64: bool = False,
                id_cluster: int = 0, diag_rule: int = 0, bump=(0.5, 0.5, 32.0),
                per_box: bool = False, schur_mma_sync: bool = False, class_order: int = 0,
-               stream=None) -> Factor:
+               wait_polls: int = 0, stream=None) -> Factor:
     lib = _load()
     p = _Params()
     p.kind, p.h, p.kappa = kind, h, kappa
@@ -175,6 +175,7 @@ def rss_factor(tree: Tree, kind: int = LAPLACE, eps: float = 1e-6, h: float = 0.
     p.diag_rule = diag_rule
     p.per_box = 1 if per_box else 0
     p.class_order = int(class_order)
+    p.wait_polls = int(wait_polls)
     out = ctypes.c_void_p()
     _check(lib.rss_factor(tree.handle, ctypes.byref(p), _stream_handle(stream), ctypes.byref(out)))
     return Factor(out, tree.n, kind in (HELMHOLTZ, TEST_POLY, HELMHOLTZ_LS), tree)
@@ -186,6 +187,24 @@ def rss_self_integral(kind: int, h: float, kappa: float = 0.0) -> complex:
     re, im = ctypes.c_double(), ctypes.c_double()
     _check(lib.rss_self_integral(kind, h, kappa, ctypes.byref(re), ctypes.byref(im)))
     return complex(re.value, im.value)
+
+
+def _columns(t, n: int, name: str) -> tuple[int, int]:
+    """(nrhs, ld) of an n x nrhs column-major tensor: shape (n,) or (n, nrhs) with
+    stride (1, ld).  With more than one column, ld must be at least n, so that the
+    columns do not overlap (an expanded tensor, whose columns share storage, is
+    refused: the library would read and write n * nrhs entries through it)."""
+    if t.dim() not in (1, 2):
+        raise ValueError(f"{name} must be 1-D or 2-D")
+    if t.shape[0] != n:
+        raise ValueError(f"{name} has the wrong number of rows")
+    if t.stride(0) != 1:
+        raise ValueError(f"{name} must be column-major: shape (n, nrhs), stride (1, ld)")
+    if t.dim() == 1 or t.shape[1] == 1:
+        return 1, n
+    if t.stride(1) < n:
+        raise ValueError(f"{name}: columns overlap (stride {t.stride(1)} < {n} rows)")
+    return t.shape[1], t.stride(1)
 
 
 def _dev_vector(f: Factor, t, name):
@@ -206,10 +225,9 @@ def rss_matvec(f: Factor, x, y=None, stream=None):
         y = torch.empty_like(x) if x.dim() == 1 else torch.empty(x.shape[1], x.shape[0], dtype=x.dtype,
                                                                   device=x.device).T
     y = _dev_vector(f, y, "y")
-    nrhs = 1 if x.dim() == 1 else x.shape[1]
-    ld = f.n if x.dim() == 1 else max(x.stride(1), f.n)
-    if x.dim() == 2 and max(y.stride(1), f.n) != ld:
-        raise ValueError("x and y must have the same leading dimension")
+    nrhs, ld = _columns(x, f.n, "x")
+    if _columns(y, f.n, "y") != (nrhs, ld):
+        raise ValueError("x and y must have the same shape and leading dimension")
     _check(_load().rss_matvec(f.handle, x.data_ptr(), y.data_ptr(), nrhs, ld, _stream_handle(stream)))
     return y
 
@@ -236,6 +254,8 @@ def rss_solve(f: Factor, b, stream=None):
         want = np.complex128 if f.is_complex else np.float64
         if b.dtype != want:
             raise TypeError(f"b must be {want.__name__}")
+        if not b.flags.writeable:
+            raise ValueError("b must be writeable (it is overwritten by the solution)")
         if b.ndim == 1:
             nrhs, ldb = 1, b.shape[0]
             if not b.flags.c_contiguous:
@@ -246,6 +266,8 @@ def rss_solve(f: Factor, b, stream=None):
             nrhs = b.shape[1]
             # a single column may carry any stride for its (unused) second axis
             ldb = b.shape[0] if nrhs == 1 else b.strides[1] // b.itemsize
+            if nrhs > 1 and ldb < b.shape[0]:
+                raise ValueError(f"b: columns overlap (stride {ldb} < {b.shape[0]} rows)")
         if b.shape[0] != f.n:
             raise ValueError("b has the wrong number of rows")
         _check(lib.rss_solve(f.handle, b.ctypes.data, nrhs, ldb, _stream_handle(stream)))
@@ -254,16 +276,7 @@ def rss_solve(f: Factor, b, stream=None):
     want = torch.complex128 if f.is_complex else torch.float64
     if b.dtype != want:
         raise TypeError(f"b must be {want}")
-    if b.dim() == 1:
-        if b.stride(0) != 1:
-            raise ValueError("b must be contiguous")
-        nrhs, ldb = 1, b.shape[0]
-    else:
-        if b.stride(0) != 1:
-            raise ValueError("b must be column-major: shape (n, nrhs), stride (1, ldb)")
-        nrhs, ldb = b.shape[1], max(b.stride(1), b.shape[0])
-    if b.shape[0] != f.n:
-        raise ValueError("b has the wrong number of rows")
+    nrhs, ldb = _columns(b, f.n, "b")
     _check(lib.rss_solve(f.handle, b.data_ptr(), nrhs, ldb, _stream_handle(stream)))
     return b
 
@@ -276,16 +289,7 @@ def rss_solve_noalloc(f: Factor, b, stream=None):
     want = torch.complex128 if f.is_complex else torch.float64
     if not isinstance(b, torch.Tensor) or not b.is_cuda or b.dtype != want:
         raise TypeError(f"b must be a CUDA tensor of {want}")
-    if b.dim() == 1:
-        if b.stride(0) != 1:
-            raise ValueError("b must be contiguous")
-        nrhs, ldb = 1, b.shape[0]
-    else:
-        if b.stride(0) != 1:
-            raise ValueError("b must be column-major: shape (n, nrhs), stride (1, ldb)")
-        nrhs, ldb = b.shape[1], max(b.stride(1), b.shape[0])
-    if b.shape[0] != f.n:
-        raise ValueError("b has the wrong number of rows")
+    nrhs, ldb = _columns(b, f.n, "b")
     _check(_load().rss_solve_noalloc(f.handle, b.data_ptr(), nrhs, ldb, _stream_handle(stream)))
     return b
 

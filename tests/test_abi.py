@@ -73,3 +73,34 @@ def test_self_integral_is_host_only_and_matches_oracle():
             assert abs(P.rss_self_integral(P.HELMHOLTZ, h, kappa) - o) <= 1e-12 * abs(o)
     with pytest.raises(P.RSSError, match="EINVAL"):
         P.rss_self_integral(P.HELMHOLTZ, 1 / 64, 0.0)
+
+
+def test_binding_refuses_overlapping_columns(lib):
+    """A right-hand-side matrix whose columns share storage (an expanded tensor, a
+    broadcast array: stride < n) or that cannot be written is refused by the
+    binding before anything reaches the library, which would otherwise read and
+    write n * nrhs entries through it."""
+    import torch
+
+    import paper_2310_15458_gb300 as P
+    n = 256
+    fake = P.rss.Factor(None, n, False, None)     # never passed to the library
+    b = torch.ones(n, 1, dtype=torch.float64).expand(n, 4)
+    assert b.stride() == (1, 0)
+    with pytest.raises(ValueError, match="overlap"):
+        P.rss_solve(fake, b)
+    short = torch.zeros(4, n - 1, dtype=torch.float64).T   # stride n - 1 < n
+    with pytest.raises(ValueError, match="wrong number of rows"):
+        P.rss_solve(fake, short)
+    rows = torch.zeros(2 * n, 3, dtype=torch.float64)[::2]   # stride(0) = 2
+    with pytest.raises(ValueError, match="column-major"):
+        P.rss_solve(fake, rows)
+    arr = np.broadcast_to(np.ones((n, 1)), (n, 4))
+    with pytest.raises(ValueError):
+        P.rss_solve(fake, arr)
+    overl = np.lib.stride_tricks.as_strided(np.zeros(n + 8), shape=(n, 4), strides=(8, 16))
+    with pytest.raises(ValueError, match="overlap"):
+        P.rss_solve(fake, overl)
+    # one column may carry any stride along its unused second axis
+    one = torch.zeros(1, n, dtype=torch.float64).T
+    assert P.rss._columns(one, n, "b") == (1, n)

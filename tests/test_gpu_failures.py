@@ -1,0 +1,82 @@
+"""Error statuses of rss_factor that come from the device: RSS_ENUMERIC (a zero
+pivot in the LU of Eq. 8, which supposes X_RR non-singular) and RSS_ETIMEOUT (a
+bounded barrier wait of the tensor-core Schur update that runs out).
+
+Neither test faults or hangs the GPU.  The zero pivot is an exactly singular
+input that the LU kernels detect and report; after it, every kernel still reads
+in-bounds pivot indices.  The timeout is forced by the wait_polls parameter,
+which makes the first barrier wait give up without polling; the CTA then waits
+(with the long drain limit) for the products it already issued, frees its tensor
+memory and returns.  After each failure the same process factors and solves a
+normal problem, so the CUDA context is still usable.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import workloads as W
+from oracle import rss as orss
+from oracle.dense import relres
+from oracle.rss import KernelSpec
+
+pytestmark = [pytest.mark.gpu, pytest.mark.filterwarnings("ignore::RuntimeWarning")]
+
+
+@pytest.fixture(scope="module")
+def P():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2310_15458_gb300 as P
+    return P
+
+
+def _still_works(P, side=32):
+    pts = W.grid_points(side)
+    f = P.rss_factor(P.rss_build_tree(pts, 16), kind=P.LAPLACE, eps=1e-8, h=1 / side)
+    b = W.gaussian_rhs(side * side, 1, False, 3)
+    x = torch.from_numpy(b[:, 0].copy()).cuda()
+    P.rss_solve(f, x)
+    torch.cuda.synchronize()
+    assert relres(pts, KernelSpec("laplace", h=1 / side), x.cpu().numpy()[:, None], b) <= 1e-7
+
+
+@pytest.mark.parametrize("side,where", [(64, "elimination"), (16, "top")])
+def test_zero_matrix_returns_enumeric(P, side, where):
+    """A = 0 (the real polynomial test kernel with no terms and a zero diagonal).
+    With leaf 64 on a 64 x 64 grid every leaf box has k = 0 (its proxy stack is
+    zero) and X_RR = 0, so the LU of the first box stops at a zero pivot; on a
+    16 x 16 grid there is no compressed level and the dense top LU meets it.  The
+    oracle rejects the same matrix."""
+    pts = W.grid_points(side)
+    spec = KernelSpec("rpoly", h=1 / side, coef=(), scale=1.0, diag=0.0)
+    with pytest.raises(np.linalg.LinAlgError):
+        orss.factor(pts, spec, 1e-6, leaf=64)
+    tree = P.rss_build_tree(pts, 64)
+    with pytest.raises(P.RSSError, match="ENUMERIC") as ei:
+        P.rss_factor(tree, kind=P.TEST_RPOLY, eps=1e-6, h=1 / side, coef=(), diag=0.0)
+    assert ei.value.status == 4
+    assert ("top" in str(ei.value)) == (where == "top")
+    _still_works(P)
+
+
+@pytest.mark.parametrize("kind", ["laplace", "helmholtz"])
+def test_schur_barrier_timeout_returns_etimeout(P, kind):
+    """wait_polls = -1 makes the first barrier wait of the tensor-core Schur update
+    (real: k_schur_tc, complex: k_schur_tc_c) give up at once: rss_factor must
+    return RSS_ETIMEOUT, and a factorization with the default limit must then
+    succeed in the same process and give the oracle's ranks."""
+    side = 64
+    pts = W.grid_points(side)
+    tree = P.rss_build_tree(pts, 64)
+    kw = dict(kind=P.LAPLACE if kind == "laplace" else P.HELMHOLTZ, eps=1e-6, h=1 / side, kappa=25.0)
+    with pytest.raises(P.RSSError, match="ETIMEOUT") as ei:
+        P.rss_factor(tree, wait_polls=-1, **kw)
+    assert ei.value.status == 5
+    with pytest.raises(P.RSSError, match="EINVAL"):
+        P.rss_factor(tree, wait_polls=-2, **kw)
+    f = P.rss_factor(tree, **kw)
+    fac = orss.factor(pts, KernelSpec(kind, h=1 / side, kappa=25.0), 1e-6, leaf=64)
+    for g in (8, 4):
+        assert np.array_equal(P.rss_level_ranks(f, g), fac.ranks[g])
+    _still_works(P)

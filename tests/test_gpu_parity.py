@@ -137,6 +137,49 @@ def test_helmholtz_records_and_solution_match_oracle(P):
     assert relres(pts, spec, x, b) <= 10 * eps
 
 
+@pytest.mark.parametrize("kappa", [25.0, 50.0], ids=["kappa25", "kappa50"])
+def test_helmholtz_leaf64_every_record_matches_oracle(P, kappa):
+    """128 x 128 Helmholtz, leaf 64, eps 1e-6: every record of the levels with box
+    grids 16, 8 and 4.  The merged boxes of the two coarse levels hold about 100
+    points, so this reaches the complex elimination of boxes too large for the
+    on-chip kernel, the complex panel products and Schur update on the tensor cores
+    at full operand sizes, and the real-stack ID on thread-block clusters.
+    kappa = 50 is the wavenumber of the 2048 x 2048 workload."""
+    side, eps = 128, 1e-6
+    pts = W.grid_points(side)
+    spec = KernelSpec("helmholtz", h=1 / side, kappa=kappa)
+    f = gpu_factor(P, pts, spec, eps, 64)
+    fac = orss.factor(pts, spec, eps, leaf=64)
+    for g in (16, 8, 4):
+        assert np.array_equal(P.rss_level_ranks(f, g), fac.ranks[g])
+    assert max(rec.S.size + rec.R.size for rec in fac.records) > 80
+    assert _compare_records(P, f, fac, rec_tol(eps)) == len(fac.records)
+    b = W.gaussian_rhs(side * side, 2, True, 1004)
+    x = gpu_solve(P, f, b)
+    assert rel(x, orss.solve(fac, b)) < 1e-9
+    assert relres(pts, spec, x, b) <= 10 * eps
+
+
+def test_laplace_256x256_every_record_matches_oracle(P):
+    """256 x 256 Laplace, leaf 64, eps 1e-6: every record of all four compressed
+    levels (box grids 32, 16, 8, 4).  Covers the one-CTA ID (colour classes of
+    about 114 boxes), the cluster ID (28 boxes and fewer), and the real panel
+    products and Schur update at n_B of about 80 to 100."""
+    side, eps = 256, 1e-6
+    pts = W.grid_points(side)
+    spec = KernelSpec("laplace", h=1 / side)
+    f = gpu_factor(P, pts, spec, eps, 64)
+    fac = orss.factor(pts, spec, eps, leaf=64)
+    for g in (32, 16, 8, 4):
+        assert np.array_equal(P.rss_level_ranks(f, g), fac.ranks[g])
+    assert max(rec.S.size + rec.R.size for rec in fac.records) > 80
+    assert _compare_records(P, f, fac, rec_tol(eps)) == len(fac.records)
+    b = W.gaussian_rhs(side * side, 1, False, 1003)
+    x = gpu_solve(P, f, b)
+    assert rel(x, orss.solve(fac, b)) < 1e-9
+    assert relres(pts, spec, x, b) <= 10 * eps
+
+
 def test_ragged_rhs_chunks_host_buffers_and_user_order(P):
     """nrhs = 9 (a ragged chunk of 8), host-buffer solve == device solve, shuffled points."""
     side, eps = 32, 1e-6

@@ -58,15 +58,38 @@ def test_served_results_equal_solo_results(P, fp64):
     assert st["requests"] == 48
     assert st["batches"] < 48 and st["max_requests_per_batch"] > 1
     assert st["device_bytes_in_use"] == 0
+    # the real factors' slice caches (panels of up to 64 columns take the
+    # tensor-core sweeps) were built by rss_server_add and charged to the budget
+    assert (st["device_bytes_reserved"] > 0) == (not fp64)
 
 
 def test_server_refuses_requests_beyond_its_budget(P):
     tree = P.rss_build_tree(W.grid_points(32), 16)
     f = P.rss_factor(tree, kind=0, eps=1e-6, h=1 / 32)
-    srv = P.rss_server_create(64 * 1024, 8)           # 64 KiB: 4 columns of n = 1024 at most
+    srv = P.rss_server_create(64 * 1024, 8)   # 64 KiB: panel + solve copy + workspace of 2 columns fit, 8 do not
     fid = P.rss_server_add(srv, f)
     ok = P.rss_server_submit(srv, fid, W.gaussian_rhs(1024, 2, False, 1))
     big = P.rss_server_submit(srv, fid, W.gaussian_rhs(1024, 8, False, 2))
     P.rss_server_wait(srv, ok, timeout=60.0)
     with pytest.raises(P.RSSError, match="ENOMEM"):
         P.rss_server_wait(srv, big, timeout=60.0)
+
+
+def test_server_add_charges_the_slice_cache(P):
+    """A real factor served with panels of 32 or more columns needs the digit-slice
+    cache of its sweeps; rss_server_add builds it and charges it to the budget, and
+    refuses the factorization (RSS_ENOMEM) when it does not fit.  With panels of at
+    most 16 columns no cache is needed."""
+    side = 64
+    f = P.rss_factor(P.rss_build_tree(W.grid_points(side), 64), kind=0, eps=1e-6, h=1 / side)
+    small = P.rss_server_create(256 * 1024, 64)
+    with pytest.raises(P.RSSError, match="ENOMEM"):
+        P.rss_server_add(small, f)
+    narrow = P.rss_server_create(256 * 1024, 16)
+    fid = P.rss_server_add(narrow, f)
+    assert P.rss_server_stats(narrow)["device_bytes_reserved"] == 0
+    b = W.gaussian_rhs(f.n, 3, False, 9)
+    x, _ = P.rss_server_wait(narrow, P.rss_server_submit(narrow, fid, b), timeout=60.0)
+    solo = np.asfortranarray(b.copy())
+    P.rss_solve(f, solo)
+    assert np.array_equal(x, solo)

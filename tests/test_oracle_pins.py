@@ -101,6 +101,47 @@ def test_cpqr_exact_low_rank_and_ties():
     assert perm[0] < 3
 
 
+def _orthogonal_columns(norms2, scale=1.0):
+    """Columns that are scaled, distinct unit vectors: a Householder step mixes only
+    the rows of the pivot, so every downdated norm stays exact and the pivot choice
+    depends on the given squared norms alone."""
+    n = len(norms2)
+    Y = np.zeros((n + 2, n))
+    Y[np.arange(n), np.arange(n)] = np.sqrt(np.asarray(norms2, dtype=float)) * scale
+    return Y
+
+
+@pytest.mark.parametrize("scale", [1.0, 1e-5, 1e4])
+def test_cpqr_tie_window(scale):
+    """The pivot rule: the largest remaining squared norm wins unless another column
+    lies within 1e-6 of it (relative), and among those the lowest original column
+    wins.  A window of 1e-4 would take the lower column at 2e-6 apart; a window of
+    1e-8 (or none) would take the larger one at 1e-7 apart.  The rule is relative,
+    so scaling Y changes nothing."""
+    for delta, first in ((2e-6, 1), (1e-7, 0), (5e-6, 1), (5e-7, 0)):
+        _, perm, _, _ = cpqr_id(_orthogonal_columns([1.0, 1.0 + delta, 0.5, 0.25], scale), 0.0)
+        assert perm[0] == first, (delta, perm)
+    # the same window at a later step (column 0 is taken first, then 1 and 2 compete)
+    for delta, second in ((2e-6, 2), (1e-7, 1)):
+        _, perm, _, _ = cpqr_id(_orthogonal_columns([4.0, 1.0, 1.0 + delta, 0.25], scale), 0.0)
+        assert perm[0] == 0 and perm[1] == second, (delta, perm)
+    # a larger column that comes first in the original order wins either way
+    _, perm, _, _ = cpqr_id(_orthogonal_columns([1.0 + 2e-6, 1.0, 0.5], scale), 0.0)
+    assert perm[0] == 0
+
+
+def test_cpqr_tie_window_absolute_floor():
+    """Deep in the ID the remaining norms are tiny next to the largest initial one
+    (y2max), and their rounding noise is set by y2max: columns within
+    1e-12 sqrt(n_max y2max) of the maximum n_max count as tied as well."""
+    # y2max = 1, n_max = 1e-13: the floor is 1e-12 * sqrt(1e-13) = 3.2e-19 (the
+    # relative part adds 1e-19)
+    _, perm, _, _ = cpqr_id(_orthogonal_columns([1.0, 1e-13, 1e-13 + 2e-19]), 0.0)
+    assert list(perm[:2]) == [0, 1]
+    _, perm, _, _ = cpqr_id(_orthogonal_columns([1.0, 1e-13, 1e-13 + 1e-18]), 0.0)
+    assert list(perm[:2]) == [0, 2]
+
+
 def test_cpqr_of_conjugate_stack_equals_real_stack():
     """[X; conj X] and [Re X; Im X] have proportional Gram matrices (2 Re X^H X),
     so column-pivoted QR gives both the same pivots and rank, and T is real."""

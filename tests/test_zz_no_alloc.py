@@ -2,10 +2,11 @@
 
 It serves callers that cannot allocate at call time (a framework allocator
 holding the device's memory, a latency-bound serving loop).  Its results must
-equal rss_solve's; it is called twice in a row on the same factorization to
-show that what one call leaves in the shared scratch array does not leak into
-the next.  This file is collected last so that a run stopping at the first
-failure has already run every other test.
+equal rss_solve's; it is called twice in a row on the same factorization, with
+different right-hand sides and column counts, to show that what one call leaves
+in the shared scratch array does not leak into the next.  This file is
+collected last so that a run stopping at the first failure has already run
+every other test.
 """
 import numpy as np
 import pytest
@@ -29,21 +30,22 @@ def _cols(b):
     return torch.from_numpy(np.ascontiguousarray(b.T)).cuda().T   # (n, nrhs) column-major
 
 
-@pytest.mark.parametrize("kind,side,leaf,nrhs", [(0, 64, 64, 3), (1, 32, 16, 2)],
-                         ids=["laplace-f64", "helmholtz-c128"])
-def test_noalloc_matches_rss_solve_twice(P, kind, side, leaf, nrhs):
+@pytest.mark.parametrize("kind,side,leaf", [(0, 64, 64), (1, 32, 16)], ids=["laplace-f64", "helmholtz-c128"])
+def test_noalloc_matches_rss_solve_twice(P, kind, side, leaf):
+    """Two calls in a row that differ: the first with 36 right-hand sides (more
+    columns, and the multi-column sweep workspace), the second with 3 columns of a
+    fresh b.  Whatever the first call leaves in the shared scratch array must not
+    reach the second call's result; each must equal rss_solve's."""
     tree = P.rss_build_tree(W.grid_points(side), leaf)
     f = P.rss_factor(tree, kind=kind, eps=1e-8, h=1.0 / side, kappa=25.0)
-    b = W.gaussian_rhs(side * side, nrhs, kind == 1, 11)
-    ref = _cols(b)
-    P.rss_solve(f, ref)
-    torch.cuda.synchronize()
-    ref = ref.cpu().numpy()
-    for call in range(2):
+    for call, (nrhs, seed) in enumerate(((36, 11), (3, 12))):
+        b = W.gaussian_rhs(side * side, nrhs, kind == 1, seed)
+        ref = _cols(b)
+        P.rss_solve(f, ref)
         x = _cols(b)
         P.rss_solve_noalloc(f, x)
         torch.cuda.synchronize()
-        x = x.cpu().numpy()
+        ref, x = ref.cpu().numpy(), x.cpu().numpy()
         err = np.linalg.norm(x - ref) / np.linalg.norm(ref)
         assert err <= 1e-12, (call, err)
 
