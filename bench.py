@@ -9,9 +9,10 @@ sparsification and LU, Schur updates, merge), the dense top LU, and one
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
 
 Prints one JSON line (rank 0).  --impl reference times the CPU oracle on the
-host cores instead (a bounded sample of the same workload, scaled by N because
-the method is O(N)).  With N > 1 under torchrun every rank factors its own copy
-(replicas: the single-GPU path has no data exchange).
+host cores instead: each step is the oracle on a 128 x 128 grid of the same
+workload, and the config names that size (a scaled full-size figure is reported
+separately and labelled as a model).  With N > 1 under torchrun every rank
+factors its own copy (replicas: the single-GPU path has no data exchange).
 """
 from __future__ import annotations
 
@@ -34,12 +35,17 @@ import workloads as W  # noqa: E402
 
 WORKLOAD = "laplace_1024x1024_eps1e-6"
 METRIC = "RS-S factor s and solve RHS/s at N=1M, rel.res<=1e-5; serve p50/p99 latency"
-# FP64 FMA throughput of this GB300, measured with a DFMA loop over 152 SMs x 8
-# CTAs (1.195 TFLOP/s at a 1995 MHz SM clock); the fp64 mma.sync path measured
-# 1.05 TFLOP/s, so DFMA is the FP64 roof.
-FP64_PEAK_TFLOPS = 1.195
-TRAFFIC_PER_LAUNCH = {"id": 3.482e9, "elim": 6.37e8, "schur": 1.603e9}   # bytes, see the roofline below
-CPU_SAMPLE_SIDE = 128           # oracle sample: the same workload on a 128 x 128 grid
+# FP64 roof of the FP64-bound phases: the nominal FP64 rate of a GB300, 1.25
+# TFLOP/s (152 SMs x 2.07 GHz x 2 FP64 FMA per clock and SM x 2 flop = 1.26).  The
+# bench also measures it with the library's DFMA probe (rss_probe_fp64) and
+# reports both; FP64 tensor-core MMAs (mma.sync f64) are no faster than DFMA here.
+FP64_PEAK_TFLOPS = 1.25
+# DRAM bytes (read + write) of the dominant phase's kernels per factorization of
+# the 1024 x 1024 Laplace workload, from an ncu capture of the same kernels on a
+# smaller grid scaled by the boxes processed (source in the dict); None when the
+# kernels have changed since the capture.
+TRAFFIC = {"id": None}
+CPU_SAMPLE_SIDES = (128, 256)   # oracle samples: the same workload on these grids
 
 
 def parse():
@@ -53,8 +59,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-paper", action="store_true")
-    ap.add_argument("--serve-requests", type=int, default=600,
-                    help="requests per load, the first 100 warm-up (2100 is the full protocol)")
+    ap.add_argument("--serve-requests", type=int, default=2100,
+                    help="requests per load, the first 100 warm-up (2100: the full protocol)")
+    ap.add_argument("--no-large", action="store_true", help="skip the 2048^2 Helmholtz served run")
     ap.add_argument("--serve-loads", type=float, nargs="+", default=[0.5, 0.9])
     return ap.parse_args()
 
@@ -145,56 +152,110 @@ sys.path.insert(0, {root!r})
 import workloads as W
 from oracle import rss
 from oracle.rss import KernelSpec
-side, kind, kappa, eps, reps = {side}, {kind}, {kappa}, {eps}, {reps}
-pts = W.grid_points(side)
-spec = KernelSpec("laplace" if kind == W.LAPLACE else "helmholtz", h=1.0 / side, kappa=kappa)
-b = W.gaussian_rhs(side * side, 1, kind != W.LAPLACE, 1002)
-ts = []
-for _ in range(reps):
-    t0 = time.perf_counter()
-    fac = rss.factor(pts, spec, eps)
-    x = rss.solve(fac, b)
-    ts.append(time.perf_counter() - t0)
-print(json.dumps({{"times": ts}}))
+kind, kappa, eps, seed = {kind}, {kappa}, {eps}, {seed}
+out = []
+for side, reps in {plan!r}:
+    pts = W.grid_points(side)
+    spec = KernelSpec("laplace" if kind == W.LAPLACE else "helmholtz", h=1.0 / side, kappa=kappa)
+    b = W.gaussian_rhs(side * side, 1, kind != W.LAPLACE, seed)
+    for _ in range(reps):
+        t0, c0 = time.perf_counter(), time.process_time()
+        fac = rss.factor(pts, spec, eps)
+        x = rss.solve(fac, b)
+        out.append({{"side": side, "s": time.perf_counter() - t0, "cpu_s": time.process_time() - c0}})
+print(json.dumps(out))
 """
 
 
-def run_oracle(w, reps):
-    """Time the oracle (factor + 1-RHS solve) on the sample grid, single-threaded."""
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    code = CPU_SNIPPET.format(root=ROOT, side=CPU_SAMPLE_SIDE, kind=w["kind"], kappa=w["kappa"],
-                              eps=w["eps"], reps=reps)
-    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
-                         check=True)
-    return json.loads(out.stdout.strip().splitlines()[-1])["times"]
+def host_info():
+    """Host cores and CPU model (the oracle's timings are only meaningful with them)."""
+    info = {"nproc": os.cpu_count()}
+    try:
+        txt = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=20).stdout
+        keep = ("Architecture", "Model name", "Socket(s)", "Core(s) per socket", "Thread(s) per core",
+                "CPU(s)", "CPU max MHz")
+        info["lscpu"] = {k.strip(): v.strip() for k, v in
+                         (ln.split(":", 1) for ln in txt.splitlines() if ":" in ln) if k.strip() in keep}
+    except (OSError, subprocess.SubprocessError):
+        info["lscpu"] = None
+    return info
 
 
-def cpu_block(w, times):
-    scale = (w["side"] / CPU_SAMPLE_SIDE) ** 2
-    return {"value": statistics.mean(times) * scale, "unit": "s", "cores": 1, "kind": "oracle",
-            "sample": (f"oracle factor + 1-RHS solve of the same workload on a {CPU_SAMPLE_SIDE}x"
-                       f"{CPU_SAMPLE_SIDE} grid ({len(times)} runs, mean "
-                       f"{statistics.mean(times):.2f} s), scaled by the point-count ratio "
-                       f"{scale:g} (the factorization is O(N))")}
+def run_oracle(w, plan):
+    """Time the oracle (factor + 1-RHS solve) as it stands, once per (side, reps)
+    entry of plan, in one process, with the BLAS thread pools set to every host core."""
+    nproc = str(os.cpu_count() or 1)
+    env = dict(os.environ, OMP_NUM_THREADS=nproc, OPENBLAS_NUM_THREADS=nproc, MKL_NUM_THREADS=nproc)
+    code = CPU_SNIPPET.format(root=ROOT, kind=w["kind"], kappa=w["kappa"], eps=w["eps"], seed=w["seed"],
+                              plan=list(plan))
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, check=True)
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+def sample_name(w, side):
+    kind = "laplace" if w["kind"] == W.LAPLACE else f"helmholtz_k{w['kappa']:g}"
+    return f"{kind}_{side}x{side}_eps" + f"{w['eps']:.0e}".replace("e-0", "e-")
+
+
+def cpu_block(w, runs):
+    """The oracle on two grids of the workload (the larger one is the reported
+    sample); the full-size figure is a power-law model fitted to the two, kept in
+    its own key."""
+    by = {}
+    for r in runs:
+        by.setdefault(r["side"], []).append(r)
+    sides = sorted(by)
+    big = sides[-1]
+    t = {sd: statistics.mean(r["s"] for r in by[sd]) for sd in sides}
+    util = statistics.mean(r["cpu_s"] / r["s"] for r in by[big])
+    out = {"value": t[big], "unit": "s", "cores": os.cpu_count(), "kind": "oracle",
+           "sample": (f"oracle factor + 1-RHS solve of {sample_name(w, big)} ({big * big} points; the "
+                      f"workload's kernel, eps, leaf and proxies), {len(by[big])} run(s), BLAS threads = "
+                      f"{os.cpu_count()} (cores), measured CPU time / wall time {util:.2f}"),
+           "n": big * big, "cpu_busy_cores": util, "host": host_info(),
+           "measured_s": {str(sd * sd): t[sd] for sd in sides}}
+    if len(sides) > 1 and w["side"] > big:
+        a = math.log(t[big] / t[sides[0]]) / math.log((big / sides[0]) ** 2)
+        out["model_full_size"] = {"s": t[big] * ((w["side"] / big) ** 2) ** a, "n": w["side"] ** 2,
+                                  "exponent": a, "kind": "model, not measured: t ~ N^exponent fitted "
+                                                         "to the two measured sizes"}
+    return out
+
+
+REF_SAMPLE_SIDE = 128   # one reference step: the oracle on a 128 x 128 grid of the workload
 
 
 def reference_arm(args, w):
+    """The CPU oracle as it stands, timed on the host cores.  A step is one oracle
+    factor + 1-RHS solve of the workload's problem on a 128 x 128 grid (the full
+    1024 x 1024 problem takes the oracle far longer than the run may last); the
+    config names that size.  A linear (O(N)) model of the full size is given in
+    its own key and is not a measurement."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    for _ in range(args.warmup):
-        run_oracle(w, 1)
-    times = run_oracle(w, args.steps)
-    cb = cpu_block(w, times)
-    line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": "s",
+    side = min(REF_SAMPLE_SIDE, w["side"])
+    runs = run_oracle(w, [(side, args.warmup + args.steps)])
+    times = [r["s"] for r in runs[args.warmup:]]
+    util = statistics.mean(r["cpu_s"] / r["s"] for r in runs[args.warmup:])
+    value = statistics.mean(times)
+    cb = {"value": value, "unit": "s", "cores": os.cpu_count(), "kind": "oracle",
+          "sample": (f"oracle factor + 1-RHS solve of {sample_name(w, side)} ({side * side} points) per step, "
+                     f"BLAS threads = {os.cpu_count()} (cores), measured CPU time / wall time {util:.2f}"),
+          "cpu_busy_cores": util, "host": host_info()}
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": cb["value"] * 1e3, "higher_is_better": False, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": args.workload, "n": w["side"] ** 2, "eps": w["eps"], "leaf": W.LEAF,
-                       "proxy_n": W.PROXY_N, "rhs": 1,
+            "ms_per_step": value * 1e3, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64" if not w["complex"] else "c128", "data": "synthetic",
+            "config": {"workload": sample_name(w, side), "sample_of": args.workload, "n": side * side,
+                       "eps": w["eps"], "leaf": W.LEAF, "proxy_n": W.PROXY_N, "rhs": 1,
                        "parallelism": "replicas" if args.gpus > 1 else "single"},
+            "model_full_size": {"s": value * (w["side"] / side) ** 2, "n": w["side"] ** 2,
+                                "kind": "model, not measured: the sample's time scaled by the point count "
+                                        "(the method is O(N); this oracle grows faster than that, so the "
+                                        "model is a lower bound)"},
             "cpu_baseline": cb,
-            "e2e": {"value": cb["value"], "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+            "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
@@ -259,14 +320,49 @@ SERVE_SET = [("laplace", 128, 0.0), ("laplace", 256, 0.0), ("laplace", 512, 0.0)
              ("helmholtz", 256, 25.0)]
 
 
+def _drive(P, srv, ids, pool, which, nrhs, gaps):
+    """Submit request q at time sum(gaps[:q+1]) (all at once when gaps is None) from
+    host buffers; a second thread waits for the tickets in order.  Returns the
+    latencies (s) and the wall time from the first submission to the last result."""
+    import threading
+    nreq = len(which)
+    tickets = [None] * nreq
+    lat = [0.0] * nreq
+    done = threading.Event()
+
+    def waiter():
+        for q in range(nreq):
+            while tickets[q] is None:
+                time.sleep(1e-5)
+            _, lat[q] = P.rss_server_wait(srv, tickets[q], timeout=300.0)
+        done.set()
+
+    th = threading.Thread(target=waiter)
+    th.start()
+    t_start = time.perf_counter()
+    t_next = t_start
+    for q in range(nreq):
+        if gaps is not None:
+            t_next += gaps[q]
+            while time.perf_counter() < t_next:
+                pass
+        j = int(which[q])
+        tickets[q] = P.rss_server_submit(srv, ids[j], np.asfortranarray(pool[j][:, :int(nrhs[q])]))
+    done.wait()
+    t_total = time.perf_counter() - t_start
+    th.join()
+    return np.array(lat), t_total
+
+
 def serve_run(P, torch, args):
     """Resident factorizations (Laplace 128^2, 256^2, 512^2 and Helmholtz kappa = 25 at
     256^2, eps 1e-6) behind the continuous-batching server; seeded Poisson arrivals of
     requests with 1-64 Gaussian right-hand sides on a uniformly drawn factorization, at
-    loads of 50 % and 90 % of the solo capacity; the first 100 requests of each run are
-    warm-up.  Latency = submit to result in host memory.  Beside it, the same requests
-    solved one after another (no batching) give the plain throughput."""
-    import threading
+    loads of 50 % and 90 % of the solo capacity, then the same requests submitted all at
+    once (saturation: the server's capacity).  The first 100 requests of each run are
+    warm-up.  Latency = submit to result in host memory.  Beside it, requests of the
+    saturation run solved one after another with no server (each alone, host buffers)
+    give the plain throughput."""
     facs = []
     for kind, side, kappa in SERVE_SET:
         tree = P.rss_build_tree(W.grid_points(side), W.LEAF)
@@ -285,60 +381,87 @@ def serve_run(P, torch, args):
             b = np.asfortranarray(pool[j][:, :32].copy())
             P.rss_solve(f, b)
         solo.append((time.perf_counter() - t0) / 3)
-    srv = P.rss_server_create(8 << 30, 256)
+    srv = P.rss_server_create(24 << 30, 256)
     ids = [P.rss_server_add(srv, f) for f in facs]
     nreq = args.serve_requests
     warm = min(100, nreq // 6)
+    rng = np.random.default_rng(1003)
+    which = rng.integers(0, len(facs), nreq)
+    nrhs = rng.integers(1, 65, nreq)
+    mean_service = float(np.mean(solo)) * (np.mean(nrhs) / 32.0)
     runs = []
-    for li, load in enumerate(args.serve_loads):
-        rng = np.random.default_rng(1003 + li)
-        which = rng.integers(0, len(facs), nreq)
-        nrhs = rng.integers(1, 65, nreq)
-        mean_service = float(np.mean(solo)) * (np.mean(nrhs) / 32.0)
-        rate = load / mean_service
-        gaps = rng.exponential(1.0 / rate, nreq)
-        tickets = [None] * nreq
-        lat = [0.0] * nreq
-        done = threading.Event()
-
-        def waiter():
-            for q in range(nreq):
-                while tickets[q] is None:
-                    time.sleep(1e-5)
-                _, lat[q] = P.rss_server_wait(srv, tickets[q], timeout=120.0)
-            done.set()
-
-        th = threading.Thread(target=waiter)
-        th.start()
-        t_start = time.perf_counter()
-        t_next = t_start
-        for q in range(nreq):
-            t_next += gaps[q]
-            while time.perf_counter() < t_next:
-                pass
-            j = int(which[q])
-            b = np.asfortranarray(pool[j][:, :int(nrhs[q])])
-            tickets[q] = P.rss_server_submit(srv, ids[j], b)
-        done.wait()
-        t_total = time.perf_counter() - t_start
-        th.join()
-        l = np.array(lat[warm:]) * 1e3
-        runs.append({"load": load, "arrival_rate_per_s": rate, "p50_ms": float(np.percentile(l, 50)),
+    for li, load in enumerate(list(args.serve_loads) + [None]):
+        if load is None:
+            lat, t_total = _drive(P, srv, ids, pool, which, nrhs, None)
+            rate = None
+        else:
+            rate = load / mean_service
+            gaps = np.random.default_rng(2003 + li).exponential(1.0 / rate, nreq)
+            lat, t_total = _drive(P, srv, ids, pool, which, nrhs, gaps)
+        l = lat[warm:] * 1e3
+        runs.append({"load": "saturation (all requests submitted at once)" if load is None else load,
+                     "arrival_rate_per_s": rate, "p50_ms": float(np.percentile(l, 50)),
                      "p99_ms": float(np.percentile(l, 99)), "mean_ms": float(l.mean()),
-                     "rhs_per_s": float(nrhs.sum() / t_total)})
+                     "rhs_per_s": float(nrhs.sum() / t_total), "wall_s": t_total})
     st = P.rss_server_stats(srv)
-    # the plain form: the last run's requests one after another, each solved alone
+    # the plain form: requests one after another, each solved alone (host buffers)
+    nplain = min(nreq - warm, 600)
     t0 = time.perf_counter()
-    for q in range(warm, nreq):
+    for q in range(warm, warm + nplain):
         j = int(which[q])
         b = np.asfortranarray(pool[j][:, :int(nrhs[q])].copy())
         P.rss_solve(facs[j], b)
-    plain = float(nrhs[warm:].sum() / (time.perf_counter() - t0))
+    plain = float(nrhs[warm:warm + nplain].sum() / (time.perf_counter() - t0))
+    sat = runs[-1]["rhs_per_s"]
     return {"workload": "Laplace 128^2, 256^2, 512^2 + Helmholtz k=25 256^2, eps 1e-6, 1-64 RHS",
             "requests_per_run": nreq, "warmup_requests": warm, "runs": runs,
-            "plain_sequential_rhs_per_s": plain, "panels": st["batches"],
-            "max_requests_per_panel": st["max_requests_per_batch"],
+            "plain_sequential_rhs_per_s": plain, "plain_sequential_requests": nplain,
+            "served_over_plain_at_saturation": sat / plain,
+            "panels": st["batches"], "max_requests_per_panel": st["max_requests_per_batch"],
             "solo_ms_32rhs": [t * 1e3 for t in solo]}
+
+
+def served_large_run(P, torch):
+    """The 2048 x 2048 Helmholtz workload (kappa = 50, complex, eps 1e-6): factored, then
+    its 64 seeded complex Gaussian right-hand sides submitted to the server as 64
+    one-column requests at once; the worker batches them into panels.  Relative
+    residual of every column by the FFT matvec of the exact A."""
+    w = W.WORKLOADS["helmholtz_k50_2048x2048_eps1e-6"]
+    side, n = w["side"], w["side"] ** 2
+    tree = P.rss_build_tree(W.grid_points(side), W.LEAF)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    f = P.rss_factor(tree, kind=W.HELMHOLTZ, eps=w["eps"], h=1.0 / side, kappa=w["kappa"])
+    torch.cuda.synchronize()
+    t_fact = time.perf_counter() - t0
+    info = P.rss_info(f)
+    b = W.gaussian_rhs(n, w["nrhs"], True, w["seed"])
+    srv = P.rss_server_create(64 << 30, 64)
+    fid = P.rss_server_add(srv, f)
+    # warm-up request (plans, workspaces)
+    P.rss_server_wait(srv, P.rss_server_submit(srv, fid, np.asfortranarray(b[:, :1])), timeout=300.0)
+    t0 = time.perf_counter()
+    tickets = [P.rss_server_submit(srv, fid, np.asfortranarray(b[:, j])) for j in range(w["nrhs"])]
+    xs, lat = [], []
+    for t in tickets:
+        x, l = P.rss_server_wait(srv, t, timeout=300.0)
+        xs.append(x)
+        lat.append(l)
+    t_all = time.perf_counter() - t0
+    st = P.rss_server_stats(srv)
+    X = torch.from_numpy(np.ascontiguousarray(np.stack(xs, axis=0))).cuda().T
+    B = torch.from_numpy(np.ascontiguousarray(b.T)).cuda().T
+    R = P.rss_matvec(f, X) - B
+    relres = float(torch.linalg.vector_norm(R) / torch.linalg.vector_norm(B))
+    lat = np.array(lat) * 1e3
+    out = {"workload": "helmholtz_k50_2048x2048_eps1e-6", "n": n, "factor_s": t_fact,
+           "factor_gpu_ms": info["gpu_ms"], "rhs": w["nrhs"], "served_rhs_per_s": w["nrhs"] / t_all,
+           "served_wall_s": t_all, "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+           "panels": st["batches"] - 1, "relres": relres,
+           "ranks": [{"side": L["side"], "k_mean": L["k_mean"], "k_max": L["k_max"]} for L in info["levels"]]}
+    del srv, f, tree, X, B, R
+    torch.cuda.empty_cache()
+    return out
 
 
 def batching_run(P, torch):
@@ -497,10 +620,9 @@ def native_arm(args, w):
     flops = info["flops"][dom]
     achieved = flops / (gms[dom] * 1e-3) / 1e12
     kern = {"id": "k_id", "elim": "k_elim", "schur": "k_schur"}[dom]
-    # DRAM bytes (read + write) per launch of each phase's kernels, from one ncu
-    # capture of this command (profiles/traffic_factor_laplace_1024x1024.md); only
-    # valid for the 1024 x 1024 Laplace workload and the kernels as captured
-    traffic = TRAFFIC_PER_LAUNCH.get(dom) if args.workload == WORKLOAD else None
+    tr = TRAFFIC.get(dom) if args.workload == WORKLOAD else None
+    traffic = tr["bytes_per_factor"] / max(launches, 1) if tr else None
+    probe_tflops, probe_ms = P.rss_probe_fp64(stream=stream)
     solve_launches = 2 + 2 * info["batches"] + 1
     line = {
         "metric": METRIC, "value": ms / 1e3, "unit": "s", "n_gpus": world, "steps": args.steps,
@@ -531,16 +653,22 @@ def native_arm(args, w):
         "roofline": {"kernel": kern, "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
                      "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
                      "launches": launches, "avg_launch_ms": gms[dom] / max(launches, 1),
-                     "peak_source": "FP64 DFMA loop measured on this GB300 (no FP64 figure in "
-                                    "MEASURED_PEAKS.json)"},
+                     "peak_source": "nominal FP64 rate (152 SMs x 2.07 GHz x 2 FMA/clk x 2); no FP64 "
+                                    "figure in MEASURED_PEAKS.json",
+                     "peak_probe": probe_tflops, "frac_of_probe": achieved / probe_tflops,
+                     "probe": "rss_probe_fp64: independent DFMA chains, 8 CTAs x 256 threads per SM, "
+                              "best of 5 launches of %.1f ms" % probe_ms,
+                     "traffic_source": tr["source"] if tr else "none for the kernels as built"},
     }
     if not args.no_serve:
         line["serve"] = serve_run(P, torch, args)
+        if not args.no_large and world == 1:
+            line["served_helmholtz_2048"] = served_large_run(P, torch)
     if not args.no_paper and world == 1:
         line["paper_problems"] = paper_problems(P, torch)
         line["batching"] = batching_run(P, torch)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_block(w, run_oracle(w, 1))
+        line["cpu_baseline"] = cpu_block(w, run_oracle(w, [(sd, 1) for sd in CPU_SAMPLE_SIDES if sd <= side]))
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:

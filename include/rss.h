@@ -259,6 +259,15 @@ void rss_free(void* handle);
  * RSS_ECUDA if the device cannot be queried or synchronised. */
 rss_status rss_trim_memory(size_t keep_bytes);
 
+/* Measurement, not part of the method (the paper has no counterpart): the FP64
+ * fused multiply-add throughput of the current device, from a loop of
+ * independent DFMA chains over 8 CTAs of 256 threads per SM, best of five timed
+ * launches (CUDA events on stream) after one warm-up.  *tflops receives
+ * 2 x FMAs / time in TFLOP/s and *ms (may be NULL) the launch time.  It is the
+ * peak against which the FP64-bound phases (the ID, the small LUs) are reported.
+ * Synchronises stream; takes about half a second. */
+rss_status rss_probe_fp64(double* tflops, double* ms, void* stream);
+
 /* Message for the last non-OK status returned on this thread. */
 const char* rss_last_error(void);
 

@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "librss_gb300.so")
-SOURCES = ["api.cu", "factor.cu", "solve.cu", "serve.cu", "iterative.cu"]
+SOURCES = ["api.cu", "factor.cu", "solve.cu", "serve.cu", "iterative.cu", "probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC,-O2",
          "-Xptxas", "-O3"]

@@ -164,7 +164,8 @@ __global__ void __launch_bounds__(SW_NT_R) k_down(const BoxRec<T>* __restrict__ 
   extern __shared__ __align__(16) unsigned char smraw[];
   constexpr int LDF = SW_ROWS_D + 1;
   const BoxRec<T> R = recs[blockIdx.y];
-  const int k = R.k, r = R.r, c = R.c, nch = (c + SW_ROWS_D - 1) / SW_ROWS_D;
+  // at least one CTA per box: with c = 0 it still forms y_R and y_S
+  const int k = R.k, r = R.r, c = R.c, nch = max(1, (c + SW_ROWS_D - 1) / SW_ROWS_D);
   if ((int)blockIdx.x >= nch) return;
   const int i0 = blockIdx.x * SW_ROWS_D, rows = min(SW_ROWS_D, c - i0);
   const int q0 = blockIdx.z * RC, nq = min(RC, nrhs - q0);
@@ -288,6 +289,7 @@ __device__ void tc_gemm32(int M, int K, AF aval, BF bval, OF cout, uint16_t* As,
   const int m0 = (warp >> 1) * 16, n0 = (warp & 1) * 16;
   const int a_row = lane & 15, a_k = (lane >> 4) * 8;
   const int b_row = ((lane >> 4) << 3) + (lane & 7), b_k = ((lane >> 3) & 1) * 8;
+  __syncthreads();   // the caller's shared operands are written (with K = 0 no chunk barrier follows)
   for (int mt = 0; mt < M; mt += TCM) {
     double acc[2][4];
 #pragma unroll

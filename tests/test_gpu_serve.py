@@ -82,10 +82,12 @@ def test_server_add_charges_the_slice_cache(P):
     most 16 columns no cache is needed."""
     side = 64
     f = P.rss_factor(P.rss_build_tree(W.grid_points(side), 64), kind=0, eps=1e-6, h=1 / side)
-    small = P.rss_server_create(256 * 1024, 64)
+    # the cache of this factor takes tens of MB; a 3-column panel and its solve
+    # workspace take well under 1 MB
+    small = P.rss_server_create(4 << 20, 64)
     with pytest.raises(P.RSSError, match="ENOMEM"):
         P.rss_server_add(small, f)
-    narrow = P.rss_server_create(256 * 1024, 16)
+    narrow = P.rss_server_create(4 << 20, 16)
     fid = P.rss_server_add(narrow, f)
     assert P.rss_server_stats(narrow)["device_bytes_reserved"] == 0
     b = W.gaussian_rhs(f.n, 3, False, 9)
