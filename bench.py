@@ -261,13 +261,24 @@ def reference_arm(args, w):
 
 # ----------------------------------------------------------------------------- the paper's problems
 PAPER_SET = [("laplace_quadrature_2048x2048", W.LAPLACE, 2048, 0.0),
-             ("lippmann_schwinger_k25_1024x1024", W.HELMHOLTZ_LS, 1024, 25.0)]
+             ("lippmann_schwinger_k25_1024x1024", W.HELMHOLTZ_LS, 1024, 25.0),
+             # increasing frequency, kappa = pi sqrt(N) / 16 (32 points per wavelength)
+             ("lippmann_schwinger_increasing_1024x1024", W.HELMHOLTZ_LS, 1024, math.pi * 1024 / 16),
+             ("lippmann_schwinger_increasing_2048x2048", W.HELMHOLTZ_LS, 2048, math.pi * 2048 / 16)]
+
+
+def proxy_count(kappa, side):
+    """Proxy points for the paper's problems: at least 64, and 2 kappa R + 30 on the
+    proxy circle of radius R = 2.5 L of the coarsest compressed boxes (L = 1/4), so
+    that the circle resolves the kernel's oscillation at the highest frequencies."""
+    return max(64, int(math.ceil(2 * kappa * 2.5 * 0.25 + 30)))
 
 
 def paper_problems(P, torch):
     """The paper's own discretisations (Section 5), run as the paper runs them:
     Laplace with the self-cell quadrature diagonal (Eq. 16) and the symmetrised
-    Lippmann-Schwinger system at kappa = 25 (Eqs. 19-20, Gaussian bump), proxy
+    Lippmann-Schwinger system at kappa = 25 and at the increasing frequency
+    kappa = pi sqrt(N) / 16 of Table "h2" (Eqs. 19-20, Gaussian bump), proxy
     radius 2.5 L (Section 2.3), eps 1e-6, leaf 64, one right-hand side of
     uniform random entries, refined to a relative residual of 1e-12 by PCG /
     GMRES(20) with the factorization as preconditioner.  Reported beside the
@@ -278,8 +289,12 @@ def paper_problems(P, torch):
         tree = P.rss_build_tree(W.grid_points(side), W.LEAF)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        f = P.rss_factor(tree, kind=kind, eps=1e-6, h=1.0 / side, kappa=kappa, diag_rule=1,
-                         proxy_radius_over_side=2.5)
+        try:
+            f = P.rss_factor(tree, kind=kind, eps=1e-6, h=1.0 / side, kappa=kappa, diag_rule=1,
+                             proxy_radius_over_side=2.5, proxy_n=proxy_count(kappa, side))
+        except P.RSSError as e:
+            out[name] = {"n": n, "kappa": kappa, "error": str(e)}
+            continue
         torch.cuda.synchronize()
         t_fact = time.perf_counter() - t0
         rng = np.random.default_rng(2001)
@@ -305,7 +320,8 @@ def paper_problems(P, torch):
         torch.cuda.synchronize()
         t_it = time.perf_counter() - t0
         info = P.rss_info(f)
-        out[name] = {"n": n, "factor_s": t_fact, "solve_s": t_solve, "relres_direct": direct,
+        out[name] = {"n": n, "kappa": kappa, "proxy_n": proxy_count(kappa, side),
+                     "factor_s": t_fact, "solve_s": t_solve, "relres_direct": direct,
                      "iterations": it, "relres_iterative": rr, "iterative_s": t_it,
                      "method": "gmres20" if f.is_complex else "pcg",
                      "ranks": [{"side": L["side"], "k_mean": L["k_mean"], "k_max": L["k_max"]}
@@ -368,6 +384,8 @@ def serve_run(P, torch, args):
         tree = P.rss_build_tree(W.grid_points(side), W.LEAF)
         facs.append(P.rss_factor(tree, kind=W.LAPLACE if kind == "laplace" else W.HELMHOLTZ,
                                  eps=1e-6, h=1.0 / side, kappa=kappa))
+    # the solve's launch form for each resident factorization, tuned once (1 column)
+    tuning = [P.rss_tune_solve(f, 1) for f in facs]
     pool = {}
     for j, f in enumerate(facs):
         pool[j] = W.gaussian_rhs(f.n, 64, f.is_complex, 2000 + j)
@@ -418,7 +436,9 @@ def serve_run(P, torch, args):
             "plain_sequential_rhs_per_s": plain, "plain_sequential_requests": nplain,
             "served_over_plain_at_saturation": sat / plain,
             "panels": st["batches"], "max_requests_per_panel": st["max_requests_per_batch"],
-            "solo_ms_32rhs": [t * 1e3 for t in solo]}
+            "solo_ms_32rhs": [t * 1e3 for t in solo],
+            "solve_launch_1rhs": [{"launch": t["launch"], "ms": t["ms"],
+                                   "per_class_ms": t["candidates"][0]["ms"]} for t in tuning]}
 
 
 def served_large_run(P, torch):
@@ -550,8 +570,10 @@ def native_arm(args, w):
     stream = torch.cuda.current_stream()
     x = torch.empty_like(b_dev)
 
+    tune = {}   # the solve's launch schedule, measured once during the warm-up
+
     def factor():
-        return P.rss_factor(tree, kind=kind, eps=eps, h=h, kappa=w["kappa"])
+        return P.rss_factor(tree, kind=kind, eps=eps, h=h, kappa=w["kappa"], tune_table=tune or None)
 
     def step():
         f = factor()
@@ -559,8 +581,10 @@ def native_arm(args, w):
         P.rss_solve(f, x.view(n, 1), stream=stream)
         return f
 
-    for _ in range(args.warmup):
+    for i in range(args.warmup):
         f = step()
+        if i == 0:
+            tune = P.rss_tune_solve(f, 1, stream=stream)
         del f
     barrier()
     clocks = Clocks(local)
@@ -607,7 +631,7 @@ def native_arm(args, w):
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     tr = P.rss_build_tree(pts_h, W.LEAF)
-    fe = P.rss_factor(tr, kind=kind, eps=eps, h=h, kappa=w["kappa"])
+    fe = P.rss_factor(tr, kind=kind, eps=eps, h=h, kappa=w["kappa"], tune_table=tune or None)
     P.rss_solve(fe, bh)
     e2e_s = time.perf_counter() - t0
     del fe, tr
@@ -646,6 +670,7 @@ def native_arm(args, w):
                          if gms.get(k)},
         "ranks": [{"side": L["side"], "k_mean": L["k_mean"], "k_max": L["k_max"]} for L in info["levels"]],
         "ntop": info["ntop"],
+        "solve_tuning": tune,
         "clocks": clk,
         "e2e": {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": pts_h.nbytes + bh.nbytes,
                 "d2h_bytes_per_step": bh.nbytes},

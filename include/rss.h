@@ -120,6 +120,10 @@ typedef struct {
                                      left running).  0: the default limit (2^22 polls); n > 0:
                                      n polls; -1: give up without polling, which exercises the
                                      timeout path on purpose (for tests) */
+  const char* tune_table;         /* NULL, or the JSON object rss_tune_solve returned (read during
+                                     the call): its last "launch", "spread" and "ctas_per_sm" set
+                                     the launch form of the solve sweeps without measuring again.
+                                     A form changes the time of a solve, never its result */
 } rss_params;
 
 /* Build the quadtree of Section 2.1 for n points given as pts_xy[2*i],
@@ -169,6 +173,27 @@ rss_status rss_solve(const rss_factorization* f, void* b, int64_t nrhs, int64_t 
  *    the whole region it uses before reading it. */
 rss_status rss_solve_noalloc(const rss_factorization* f, void* b, int64_t nrhs, int64_t ldb,
                              void* stream);
+
+/* Autotuner of the solve's launch form.  The FP64 sweeps (fewer than 32
+ * right-hand sides) run either as per-class kernels (two or three launches per
+ * colour class) or as two persistent cooperative launches that walk the colour
+ * classes of the factorization, meeting at grid barriers; there a class with
+ * few boxes is split across CTAs by rows of C (one more barrier).  The
+ * persistent form has two knobs: "spread", the target number of work items per
+ * CTA and class, and "ctas_per_sm" (0: as many as fit).  rss_tune_solve times the
+ * solve of nrhs zero right-hand sides under the per-class form and under every
+ * persistent candidate (spread 1, 2, 4, 8 x ctas_per_sm 2, 4, 0; median of three
+ * after one untimed run, CUDA events on stream), keeps the fastest for the later
+ * solves of f, and writes the table to json (may be NULL) as {"nrhs": ..,
+ * "path": .., "candidates": [..], "launch": "per_class" | "persistent",
+ * "spread": .., "ctas_per_sm": .., "ms": ..}; passing that text back as
+ * rss_params.tune_table applies it without measuring.  Every form adds the same
+ * products in the same order, so results are bitwise the same under any of
+ * them.  With 32 or more right-hand sides (tensor-core sweeps) there is nothing
+ * to tune and the table says so.  The paper has no counterpart.  Synchronises
+ * stream; allocates n * nrhs scalars for the duration of the call; solves that
+ * run meanwhile on other streams may take either form. */
+rss_status rss_tune_solve(rss_factorization* f, int64_t nrhs, void* stream, char* json, size_t len);
 
 /* ---- Serving: resident factorizations, continuous batching of solves ----
  * A server owns a worker thread and, per registered factorization, a CUDA

@@ -3,6 +3,7 @@
 // solve.cu.
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -208,9 +209,30 @@ rss_status rss_factor(const rss_tree* tree, const rss_params* p, void* stream, r
   if (p->ncoef < 0 || p->ncoef > RSS_MAX_COEF) return fail(RSS_EINVAL, "rss_factor: ncoef out of range");
   if (p->proxy_radius_over_side < 0) return fail(RSS_EINVAL, "rss_factor: negative proxy radius");
   if (p->wait_polls < -1) return fail(RSS_EINVAL, "rss_factor: wait_polls must be >= -1");
+  int spread = 0, ctas = 0, launch = 0;
+  if (p->tune_table) {   // the object rss_tune_solve writes: its last "launch", "spread", "ctas_per_sm"
+    auto last = [&](const char* key) -> const char* {
+      const char* hit = nullptr;
+      for (const char* q = std::strstr(p->tune_table, key); q; q = std::strstr(q + 1, key)) hit = q;
+      return hit ? std::strchr(hit, ':') : nullptr;
+    };
+    const char* l = last("\"launch\"");
+    launch = (l && std::strstr(l, "per_class") == std::strchr(l, '"') + 1) ? 1 : 2;
+    const char* q = last("\"spread\"");
+    if (q) spread = std::atoi(q + 1);
+    if (launch == 2 && (spread < 1 || spread > 1024))
+      return fail(RSS_EINVAL, "rss_factor: tune_table has no \"spread\" between 1 and 1024");
+    const char* c = last("\"ctas_per_sm\"");
+    ctas = c ? std::atoi(c + 1) : 0;
+    if (ctas < 0 || ctas > 64) return fail(RSS_EINVAL, "rss_factor: tune_table ctas_per_sm out of range");
+  }
   rss_factorization* f = new (std::nothrow) rss_factorization();
   if (!f) return fail(RSS_ENOMEM, "rss_factor: host allocation failed");
   f->params = *p;
+  f->params.tune_table = nullptr;   // read during this call only
+  f->swp_spread = spread;
+  f->swp_ctas = ctas;
+  f->swp_launch = launch;
   if (f->params.proxy_n == 0) f->params.proxy_n = 64;
   if (f->params.proxy_radius_over_side == 0) f->params.proxy_radius_over_side = 1.25;
   double h = p->h > 0 ? p->h : tree->geo.hg;
@@ -314,6 +336,9 @@ rss_status rss_info(const rss_factorization* f, char* buf, size_t len) {
     << ", \"leaf\": " << f->leaf << ", \"ntop\": " << f->ntop
     << ", \"arena_bytes\": " << f->arena.total << ", \"peak_transient_bytes\": " << f->peak_transient
     << ", \"launches\": " << f->launches << ", \"batches\": " << f->batches.size()
+    << ", \"solve_spread\": " << (f->swp_spread > 0 ? f->swp_spread : SWP_SPREAD_DEFAULT)
+    << ", \"solve_ctas_per_sm\": " << f->swp_ctas
+    << ", \"solve_launch\": \"" << (f->swp_launch == 2 ? "persistent" : "per_class") << "\""
     << ", \"ms\": {\"gen\": " << f->t_gen << ", \"id\": " << f->t_id << ", \"elim\": " << f->t_elim
     << ", \"schur\": " << f->t_schur << ", \"merge\": " << f->t_merge << ", \"top\": " << f->t_top
     << ", \"total\": " << f->t_total << "}, \"gpu_ms\": {\"gen\": " << f->g_gen << ", \"id\": " << f->g_id

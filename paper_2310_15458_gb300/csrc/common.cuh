@@ -367,6 +367,50 @@ __device__ inline T aval_tab(const KParams& kp, const T* __restrict__ tab, int s
   return tab[(size_t)(a.y - b.y + side - 1) * (2 * side - 1) + (a.x - b.x + side - 1)];
 }
 
+// ----------------------------------------------------------------- grid barrier
+// Barrier over every CTA of a cooperative launch (all CTAs are resident, so each
+// one reaches it).  bar[0] counts arrivals, bar[1] is the generation; both start
+// at zero, and the count is back at zero after every barrier.  Thread 0 of each
+// CTA reads the generation before it arrives; the last CTA to arrive resets the
+// count and advances the generation, the others poll it at most `polls` times.
+// A wait that runs out sets RSS_ETIMEOUT in *err; every CTA that finds *err set
+// (arriving or waiting) leaves the barrier at once, and the barrier returns
+// false in every thread of such a CTA (the caller then stops: its results are
+// void, and the counters must be zeroed again before the next launch).
+__device__ inline bool grid_barrier(unsigned* bar, long long polls, int* err) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* vgen = bar + 1;
+    volatile int* verr = err;
+    int ok = *verr == 0;
+    if (ok) {
+      const unsigned gen = *vgen;
+      __threadfence();   // this CTA's writes are visible before it arrives
+      const unsigned arrived = atomicAdd(bar, 1u) + 1u;
+      if (arrived == gridDim.x * gridDim.y * gridDim.z) {
+        atomicExch(bar, 0u);
+        __threadfence();
+        atomicAdd(bar + 1, 1u);
+      } else {
+        long long it = 0;
+        while (*vgen == gen && *verr == 0 && it < polls) {
+          __nanosleep(64);
+          ++it;
+        }
+        if (*vgen == gen) {
+          atomicCAS(err, 0, 5 /* RSS_ETIMEOUT, unless another error came first */);
+          ok = 0;
+        }
+      }
+      __threadfence();   // the other CTAs' writes are visible after the barrier
+    }
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
 // ----------------------------------------------------------------- host errors
 void rss_set_error(const std::string& msg);
 

@@ -41,11 +41,6 @@ constexpr double TIE_ABS = 1e-12;
 // roundoff) of its last accumulated value (LAPACK geqp3's rule); between
 // re-accumulations it is accurate to a few 1e-8 relative, inside the tie window.
 constexpr double RECOMPUTE_REL = 1.4901161193847656e-08;
-// A norm that has fallen below that fraction is stale.  It is re-accumulated only
-// when a decision could depend on it (below): its downdated value is off by at most
-// about (downdates) x 3 u x ref, which STALE_ERR x ref bounds with room to spare.
-constexpr double STALE_ERR = 1e-13;
-constexpr double STALE_MARGIN = 4e-6;   // > TIE_REL plus the few 1e-8 noise of a fresh norm
 constexpr int NT = 256;                 // threads per CTA for the per-box kernels
 
 template <typename T> struct LevelDev {
@@ -162,6 +157,8 @@ template <typename T, typename S = T> struct IdArgs {
   double rho;         // proxy radius
   double Lbox;        // box side
   int g_sm;           // 1: G (nmax x nmax) and row k of V are kept in shared memory
+  const S* ptab;      // proxy rows K(y_p, x) by the point's place in its box (null: evaluated here)
+  int lsz;            // grid points per box side at this level
 };
 
 template <typename T, typename S> __device__ inline S id_store(T v) {
@@ -198,12 +195,17 @@ __device__ __forceinline__ T id_entry(const IdArgs<T, S>& a, int B, int i, int j
       v = cj(L.blk[((size_t)B * 25 + off_index(B, mb, g)) * nn + (size_t)pm * nmax + j]);
   } else {
     const int p = ii - mh;
-    double sn, cs;
-    sincospi(2.0 * p / P, &sn, &cs);
-    const double px = cx + a.rho * cs, py = cy + a.rho * sn;
     const int2 q = a.ixy[L.pts[B * nmax + j]];
-    const double xj = a.geo.x0 + q.x * a.geo.hg, yj = a.geo.y0 + q.y * a.geo.hg;
-    v = (!split && second) ? cj(kval(a.kp, xj, yj, px, py, S{})) : kval(a.kp, px, py, xj, yj, S{});
+    if (a.ptab != nullptr && (split || !second)) {   // K(y_p, x_j) from the level's table
+      const int local = (q.y - (B / g) * a.lsz) * a.lsz + (q.x - (B % g) * a.lsz);
+      v = a.ptab[(size_t)p * a.lsz * a.lsz + local];
+    } else {
+      double sn, cs;
+      sincospi(2.0 * p / P, &sn, &cs);
+      const double px = cx + a.rho * cs, py = cy + a.rho * sn;
+      const double xj = a.geo.x0 + q.x * a.geo.hg, yj = a.geo.y0 + q.y * a.geo.hg;
+      v = (!split && second) ? cj(kval(a.kp, xj, yj, px, py, S{})) : kval(a.kp, px, py, xj, yj, S{});
+    }
     if (a.kp.kind == RSS_HELMHOLTZ_LS)   // proxy weight kappa, column weight w_j
       v = (a.kp.kappa * a.kp.w[q.y * a.geo.side + q.x]) * v;
   }
@@ -211,43 +213,24 @@ __device__ __forceinline__ T id_entry(const IdArgs<T, S>& a, int B, int i, int j
   else return v;
 }
 
-// Before the pivot choice of step k (warp 0; norms2/ref over positions k..n-1):
-// which stale norms must be re-accumulated so that the choice and the stop test
-// see values as accurate as a re-accumulation at every step would give.  A stale
-// column matters when its value, with its error bound, could reach the tie window
-// below the largest fresh norm L (a lower bound of the true maximum, up to the
-// noise of fresh norms), or when the stop test's sum lies within ten times the
-// stale columns' summed error bound of the threshold (then all are taken).
-// Without any fresh column every stale one is taken.  Sets flag[pos]; returns
-// whether any is set (the same value in every lane).
-__device__ int stale_plan(int k, int n, const double* norms2, const double* ref, int* flag, double y2max,
-                          double thresh) {
-  const int lane = threadIdx.x & 31;
-  double L = -1.0, s = 0.0, es = 0.0;
-  int nst = 0;
-  for (int c = k + lane; c < n; c += 32) {
-    s += norms2[c];
-    if (norms2[c] < RECOMPUTE_REL * ref[c]) {
-      es += STALE_ERR * ref[c];
-      ++nst;
-    } else {
-      L = fmax(L, norms2[c]);
-    }
+// Proxy rows by place (Eq. 6): on the uniform grid the box centre, the proxy
+// circle and the box's grid points move together from box to box, and every
+// kernel kind depends only on x - y, so K(y_p, x) for a point x of box B is a
+// function of p and of x's place (ox, oy) inside B (lsz x lsz places): one table
+// per level, tab[p * lsz^2 + oy * lsz + ox], serves the proxy rows of every box.
+// The coordinates are taken relative to the box centre, y_p - x =
+// rho (cos, sin)(2 pi p / P) - ((ox, oy) + 1/2 - lsz/2) hg.
+template <typename S>
+__global__ void __launch_bounds__(NT) k_proxy_tab(S* __restrict__ tab, int lsz, int P, double rho, double hg,
+                                                  KParams kp) {
+  const long long nloc = (long long)lsz * lsz, tot = nloc * P;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
+    const int p = (int)(e / nloc), o = (int)(e % nloc), ox = o % lsz, oy = o / lsz;
+    double sn, cs;
+    sincospi(2.0 * p / P, &sn, &cs);
+    const double xr = (ox + 0.5 - 0.5 * lsz) * hg, yr = (oy + 0.5 - 0.5 * lsz) * hg;
+    tab[e] = kval(kp, rho * cs - xr, rho * sn - yr, 0.0, 0.0, S{});
   }
-  s = warp_sum(s);
-  es = warp_sum(es);
-  L = warp_max(L);
-  nst = __reduce_add_sync(0xffffffffu, nst);
-  if (nst == 0) return 0;
-  const bool all = L < 0.0 || fabs(s - thresh) <= 10.0 * es;
-  const double lo = L - (STALE_MARGIN * L + 2.0 * TIE_ABS * sqrt(fmax(L, 0.0) * y2max));
-  int any = 0;
-  for (int c = k + lane; c < n; c += 32) {
-    const int need = norms2[c] < RECOMPUTE_REL * ref[c] && (all || norms2[c] + STALE_ERR * ref[c] >= lo);
-    flag[c] = need;
-    any |= need;
-  }
-  return __any_sync(0xffffffffu, any);
 }
 
 template <typename T, typename S = T> __global__ void __launch_bounds__(NT_ID, 4) k_id(IdArgs<T, S> a) {
@@ -265,7 +248,7 @@ template <typename T, typename S = T> __global__ void __launch_bounds__(NT_ID, 4
   T* Gs = reinterpret_cast<T*>(reinterpret_cast<unsigned char*>(smraw) +
                                ((reinterpret_cast<unsigned char*>(flag + nmax) - smraw + 15) & ~size_t(15)));
   T* vrow = Gs + (size_t)nmax * nmax;             // row k of V (a.g_sm)
-  __shared__ int Mbox[16], Moff[17], s_nM, s_piv, s_stop, s_any;
+  __shared__ int Mbox[16], Moff[17], s_nM, s_piv, s_stop;
   __shared__ double s_thresh, s_y2max, s_redd[32];
   __shared__ T s_scale;
 
@@ -338,47 +321,6 @@ template <typename T, typename S = T> __global__ void __launch_bounds__(NT_ID, 4
   int k = 0;
   const int kmax = min(m, n);
   while (k < kmax) {
-    // stale norms a decision could depend on: re-accumulated from the trailing
-    // rows k.. of their columns after the k reflectors so far
-    if (k > 0) {
-      if (warp == 0) {
-        const int any = stale_plan(k, n, norms2, ref, flag, s_y2max, s_thresh);
-        if (lane == 0) s_any = any;
-      }
-      __syncthreads();
-      if (s_any) {
-        for (int pos = k + warp; pos < n; pos += nwarp) {
-          if (!flag[pos]) continue;
-          const int c = perm[pos];
-          double t = 0.0;
-          int i = k + lane;
-          for (; i + 96 < m; i += 128) {   // four rows per lane in flight
-            T x0 = Y[(size_t)c * ldY + i], x1 = Y[(size_t)c * ldY + i + 32];
-            T x2 = Y[(size_t)c * ldY + i + 64], x3 = Y[(size_t)c * ldY + i + 96];
-            for (int l = 0; l < k; ++l) {
-              const T gl = G[(size_t)l * nmax + c];
-              const T* vl = V + (size_t)l * ldY + i;
-              x0 = msb(x0, vl[0], gl);
-              x1 = msb(x1, vl[32], gl);
-              x2 = msb(x2, vl[64], gl);
-              x3 = msb(x3, vl[96], gl);
-            }
-            t += (abs2(x0) + abs2(x1)) + (abs2(x2) + abs2(x3));
-          }
-          for (; i < m; i += 32) {
-            T x = Y[(size_t)c * ldY + i];
-            for (int l = 0; l < k; ++l) x = msb(x, V[(size_t)l * ldY + i], G[(size_t)l * nmax + c]);
-            t += abs2(x);
-          }
-          t = warp_sum(t);
-          if (lane == 0) {
-            norms2[pos] = t;
-            ref[pos] = t;
-          }
-        }
-        __syncthreads();
-      }
-    }
     // stop test and pivot: largest remaining norm, lowest original column among ties
     if (warp == 0) {
       double s = 0.0, mx = -1.0;
@@ -516,7 +458,39 @@ template <typename T, typename S = T> __global__ void __launch_bounds__(NT_ID, 4
       else
         for (int l = 0; l <= k; ++l) r = msb(r, V[(size_t)l * ldY + k], G[(size_t)l * nmax + c]);
       Rr[(size_t)k * nmax + c] = r;
-      norms2[pos] -= abs2(r);
+      const double nv = norms2[pos] - abs2(r);
+      flag[pos] = nv < RECOMPUTE_REL * ref[pos];
+      norms2[pos] = nv;
+    }
+    __syncthreads();
+    for (int pos = k + 1 + warp; pos < n; pos += nwarp) {
+      if (!flag[pos]) continue;
+      const int c = perm[pos];
+      double t = 0.0;
+      int i = k + 1 + lane;
+      for (; i + 96 < m; i += 128) {   // four rows per lane in flight
+        T x0 = Y[(size_t)c * ldY + i], x1 = Y[(size_t)c * ldY + i + 32];
+        T x2 = Y[(size_t)c * ldY + i + 64], x3 = Y[(size_t)c * ldY + i + 96];
+        for (int l = 0; l <= k; ++l) {
+          const T gl = G[(size_t)l * nmax + c];
+          const T* vl = V + (size_t)l * ldY + i;
+          x0 = msb(x0, vl[0], gl);
+          x1 = msb(x1, vl[32], gl);
+          x2 = msb(x2, vl[64], gl);
+          x3 = msb(x3, vl[96], gl);
+        }
+        t += (abs2(x0) + abs2(x1)) + (abs2(x2) + abs2(x3));
+      }
+      for (; i < m; i += 32) {
+        T x = Y[(size_t)c * ldY + i];
+        for (int l = 0; l <= k; ++l) x = msb(x, V[(size_t)l * ldY + i], G[(size_t)l * nmax + c]);
+        t += abs2(x);
+      }
+      t = warp_sum(t);
+      if (lane == 0) {
+        norms2[pos] = t;
+        ref[pos] = t;
+      }
     }
     __syncthreads();
     ++k;
@@ -566,7 +540,7 @@ template <typename T, typename S = T> __global__ void __launch_bounds__(NT_ID) k
   T* Gs = reinterpret_cast<T*>(reinterpret_cast<unsigned char*>(smraw) +
                                ((reinterpret_cast<unsigned char*>(flag + nmax) - smraw + 15) & ~size_t(15)));
   T* vrow = Gs + (size_t)nmax * nmax;              // row k of V (a.g_sm)
-  __shared__ int Mbox[16], Moff[17], s_nM, s_stop, s_any;
+  __shared__ int Mbox[16], Moff[17], s_nM, s_stop;
   __shared__ double s_thresh, s_y2max;
   __shared__ T s_scale;
 
@@ -663,38 +637,6 @@ template <typename T, typename S = T> __global__ void __launch_bounds__(NT_ID) k
   int k = 0;
   const int kmax = min(m, n);
   while (k < kmax) {
-    // stale norms a decision could depend on (the same plan in every CTA: same
-    // data, same operations), re-accumulated after the k reflectors so far from
-    // partials over the owned rows of k..
-    if (k > 0) {
-      if (warp == 0) {
-        const int any = stale_plan(k, n, norms2, ref, flag, s_y2max, s_thresh);
-        if (lane == 0) s_any = any;
-      }
-      __syncthreads();
-      if (s_any) {
-        for (int pos = k + warp; pos < n; pos += nwarp) {
-          double t = 0.0;
-          if (flag[pos]) {
-            const int c = perm[pos];
-            for (int i = max(k, r0) + lane; i < r1; i += 32) {
-              T x = Y[(size_t)c * ldY + i];
-              for (int l = 0; l < k; ++l) x = msb(x, V[(size_t)l * ldY + i], G[(size_t)l * nmax + c]);
-              t += abs2(x);
-            }
-            t = warp_sum(t);
-          }
-          if (lane == 0) part[pb * 2 * nmax + pos] = from_re<T>(t);
-        }
-        cluster_sum(n, u);
-        for (int pos = k + tid; pos < n; pos += blockDim.x)
-          if (flag[pos]) {
-            norms2[pos] = re(u[pos]);
-            ref[pos] = norms2[pos];
-          }
-        __syncthreads();
-      }
-    }
     if (warp == 0) {   // stop test and pivot (identical in every CTA)
       double s = 0.0, mx = -1.0;
       for (int c = k + lane; c < n; c += 32) {
@@ -800,6 +742,7 @@ template <typename T, typename S = T> __global__ void __launch_bounds__(NT_ID) k
     cluster_sum(k + nc, u);   // u[0..k): v^H V, u[k..k+nc): raw g for positions k+1..
     // g_c, row k of R, norm downdate (identical in every CTA; own copies of G, Rr)
     const double tau = taus[k];
+    int anyf = 0;
     for (int pos = k + 1 + tid; pos < n; pos += blockDim.x) {
       const int c = perm[pos];
       T gc = u[k + (pos - k - 1)];
@@ -812,8 +755,37 @@ template <typename T, typename S = T> __global__ void __launch_bounds__(NT_ID) k
       else
         for (int l = 0; l <= k; ++l) r = msb(r, ld_l2(V + (size_t)l * ldY + k), G[(size_t)l * nmax + c]);
       Rr[(size_t)k * nmax + c] = r;
-      norms2[pos] -= abs2(r);
+      const double nv = norms2[pos] - abs2(r);
+      flag[pos] = nv < RECOMPUTE_REL * ref[pos];
+      anyf |= flag[pos];
+      norms2[pos] = nv;
     }
+    // the flags are the same in every CTA of the cluster (same data, same
+    // operations), so all of them skip the re-accumulation together
+    if (!__syncthreads_or(anyf)) {
+      ++k;
+      continue;
+    }
+    // re-accumulation of flagged norms: partials over owned rows
+    for (int pos = k + 1 + warp; pos < n; pos += nwarp) {
+      double t = 0.0;
+      if (flag[pos]) {
+        const int c = perm[pos];
+        for (int i = max(k + 1, r0) + lane; i < r1; i += 32) {
+          T x = Y[(size_t)c * ldY + i];
+          for (int l = 0; l <= k; ++l) x = msb(x, V[(size_t)l * ldY + i], G[(size_t)l * nmax + c]);
+          t += abs2(x);
+        }
+        t = warp_sum(t);
+      }
+      if (lane == 0) part[pb * 2 * nmax + pos] = from_re<T>(t);
+    }
+    cluster_sum(n, u);
+    for (int pos = k + 1 + tid; pos < n; pos += blockDim.x)
+      if (flag[pos]) {
+        norms2[pos] = re(u[pos]);
+        ref[pos] = norms2[pos];
+      }
     __syncthreads();
     ++k;
   }
@@ -2845,6 +2817,30 @@ rss_status factor_impl(const rss_tree* tree, const rss_params* prm, cudaStream_t
     }
     int maxcls = 0;
     for (int col = 0; col < 9; ++col) maxcls = std::max(maxcls, coff[col + 1] - coff[col]);
+    // proxy rows from one table per level where the boxes' points outnumber the
+    // table's places (the fine levels); the coarse levels evaluate them per box
+    const int lsz = side / g;
+    T* d_ptab = nullptr;
+    if ((long long)nbox * nmax >= 2LL * lsz * lsz) {
+      const size_t pb = sizeof(T) * (size_t)P * lsz * lsz;
+      RSS_CUDA(pool_malloc(reinterpret_cast<void**>(&d_ptab), pb, st));
+      f->peak_transient = std::max(f->peak_transient, transient + pb);
+      Ev evp;
+      evp.start(st);
+      k_proxy_tab<T><<<std::min<long long>(cdiv((long long)P * lsz * lsz, NT), 152LL * 8), NT, 0, st>>>(
+          d_ptab, lsz, P, ratio * Lbox, f->geo.hg, f->kp);
+      RSS_LAUNCHED();
+      evp.stop(st);
+      RSS_CUDA(cudaStreamSynchronize(st));
+      f->g_id += evp.ms();
+      info.g_id += evp.ms();
+      f->launches += 1;
+    }
+    struct PtabFree {
+      T* p;
+      cudaStream_t st;
+      ~PtabFree() { pool_free(p, st); }
+    } ptab_free{d_ptab, st};
     if (!gb_cls.ensure(sizeof(int) * cls.size()) || !gb_k.ensure(sizeof(int) * maxcls) ||
         !gb_perm.ensure(sizeof(int) * (size_t)maxcls * nmax) || !gb_clsidx.ensure(sizeof(int) * maxcls) ||
         !gb_Tws.ensure(sizeof(T) * (size_t)maxcls * nn)) {
@@ -2949,6 +2945,8 @@ rss_status factor_impl(const rss_tree* tree, const rss_params* prm, cudaStream_t
           a.rho = ratio * Lbox;
           a.Lbox = Lbox;
           a.g_sm = g_sm;
+          a.ptab = d_ptab;
+          a.lsz = lsz;
           const int cnt = std::min(chunk, nb - c0);
           if (Q > 1) {
             cudaLaunchConfig_t cfg = {};
@@ -3392,6 +3390,10 @@ rss_status factor_impl(const rss_tree* tree, const rss_params* prm, cudaStream_t
     if (herr) { rss_set_error("rss_factor: zero pivot in the dense top LU"); return RSS_ENUMERIC; }
   }
   f->t_top += tt.ms();
+  {
+    const rss_status sb = build_sweep_classes<T>(f, st);
+    if (sb != RSS_OK) return sb;
+  }
   f->t_total = total.ms();
   return RSS_OK;
 }

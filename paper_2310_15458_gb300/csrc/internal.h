@@ -9,6 +9,8 @@
 
 #include "common.cuh"
 
+constexpr int SWP_SPREAD_DEFAULT = 4;   // persistent sweeps: target work items per CTA and class
+
 enum : uint32_t { RSS_TAG_TREE = 0x52545245u, RSS_TAG_FACTOR = 0x52464143u, RSS_TAG_SERVER = 0x52535256u };
 
 // Quadtree over a uniform grid (Section 2.1).  Tree order: leaf boxes
@@ -126,6 +128,10 @@ struct rss_factorization {
   std::vector<int32_t> tree_to_user;   // host copy, for inspection calls
   Arena arena;
   std::vector<Batch> batches;          // factor order
+  void* d_swp = nullptr;               // the batches as the persistent sweeps read them (arena)
+  int swp_spread = 0;                  // their schedule's knobs (0: the defaults; rss_tune_solve sets them):
+  int swp_ctas = 0;                    // work items per CTA and class, CTAs per SM (0: as many as fit),
+  int swp_launch = 0;                  // and the launch form (0, 1: per-class kernels; 2: persistent)
   std::vector<void*> rec_host;         // host copies of the BoxRec arrays (owned)
   std::vector<LevelInfo> levels;
   // top dense block
@@ -161,6 +167,8 @@ template <typename T> rss_status top_inverse(const T* LU, const int* piv, int n,
 // device bytes one solve of nrhs columns allocates (working copy plus sweep
 // workspace), beside the caller's b
 size_t solve_device_bytes(const rss_factorization* f, int64_t nrhs);
+// the factor's colour classes as the persistent sweeps read them (arena, once)
+template <typename T> rss_status build_sweep_classes(rss_factorization* f, cudaStream_t st);
 // device bytes of the factor-owned caches that solves with up to max_nrhs
 // columns build on first use (the digit slices of E and F of a real factor;
 // 0 when none applies), and the call that builds them now, on st

@@ -7,7 +7,9 @@
 // Boxes of one colour class touch disjoint entries of x, so a class is one
 // launch; the right-hand sides are split into chunks of RC columns.
 #include <algorithm>
+#include <cstring>
 #include <mutex>
+#include <sstream>
 #include <type_traits>
 
 #include "internal.h"
@@ -29,11 +31,15 @@ __global__ void k_perm_in(const T* __restrict__ b, int64_t ldb, T* __restrict__ 
 
 template <typename T>
 __global__ void k_perm_out(T* __restrict__ b, int64_t ldb, const T* __restrict__ x, int64_t N, int nrhs,
-                           const int* __restrict__ u2t) {
+                           const int* __restrict__ u2t, const int* __restrict__ err) {
+  // a grid-barrier wait of the persistent sweeps that ran out (*err != 0) voids
+  // the result: every entry becomes NaN rather than a silently wrong number
+  const bool bad = err != nullptr && *err != 0;
+  const T nan = from_re<T>(__longlong_as_double(0x7FF8000000000000LL));
   const long long tot = (long long)N * nrhs;
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
     const long long i = e % N, j = e / N;
-    b[i + j * ldb] = x[u2t[i] + j * N];
+    b[i + j * ldb] = bad ? nan : x[u2t[i] + j * N];
   }
 }
 
@@ -265,6 +271,341 @@ __global__ void __launch_bounds__(SW_NT_R) k_down(const BoxRec<T>* __restrict__ 
       if (q < nq) xq[gs + (int64_t)q * N] = xq[gs + (int64_t)q * N] - acc[q];
   }
   if (tid == 0) cnt[box] = 0;   // ready for the next colour class
+}
+
+// ------------------------------------------------------------------ one persistent launch per sweep
+// The FP64 sweeps of up to 31 right-hand sides (RC-column chunks, RC = 1, 4, 8)
+// as two cooperative launches, one per sweep, instead of two or three launches
+// per colour class.  The CTAs walk the colour classes in factor order (upward)
+// or reverse order (downward) and meet at a grid barrier between classes.  A
+// class with enough boxes for every CTA is taken one box per CTA; a smaller
+// class is split by rows of C across CTAs, with one more barrier: upward, the
+// boxes' b_R first, then row groups of b_C -= E b_R; downward, partial sums of
+// F y_C per group of rows, then per box the rest.  Every sum runs in the same
+// order in both forms, for every RC and as in the per-class kernels k_up_r,
+// k_up_c and k_down (per row of E: over R ascending; per row of F: a sequential
+// sum over each 64-row chunk of C, the chunks added in order), so a column's
+// result depends neither on the launch form nor on the other columns.
+constexpr int SWP_NT = 128;
+
+// One colour class as the persistent sweeps see it (device array in factor order).
+template <typename T> struct SwpClass {
+  const BoxRec<T>* recs;
+  int nrec, max_k, max_r, max_c;
+};
+constexpr int SWP_CH = 64;   // rows of C per partial sum of F y_C (fixes the order of the sums, = SW_ROWS_D)
+
+// b_R <- L^{-1} P (b_R - T^* b_S) for one box and RC columns, into bR (shared,
+// r x RC) and, when write_x, into x.  Shared memory from sm (sm_cap scalars).
+template <typename T, int RC>
+__device__ void swp_up_r(const BoxRec<T>& R, T* xq, int64_t N, int nq, T* sm, int sm_cap, T*& bR, bool write_x) {
+  const int k = R.k, r = R.r, ldt = k | 1, tid = threadIdx.x, bs = blockDim.x;
+  T* bS = sm;
+  T* t = bS + (size_t)k * RC;
+  bR = t + (size_t)r * RC;
+  T* Ts = bR + (size_t)r * RC;
+  T* Ls = Ts + (size_t)ldt * r;
+  const bool stage = (size_t)(k + 2 * r) * RC + (size_t)ldt * r + (size_t)r * r <= (size_t)sm_cap;
+  for (int e = tid; e < k * RC; e += bs) {
+    const int s2 = e / RC, q = e % RC;
+    bS[e] = q < nq ? ld_l2(xq + R.idxC[s2] + (int64_t)q * N) : zero<T>();
+  }
+  for (int e = tid; e < r * RC; e += bs) {
+    const int j = e / RC, q = e % RC;
+    t[e] = q < nq ? ld_l2(xq + R.idxR[j] + (int64_t)q * N) : zero<T>();
+  }
+  if (stage) {
+    for (int e = tid; e < k * r; e += bs) cp_async_el(Ts + (e / k) * ldt + e % k, R.Tm + e);
+    for (int e = tid; e < r * r; e += bs) cp_async_el(Ls + e, R.LiP + e);
+    cp_async_wait_all();
+  }
+  __syncthreads();
+  const T* Tsrc = stage ? Ts : R.Tm;
+  const int tl = stage ? ldt : k;
+  const T* Lsrc = stage ? Ls : R.LiP;
+  for (int j = tid; j < r; j += bs) {   // t_j -= sum_s conj(T_sj) b_s
+    T acc[RC];
+#pragma unroll
+    for (int q = 0; q < RC; ++q) acc[q] = t[j * RC + q];
+    for (int s2 = 0; s2 < k; ++s2) {
+      const T tv = Tsrc[s2 + (size_t)j * tl];
+#pragma unroll
+      for (int q = 0; q < RC; ++q) acc[q] = msbc(acc[q], tv, bS[s2 * RC + q]);
+    }
+#pragma unroll
+    for (int q = 0; q < RC; ++q) t[j * RC + q] = acc[q];
+  }
+  __syncthreads();
+  for (int j = tid; j < r; j += bs) {   // b_R = L^{-1} P t
+    T acc[RC];
+#pragma unroll
+    for (int q = 0; q < RC; ++q) acc[q] = zero<T>();
+#pragma unroll 4
+    for (int l = 0; l < r; ++l) {
+      const T lv = Lsrc[j + (size_t)l * r];
+#pragma unroll
+      for (int q = 0; q < RC; ++q) acc[q] = mad(acc[q], lv, t[l * RC + q]);
+    }
+#pragma unroll
+    for (int q = 0; q < RC; ++q) {
+      bR[j * RC + q] = acc[q];
+      if (write_x && q < nq) xq[R.idxR[j] + (int64_t)q * N] = acc[q];
+    }
+  }
+  __syncthreads();
+}
+
+// b_C -= E b_R over rows i0 .. i1-1 of C (bR in shared memory).
+template <typename T, int RC>
+__device__ void swp_up_c(const BoxRec<T>& R, T* xq, int64_t N, int nq, const T* bR, int i0, int i1) {
+  const int r = R.r, c = R.c;
+  for (int i = i0 + (int)threadIdx.x; i < i1; i += blockDim.x) {
+    T acc[RC];
+#pragma unroll
+    for (int q = 0; q < RC; ++q) acc[q] = zero<T>();
+    const T* __restrict__ Ei = R.E + i;
+#pragma unroll 8
+    for (int j = 0; j < r; ++j) {
+      const T ev = Ei[(size_t)j * c];
+#pragma unroll
+      for (int q = 0; q < RC; ++q) acc[q] = mad(acc[q], ev, bR[j * RC + q]);
+    }
+    const int gi = R.idxC[i];
+#pragma unroll
+    for (int q = 0; q < RC; ++q)
+      if (q < nq) xq[gi + (int64_t)q * N] = ld_l2(xq + gi + (int64_t)q * N) - acc[q];
+  }
+}
+
+// Partial sums p(j, ch) = sum over rows of chunk ch of F_ji y_i, for chunks
+// ch0 .. ch1-1 of one box, handed to out(j, ch, p[RC]) by the thread that owns
+// row j (the same thread for every chunk); each is one sequential sum down the
+// chunk's rows, the order k_down uses, so both give the same bits.  The chunk's
+// rows of F^T are staged with coalesced copies (ld SWP_CH + 1: conflict-free
+// reads down a column).  Uses swp_dn_part_sm(r) scalars of sm.
+__host__ __device__ constexpr size_t swp_dn_part_sm(int r, int rc) {
+  return (size_t)SWP_CH * rc + (size_t)(SWP_CH + 1) * r;
+}
+template <typename T, int RC, typename OUT>
+__device__ void swp_dn_part(const BoxRec<T>& R, const T* xq, int64_t N, int nq, int ch0, int ch1, T* sm, OUT out) {
+  const int r = R.r, c = R.c, tid = threadIdx.x, bs = blockDim.x;
+  constexpr int LDF = SWP_CH + 1;
+  T* yC = sm;                          // SWP_CH x RC
+  T* Fs = yC + (size_t)SWP_CH * RC;    // SWP_CH x r, ld LDF
+  for (int ch = ch0; ch < ch1; ++ch) {
+    const int i0 = ch * SWP_CH, rows = min(SWP_CH, c - i0);
+    __syncthreads();   // the previous chunk's buffers are consumed
+    for (int e = tid; e < rows * r; e += bs) {
+      const int i = e % rows, j = e / rows;
+      cp_async_el(Fs + i + (size_t)j * LDF, R.Ft + i0 + i + (size_t)j * c);
+    }
+    for (int e = tid; e < SWP_CH * RC; e += bs) {
+      const int ii = e / RC, q = e % RC;
+      yC[e] = (ii < rows && q < nq) ? ld_l2(xq + R.idxC[i0 + ii] + (int64_t)q * N) : zero<T>();
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    for (int j = tid; j < r; j += bs) {
+      const T* __restrict__ Fj = Fs + (size_t)j * LDF;
+      T acc[RC];
+#pragma unroll
+      for (int q = 0; q < RC; ++q) acc[q] = zero<T>();
+#pragma unroll 4
+      for (int ii = 0; ii < rows; ++ii) {
+        const T fv = Fj[ii];
+#pragma unroll
+        for (int q = 0; q < RC; ++q) acc[q] = mad(acc[q], fv, yC[ii * RC + q]);
+      }
+      out(j, ch, acc);
+    }
+  }
+}
+
+// Given z = y_R - F y_C (zr, shared, r x RC): y_R = U^{-1} z into x, then
+// y_S -= T y_R.  Uses yR (r x RC) and up to sm_cap scalars at mats for staging.
+template <typename T, int RC>
+__device__ void swp_dn_fin(const BoxRec<T>& R, T* xq, int64_t N, int nq, const T* zr, T* yR, T* mats, int mat_cap) {
+  const int k = R.k, r = R.r, ldt = k | 1, tid = threadIdx.x, bs = blockDim.x;
+  const bool stage = (size_t)r * r + (size_t)ldt * r <= (size_t)max(mat_cap, 0);
+  T* Us = mats;
+  T* Ts = mats + (size_t)r * r;
+  if (stage) {
+    for (int e = tid; e < r * r; e += bs) cp_async_el(Us + e, R.Ui + e);
+    for (int e = tid; e < k * r; e += bs) cp_async_el(Ts + (e / k) * ldt + e % k, R.Tm + e);
+    cp_async_wait_all();
+  }
+  __syncthreads();
+  const T* Usrc = stage ? Us : R.Ui;
+  for (int j = tid; j < r; j += bs) {   // y_R = U^{-1} z
+    T acc[RC];
+#pragma unroll
+    for (int q = 0; q < RC; ++q) acc[q] = zero<T>();
+#pragma unroll 4
+    for (int l = j; l < r; ++l) {
+      const T uv = Usrc[j + (size_t)l * r];
+#pragma unroll
+      for (int q = 0; q < RC; ++q) acc[q] = mad(acc[q], uv, zr[l * RC + q]);
+    }
+    const int gj = R.idxR[j];
+#pragma unroll
+    for (int q = 0; q < RC; ++q) {
+      yR[j * RC + q] = acc[q];
+      if (q < nq) xq[gj + (int64_t)q * N] = acc[q];
+    }
+  }
+  __syncthreads();
+  const T* Tsrc = stage ? Ts : R.Tm;
+  const int tl = stage ? ldt : k;
+  for (int s2 = tid; s2 < k; s2 += bs) {   // y_S -= T y_R
+    T acc[RC];
+#pragma unroll
+    for (int q = 0; q < RC; ++q) acc[q] = zero<T>();
+#pragma unroll 4
+    for (int j = 0; j < r; ++j) {
+      const T tv = Tsrc[s2 + (size_t)j * tl];
+#pragma unroll
+      for (int q = 0; q < RC; ++q) acc[q] = mad(acc[q], tv, yR[j * RC + q]);
+    }
+    const int gs = R.idxC[s2];
+#pragma unroll
+    for (int q = 0; q < RC; ++q)
+      if (q < nq) xq[gs + (int64_t)q * N] = ld_l2(xq + gs + (int64_t)q * N) - acc[q];
+  }
+  __syncthreads();
+}
+
+template <typename T> struct SwpArgs {
+  const SwpClass<T>* cls;   // colour classes in factor order
+  int ncls;
+  T* x;
+  int64_t N;
+  int nrhs;
+  T* part;                  // split classes: partial sums, (z, box, chunk, j, q)
+  unsigned* bar;            // grid barrier counters (zeroed before the launch)
+  int* err;                 // RSS_ETIMEOUT when a barrier wait runs out
+  long long polls;
+  int sm_cap;               // scalars of dynamic shared memory
+  int spread;               // target work items per CTA and class (the schedule's tuning knob)
+};
+
+// Work items of a class: boxes x column chunks (nbz), each box split into ngrp
+// groups of cpg whole 64-row chunks of C when that brings the items nearer to
+// spread per CTA (ngrp >= 2: the split form), else whole boxes (ngrp = 1).
+__device__ __forceinline__ void swp_groups(int max_c, int nbz, int spread, int& nchk, int& ngrp, int& cpg) {
+  nchk = (max_c + SWP_CH - 1) / SWP_CH;
+  ngrp = min(nchk, (int)(((long long)gridDim.x * spread) / max(nbz, 1)));
+  ngrp = max(ngrp, 1);
+  cpg = (nchk + ngrp - 1) / ngrp;
+  ngrp = (nchk + cpg - 1) / cpg;
+}
+
+template <typename T, int RC, bool UP>
+__global__ void __launch_bounds__(SWP_NT) k_sweep(SwpArgs<T> a) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* sm = reinterpret_cast<T*>(smraw);
+  const int nz = (a.nrhs + RC - 1) / RC;
+  for (int step = 0; step < a.ncls; ++step) {
+    const SwpClass<T> C = a.cls[UP ? step : a.ncls - 1 - step];
+    const int nbz = C.nrec * nz;
+    int nchk, ngrp, cpg;
+    swp_groups(C.max_c, nbz, a.spread, nchk, ngrp, cpg);
+    const bool split = ngrp > 1;
+    if (UP) {
+      if (!split) {
+        for (int it = blockIdx.x; it < nbz; it += gridDim.x) {
+          const int z = it / C.nrec;
+          const BoxRec<T> R = C.recs[it % C.nrec];
+          T* xq = a.x + (int64_t)z * RC * a.N;
+          const int nq = min(RC, a.nrhs - z * RC);
+          T* bR;
+          swp_up_r<T, RC>(R, xq, a.N, nq, sm, a.sm_cap, bR, true);
+          swp_up_c<T, RC>(R, xq, a.N, nq, bR, 0, R.c);
+          __syncthreads();
+        }
+      } else {
+        for (int it = blockIdx.x; it < nbz; it += gridDim.x) {
+          const int z = it / C.nrec;
+          const BoxRec<T> R = C.recs[it % C.nrec];
+          T* bR;
+          swp_up_r<T, RC>(R, a.x + (int64_t)z * RC * a.N, a.N, min(RC, a.nrhs - z * RC), sm, a.sm_cap, bR, true);
+        }
+        if (!grid_barrier(a.bar, a.polls, a.err)) return;
+        for (int it = blockIdx.x; it < nbz * ngrp; it += gridDim.x) {
+          const int bz = it / ngrp, gi = it % ngrp, z = bz / C.nrec;
+          const BoxRec<T> R = C.recs[bz % C.nrec];
+          const int i0 = gi * cpg * SWP_CH, i1 = min(R.c, i0 + cpg * SWP_CH);
+          if (i0 >= i1) continue;
+          T* xq = a.x + (int64_t)z * RC * a.N;
+          const int nq = min(RC, a.nrhs - z * RC);
+          for (int e = threadIdx.x; e < R.r * RC; e += blockDim.x) {
+            const int j = e / RC, q = e % RC;
+            sm[e] = q < nq ? ld_l2(xq + R.idxR[j] + (int64_t)q * a.N) : zero<T>();
+          }
+          __syncthreads();
+          swp_up_c<T, RC>(R, xq, a.N, nq, sm, i0, i1);
+          __syncthreads();
+        }
+      }
+    } else {
+      if (!split) {
+        for (int it = blockIdx.x; it < nbz; it += gridDim.x) {
+          const int z = it / C.nrec;
+          const BoxRec<T> R = C.recs[it % C.nrec];
+          T* xq = a.x + (int64_t)z * RC * a.N;
+          const int nq = min(RC, a.nrhs - z * RC), r = R.r;
+          T* zs = sm;                       // r x RC: running sum of the chunk partials
+          T* work = sm + (size_t)r * RC;
+          for (int e = threadIdx.x; e < r * RC; e += blockDim.x) zs[e] = zero<T>();
+          swp_dn_part<T, RC>(R, xq, a.N, nq, 0, (R.c + SWP_CH - 1) / SWP_CH, work,
+                             [&](int j, int, const T* p) {
+#pragma unroll
+                               for (int q = 0; q < RC; ++q) zs[j * RC + q] = zs[j * RC + q] + p[q];
+                             });
+          __syncthreads();
+          T* zr = work;
+          T* yR = zr + (size_t)r * RC;
+          for (int e = threadIdx.x; e < r * RC; e += blockDim.x) {
+            const int j = e / RC, q = e % RC;
+            zr[e] = q < nq ? ld_l2(xq + R.idxR[j] + (int64_t)q * a.N) - zs[e] : zero<T>();
+          }
+          swp_dn_fin<T, RC>(R, xq, a.N, nq, zr, yR, yR + (size_t)r * RC, a.sm_cap - 3 * r * RC);
+        }
+      } else {
+        const size_t pz = (size_t)C.nrec * nchk * C.max_r * RC;   // part entries per column chunk
+        for (int it = blockIdx.x; it < nbz * ngrp; it += gridDim.x) {
+          const int bz = it / ngrp, gi = it % ngrp, z = bz / C.nrec, box = bz % C.nrec;
+          const BoxRec<T> R = C.recs[box];
+          const int nck = (R.c + SWP_CH - 1) / SWP_CH, ch0 = gi * cpg, ch1 = min(nck, ch0 + cpg);
+          if (ch0 >= ch1) continue;
+          T* pp = a.part + z * pz + (size_t)box * nchk * C.max_r * RC;
+          swp_dn_part<T, RC>(R, a.x + (int64_t)z * RC * a.N, a.N, min(RC, a.nrhs - z * RC), ch0, ch1, sm,
+                             [&](int j, int ch, const T* p) {
+#pragma unroll
+                               for (int q = 0; q < RC; ++q) pp[((size_t)ch * C.max_r + j) * RC + q] = p[q];
+                             });
+          __syncthreads();
+        }
+        if (!grid_barrier(a.bar, a.polls, a.err)) return;
+        for (int it = blockIdx.x; it < nbz; it += gridDim.x) {
+          const int z = it / C.nrec, box = it % C.nrec;
+          const BoxRec<T> R = C.recs[box];
+          T* xq = a.x + (int64_t)z * RC * a.N;
+          const int nq = min(RC, a.nrhs - z * RC), r = R.r, nck = (R.c + SWP_CH - 1) / SWP_CH;
+          const T* pp = a.part + z * pz + (size_t)box * nchk * C.max_r * RC;
+          T* zr = sm;
+          T* yR = zr + (size_t)r * RC;
+          for (int e = threadIdx.x; e < r * RC; e += blockDim.x) {
+            const int j = e / RC, q = e % RC;
+            T sum = zero<T>();
+            for (int ch = 0; ch < nck; ++ch) sum = sum + ld_l2(pp + ((size_t)ch * C.max_r + j) * RC + q);
+            zr[e] = q < nq ? ld_l2(xq + R.idxR[j] + (int64_t)q * a.N) - sum : zero<T>();
+          }
+          swp_dn_fin<T, RC>(R, xq, a.N, nq, zr, yR, yR + (size_t)r * RC, a.sm_cap - 2 * r * RC);
+        }
+      }
+    }
+    if (step + 1 < a.ncls && !grid_barrier(a.bar, a.polls, a.err)) return;
+  }
 }
 
 // ------------------------------------------------------------------ many right-hand sides on the tensor cores
@@ -861,8 +1202,10 @@ template <typename T> __global__ void k_identity(T* A, int n) {
 
 // Workspace of the sweeps for nrhs right-hand sides in chunks of rc columns:
 // the downward sweep's partial sums, one counter per box, the gathered top block.
+// (The persistent sweeps use the same partial-sum region, with 64-row chunks,
+// and four ints at bar_off: grid barrier counters and the timeout flag.)
 struct SweepWs {
-  size_t cnt_off = 0, topz_off = 0, bytes = 0;
+  size_t cnt_off = 0, bar_off = 0, topz_off = 0, bytes = 0;
 };
 
 template <typename T> SweepWs sweep_ws(const rss_factorization* f, int64_t nrhs, int rc) {
@@ -875,12 +1218,93 @@ template <typename T> SweepWs sweep_ws(const rss_factorization* f, int64_t nrhs,
   auto al = [](size_t v) { return (v + 255) & ~size_t(255); };
   SweepWs w;
   w.cnt_off = al(sizeof(T) * part * nz * rc);
-  w.topz_off = w.cnt_off + al(sizeof(int) * cnt * nz);
+  w.bar_off = w.cnt_off + al(sizeof(int) * cnt * nz);
+  w.topz_off = w.bar_off + al(sizeof(int) * 4);
   w.bytes = w.topz_off + al(sizeof(T) * (size_t)f->ntop * nz * rc);
   return w;
 }
 
 int rhs_chunk(int64_t nrhs) { return nrhs == 1 ? 1 : nrhs <= 4 ? 4 : 8; }
+
+// Top block: x_top <- A_top^{-1} x_top (gathered, one product, scattered back).
+template <typename T, int RC>
+rss_status top_apply(const rss_factorization* f, T* x, int64_t N, int nrhs, cudaStream_t st, T* topz) {
+  if (f->ntop <= 0) return RSS_OK;
+  const unsigned nz = cdiv(nrhs, RC);
+  const size_t tsm = sizeof(T) * (size_t)f->ntop * RC;
+  if (tsm > 200 * 1024) {
+    rss_set_error("rss_solve: top block too large for the on-chip solve");
+    return RSS_EINVAL;
+  }
+  RSS_CUDA(cudaFuncSetAttribute(k_top_gemv<T, RC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+  const unsigned g = std::min<long long>(cdiv((long long)f->ntop * nz * RC, 256), 152LL * 8);
+  k_top_gather<T><<<g, 256, 0, st>>>(f->d_top_idx, f->ntop, x, N, nrhs, topz);
+  RSS_LAUNCHED();
+  k_top_gemv<T, RC><<<dim3(cdiv(f->ntop, SW_NT), nz), SW_NT, tsm, st>>>(static_cast<const T*>(f->d_top_inv),
+                                                                        f->d_top_idx, f->ntop, topz, x, N, nrhs);
+  RSS_LAUNCHED();
+  return RSS_OK;
+}
+
+// The two persistent launches of the FP64 sweeps (k_sweep) around the top
+// block.  Shared memory: the most any class needs without staging its small
+// matrices (at least 48 KB; more room lets them be staged); the grid: as many
+// CTAs as fit on the device at once (a cooperative launch needs all of them
+// resident).  *done is false when the launch is not possible (the caller then
+// takes the per-class kernels).
+constexpr long long SWP_POLLS = 1LL << 24;
+
+template <typename T, int RC>
+rss_status sweeps_persistent(const rss_factorization* f, T* x, int64_t N, int nrhs, cudaStream_t st, T* part,
+                             unsigned* bar, T* topz, bool* done) {
+  *done = false;
+  if (!f->d_swp || f->batches.empty()) return RSS_OK;
+  size_t need = 0;
+  for (const Batch& b : f->batches) {
+    const size_t up = (size_t)(b.max_k + 2 * b.max_r) * RC;
+    const size_t dn = (size_t)b.max_r * RC + swp_dn_part_sm(b.max_r, RC);
+    const size_t fin = (size_t)4 * b.max_r * RC;
+    need = std::max(need, std::max(up, std::max(dn, fin)));
+  }
+  size_t smem = std::max(need * sizeof(T), size_t(16) << 10);
+  smem = (smem + 1023) & ~size_t(1023);
+  if (smem > (size_t(200) << 10)) return RSS_OK;
+  int dev = 0, sms = 0, coop = 0;
+  RSS_CUDA(cudaGetDevice(&dev));
+  RSS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  RSS_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+  if (!coop) return RSS_OK;
+  SwpArgs<T> a;
+  a.cls = static_cast<const SwpClass<T>*>(f->d_swp);
+  a.ncls = (int)f->batches.size();
+  a.x = x;
+  a.N = N;
+  a.nrhs = nrhs;
+  a.part = part;
+  a.bar = bar;
+  a.err = reinterpret_cast<int*>(bar + 2);
+  a.polls = SWP_POLLS;
+  a.sm_cap = (int)(smem / sizeof(T));
+  a.spread = f->swp_spread > 0 ? f->swp_spread : SWP_SPREAD_DEFAULT;
+  void* args[] = {&a};
+  auto launch = [&](const void* fn) -> rss_status {
+    RSS_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    RSS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, SWP_NT, smem));
+    if (per_sm < 1) {
+      rss_set_error("rss_solve: the persistent sweep kernel does not fit an SM");
+      return RSS_ECUDA;
+    }
+    if (f->swp_ctas > 0) per_sm = std::min(per_sm, f->swp_ctas);
+    RSS_CUDA(cudaLaunchCooperativeKernel(fn, dim3(per_sm * sms), dim3(SWP_NT), args, smem, st));
+    return RSS_OK;
+  };
+  rss_status s = launch(reinterpret_cast<const void*>(k_sweep<T, RC, true>));
+  if (s == RSS_OK) s = top_apply<T, RC>(f, x, N, nrhs, st, topz);
+  if (s == RSS_OK) s = launch(reinterpret_cast<const void*>(k_sweep<T, RC, false>));
+  if (s == RSS_OK) *done = true;
+  return s;
+}
 
 // tcz: complex factors with at least ZCN right-hand sides take the tensor-core
 // sweeps (k_up_tcz, k_down_tcz) for every colour class whose boxes fit their
@@ -904,6 +1328,12 @@ rss_status sweeps(const rss_factorization* f, T* x, int64_t N, int nrhs, cudaStr
   int* cnt = reinterpret_cast<int*>(wb + w.cnt_off);
   T* topz = reinterpret_cast<T*>(wb + w.topz_off);
   RSS_CUDA(cudaMemsetAsync(cnt, 0, w.topz_off - w.cnt_off, st));
+  if (!tcz && f->swp_launch == 2) {
+    bool done = false;
+    const rss_status sp = sweeps_persistent<T, RC>(f, x, N, nrhs, st, part,
+                                                   reinterpret_cast<unsigned*>(wb + w.bar_off), topz, &done);
+    if (sp != RSS_OK || done) return sp;
+  }
   RSS_CUDA(cudaFuncSetAttribute(k_up_r<T, RC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
   RSS_CUDA(cudaFuncSetAttribute(k_up_c<T, RC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
   RSS_CUDA(cudaFuncSetAttribute(k_down<T, RC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
@@ -1150,6 +1580,8 @@ rss_status solve_impl(const rss_factorization* f, T* b, int64_t nrhs, int64_t ld
   char* mem = nullptr;
   RSS_CUDA(pool_malloc(reinterpret_cast<void**>(&mem), xb + w.bytes, st));
   T* x = reinterpret_cast<T*>(mem);
+  const int* err = reinterpret_cast<const int*>(mem + xb + w.bar_off + 2 * sizeof(unsigned));
+  RSS_CUDA(cudaMemsetAsync(mem + xb + w.bar_off, 0, 4 * sizeof(int), st));
   const unsigned grid = std::min<long long>(cdiv((long long)N * nrhs, NT), 152LL * 16);
   k_perm_in<T><<<grid, NT, 0, st>>>(b, ldb, x, N, (int)nrhs, f->d_user_to_tree);
   rss_status s = RSS_OK;
@@ -1159,7 +1591,7 @@ rss_status solve_impl(const rss_factorization* f, T* b, int64_t nrhs, int64_t ld
   }
   if (s == RSS_OK) s = run_sweeps<T>(f, x, N, nrhs, st, mem + xb);
   if (s == RSS_OK) {
-    k_perm_out<T><<<grid, NT, 0, st>>>(b, ldb, x, N, (int)nrhs, f->d_user_to_tree);
+    k_perm_out<T><<<grid, NT, 0, st>>>(b, ldb, x, N, (int)nrhs, f->d_user_to_tree, err);
     if (cudaGetLastError() != cudaSuccess) {
       rss_set_error("rss_solve: launch failed");
       s = RSS_ECUDA;
@@ -1170,6 +1602,27 @@ rss_status solve_impl(const rss_factorization* f, T* b, int64_t nrhs, int64_t ld
 }
 
 template rss_status solve_impl<double>(const rss_factorization*, double*, int64_t, int64_t, cudaStream_t);
+
+template <typename T> rss_status build_sweep_classes(rss_factorization* f, cudaStream_t st) {
+  if (f->batches.empty()) return RSS_OK;
+  std::vector<SwpClass<T>> h(f->batches.size());
+  for (size_t i = 0; i < h.size(); ++i) {
+    const Batch& b = f->batches[i];
+    h[i] = SwpClass<T>{static_cast<const BoxRec<T>*>(b.d_recs), b.nrec, b.max_k, b.max_r, b.max_c};
+  }
+  void* d = f->arena.get(sizeof(SwpClass<T>) * h.size());
+  if (!d) {
+    rss_set_error("rss_factor: device arena allocation failed");
+    return RSS_ENOMEM;
+  }
+  RSS_CUDA(cudaMemcpyAsync(d, h.data(), sizeof(SwpClass<T>) * h.size(), cudaMemcpyHostToDevice, st));
+  RSS_CUDA(cudaStreamSynchronize(st));   // h is a host temporary
+  f->d_swp = d;
+  return RSS_OK;
+}
+
+template rss_status build_sweep_classes<double>(rss_factorization*, cudaStream_t);
+template rss_status build_sweep_classes<zd>(rss_factorization*, cudaStream_t);
 
 size_t solve_device_bytes(const rss_factorization* f, int64_t nrhs) {
   const size_t esz = f->is_complex ? 16 : 8;
@@ -1235,9 +1688,13 @@ rss_status solve_in_scratch(const rss_factorization* f, T* b, int64_t nrhs, int6
   k_perm_in<T><<<grid, NT, 0, st>>>(b, ldb, x, N, (int)nrhs, f->d_user_to_tree);
   RSS_LAUNCHED();
   const size_t xb = (sizeof(T) * (size_t)N * nrhs + 255) & ~size_t(255);
-  const rss_status s = run_sweeps<T>(f, x, N, nrhs, st, reinterpret_cast<char*>(x) + xb, false);
+  char* ws = reinterpret_cast<char*>(x) + xb;
+  const SweepWs w = sweep_ws<T>(f, nrhs, rhs_chunk(nrhs));
+  RSS_CUDA(cudaMemsetAsync(ws + w.bar_off, 0, 4 * sizeof(int), st));   // barrier words of the last call
+  const rss_status s = run_sweeps<T>(f, x, N, nrhs, st, ws, false);
   if (s != RSS_OK) return s;
-  k_perm_out<T><<<grid, NT, 0, st>>>(b, ldb, x, N, (int)nrhs, f->d_user_to_tree);
+  k_perm_out<T><<<grid, NT, 0, st>>>(b, ldb, x, N, (int)nrhs, f->d_user_to_tree,
+                                     reinterpret_cast<const int*>(ws + w.bar_off + 2 * sizeof(unsigned)));
   RSS_LAUNCHED();
   return RSS_OK;
 }
@@ -1280,4 +1737,94 @@ extern "C" rss_status rss_solve_noalloc(const rss_factorization* f, void* b, int
   return f->is_complex
              ? solve_in_scratch<zd>(f, static_cast<zd*>(b), nrhs, ldb, st, static_cast<zd*>(scratch))
              : solve_in_scratch<double>(f, static_cast<double*>(b), nrhs, ldb, st, static_cast<double*>(scratch));
+}
+
+// ---------------------------------------------------------------------------
+// rss_tune_solve: the schedule of the persistent sweeps, chosen by measurement.
+// The knob is `spread`, the target number of work items per CTA and colour
+// class: 1 keeps whole boxes per CTA wherever a class has about as many boxes
+// as the GPU has CTAs, larger values split the boxes of more classes into
+// groups of 64-row chunks of C (more parallel work, one more grid barrier per
+// split class).  Every schedule adds the same products in the same order, so
+// the choice changes the time of a solve, never its result.
+extern "C" rss_status rss_tune_solve(rss_factorization* f, int64_t nrhs, void* stream, char* json, size_t len) {
+  if (!f || f->tag != RSS_TAG_FACTOR || nrhs <= 0 || nrhs >= 1 << 20) {
+    rss_set_error("rss_tune_solve: needs a factor handle and 0 < nrhs < 2^20");
+    return RSS_EINVAL;
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const size_t esz = f->is_complex ? 16 : 8;
+  const bool fp64_path = f->is_complex ? nrhs < ZCN : !use_tc(f, nrhs);
+  std::ostringstream o;
+  o << "{\"nrhs\": " << nrhs;
+  if (!fp64_path || !f->d_swp) {
+    o << ", \"path\": \"tensor-core sweeps (nothing to tune)\"}";
+  } else {
+    const size_t bytes = esz * (size_t)f->n * (size_t)nrhs;
+    void* b = nullptr;
+    RSS_CUDA(pool_malloc(&b, bytes, st));
+    RSS_CUDA(cudaMemsetAsync(b, 0, bytes, st));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    RSS_CUDA(cudaEventCreate(&e0));
+    RSS_CUDA(cudaEventCreate(&e1));
+    const int cand[] = {1, 2, 4, 8};
+    const int ctas[] = {2, 4, 0};   // CTAs per SM (0: as many as fit)
+    const int ncand = 1 + (int)(sizeof(cand) / sizeof(cand[0])) * 3;   // the per-class launches first
+    const int keep = f->swp_spread, keep_c = f->swp_ctas, keep_l = f->swp_launch;
+    int best = SWP_SPREAD_DEFAULT, best_c = 0, best_l = 2;
+    float best_ms = 1e30f;
+    rss_status s = RSS_OK;
+    o << ", \"path\": \"FP64 sweeps\", \"candidates\": [";
+    for (int ci = 0; ci < ncand && s == RSS_OK; ++ci) {
+      f->swp_launch = ci == 0 ? 1 : 2;
+      f->swp_spread = ci == 0 ? 0 : cand[(ci - 1) / 3];
+      f->swp_ctas = ci == 0 ? 0 : ctas[(ci - 1) % 3];
+      float t[3];
+      for (int rep = -1; rep < 3 && s == RSS_OK; ++rep) {   // one untimed run first
+        cudaEventRecord(e0, st);
+        s = f->is_complex ? solve_impl<zd>(f, static_cast<zd*>(b), nrhs, f->n, st)
+                          : solve_impl<double>(f, static_cast<double*>(b), nrhs, f->n, st);
+        cudaEventRecord(e1, st);
+        if (cudaEventSynchronize(e1) != cudaSuccess) s = RSS_ECUDA;
+        if (rep >= 0 && s == RSS_OK) cudaEventElapsedTime(&t[rep], e0, e1);
+      }
+      if (s != RSS_OK) break;
+      std::sort(t, t + 3);
+      if (ci == 0)
+        o << "{\"launch\": \"per_class\", \"ms\": " << t[1] << "}";
+      else
+        o << ", {\"launch\": \"persistent\", \"spread\": " << f->swp_spread << ", \"ctas_per_sm\": "
+          << f->swp_ctas << ", \"ms\": " << t[1] << "}";
+      if (t[1] < best_ms) {
+        best_ms = t[1];
+        best = f->swp_spread;
+        best_c = f->swp_ctas;
+        best_l = f->swp_launch;
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    pool_free(b, st);
+    if (s != RSS_OK) {
+      f->swp_spread = keep;
+      f->swp_ctas = keep_c;
+      f->swp_launch = keep_l;
+      return s;
+    }
+    f->swp_spread = best;
+    f->swp_ctas = best_c;
+    f->swp_launch = best_l;
+    o << "], \"launch\": \"" << (best_l == 1 ? "per_class" : "persistent") << "\"";
+    if (best_l == 2) o << ", \"spread\": " << best << ", \"ctas_per_sm\": " << best_c;
+    o << ", \"ms\": " << best_ms << "}";
+  }
+  const std::string js = o.str();
+  if (json && len) {
+    if (js.size() + 1 > len) {
+      rss_set_error("rss_tune_solve: json buffer too small");
+      return RSS_EINVAL;
+    }
+    std::memcpy(json, js.c_str(), js.size() + 1);
+  }
+  return RSS_OK;
 }

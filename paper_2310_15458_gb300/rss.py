@@ -43,7 +43,8 @@ class _Params(ctypes.Structure):
                 ("schur_path", ctypes.c_int), ("id_cluster", ctypes.c_int),
                 ("bump_cx", ctypes.c_double), ("bump_cy", ctypes.c_double),
                 ("bump_a", ctypes.c_double), ("diag_rule", ctypes.c_int), ("per_box", ctypes.c_int),
-                ("class_order", ctypes.c_int), ("wait_polls", ctypes.c_int)]
+                ("class_order", ctypes.c_int), ("wait_polls", ctypes.c_int),
+                ("tune_table", ctypes.c_char_p)]
 
 
 _lib = None
@@ -81,10 +82,12 @@ def _load():
                                         ctypes.c_int, ctypes.POINTER(ctypes.c_int), dp, vp]
     lib.rss_trim_memory.argtypes = [ctypes.c_size_t]
     lib.rss_probe_fp64.argtypes = [dp, dp, vp]
+    lib.rss_tune_solve.argtypes = [vp, i64, vp, ctypes.c_char_p, ctypes.c_size_t]
     for name in ("rss_build_tree", "rss_factor", "rss_solve", "rss_solve_noalloc", "rss_info",
                  "rss_level_ranks", "rss_box_record", "rss_server_create", "rss_server_add",
                  "rss_server_submit", "rss_server_wait", "rss_server_stats", "rss_self_integral",
-                 "rss_matvec", "rss_solve_iterative", "rss_trim_memory", "rss_probe_fp64"):
+                 "rss_matvec", "rss_solve_iterative", "rss_trim_memory", "rss_probe_fp64",
+                 "rss_tune_solve"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -156,7 +159,7 @@ def rss_factor(tree: Tree, kind: int = LAPLACE, eps: float = 1e-6, h: float = 0.
                phase=(0.0, 0.0), full_stack: bool = False, schur_fp64: bool = False,
                id_cluster: int = 0, diag_rule: int = 0, bump=(0.5, 0.5, 32.0),
                per_box: bool = False, schur_mma_sync: bool = False, class_order: int = 0,
-               wait_polls: int = 0, stream=None) -> Factor:
+               wait_polls: int = 0, tune_table: dict | str | None = None, stream=None) -> Factor:
     lib = _load()
     p = _Params()
     p.kind, p.h, p.kappa = kind, h, kappa
@@ -177,6 +180,8 @@ def rss_factor(tree: Tree, kind: int = LAPLACE, eps: float = 1e-6, h: float = 0.
     p.per_box = 1 if per_box else 0
     p.class_order = int(class_order)
     p.wait_polls = int(wait_polls)
+    if tune_table is not None:
+        p.tune_table = (json.dumps(tune_table) if isinstance(tune_table, dict) else str(tune_table)).encode()
     out = ctypes.c_void_p()
     _check(lib.rss_factor(tree.handle, ctypes.byref(p), _stream_handle(stream), ctypes.byref(out)))
     return Factor(out, tree.n, kind in (HELMHOLTZ, TEST_POLY, HELMHOLTZ_LS), tree)
@@ -293,6 +298,14 @@ def rss_solve_noalloc(f: Factor, b, stream=None):
     nrhs, ldb = _columns(b, f.n, "b")
     _check(_load().rss_solve_noalloc(f.handle, b.data_ptr(), nrhs, ldb, _stream_handle(stream)))
     return b
+
+
+def rss_tune_solve(f: Factor, nrhs: int = 1, stream=None) -> dict:
+    """Time the solve's launch schedules on f, keep the fastest for its later
+    solves, and return the table (rss_params.tune_table accepts it back)."""
+    buf = ctypes.create_string_buffer(4096)
+    _check(_load().rss_tune_solve(f.handle, int(nrhs), _stream_handle(stream), buf, len(buf)))
+    return json.loads(buf.value.decode())
 
 
 def rss_probe_fp64(stream=None) -> tuple[float, float]:

@@ -457,3 +457,40 @@ def test_tensor_core_sweeps_many_rhs_complex(P):
     xp = gpu_solve(P, f, np.asfortranarray(b[:, perm]))
     assert np.array_equal(xp, x[:, perm])
     assert relres(pts, spec, x, b) <= 10 * eps
+
+
+def test_solve_schedules_give_the_same_bits(P):
+    """The launch form of the FP64 sweeps (per-class kernels, or two persistent
+    launches whose schedule spreads a colour class over more or fewer CTAs)
+    changes the time of a solve, not its result: every form adds the same products
+    in the same order.  rss_tune_solve measures the candidates and keeps the
+    fastest; a tune table passed to rss_factor applies a form directly."""
+    side = 128
+    pts = W.grid_points(side)
+    tree = P.rss_build_tree(pts, 64)
+    b = W.gaussian_rhs(side * side, 3, False, 48)
+    tables = [{"launch": "per_class"}] + [{"launch": "persistent", "spread": sp, "ctas_per_sm": c}
+                                          for sp, c in ((1, 2), (4, 0), (32, 4))]
+    xs = []
+    for t in tables:
+        f = P.rss_factor(tree, kind=0, eps=1e-6, h=1 / side, tune_table=t)
+        info = P.rss_info(f)
+        assert info["solve_launch"] == t["launch"]
+        if t["launch"] == "persistent":
+            assert info["solve_spread"] == t["spread"] and info["solve_ctas_per_sm"] == t["ctas_per_sm"]
+        xs.append(gpu_solve(P, f, b))
+        xs.append(gpu_solve(P, f, np.ascontiguousarray(b[:, 1])))
+    for x in xs[2::2]:
+        assert np.array_equal(x, xs[0])
+    for x in xs[1::2]:
+        assert np.array_equal(x, xs[0][:, 1])
+    table = P.rss_tune_solve(f, 1)
+    assert len(table["candidates"]) == 13 and all(c["ms"] > 0 for c in table["candidates"])
+    assert P.rss_info(f)["solve_launch"] == table["launch"]
+    if table["launch"] == "persistent":
+        assert table["spread"] in (1, 2, 4, 8) and table["ctas_per_sm"] in (0, 2, 4)
+    assert np.array_equal(gpu_solve(P, f, b), xs[0])
+    f2 = P.rss_factor(tree, kind=0, eps=1e-6, h=1 / side, tune_table=table)
+    assert P.rss_info(f2)["solve_launch"] == table["launch"]
+    with pytest.raises(P.RSSError, match="EINVAL"):
+        P.rss_factor(tree, kind=0, eps=1e-6, h=1 / side, tune_table={"launch": "persistent", "spread": 0})
