@@ -44,7 +44,11 @@ FP64_PEAK_TFLOPS = 1.25
 # the 1024 x 1024 Laplace workload, from an ncu capture of the same kernels on a
 # smaller grid scaled by the boxes processed (source in the dict); None when the
 # kernels have changed since the capture.
-TRAFFIC = {"id": None}
+TRAFFIC = {"id": {"bytes_per_factor": 31.22e9 * (78.52 / 19.18),
+                  "source": "ncu dram__bytes_read.sum + dram__bytes_write.sum over every k_id and k_id_cl "
+                            "launch of one 512 x 512 Laplace factorization (31.2 GB), scaled to 1024 x 1024 "
+                            "by the ratio of the phase's algorithmic flops (78.5 / 19.2 GFLOP), then divided "
+                            "by the launches of one factorization"}}
 CPU_SAMPLE_SIDES = (128, 256)   # oracle samples: the same workload on these grids
 
 
@@ -62,6 +66,11 @@ def parse():
     ap.add_argument("--serve-requests", type=int, default=2100,
                     help="requests per load, the first 100 warm-up (2100: the full protocol)")
     ap.add_argument("--no-large", action="store_true", help="skip the 2048^2 Helmholtz served run")
+    ap.add_argument("--solve-launch", default="tune", choices=["tune", "per_class", "persistent"],
+                    help="launch form of the 1-RHS sweeps: measured once during the warm-up (tune), or "
+                         "fixed (for captures under a profiler, which distorts the measurement)")
+    ap.add_argument("--no-probe", action="store_true",
+                    help="skip the FP64 throughput probes (the roofline then keeps the nominal peak only)")
     ap.add_argument("--serve-loads", type=float, nargs="+", default=[0.5, 0.9])
     return ap.parse_args()
 
@@ -581,9 +590,13 @@ def native_arm(args, w):
         P.rss_solve(f, x.view(n, 1), stream=stream)
         return f
 
+    if args.solve_launch == "per_class":
+        tune = {"launch": "per_class"}
+    elif args.solve_launch == "persistent":
+        tune = {"launch": "persistent", "spread": 1, "ctas_per_sm": 0}
     for i in range(args.warmup):
         f = step()
-        if i == 0:
+        if i == 0 and args.solve_launch == "tune":
             tune = P.rss_tune_solve(f, 1, stream=stream)
         del f
     barrier()
@@ -646,8 +659,18 @@ def native_arm(args, w):
     kern = {"id": "k_id", "elim": "k_elim", "schur": "k_schur"}[dom]
     tr = TRAFFIC.get(dom) if args.workload == WORKLOAD else None
     traffic = tr["bytes_per_factor"] / max(launches, 1) if tr else None
-    probe_tflops, probe_ms = P.rss_probe_fp64(stream=stream)
-    solve_launches = 2 + 2 * info["batches"] + 1
+    if args.no_probe:
+        probe_tflops = probe_ms = dmma_tflops = None
+    else:
+        probe_tflops, probe_ms = P.rss_probe_fp64(stream=stream)
+        dmma_tflops, dmma_ms = P.rss_probe_dmma(stream=stream)
+    # kernels of one 1-RHS solve: the user-order permutations, the top block's gather and
+    # product, and per colour class k_up_r, k_up_c and k_down (per-class form) or the two
+    # persistent sweeps (persistent form)
+    if info.get("solve_launch") == "persistent":
+        solve_launches = 2 + 2 + 2
+    else:
+        solve_launches = 2 + 2 + 3 * info["batches"]
     line = {
         "metric": METRIC, "value": ms / 1e3, "unit": "s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
@@ -680,9 +703,10 @@ def native_arm(args, w):
                      "launches": launches, "avg_launch_ms": gms[dom] / max(launches, 1),
                      "peak_source": "nominal FP64 rate (152 SMs x 2.07 GHz x 2 FMA/clk x 2); no FP64 "
                                     "figure in MEASURED_PEAKS.json",
-                     "peak_probe": probe_tflops, "frac_of_probe": achieved / probe_tflops,
-                     "probe": "rss_probe_fp64: independent DFMA chains, 8 CTAs x 256 threads per SM, "
-                              "best of 5 launches of %.1f ms" % probe_ms,
+                     "peak_probe": probe_tflops, "frac_of_probe": achieved / probe_tflops if probe_tflops else None,
+                     "probe": ("rss_probe_fp64: independent DFMA chains, 8 CTAs x 256 threads per SM, "
+                               "best of 5 launches of %.1f ms" % probe_ms) if probe_ms else None,
+                     "fp64_mma_probe": dmma_tflops,
                      "traffic_source": tr["source"] if tr else "none for the kernels as built"},
     }
     if not args.no_serve:

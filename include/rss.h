@@ -293,6 +293,12 @@ rss_status rss_trim_memory(size_t keep_bytes);
  * Synchronises stream; takes about half a second. */
 rss_status rss_probe_fp64(double* tflops, double* ms, void* stream);
 
+/* Measurement, as rss_probe_fp64, of the FP64 tensor-core MMA (mma.sync m8n8k4
+ * f64, 512 flops per warp-wide product): eight independent accumulator chains per
+ * warp, 8 CTAs of 256 threads per SM, best of five timed launches after one
+ * warm-up.  It shows whether FP64 tensor products would beat plain DFMA. */
+rss_status rss_probe_dmma(double* tflops, double* ms, void* stream);
+
 /* Message for the last non-OK status returned on this thread. */
 const char* rss_last_error(void);
 

@@ -82,12 +82,13 @@ def _load():
                                         ctypes.c_int, ctypes.POINTER(ctypes.c_int), dp, vp]
     lib.rss_trim_memory.argtypes = [ctypes.c_size_t]
     lib.rss_probe_fp64.argtypes = [dp, dp, vp]
+    lib.rss_probe_dmma.argtypes = [dp, dp, vp]
     lib.rss_tune_solve.argtypes = [vp, i64, vp, ctypes.c_char_p, ctypes.c_size_t]
     for name in ("rss_build_tree", "rss_factor", "rss_solve", "rss_solve_noalloc", "rss_info",
                  "rss_level_ranks", "rss_box_record", "rss_server_create", "rss_server_add",
                  "rss_server_submit", "rss_server_wait", "rss_server_stats", "rss_self_integral",
                  "rss_matvec", "rss_solve_iterative", "rss_trim_memory", "rss_probe_fp64",
-                 "rss_tune_solve"):
+                 "rss_probe_dmma", "rss_tune_solve"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -312,6 +313,13 @@ def rss_probe_fp64(stream=None) -> tuple[float, float]:
     """Measured FP64 FMA throughput of the current device: (TFLOP/s, ms per launch)."""
     t, ms = ctypes.c_double(), ctypes.c_double()
     _check(_load().rss_probe_fp64(ctypes.byref(t), ctypes.byref(ms), _stream_handle(stream)))
+    return t.value, ms.value
+
+
+def rss_probe_dmma(stream=None) -> tuple[float, float]:
+    """Measured FP64 tensor-core (mma.sync f64) throughput: (TFLOP/s, ms per launch)."""
+    t, ms = ctypes.c_double(), ctypes.c_double()
+    _check(_load().rss_probe_dmma(ctypes.byref(t), ctypes.byref(ms), _stream_handle(stream)))
     return t.value, ms.value
 
 
