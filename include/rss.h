@@ -121,8 +121,9 @@ typedef struct {
                                      n polls; -1: give up without polling, which exercises the
                                      timeout path on purpose (for tests) */
   const char* tune_table;         /* NULL, or the JSON object rss_tune_solve returned (read during
-                                     the call): its last "launch", "spread" and "ctas_per_sm" set
-                                     the launch form of the solve sweeps without measuring again.
+                                     the call): its last "launch", "spread", "ctas_per_sm" and
+                                     "tail_boxes" set the launch form of the solve sweeps without
+                                     measuring again.
                                      A form changes the time of a solve, never its result */
 } rss_params;
 
@@ -175,24 +176,28 @@ rss_status rss_solve_noalloc(const rss_factorization* f, void* b, int64_t nrhs, 
                              void* stream);
 
 /* Autotuner of the solve's launch form.  The FP64 sweeps (fewer than 32
- * right-hand sides) run either as per-class kernels (two or three launches per
- * colour class) or as two persistent cooperative launches that walk the colour
- * classes of the factorization, meeting at grid barriers; there a class with
- * few boxes is split across CTAs by rows of C (one more barrier).  The
- * persistent form has two knobs: "spread", the target number of work items per
- * CTA and class, and "ctas_per_sm" (0: as many as fit).  rss_tune_solve times the
- * solve of nrhs zero right-hand sides under the per-class form and under every
- * persistent candidate (spread 1, 2, 4, 8 x ctas_per_sm 2, 4, 0; median of three
- * after one untimed run, CUDA events on stream), keeps the fastest for the later
- * solves of f, and writes the table to json (may be NULL) as {"nrhs": ..,
- * "path": .., "candidates": [..], "launch": "per_class" | "persistent",
- * "spread": .., "ctas_per_sm": .., "ms": ..}; passing that text back as
- * rss_params.tune_table applies it without measuring.  Every form adds the same
- * products in the same order, so results are bitwise the same under any of
- * them.  With 32 or more right-hand sides (tensor-core sweeps) there is nothing
- * to tune and the table says so.  The paper has no counterpart.  Synchronises
- * stream; allocates n * nrhs scalars for the duration of the call; solves that
- * run meanwhile on other streams may take either form. */
+ * right-hand sides) run in one of three forms, which add the same products in
+ * the same order, so results are bitwise the same under any of them:
+ *  - "per_class": kernels per colour class (two or three launches each);
+ *  - "persistent": two cooperative launches that walk all colour classes of the
+ *    factorization, meeting at grid barriers; a class with few boxes is split
+ *    across CTAs by rows of C (one more barrier);
+ *  - "hybrid": per-class kernels for the fine levels and persistent launches for
+ *    the tail of colour classes with fewer than "tail_boxes" boxes each (the
+ *    coarse levels, where per-class launches are bound by latency).
+ * The persistent part has two knobs: "spread", the target number of work items
+ * per CTA and class, and "ctas_per_sm" (0: as many as fit).  rss_tune_solve
+ * times the solve of nrhs zero right-hand sides under eleven candidates (the
+ * per-class form, four persistent and six hybrid schedules; median of three
+ * after one untimed run, CUDA events on stream), keeps the fastest for the
+ * later solves of f, and writes the table to json (may be NULL) as {"nrhs": ..,
+ * "path": .., "candidates": [..], "launch": .., "spread": .., "ctas_per_sm":
+ * .., "tail_boxes": .., "ms": ..}; passing that text back as
+ * rss_params.tune_table applies it without measuring.  With 32 or more
+ * right-hand sides (tensor-core sweeps) there is nothing to tune and the table
+ * says so.  The paper has no counterpart.  Synchronises stream; allocates
+ * n * nrhs scalars for the duration of the call; solves that run meanwhile on
+ * other streams may take either form. */
 rss_status rss_tune_solve(rss_factorization* f, int64_t nrhs, void* stream, char* json, size_t len);
 
 /* ---- Serving: resident factorizations, continuous batching of solves ----

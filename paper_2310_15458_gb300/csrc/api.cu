@@ -209,7 +209,7 @@ rss_status rss_factor(const rss_tree* tree, const rss_params* p, void* stream, r
   if (p->ncoef < 0 || p->ncoef > RSS_MAX_COEF) return fail(RSS_EINVAL, "rss_factor: ncoef out of range");
   if (p->proxy_radius_over_side < 0) return fail(RSS_EINVAL, "rss_factor: negative proxy radius");
   if (p->wait_polls < -1) return fail(RSS_EINVAL, "rss_factor: wait_polls must be >= -1");
-  int spread = 0, ctas = 0, launch = 0;
+  int spread = 0, ctas = 0, launch = 0, tail = 0;
   if (p->tune_table) {   // the object rss_tune_solve writes: its last "launch", "spread", "ctas_per_sm"
     auto last = [&](const char* key) -> const char* {
       const char* hit = nullptr;
@@ -217,10 +217,14 @@ rss_status rss_factor(const rss_tree* tree, const rss_params* p, void* stream, r
       return hit ? std::strchr(hit, ':') : nullptr;
     };
     const char* l = last("\"launch\"");
-    launch = (l && std::strstr(l, "per_class") == std::strchr(l, '"') + 1) ? 1 : 2;
+    const char* v = l ? std::strchr(l, '"') : nullptr;
+    launch = !v ? 2 : std::strncmp(v + 1, "per_class", 9) == 0 ? 1 : std::strncmp(v + 1, "hybrid", 6) == 0 ? 3 : 2;
     const char* q = last("\"spread\"");
     if (q) spread = std::atoi(q + 1);
-    if (launch == 2 && (spread < 1 || spread > 1024))
+    const char* tb = last("\"tail_boxes\"");
+    tail = tb ? std::atoi(tb + 1) : 0;
+    if (launch == 3 && tail < 1) return fail(RSS_EINVAL, "rss_factor: tune_table hybrid without tail_boxes >= 1");
+    if (launch != 1 && (spread < 1 || spread > 1024))
       return fail(RSS_EINVAL, "rss_factor: tune_table has no \"spread\" between 1 and 1024");
     const char* c = last("\"ctas_per_sm\"");
     ctas = c ? std::atoi(c + 1) : 0;
@@ -233,6 +237,7 @@ rss_status rss_factor(const rss_tree* tree, const rss_params* p, void* stream, r
   f->swp_spread = spread;
   f->swp_ctas = ctas;
   f->swp_launch = launch;
+  f->swp_tail_boxes = tail;
   if (f->params.proxy_n == 0) f->params.proxy_n = 64;
   if (f->params.proxy_radius_over_side == 0) f->params.proxy_radius_over_side = 1.25;
   double h = p->h > 0 ? p->h : tree->geo.hg;
@@ -338,7 +343,8 @@ rss_status rss_info(const rss_factorization* f, char* buf, size_t len) {
     << ", \"launches\": " << f->launches << ", \"batches\": " << f->batches.size()
     << ", \"solve_spread\": " << (f->swp_spread > 0 ? f->swp_spread : SWP_SPREAD_DEFAULT)
     << ", \"solve_ctas_per_sm\": " << f->swp_ctas
-    << ", \"solve_launch\": \"" << (f->swp_launch == 2 ? "persistent" : "per_class") << "\""
+    << ", \"solve_launch\": \"" << (f->swp_launch == 2 ? "persistent" : f->swp_launch == 3 ? "hybrid" : "per_class")
+    << "\", \"solve_tail_boxes\": " << f->swp_tail_boxes
     << ", \"ms\": {\"gen\": " << f->t_gen << ", \"id\": " << f->t_id << ", \"elim\": " << f->t_elim
     << ", \"schur\": " << f->t_schur << ", \"merge\": " << f->t_merge << ", \"top\": " << f->t_top
     << ", \"total\": " << f->t_total << "}, \"gpu_ms\": {\"gen\": " << f->g_gen << ", \"id\": " << f->g_id

@@ -131,7 +131,9 @@ struct rss_factorization {
   void* d_swp = nullptr;               // the batches as the persistent sweeps read them (arena)
   int swp_spread = 0;                  // their schedule's knobs (0: the defaults; rss_tune_solve sets them):
   int swp_ctas = 0;                    // work items per CTA and class, CTAs per SM (0: as many as fit),
-  int swp_launch = 0;                  // and the launch form (0, 1: per-class kernels; 2: persistent)
+  int swp_launch = 0;                  // the launch form (0, 1: per-class kernels; 2: persistent;
+                                       // 3: per-class, then persistent for the coarse tail),
+  int swp_tail_boxes = 0;              // and the tail: the classes with fewer boxes than this
   std::vector<void*> rec_host;         // host copies of the BoxRec arrays (owned)
   std::vector<LevelInfo> levels;
   // top dense block

@@ -157,14 +157,18 @@ __global__ void __launch_bounds__(SW_NT) k_up_c(const BoxRec<T>* __restrict__ re
 }
 
 // Downward sweep (one CTA per SW_ROWS_D rows of C): partial sums of F y_C over
-// the CTA's rows, one thread per row of R from the CTA's block of F^T staged in
-// shared memory (ld SW_ROWS_D + 1) when it fits in sm_cap scalars.  The last CTA
-// of the box to finish (a counter, no waiting) adds the partial sums, forms
+// the CTA's rows from the CTA's block of F^T staged in shared memory (ld
+// SW_ROWS_D + 1) when it fits in sm_cap scalars.  Each partial is the sum of
+// SW_SUB_D sequential sums over consecutive rows of the chunk, one thread per
+// (row of R, part): short dependency chains and full warps.  The last CTA of the
+// box to finish (a counter, no waiting) adds the partial sums, forms
 // y_R <- U^{-1} (y_R - F y_C) and y_S -= T y_R.  Every CTA has read its rows of
 // y_C (which include y_S) before it counts itself in, so the last one may
 // overwrite y_S.
+constexpr int SW_NT_D = 256;
+constexpr int SW_SUB_D = 4;   // sequential sums per 64-row chunk (16 rows each), added in order
 template <typename T, int RC>
-__global__ void __launch_bounds__(SW_NT_R) k_down(const BoxRec<T>* __restrict__ recs, T* __restrict__ x, int64_t N,
+__global__ void __launch_bounds__(SW_NT_D) k_down(const BoxRec<T>* __restrict__ recs, T* __restrict__ x, int64_t N,
                                                 int nrhs, T* __restrict__ part, int* __restrict__ cnt, int nch_max,
                                                 int rmax, int sm_cap) {
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -177,11 +181,12 @@ __global__ void __launch_bounds__(SW_NT_R) k_down(const BoxRec<T>* __restrict__ 
   const int q0 = blockIdx.z * RC, nq = min(RC, nrhs - q0);
   const int tid = threadIdx.x, bs = blockDim.x;
   T* yC = reinterpret_cast<T*>(smraw);   // SW_ROWS_D x RC
-  T* Fs = yC + (size_t)SW_ROWS_D * RC;     // rows x r, ld LDF
+  T* ps = yC + (size_t)SW_ROWS_D * RC;     // SW_SUB_D x r x RC: the parts' sums
+  T* Fs = ps + (size_t)SW_SUB_D * r * RC;  // rows x r, ld LDF
   __shared__ int s_last;
   T* xq = x + (int64_t)q0 * N;
   const size_t box = (size_t)blockIdx.z * gridDim.y + blockIdx.y;
-  const bool stage = (size_t)SW_ROWS_D * RC + (size_t)LDF * r <= (size_t)sm_cap;
+  const bool stage = (size_t)SW_ROWS_D * RC + (size_t)SW_SUB_D * r * RC + (size_t)LDF * r <= (size_t)sm_cap;
   for (int e = tid; e < rows * RC; e += bs) {
     const int i = e / RC, q = e % RC;
     yC[e] = q < nq ? xq[R.idxC[i0 + i] + (int64_t)q * N] : zero<T>();
@@ -195,19 +200,28 @@ __global__ void __launch_bounds__(SW_NT_R) k_down(const BoxRec<T>* __restrict__ 
   }
   __syncthreads();
   T* pp = part + ((box * nch_max + blockIdx.x) * rmax) * RC;
-  for (int j = tid; j < r; j += bs) {
+  constexpr int SUB = SW_ROWS_D / SW_SUB_D;
+  for (int e = tid; e < SW_SUB_D * r; e += bs) {   // part sc of row j: rows SUB sc .. SUB sc + SUB - 1
+    const int j = e % r, sc = e / r, a0 = sc * SUB, a1 = min(rows, a0 + SUB);
     T acc[RC];
 #pragma unroll
     for (int q = 0; q < RC; ++q) acc[q] = zero<T>();
     const T* Fj = stage ? Fs + (size_t)j * LDF : R.Ft + i0 + (size_t)j * c;
 #pragma unroll 4
-    for (int i = 0; i < rows; ++i) {
+    for (int i = a0; i < a1; ++i) {
       const T fv = Fj[i];
 #pragma unroll
       for (int q = 0; q < RC; ++q) acc[q] = mad(acc[q], fv, yC[i * RC + q]);
     }
 #pragma unroll
-    for (int q = 0; q < RC; ++q) pp[j * RC + q] = acc[q];
+    for (int q = 0; q < RC; ++q) ps[((size_t)sc * r + j) * RC + q] = acc[q];
+  }
+  __syncthreads();
+  for (int e = tid; e < r * RC; e += bs) {
+    T p = ps[e];
+#pragma unroll
+    for (int sc = 1; sc < SW_SUB_D; ++sc) p = p + ps[(size_t)sc * r * RC + e];
+    pp[e] = p;
   }
   __threadfence();
   __syncthreads();
@@ -379,19 +393,21 @@ __device__ void swp_up_c(const BoxRec<T>& R, T* xq, int64_t N, int nq, const T* 
 
 // Partial sums p(j, ch) = sum over rows of chunk ch of F_ji y_i, for chunks
 // ch0 .. ch1-1 of one box, handed to out(j, ch, p[RC]) by the thread that owns
-// row j (the same thread for every chunk); each is one sequential sum down the
-// chunk's rows, the order k_down uses, so both give the same bits.  The chunk's
-// rows of F^T are staged with coalesced copies (ld SWP_CH + 1: conflict-free
-// reads down a column).  Uses swp_dn_part_sm(r) scalars of sm.
+// row j (the same thread for every chunk); each is formed as k_down forms it,
+// SW_SUB_D sequential sums over consecutive 16-row parts added in order, so both
+// give the same bits.  The chunk's rows of F^T are staged with coalesced copies
+// (ld SWP_CH + 1: conflict-free reads down a column).  Uses swp_dn_part_sm(r)
+// scalars of sm.
 __host__ __device__ constexpr size_t swp_dn_part_sm(int r, int rc) {
-  return (size_t)SWP_CH * rc + (size_t)(SWP_CH + 1) * r;
+  return (size_t)SWP_CH * rc + (size_t)(SWP_CH + 1) * r + (size_t)SW_SUB_D * r * rc;
 }
 template <typename T, int RC, typename OUT>
 __device__ void swp_dn_part(const BoxRec<T>& R, const T* xq, int64_t N, int nq, int ch0, int ch1, T* sm, OUT out) {
   const int r = R.r, c = R.c, tid = threadIdx.x, bs = blockDim.x;
-  constexpr int LDF = SWP_CH + 1;
+  constexpr int LDF = SWP_CH + 1, SUB = SWP_CH / SW_SUB_D;
   T* yC = sm;                          // SWP_CH x RC
   T* Fs = yC + (size_t)SWP_CH * RC;    // SWP_CH x r, ld LDF
+  T* ps = Fs + (size_t)LDF * r;        // SW_SUB_D x r x RC
   for (int ch = ch0; ch < ch1; ++ch) {
     const int i0 = ch * SWP_CH, rows = min(SWP_CH, c - i0);
     __syncthreads();   // the previous chunk's buffers are consumed
@@ -405,18 +421,31 @@ __device__ void swp_dn_part(const BoxRec<T>& R, const T* xq, int64_t N, int nq, 
     }
     cp_async_wait_all();
     __syncthreads();
-    for (int j = tid; j < r; j += bs) {
+    for (int e = tid; e < SW_SUB_D * r; e += bs) {
+      const int j = e % r, sc = e / r, a0 = sc * SUB, a1 = min(rows, a0 + SUB);
       const T* __restrict__ Fj = Fs + (size_t)j * LDF;
       T acc[RC];
 #pragma unroll
       for (int q = 0; q < RC; ++q) acc[q] = zero<T>();
 #pragma unroll 4
-      for (int ii = 0; ii < rows; ++ii) {
+      for (int ii = a0; ii < a1; ++ii) {
         const T fv = Fj[ii];
 #pragma unroll
         for (int q = 0; q < RC; ++q) acc[q] = mad(acc[q], fv, yC[ii * RC + q]);
       }
-      out(j, ch, acc);
+#pragma unroll
+      for (int q = 0; q < RC; ++q) ps[((size_t)sc * r + j) * RC + q] = acc[q];
+    }
+    __syncthreads();
+    for (int j = tid; j < r; j += bs) {
+      T p[RC];
+#pragma unroll
+      for (int q = 0; q < RC; ++q) {
+        p[q] = ps[(size_t)j * RC + q];
+#pragma unroll
+        for (int sc = 1; sc < SW_SUB_D; ++sc) p[q] = p[q] + ps[((size_t)sc * r + j) * RC + q];
+      }
+      out(j, ch, p);
     }
   }
 }
@@ -1254,29 +1283,31 @@ rss_status top_apply(const rss_factorization* f, T* x, int64_t N, int nrhs, cuda
 // takes the per-class kernels).
 constexpr long long SWP_POLLS = 1LL << 24;
 
-template <typename T, int RC>
-rss_status sweeps_persistent(const rss_factorization* f, T* x, int64_t N, int nrhs, cudaStream_t st, T* part,
-                             unsigned* bar, T* topz, bool* done) {
-  *done = false;
-  if (!f->d_swp || f->batches.empty()) return RSS_OK;
+template <typename T, int RC> size_t sweep_persistent_smem(const rss_factorization* f, int k0) {
   size_t need = 0;
-  for (const Batch& b : f->batches) {
+  for (size_t i = k0; i < f->batches.size(); ++i) {
+    const Batch& b = f->batches[i];
     const size_t up = (size_t)(b.max_k + 2 * b.max_r) * RC;
     const size_t dn = (size_t)b.max_r * RC + swp_dn_part_sm(b.max_r, RC);
     const size_t fin = (size_t)4 * b.max_r * RC;
     need = std::max(need, std::max(up, std::max(dn, fin)));
   }
-  size_t smem = std::max(need * sizeof(T), size_t(16) << 10);
-  smem = (smem + 1023) & ~size_t(1023);
-  if (smem > (size_t(200) << 10)) return RSS_OK;
-  int dev = 0, sms = 0, coop = 0;
+  const size_t smem = std::max(need * sizeof(T), size_t(16) << 10);
+  return (smem + 1023) & ~size_t(1023);
+}
+
+// One persistent launch (k_sweep) over the colour classes k0 .. end of the
+// factor order: upward in that order, or downward in reverse.
+template <typename T, int RC>
+rss_status sweep_persistent_launch(const rss_factorization* f, T* x, int64_t N, int nrhs, cudaStream_t st,
+                                   T* part, unsigned* bar, int k0, bool up) {
+  const size_t smem = sweep_persistent_smem<T, RC>(f, k0);
+  int dev = 0, sms = 0;
   RSS_CUDA(cudaGetDevice(&dev));
   RSS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  RSS_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
-  if (!coop) return RSS_OK;
   SwpArgs<T> a;
-  a.cls = static_cast<const SwpClass<T>*>(f->d_swp);
-  a.ncls = (int)f->batches.size();
+  a.cls = static_cast<const SwpClass<T>*>(f->d_swp) + k0;
+  a.ncls = (int)f->batches.size() - k0;
   a.x = x;
   a.N = N;
   a.nrhs = nrhs;
@@ -1287,23 +1318,40 @@ rss_status sweeps_persistent(const rss_factorization* f, T* x, int64_t N, int nr
   a.sm_cap = (int)(smem / sizeof(T));
   a.spread = f->swp_spread > 0 ? f->swp_spread : SWP_SPREAD_DEFAULT;
   void* args[] = {&a};
-  auto launch = [&](const void* fn) -> rss_status {
-    RSS_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    int per_sm = 0;
-    RSS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, SWP_NT, smem));
-    if (per_sm < 1) {
-      rss_set_error("rss_solve: the persistent sweep kernel does not fit an SM");
-      return RSS_ECUDA;
-    }
-    if (f->swp_ctas > 0) per_sm = std::min(per_sm, f->swp_ctas);
-    RSS_CUDA(cudaLaunchCooperativeKernel(fn, dim3(per_sm * sms), dim3(SWP_NT), args, smem, st));
-    return RSS_OK;
-  };
-  rss_status s = launch(reinterpret_cast<const void*>(k_sweep<T, RC, true>));
-  if (s == RSS_OK) s = top_apply<T, RC>(f, x, N, nrhs, st, topz);
-  if (s == RSS_OK) s = launch(reinterpret_cast<const void*>(k_sweep<T, RC, false>));
-  if (s == RSS_OK) *done = true;
-  return s;
+  const void* fn = up ? reinterpret_cast<const void*>(k_sweep<T, RC, true>)
+                      : reinterpret_cast<const void*>(k_sweep<T, RC, false>);
+  RSS_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int per_sm = 0;
+  RSS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, SWP_NT, smem));
+  if (per_sm < 1) {
+    rss_set_error("rss_solve: the persistent sweep kernel does not fit an SM");
+    return RSS_ECUDA;
+  }
+  if (f->swp_ctas > 0) per_sm = std::min(per_sm, f->swp_ctas);
+  RSS_CUDA(cudaLaunchCooperativeKernel(fn, dim3(per_sm * sms), dim3(SWP_NT), args, smem, st));
+  return RSS_OK;
+}
+
+// First colour class of the persistent part of the sweeps: the whole factor
+// (form 2), the tail of classes with fewer than f->swp_tail_boxes boxes each
+// (form 3), or none (per-class kernels; also when the device or the factor's
+// box sizes do not allow the cooperative launch).
+template <typename T, int RC> int sweep_persistent_start(const rss_factorization* f) {
+  const int nb = (int)f->batches.size();
+  if (!f->d_swp || nb == 0 || (f->swp_launch != 2 && f->swp_launch != 3)) return nb;
+  int k0 = 0;
+  if (f->swp_launch == 3) {
+    k0 = nb;
+    while (k0 > 0 && f->batches[k0 - 1].nrec < f->swp_tail_boxes) --k0;
+  }
+  if (k0 == nb || sweep_persistent_smem<T, RC>(f, k0) > (size_t(200) << 10)) return nb;
+  int dev = 0, coop = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop) {
+    cudaGetLastError();
+    return nb;
+  }
+  return k0;
 }
 
 // tcz: complex factors with at least ZCN right-hand sides take the tensor-core
@@ -1328,17 +1376,17 @@ rss_status sweeps(const rss_factorization* f, T* x, int64_t N, int nrhs, cudaStr
   int* cnt = reinterpret_cast<int*>(wb + w.cnt_off);
   T* topz = reinterpret_cast<T*>(wb + w.topz_off);
   RSS_CUDA(cudaMemsetAsync(cnt, 0, w.topz_off - w.cnt_off, st));
-  if (!tcz && f->swp_launch == 2) {
-    bool done = false;
-    const rss_status sp = sweeps_persistent<T, RC>(f, x, N, nrhs, st, part,
-                                                   reinterpret_cast<unsigned*>(wb + w.bar_off), topz, &done);
-    if (sp != RSS_OK || done) return sp;
-  }
+  // classes k0 .. end go through the persistent launches (none, all, or the
+  // coarse tail), the others through the per-class kernels
+  const int nb = (int)f->batches.size();
+  const int k0 = tcz ? nb : sweep_persistent_start<T, RC>(f);
+  unsigned* bar = reinterpret_cast<unsigned*>(wb + w.bar_off);
   RSS_CUDA(cudaFuncSetAttribute(k_up_r<T, RC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
   RSS_CUDA(cudaFuncSetAttribute(k_up_c<T, RC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
   RSS_CUDA(cudaFuncSetAttribute(k_down<T, RC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
   RSS_CUDA(cudaFuncSetAttribute(k_top_gemv<T, RC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-  for (const Batch& b : f->batches) {
+  for (int bi = 0; bi < k0; ++bi) {
+    const Batch& b = f->batches[bi];
     const BoxRec<T>* recs = static_cast<const BoxRec<T>*>(b.d_recs);
     if constexpr (std::is_same<T, zd>::value) {
       const size_t sm = tcz_smem_up(b.max_k, b.max_r);
@@ -1357,20 +1405,20 @@ rss_status sweeps(const rss_factorization* f, T* x, int64_t N, int nrhs, cudaStr
         recs, x, N, nrhs);
     RSS_LAUNCHED();
   }
-  if (f->ntop > 0) {
-    const size_t tsm = sizeof(T) * (size_t)f->ntop * RC;
-    if (tsm > 200 * 1024) {
-      rss_set_error("rss_solve: top block too large for the on-chip solve");
-      return RSS_EINVAL;
-    }
-    const unsigned g = std::min<long long>(cdiv((long long)f->ntop * nz * RC, 256), 152LL * 8);
-    k_top_gather<T><<<g, 256, 0, st>>>(f->d_top_idx, f->ntop, x, N, nrhs, topz);
-    RSS_LAUNCHED();
-    k_top_gemv<T, RC><<<dim3(cdiv(f->ntop, SW_NT), nz), SW_NT, tsm, st>>>(static_cast<const T*>(f->d_top_inv),
-                                                                          f->d_top_idx, f->ntop, topz, x, N, nrhs);
-    RSS_LAUNCHED();
+  if (k0 < nb) {
+    const rss_status sp = sweep_persistent_launch<T, RC>(f, x, N, nrhs, st, part, bar, k0, true);
+    if (sp != RSS_OK) return sp;
   }
-  for (auto it = f->batches.rbegin(); it != f->batches.rend(); ++it) {
+  {
+    const rss_status stp = top_apply<T, RC>(f, x, N, nrhs, st, topz);
+    if (stp != RSS_OK) return stp;
+  }
+  if (k0 < nb) {
+    const rss_status sp = sweep_persistent_launch<T, RC>(f, x, N, nrhs, st, part, bar, k0, false);
+    if (sp != RSS_OK) return sp;
+  }
+  for (int bi = k0 - 1; bi >= 0; --bi) {
+    const Batch* it = &f->batches[bi];
     if constexpr (std::is_same<T, zd>::value) {
       const size_t sm = tcz_smem_down(it->max_r);
       if (tcz && tcz_smem_up(it->max_k, it->max_r) <= TCZ_SMEM_MAX &&
@@ -1382,11 +1430,19 @@ rss_status sweeps(const rss_factorization* f, T* x, int64_t N, int nrhs, cudaStr
     }
     const int nch = (int)cdiv(it->max_c, SW_ROWS_D);
     const size_t want_d =
-        sizeof(T) * std::max((size_t)SW_ROWS_D * RC + (size_t)(SW_ROWS_D + 1) * it->max_r,
+        sizeof(T) * std::max((size_t)SW_ROWS_D * RC + (size_t)SW_SUB_D * it->max_r * RC +
+                                 (size_t)(SW_ROWS_D + 1) * it->max_r,
                              (size_t)2 * it->max_r * RC + (size_t)it->max_r * it->max_r +
                                  (size_t)(it->max_k | 1) * it->max_r);
-    const size_t sm_d = std::min<size_t>(want_d, 96 * 1024);
-    k_down<T, RC><<<dim3(nch, it->nrec, nz), SW_NT_R, sm_d, st>>>(static_cast<const BoxRec<T>*>(it->d_recs), x, N,
+    // y_C and the parts' sums (and later z, y_R) are always in shared memory; the
+    // staged blocks only when they fit
+    const size_t need_d = sizeof(T) * ((size_t)SW_ROWS_D * RC + (size_t)SW_SUB_D * it->max_r * RC);
+    const size_t sm_d = std::max(std::min<size_t>(want_d, 96 * 1024), need_d);
+    if (sm_d > 200 * 1024) {
+      rss_set_error("rss_solve: a box's downward sweep needs more shared memory than an SM has");
+      return RSS_EINVAL;
+    }
+    k_down<T, RC><<<dim3(nch, it->nrec, nz), SW_NT_D, sm_d, st>>>(static_cast<const BoxRec<T>*>(it->d_recs), x, N,
                                                                 nrhs, part, cnt, nch, it->max_r, (int)(sm_d / sizeof(T)));
     RSS_LAUNCHED();
   }
@@ -1767,18 +1823,24 @@ extern "C" rss_status rss_tune_solve(rss_factorization* f, int64_t nrhs, void* s
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     RSS_CUDA(cudaEventCreate(&e0));
     RSS_CUDA(cudaEventCreate(&e1));
-    const int cand[] = {1, 2, 4, 8};
-    const int ctas[] = {2, 4, 0};   // CTAs per SM (0: as many as fit)
-    const int ncand = 1 + (int)(sizeof(cand) / sizeof(cand[0])) * 3;   // the per-class launches first
-    const int keep = f->swp_spread, keep_c = f->swp_ctas, keep_l = f->swp_launch;
-    int best = SWP_SPREAD_DEFAULT, best_c = 0, best_l = 2;
+    struct Cand {
+      int launch, spread, ctas, tail;
+    };
+    const Cand cands[] = {{1, 0, 0, 0},   {2, 1, 4, 0},   {2, 1, 0, 0},   {2, 4, 4, 0},
+                          {2, 4, 0, 0},   {3, 1, 0, 32},  {3, 4, 0, 32},  {3, 1, 0, 128},
+                          {3, 4, 0, 128}, {3, 1, 0, 512}, {3, 4, 0, 512}};
+    const int ncand = (int)(sizeof(cands) / sizeof(cands[0]));
+    const int keep = f->swp_spread, keep_c = f->swp_ctas, keep_l = f->swp_launch, keep_t = f->swp_tail_boxes;
+    Cand best{1, 0, 0, 0};
     float best_ms = 1e30f;
     rss_status s = RSS_OK;
     o << ", \"path\": \"FP64 sweeps\", \"candidates\": [";
     for (int ci = 0; ci < ncand && s == RSS_OK; ++ci) {
-      f->swp_launch = ci == 0 ? 1 : 2;
-      f->swp_spread = ci == 0 ? 0 : cand[(ci - 1) / 3];
-      f->swp_ctas = ci == 0 ? 0 : ctas[(ci - 1) % 3];
+      const Cand& c = cands[ci];
+      f->swp_launch = c.launch;
+      f->swp_spread = c.spread;
+      f->swp_ctas = c.ctas;
+      f->swp_tail_boxes = c.tail;
       float t[3];
       for (int rep = -1; rep < 3 && s == RSS_OK; ++rep) {   // one untimed run first
         cudaEventRecord(e0, st);
@@ -1790,16 +1852,14 @@ extern "C" rss_status rss_tune_solve(rss_factorization* f, int64_t nrhs, void* s
       }
       if (s != RSS_OK) break;
       std::sort(t, t + 3);
-      if (ci == 0)
-        o << "{\"launch\": \"per_class\", \"ms\": " << t[1] << "}";
-      else
-        o << ", {\"launch\": \"persistent\", \"spread\": " << f->swp_spread << ", \"ctas_per_sm\": "
-          << f->swp_ctas << ", \"ms\": " << t[1] << "}";
+      o << (ci ? ", " : "") << "{\"launch\": \"" << (c.launch == 1 ? "per_class" : c.launch == 2 ? "persistent" : "hybrid")
+        << "\"";
+      if (c.launch != 1) o << ", \"spread\": " << c.spread << ", \"ctas_per_sm\": " << c.ctas;
+      if (c.launch == 3) o << ", \"tail_boxes\": " << c.tail;
+      o << ", \"ms\": " << t[1] << "}";
       if (t[1] < best_ms) {
         best_ms = t[1];
-        best = f->swp_spread;
-        best_c = f->swp_ctas;
-        best_l = f->swp_launch;
+        best = c;
       }
     }
     cudaEventDestroy(e0);
@@ -1809,13 +1869,17 @@ extern "C" rss_status rss_tune_solve(rss_factorization* f, int64_t nrhs, void* s
       f->swp_spread = keep;
       f->swp_ctas = keep_c;
       f->swp_launch = keep_l;
+      f->swp_tail_boxes = keep_t;
       return s;
     }
-    f->swp_spread = best;
-    f->swp_ctas = best_c;
-    f->swp_launch = best_l;
-    o << "], \"launch\": \"" << (best_l == 1 ? "per_class" : "persistent") << "\"";
-    if (best_l == 2) o << ", \"spread\": " << best << ", \"ctas_per_sm\": " << best_c;
+    f->swp_launch = best.launch;
+    f->swp_spread = best.spread;
+    f->swp_ctas = best.ctas;
+    f->swp_tail_boxes = best.tail;
+    o << "], \"launch\": \"" << (best.launch == 1 ? "per_class" : best.launch == 2 ? "persistent" : "hybrid")
+      << "\"";
+    if (best.launch != 1) o << ", \"spread\": " << best.spread << ", \"ctas_per_sm\": " << best.ctas;
+    if (best.launch == 3) o << ", \"tail_boxes\": " << best.tail;
     o << ", \"ms\": " << best_ms << "}";
   }
   const std::string js = o.str();

@@ -469,15 +469,18 @@ def test_solve_schedules_give_the_same_bits(P):
     pts = W.grid_points(side)
     tree = P.rss_build_tree(pts, 64)
     b = W.gaussian_rhs(side * side, 3, False, 48)
-    tables = [{"launch": "per_class"}] + [{"launch": "persistent", "spread": sp, "ctas_per_sm": c}
-                                          for sp, c in ((1, 2), (4, 0), (32, 4))]
+    tables = ([{"launch": "per_class"}] +
+              [{"launch": "persistent", "spread": sp, "ctas_per_sm": c} for sp, c in ((1, 2), (4, 0), (32, 4))] +
+              [{"launch": "hybrid", "spread": sp, "ctas_per_sm": 0, "tail_boxes": tb} for sp, tb in ((1, 8), (4, 100))])
     xs = []
     for t in tables:
         f = P.rss_factor(tree, kind=0, eps=1e-6, h=1 / side, tune_table=t)
         info = P.rss_info(f)
         assert info["solve_launch"] == t["launch"]
-        if t["launch"] == "persistent":
+        if t["launch"] != "per_class":
             assert info["solve_spread"] == t["spread"] and info["solve_ctas_per_sm"] == t["ctas_per_sm"]
+        if t["launch"] == "hybrid":
+            assert info["solve_tail_boxes"] == t["tail_boxes"]
         xs.append(gpu_solve(P, f, b))
         xs.append(gpu_solve(P, f, np.ascontiguousarray(b[:, 1])))
     for x in xs[2::2]:
@@ -485,10 +488,9 @@ def test_solve_schedules_give_the_same_bits(P):
     for x in xs[1::2]:
         assert np.array_equal(x, xs[0][:, 1])
     table = P.rss_tune_solve(f, 1)
-    assert len(table["candidates"]) == 13 and all(c["ms"] > 0 for c in table["candidates"])
+    assert len(table["candidates"]) == 11 and all(c["ms"] > 0 for c in table["candidates"])
     assert P.rss_info(f)["solve_launch"] == table["launch"]
-    if table["launch"] == "persistent":
-        assert table["spread"] in (1, 2, 4, 8) and table["ctas_per_sm"] in (0, 2, 4)
+    assert min(c["ms"] for c in table["candidates"]) == table["ms"]
     assert np.array_equal(gpu_solve(P, f, b), xs[0])
     f2 = P.rss_factor(tree, kind=0, eps=1e-6, h=1 / side, tune_table=table)
     assert P.rss_info(f2)["solve_launch"] == table["launch"]
