@@ -692,6 +692,7 @@ def native_arm(args, w):
         "phase_tflops": {k: info["flops"][k] / (gms[k] * 1e-3) / 1e12 for k in ("id", "elim", "schur", "top")
                          if gms.get(k)},
         "ranks": [{"side": L["side"], "k_mean": L["k_mean"], "k_max": L["k_max"]} for L in info["levels"]],
+        "level_gpu_ms": [{"side": L["side"], **L["gpu_ms"]} for L in info["levels"]],
         "ntop": info["ntop"],
         "solve_tuning": tune,
         "clocks": clk,

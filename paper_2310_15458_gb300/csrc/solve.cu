@@ -56,11 +56,14 @@ constexpr int SW_NT_R = 64;
 constexpr int SW_ROWS_D = 64;   // rows of C per CTA in the downward sweep
 
 // Upward sweep, part 1 (one CTA per box): b_R <- L_R^{-1} P_R (b_R - T^* b_S).
-// One thread per row of R (no warp reductions: an FP64 instruction costs the
-// same with one lane or 32).  T and L^{-1} P are staged in shared memory with
-// coalesced loads when they fit in sm_cap scalars.
+// t = b_R - T^* b_S one thread per row of R; L^{-1} P t as SW_SUB_U sequential
+// sums over consecutive parts of R per row (one thread per (row, part): short
+// dependency chains, full warps), the parts added in order.  T and L^{-1} P are
+// staged in shared memory with coalesced loads when they fit in sm_cap scalars.
+constexpr int SW_NT_U = 256;
+constexpr int SW_SUB_U = 4;
 template <typename T, int RC>
-__global__ void __launch_bounds__(SW_NT_R) k_up_r(const BoxRec<T>* __restrict__ recs, T* __restrict__ x, int64_t N,
+__global__ void __launch_bounds__(SW_NT_U) k_up_r(const BoxRec<T>* __restrict__ recs, T* __restrict__ x, int64_t N,
                                                 int nrhs, int sm_cap) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const BoxRec<T> R = recs[blockIdx.x];
@@ -68,9 +71,11 @@ __global__ void __launch_bounds__(SW_NT_R) k_up_r(const BoxRec<T>* __restrict__ 
   const int q0 = blockIdx.z * RC, nq = min(RC, nrhs - q0);
   T* bS = reinterpret_cast<T*>(smraw);   // k x RC
   T* t = bS + (size_t)k * RC;            // r x RC
-  T* Ts = t + (size_t)r * RC;            // T, ld k|1
+  T* ps = t + (size_t)r * RC;            // SW_SUB_U x r x RC: the parts' sums
+  T* Ts = ps + (size_t)SW_SUB_U * r * RC;   // T, ld k|1
   T* Ls = Ts + (size_t)ldt * r;          // L^{-1} P, ld r
-  const bool stage = (size_t)(k + r) * RC + (size_t)ldt * r + (size_t)r * r <= (size_t)sm_cap;
+  const bool stage =
+      (size_t)(k + r + SW_SUB_U * r) * RC + (size_t)ldt * r + (size_t)r * r <= (size_t)sm_cap;
   const int tid = threadIdx.x, bs = blockDim.x;
   T* xq = x + (int64_t)q0 * N;
   for (int e = tid; e < k * RC; e += bs) {
@@ -103,20 +108,28 @@ __global__ void __launch_bounds__(SW_NT_R) k_up_r(const BoxRec<T>* __restrict__ 
     for (int q = 0; q < RC; ++q) t[j * RC + q] = acc[q];
   }
   __syncthreads();
-  for (int j = tid; j < r; j += bs) {    // b_R = L^{-1} P t
+  const int L4 = (r + SW_SUB_U - 1) / SW_SUB_U;
+  for (int e = tid; e < SW_SUB_U * r; e += bs) {   // part sc of row j of L^{-1} P t
+    const int j = e % r, sc = e / r, l0 = sc * L4, l1 = min(r, l0 + L4);
     T acc[RC];
 #pragma unroll
     for (int q = 0; q < RC; ++q) acc[q] = zero<T>();
 #pragma unroll 4
-    for (int l = 0; l < r; ++l) {
+    for (int l = l0; l < l1; ++l) {
       const T lv = Lsrc[j + (size_t)l * r];
 #pragma unroll
       for (int q = 0; q < RC; ++q) acc[q] = mad(acc[q], lv, t[l * RC + q]);
     }
-    const int gj = R.idxR[j];
 #pragma unroll
-    for (int q = 0; q < RC; ++q)
-      if (q < nq) xq[gj + (int64_t)q * N] = acc[q];
+    for (int q = 0; q < RC; ++q) ps[((size_t)sc * r + j) * RC + q] = acc[q];
+  }
+  __syncthreads();
+  for (int e = tid; e < r * RC; e += bs) {   // b_R = the parts added in order
+    const int j = e / RC, q = e % RC;
+    T p = ps[e];
+#pragma unroll
+    for (int sc = 1; sc < SW_SUB_U; ++sc) p = p + ps[(size_t)sc * r * RC + e];
+    if (q < nq) xq[R.idxR[j] + (int64_t)q * N] = p;
   }
 }
 
@@ -317,9 +330,11 @@ __device__ void swp_up_r(const BoxRec<T>& R, T* xq, int64_t N, int nq, T* sm, in
   T* bS = sm;
   T* t = bS + (size_t)k * RC;
   bR = t + (size_t)r * RC;
-  T* Ts = bR + (size_t)r * RC;
+  T* ps = bR + (size_t)r * RC;   // SW_SUB_U x r x RC
+  T* Ts = ps + (size_t)SW_SUB_U * r * RC;
   T* Ls = Ts + (size_t)ldt * r;
-  const bool stage = (size_t)(k + 2 * r) * RC + (size_t)ldt * r + (size_t)r * r <= (size_t)sm_cap;
+  const bool stage =
+      (size_t)(k + 2 * r + SW_SUB_U * r) * RC + (size_t)ldt * r + (size_t)r * r <= (size_t)sm_cap;
   for (int e = tid; e < k * RC; e += bs) {
     const int s2 = e / RC, q = e % RC;
     bS[e] = q < nq ? ld_l2(xq + R.idxC[s2] + (int64_t)q * N) : zero<T>();
@@ -350,21 +365,29 @@ __device__ void swp_up_r(const BoxRec<T>& R, T* xq, int64_t N, int nq, T* sm, in
     for (int q = 0; q < RC; ++q) t[j * RC + q] = acc[q];
   }
   __syncthreads();
-  for (int j = tid; j < r; j += bs) {   // b_R = L^{-1} P t
+  const int L4 = (r + SW_SUB_U - 1) / SW_SUB_U;
+  for (int e = tid; e < SW_SUB_U * r; e += bs) {   // part sc of row j of L^{-1} P t, as k_up_r
+    const int j = e % r, sc = e / r, l0 = sc * L4, l1 = min(r, l0 + L4);
     T acc[RC];
 #pragma unroll
     for (int q = 0; q < RC; ++q) acc[q] = zero<T>();
 #pragma unroll 4
-    for (int l = 0; l < r; ++l) {
+    for (int l = l0; l < l1; ++l) {
       const T lv = Lsrc[j + (size_t)l * r];
 #pragma unroll
       for (int q = 0; q < RC; ++q) acc[q] = mad(acc[q], lv, t[l * RC + q]);
     }
 #pragma unroll
-    for (int q = 0; q < RC; ++q) {
-      bR[j * RC + q] = acc[q];
-      if (write_x && q < nq) xq[R.idxR[j] + (int64_t)q * N] = acc[q];
-    }
+    for (int q = 0; q < RC; ++q) ps[((size_t)sc * r + j) * RC + q] = acc[q];
+  }
+  __syncthreads();
+  for (int e = tid; e < r * RC; e += bs) {
+    const int j = e / RC, q = e % RC;
+    T p = ps[e];
+#pragma unroll
+    for (int sc = 1; sc < SW_SUB_U; ++sc) p = p + ps[(size_t)sc * r * RC + e];
+    bR[e] = p;
+    if (write_x && q < nq) xq[R.idxR[j] + (int64_t)q * N] = p;
   }
   __syncthreads();
 }
@@ -1287,7 +1310,7 @@ template <typename T, int RC> size_t sweep_persistent_smem(const rss_factorizati
   size_t need = 0;
   for (size_t i = k0; i < f->batches.size(); ++i) {
     const Batch& b = f->batches[i];
-    const size_t up = (size_t)(b.max_k + 2 * b.max_r) * RC;
+    const size_t up = (size_t)(b.max_k + 2 * b.max_r + SW_SUB_U * b.max_r) * RC;
     const size_t dn = (size_t)b.max_r * RC + swp_dn_part_sm(b.max_r, RC);
     const size_t fin = (size_t)4 * b.max_r * RC;
     need = std::max(need, std::max(up, std::max(dn, fin)));
@@ -1396,10 +1419,14 @@ rss_status sweeps(const rss_factorization* f, T* x, int64_t N, int nrhs, cudaStr
         continue;
       }
     }
-    const size_t want_r = sizeof(T) * ((size_t)(b.max_k + b.max_r) * RC + (size_t)(b.max_k | 1) * b.max_r +
-                                       (size_t)b.max_r * b.max_r);
-    const size_t sm_r = std::min<size_t>(want_r, 96 * 1024);
-    k_up_r<T, RC><<<dim3(b.nrec, 1, nz), SW_NT_R, sm_r, st>>>(recs, x, N, nrhs, (int)(sm_r / sizeof(T)));
+    const size_t need_r = sizeof(T) * (size_t)(b.max_k + b.max_r + SW_SUB_U * b.max_r) * RC;
+    const size_t want_r = need_r + sizeof(T) * ((size_t)(b.max_k | 1) * b.max_r + (size_t)b.max_r * b.max_r);
+    const size_t sm_r = std::max(std::min<size_t>(want_r, 96 * 1024), need_r);
+    if (sm_r > 200 * 1024) {
+      rss_set_error("rss_solve: a box's upward sweep needs more shared memory than an SM has");
+      return RSS_EINVAL;
+    }
+    k_up_r<T, RC><<<dim3(b.nrec, 1, nz), SW_NT_U, sm_r, st>>>(recs, x, N, nrhs, (int)(sm_r / sizeof(T)));
     RSS_LAUNCHED();
     k_up_c<T, RC><<<dim3(cdiv(b.max_c, SW_ROWS), b.nrec, nz), SW_NT, sizeof(T) * (size_t)b.max_r * RC, st>>>(
         recs, x, N, nrhs);
