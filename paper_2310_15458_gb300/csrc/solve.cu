@@ -169,6 +169,69 @@ __global__ void __launch_bounds__(SW_NT) k_up_c(const BoxRec<T>* __restrict__ re
   }
 }
 
+// The end of a box's downward step, given z = y_R - F y_C (shared, r x RC):
+// y_R = U^{-1} z into yR (shared) and x, then y_S -= T y_R.  Each product is
+// SW_SUB_T sums over consecutive parts of its inner index (rows of U^{-1} from
+// the diagonal on, columns of T), one thread per (row, part), added in order.
+// ps: SW_SUB_T x max(r, k) x RC scalars of shared memory.  Every thread calls it.
+constexpr int SW_SUB_T = 4;
+template <typename T, int RC>
+__device__ void box_tail(const BoxRec<T>& R, T* xq, int64_t N, int nq, const T* z, T* yR, T* ps,
+                         const T* Usrc, const T* Tsrc, int tl, bool l2_reads) {
+  const int k = R.k, r = R.r, tid = threadIdx.x, bs = blockDim.x;
+  const int L4 = (r + SW_SUB_T - 1) / SW_SUB_T;
+  for (int e = tid; e < SW_SUB_T * r; e += bs) {   // part sc of row j of U^{-1} z
+    const int j = e % r, sc = e / r, l0 = max(j, sc * L4), l1 = min(r, (sc + 1) * L4);
+    T acc[RC];
+#pragma unroll
+    for (int q = 0; q < RC; ++q) acc[q] = zero<T>();
+#pragma unroll 4
+    for (int l = l0; l < l1; ++l) {
+      const T uv = Usrc[j + (size_t)l * r];
+#pragma unroll
+      for (int q = 0; q < RC; ++q) acc[q] = mad(acc[q], uv, z[l * RC + q]);
+    }
+#pragma unroll
+    for (int q = 0; q < RC; ++q) ps[((size_t)sc * r + j) * RC + q] = acc[q];
+  }
+  __syncthreads();
+  for (int e = tid; e < r * RC; e += bs) {
+    const int j = e / RC, q = e % RC;
+    T v = ps[e];
+#pragma unroll
+    for (int sc = 1; sc < SW_SUB_T; ++sc) v = v + ps[(size_t)sc * r * RC + e];
+    yR[e] = v;
+    if (q < nq) xq[R.idxR[j] + (int64_t)q * N] = v;
+  }
+  __syncthreads();
+  for (int e = tid; e < SW_SUB_T * k; e += bs) {   // part sc of row s of T y_R
+    const int s2 = e % k, sc = e / k, j0 = sc * L4, j1 = min(r, j0 + L4);
+    T acc[RC];
+#pragma unroll
+    for (int q = 0; q < RC; ++q) acc[q] = zero<T>();
+#pragma unroll 4
+    for (int j = j0; j < j1; ++j) {
+      const T tv = Tsrc[s2 + (size_t)j * tl];
+#pragma unroll
+      for (int q = 0; q < RC; ++q) acc[q] = mad(acc[q], tv, yR[j * RC + q]);
+    }
+#pragma unroll
+    for (int q = 0; q < RC; ++q) ps[((size_t)sc * k + s2) * RC + q] = acc[q];
+  }
+  __syncthreads();
+  for (int e = tid; e < k * RC; e += bs) {
+    const int s2 = e / RC, q = e % RC;
+    T v = ps[e];
+#pragma unroll
+    for (int sc = 1; sc < SW_SUB_T; ++sc) v = v + ps[(size_t)sc * k * RC + e];
+    if (q < nq) {
+      const int64_t gs = R.idxC[s2] + (int64_t)q * N;
+      xq[gs] = (l2_reads ? ld_l2(xq + gs) : xq[gs]) - v;
+    }
+  }
+  __syncthreads();
+}
+
 // Downward sweep (one CTA per SW_ROWS_D rows of C): partial sums of F y_C over
 // the CTA's rows from the CTA's block of F^T staged in shared memory (ld
 // SW_ROWS_D + 1) when it fits in sm_cap scalars.  Each partial is the sum of
@@ -244,9 +307,11 @@ __global__ void __launch_bounds__(SW_NT_D) k_down(const BoxRec<T>* __restrict__ 
   __threadfence();
   T* z = yC;                    // r x RC (the shared buffers are free now)
   T* yR = z + (size_t)r * RC;   // r x RC
-  T* Ms = yR + (size_t)r * RC;  // U^{-1} (r x r) and T (k x r, ld k|1)
+  T* pt = yR + (size_t)r * RC;  // SW_SUB_T x max(r, k) x RC
+  T* Ms = pt + (size_t)SW_SUB_T * max(r, k) * RC;   // U^{-1} (r x r) and T (k x r, ld k|1)
   const int ldt = k | 1;
-  const bool stage2 = (size_t)2 * r * RC + (size_t)r * r + (size_t)ldt * r <= (size_t)sm_cap;
+  const bool stage2 = (size_t)(2 * r + SW_SUB_T * max(r, k)) * RC + (size_t)r * r + (size_t)ldt * r <=
+                      (size_t)sm_cap;
   T* Us = Ms;
   T* Ts = Ms + (size_t)r * r;
   for (int e = tid; e < r * RC; e += bs) {
@@ -261,42 +326,7 @@ __global__ void __launch_bounds__(SW_NT_D) k_down(const BoxRec<T>* __restrict__ 
     cp_async_wait_all();
   }
   __syncthreads();
-  const T* Usrc = stage2 ? Us : R.Ui;
-  for (int j = tid; j < r; j += bs) {    // y_R = U^{-1} z
-    T acc[RC];
-#pragma unroll
-    for (int q = 0; q < RC; ++q) acc[q] = zero<T>();
-#pragma unroll 4
-    for (int l = j; l < r; ++l) {
-      const T uv = Usrc[j + (size_t)l * r];
-#pragma unroll
-      for (int q = 0; q < RC; ++q) acc[q] = mad(acc[q], uv, z[l * RC + q]);
-    }
-    const int gj = R.idxR[j];
-#pragma unroll
-    for (int q = 0; q < RC; ++q) {
-      yR[j * RC + q] = acc[q];
-      if (q < nq) xq[gj + (int64_t)q * N] = acc[q];
-    }
-  }
-  __syncthreads();
-  const T* Tsrc = stage2 ? Ts : R.Tm;
-  const int tl = stage2 ? ldt : k;
-  for (int s2 = tid; s2 < k; s2 += bs) {   // y_S -= T y_R
-    T acc[RC];
-#pragma unroll
-    for (int q = 0; q < RC; ++q) acc[q] = zero<T>();
-#pragma unroll 4
-    for (int j = 0; j < r; ++j) {
-      const T tv = Tsrc[s2 + (size_t)j * tl];
-#pragma unroll
-      for (int q = 0; q < RC; ++q) acc[q] = mad(acc[q], tv, yR[j * RC + q]);
-    }
-    const int gs = R.idxC[s2];
-#pragma unroll
-    for (int q = 0; q < RC; ++q)
-      if (q < nq) xq[gs + (int64_t)q * N] = xq[gs + (int64_t)q * N] - acc[q];
-  }
+  box_tail<T, RC>(R, xq, N, nq, z, yR, pt, stage2 ? Us : R.Ui, stage2 ? Ts : R.Tm, stage2 ? ldt : k, false);
   if (tid == 0) cnt[box] = 0;   // ready for the next colour class
 }
 
@@ -474,56 +504,23 @@ __device__ void swp_dn_part(const BoxRec<T>& R, const T* xq, int64_t N, int nq, 
 }
 
 // Given z = y_R - F y_C (zr, shared, r x RC): y_R = U^{-1} z into x, then
-// y_S -= T y_R.  Uses yR (r x RC) and up to sm_cap scalars at mats for staging.
+// y_S -= T y_R, by box_tail (the order k_down uses).  Uses yR (r x RC) and
+// mat_cap scalars at mats: the parts' sums first, then the staged matrices.
 template <typename T, int RC>
 __device__ void swp_dn_fin(const BoxRec<T>& R, T* xq, int64_t N, int nq, const T* zr, T* yR, T* mats, int mat_cap) {
   const int k = R.k, r = R.r, ldt = k | 1, tid = threadIdx.x, bs = blockDim.x;
-  const bool stage = (size_t)r * r + (size_t)ldt * r <= (size_t)max(mat_cap, 0);
-  T* Us = mats;
-  T* Ts = mats + (size_t)r * r;
+  T* pt = mats;
+  T* Us = pt + (size_t)SW_SUB_T * max(r, k) * RC;
+  T* Ts = Us + (size_t)r * r;
+  const bool stage =
+      (size_t)SW_SUB_T * max(r, k) * RC + (size_t)r * r + (size_t)ldt * r <= (size_t)max(mat_cap, 0);
   if (stage) {
     for (int e = tid; e < r * r; e += bs) cp_async_el(Us + e, R.Ui + e);
     for (int e = tid; e < k * r; e += bs) cp_async_el(Ts + (e / k) * ldt + e % k, R.Tm + e);
     cp_async_wait_all();
   }
   __syncthreads();
-  const T* Usrc = stage ? Us : R.Ui;
-  for (int j = tid; j < r; j += bs) {   // y_R = U^{-1} z
-    T acc[RC];
-#pragma unroll
-    for (int q = 0; q < RC; ++q) acc[q] = zero<T>();
-#pragma unroll 4
-    for (int l = j; l < r; ++l) {
-      const T uv = Usrc[j + (size_t)l * r];
-#pragma unroll
-      for (int q = 0; q < RC; ++q) acc[q] = mad(acc[q], uv, zr[l * RC + q]);
-    }
-    const int gj = R.idxR[j];
-#pragma unroll
-    for (int q = 0; q < RC; ++q) {
-      yR[j * RC + q] = acc[q];
-      if (q < nq) xq[gj + (int64_t)q * N] = acc[q];
-    }
-  }
-  __syncthreads();
-  const T* Tsrc = stage ? Ts : R.Tm;
-  const int tl = stage ? ldt : k;
-  for (int s2 = tid; s2 < k; s2 += bs) {   // y_S -= T y_R
-    T acc[RC];
-#pragma unroll
-    for (int q = 0; q < RC; ++q) acc[q] = zero<T>();
-#pragma unroll 4
-    for (int j = 0; j < r; ++j) {
-      const T tv = Tsrc[s2 + (size_t)j * tl];
-#pragma unroll
-      for (int q = 0; q < RC; ++q) acc[q] = mad(acc[q], tv, yR[j * RC + q]);
-    }
-    const int gs = R.idxC[s2];
-#pragma unroll
-    for (int q = 0; q < RC; ++q)
-      if (q < nq) xq[gs + (int64_t)q * N] = ld_l2(xq + gs + (int64_t)q * N) - acc[q];
-  }
-  __syncthreads();
+  box_tail<T, RC>(R, xq, N, nq, zr, yR, pt, stage ? Us : R.Ui, stage ? Ts : R.Tm, stage ? ldt : k, true);
 }
 
 template <typename T> struct SwpArgs {
@@ -1312,7 +1309,7 @@ template <typename T, int RC> size_t sweep_persistent_smem(const rss_factorizati
     const Batch& b = f->batches[i];
     const size_t up = (size_t)(b.max_k + 2 * b.max_r + SW_SUB_U * b.max_r) * RC;
     const size_t dn = (size_t)b.max_r * RC + swp_dn_part_sm(b.max_r, RC);
-    const size_t fin = (size_t)4 * b.max_r * RC;
+    const size_t fin = (size_t)(3 * b.max_r + SW_SUB_T * std::max(b.max_r, b.max_k)) * RC;
     need = std::max(need, std::max(up, std::max(dn, fin)));
   }
   const size_t smem = std::max(need * sizeof(T), size_t(16) << 10);
@@ -1459,11 +1456,13 @@ rss_status sweeps(const rss_factorization* f, T* x, int64_t N, int nrhs, cudaStr
     const size_t want_d =
         sizeof(T) * std::max((size_t)SW_ROWS_D * RC + (size_t)SW_SUB_D * it->max_r * RC +
                                  (size_t)(SW_ROWS_D + 1) * it->max_r,
-                             (size_t)2 * it->max_r * RC + (size_t)it->max_r * it->max_r +
-                                 (size_t)(it->max_k | 1) * it->max_r);
+                             (size_t)(2 * it->max_r + SW_SUB_T * std::max(it->max_r, it->max_k)) * RC +
+                                 (size_t)it->max_r * it->max_r + (size_t)(it->max_k | 1) * it->max_r);
     // y_C and the parts' sums (and later z, y_R) are always in shared memory; the
     // staged blocks only when they fit
-    const size_t need_d = sizeof(T) * ((size_t)SW_ROWS_D * RC + (size_t)SW_SUB_D * it->max_r * RC);
+    const size_t need_d =
+        sizeof(T) * std::max((size_t)SW_ROWS_D * RC + (size_t)SW_SUB_D * it->max_r * RC,
+                             (size_t)(2 * it->max_r + SW_SUB_T * std::max(it->max_r, it->max_k)) * RC);
     const size_t sm_d = std::max(std::min<size_t>(want_d, 96 * 1024), need_d);
     if (sm_d > 200 * 1024) {
       rss_set_error("rss_solve: a box's downward sweep needs more shared memory than an SM has");
