@@ -117,9 +117,12 @@ typedef struct {
                                      update polls its barrier at most this many times before it
                                      gives up, and rss_factor then returns RSS_ETIMEOUT (after
                                      the products already issued have finished, so nothing is
-                                     left running).  0: the default limit (2^22 polls); n > 0:
-                                     n polls; -1: give up without polling, which exercises the
-                                     timeout path on purpose (for tests) */
+                                     left running); a CTA of the persistent solve sweeps polls a
+                                     grid barrier at most this many times, and a solve whose
+                                     barrier ran out writes NaN into every entry of its result.
+                                     0: the default limits (2^22 and 2^24 polls); n > 0: n polls;
+                                     -1: give up without polling, which exercises the timeout
+                                     paths on purpose (for tests) */
   const char* tune_table;         /* NULL, or the JSON object rss_tune_solve returned (read during
                                      the call): its last "launch", "spread", "ctas_per_sm" and
                                      "tail_boxes" set the launch form of the solve sweeps without

@@ -1334,7 +1334,7 @@ rss_status sweep_persistent_launch(const rss_factorization* f, T* x, int64_t N, 
   a.part = part;
   a.bar = bar;
   a.err = reinterpret_cast<int*>(bar + 2);
-  a.polls = SWP_POLLS;
+  a.polls = f->params.wait_polls == 0 ? SWP_POLLS : f->params.wait_polls < 0 ? 0 : (long long)f->params.wait_polls;
   a.sm_cap = (int)(smem / sizeof(T));
   a.spread = f->swp_spread > 0 ? f->swp_spread : SWP_SPREAD_DEFAULT;
   void* args[] = {&a};

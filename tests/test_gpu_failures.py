@@ -80,3 +80,31 @@ def test_schur_barrier_timeout_returns_etimeout(P, kind):
     for g in (8, 4):
         assert np.array_equal(P.rss_level_ranks(f, g), fac.ranks[g])
     _still_works(P)
+
+
+def test_sweep_barrier_timeout_voids_the_result(P):
+    """A grid-barrier wait of the persistent solve sweeps that runs out must not leave a
+    silently wrong answer: every entry of the result becomes NaN.  wait_polls = -1
+    makes every barrier wait give up at once (the factorization takes the FP64 Schur
+    update, which has no bounded wait of its own); the same factorization with the
+    default limit solves correctly, and the per-class form does not use the barrier."""
+    side = 64
+    pts = W.grid_points(side)
+    tree = P.rss_build_tree(pts, 64)
+    table = {"launch": "persistent", "spread": 1, "ctas_per_sm": 0}
+    b = W.gaussian_rhs(side * side, 2, False, 5)
+    bt = torch.from_numpy(np.ascontiguousarray(b.T)).cuda().T
+    bad = P.rss_factor(tree, kind=P.LAPLACE, eps=1e-8, h=1 / side, schur_fp64=True, wait_polls=-1,
+                       tune_table=table)
+    x = bt.clone()
+    P.rss_solve(bad, x)
+    torch.cuda.synchronize()
+    assert bool(torch.isnan(x).all())
+    good = P.rss_factor(tree, kind=P.LAPLACE, eps=1e-8, h=1 / side, schur_fp64=True, tune_table=table)
+    for f in (good, P.rss_factor(tree, kind=P.LAPLACE, eps=1e-8, h=1 / side, schur_fp64=True, wait_polls=-1,
+                                 tune_table={"launch": "per_class"})):
+        x = bt.clone()
+        P.rss_solve(f, x)
+        torch.cuda.synchronize()
+        assert relres(pts, KernelSpec("laplace", h=1 / side), x.cpu().numpy(), b) <= 1e-7
+    _still_works(P)

@@ -496,3 +496,24 @@ def test_solve_schedules_give_the_same_bits(P):
     assert P.rss_info(f2)["solve_launch"] == table["launch"]
     with pytest.raises(P.RSSError, match="EINVAL"):
         P.rss_factor(tree, kind=0, eps=1e-6, h=1 / side, tune_table={"launch": "persistent", "spread": 0})
+
+
+@pytest.mark.parametrize("nrhs", [1, 5, 12])
+def test_solve_schedules_give_the_same_bits_complex(P, nrhs):
+    """The same property for a complex factor (Helmholtz, kappa = 25), with 1, 5 and
+    12 right-hand sides (column chunks of 1, 8 and two of 8 with a ragged one): the
+    per-class, persistent and hybrid forms give the same bits, and they meet the
+    oracle's solution."""
+    side, eps = 128, 1e-6
+    pts = W.grid_points(side)
+    tree = P.rss_build_tree(pts, 64)
+    b = W.gaussian_rhs(side * side, nrhs, True, 49)
+    xs = []
+    for t in ({"launch": "per_class"}, {"launch": "persistent", "spread": 2, "ctas_per_sm": 0},
+              {"launch": "hybrid", "spread": 1, "ctas_per_sm": 0, "tail_boxes": 20}):
+        f = P.rss_factor(tree, kind=1, eps=eps, h=1 / side, kappa=25.0, tune_table=t)
+        xs.append(gpu_solve(P, f, b if nrhs > 1 else np.ascontiguousarray(b[:, 0])))
+    assert np.array_equal(xs[1], xs[0]) and np.array_equal(xs[2], xs[0])
+    spec = KernelSpec("helmholtz", h=1 / side, kappa=25.0)
+    x0 = xs[0] if nrhs > 1 else xs[0][:, None]
+    assert relres(pts, spec, x0, b) <= 10 * eps
