@@ -330,6 +330,103 @@ __global__ void __launch_bounds__(SW_NT_D) k_down(const BoxRec<T>* __restrict__ 
   if (tid == 0) cnt[box] = 0;   // ready for the next colour class
 }
 
+// Downward sweep, one CTA per box (classes with many boxes): the same sums as
+// k_down in the same order (per 64-row chunk of C, SW_SUB_D part sums per row of
+// F added in order, the chunks added in order, then box_tail), with the chunks
+// walked by one CTA and their rows of F^T and of y_C staged by cp.async one
+// chunk ahead (two buffers), so no partial sums go through global memory.
+template <typename T, int RC>
+__host__ __device__ constexpr size_t down_box_sm(int r, int k) {
+  return (size_t)r * RC + 2 * (size_t)SW_ROWS_D * RC + 2 * (size_t)(SW_ROWS_D + 1) * r + (size_t)SW_SUB_D * r * RC >
+                 (size_t)(3 * r + SW_SUB_T * (r > k ? r : k)) * RC
+             ? (size_t)r * RC + 2 * (size_t)SW_ROWS_D * RC + 2 * (size_t)(SW_ROWS_D + 1) * r +
+                   (size_t)SW_SUB_D * r * RC
+             : (size_t)(3 * r + SW_SUB_T * (r > k ? r : k)) * RC;
+}
+template <typename T, int RC>
+__global__ void __launch_bounds__(SW_NT_D) k_down_box(const BoxRec<T>* __restrict__ recs, T* __restrict__ x, int64_t N,
+                                                      int nrhs, int sm_cap) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  constexpr int LDF = SW_ROWS_D + 1, SUB = SW_ROWS_D / SW_SUB_D;
+  const BoxRec<T> R = recs[blockIdx.x];
+  const int k = R.k, r = R.r, c = R.c, nch = (c + SW_ROWS_D - 1) / SW_ROWS_D;
+  const int q0 = blockIdx.z * RC, nq = min(RC, nrhs - q0);
+  const int tid = threadIdx.x, bs = blockDim.x;
+  T* xq = x + (int64_t)q0 * N;
+  T* zs = reinterpret_cast<T*>(smraw);                 // r x RC: the chunks' sums so far
+  T* yC[2] = {zs + (size_t)r * RC, zs + (size_t)r * RC + (size_t)SW_ROWS_D * RC};
+  T* Fs[2] = {yC[1] + (size_t)SW_ROWS_D * RC, yC[1] + (size_t)SW_ROWS_D * RC + (size_t)LDF * r};
+  T* ps = Fs[1] + (size_t)LDF * r;                     // SW_SUB_D x r x RC
+  // copies of chunk ch into buffer b (y_C zero past the chunk's rows and columns)
+  auto stage = [&](int ch, int b) {
+    const int i0 = ch * SW_ROWS_D, rows = min(SW_ROWS_D, c - i0);
+    for (int e = tid; e < rows * r; e += bs) {
+      const int i = e % rows, j = e / rows;
+      cp_async_el(Fs[b] + i + (size_t)j * LDF, R.Ft + i0 + i + (size_t)j * c);
+    }
+    for (int e = tid; e < SW_ROWS_D * RC; e += bs) {
+      const int ii = e / RC, q = e % RC;
+      if (ii < rows && q < nq) cp_async_el(yC[b] + e, xq + R.idxC[i0 + ii] + (int64_t)q * N);
+      else yC[b][e] = zero<T>();
+    }
+    cp_async_commit();
+  };
+  for (int e = tid; e < r * RC; e += bs) zs[e] = zero<T>();
+  if (nch > 0) stage(0, 0);
+  for (int ch = 0; ch < nch; ++ch) {
+    const int b = ch & 1, rows = min(SW_ROWS_D, c - ch * SW_ROWS_D);
+    if (ch + 1 < nch) {
+      stage(ch + 1, b ^ 1);   // buffer b ^ 1 was last read before the previous chunk's barrier
+      cp_async_wait_group<1>();
+    } else {
+      cp_async_wait_group<0>();
+    }
+    __syncthreads();
+    for (int e = tid; e < SW_SUB_D * r; e += bs) {
+      const int j = e % r, sc = e / r, a0 = sc * SUB, a1 = min(rows, a0 + SUB);
+      T acc[RC];
+#pragma unroll
+      for (int q = 0; q < RC; ++q) acc[q] = zero<T>();
+      const T* Fj = Fs[b] + (size_t)j * LDF;
+#pragma unroll 4
+      for (int i = a0; i < a1; ++i) {
+        const T fv = Fj[i];
+#pragma unroll
+        for (int q = 0; q < RC; ++q) acc[q] = mad(acc[q], fv, yC[b][i * RC + q]);
+      }
+#pragma unroll
+      for (int q = 0; q < RC; ++q) ps[((size_t)sc * r + j) * RC + q] = acc[q];
+    }
+    __syncthreads();
+    for (int e = tid; e < r * RC; e += bs) {   // the chunk's partial, then added to the sum so far
+      T p = ps[e];
+#pragma unroll
+      for (int sc = 1; sc < SW_SUB_D; ++sc) p = p + ps[(size_t)sc * r * RC + e];
+      zs[e] = zs[e] + p;
+    }
+  }
+  __syncthreads();   // the chunk buffers are free
+  T* z = zs + (size_t)r * RC;
+  T* yR = z + (size_t)r * RC;
+  T* pt = yR + (size_t)r * RC;
+  T* Ms = pt + (size_t)SW_SUB_T * max(r, k) * RC;
+  const int ldt = k | 1;
+  const bool stage2 = (size_t)(3 * r + SW_SUB_T * max(r, k)) * RC + (size_t)r * r + (size_t)ldt * r <= (size_t)sm_cap;
+  T* Us = Ms;
+  T* Ts = Ms + (size_t)r * r;
+  for (int e = tid; e < r * RC; e += bs) {
+    const int j = e / RC, q = e % RC;
+    z[e] = q < nq ? xq[R.idxR[j] + (int64_t)q * N] - zs[e] : zero<T>();
+  }
+  if (stage2) {
+    for (int e = tid; e < r * r; e += bs) cp_async_el(Us + e, R.Ui + e);
+    for (int e = tid; e < k * r; e += bs) cp_async_el(Ts + (e / k) * ldt + e % k, R.Tm + e);
+    cp_async_wait_all();
+  }
+  __syncthreads();
+  box_tail<T, RC>(R, xq, N, nq, z, yR, pt, stage2 ? Us : R.Ui, stage2 ? Ts : R.Tm, stage2 ? ldt : k, false);
+}
+
 // ------------------------------------------------------------------ one persistent launch per sweep
 // The FP64 sweeps of up to 31 right-hand sides (RC-column chunks, RC = 1, 4, 8)
 // as two cooperative launches, one per sweep, instead of two or three launches
@@ -1448,6 +1545,19 @@ rss_status sweeps(const rss_factorization* f, T* x, int64_t N, int nrhs, cudaStr
       if (tcz && tcz_smem_up(it->max_k, it->max_r) <= TCZ_SMEM_MAX &&
           (long long)it->nrec * nzc >= 152) {   // the same classes as upward
         k_down_tcz<<<dim3(it->nrec, nzc), TC_NT, sm, st>>>(static_cast<const BoxRec<T>*>(it->d_recs), x, N, nrhs);
+        RSS_LAUNCHED();
+        continue;
+      }
+    }
+    {   // classes with many boxes: one CTA per box, no partial sums through global memory
+      const size_t need_b = sizeof(T) * down_box_sm<T, RC>(it->max_r, it->max_k);
+      if ((long long)it->nrec * nz >= 2 * 152 && need_b <= 96 * 1024) {
+        const size_t want_b = sizeof(T) * ((size_t)(3 * it->max_r + SW_SUB_T * std::max(it->max_r, it->max_k)) * RC +
+                                           (size_t)it->max_r * it->max_r + (size_t)(it->max_k | 1) * it->max_r);
+        const size_t sm_b = std::max(need_b, std::min<size_t>(want_b, 96 * 1024));
+        RSS_CUDA(cudaFuncSetAttribute(k_down_box<T, RC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_b));
+        k_down_box<T, RC><<<dim3(it->nrec, 1, nz), SW_NT_D, sm_b, st>>>(static_cast<const BoxRec<T>*>(it->d_recs), x,
+                                                                       N, nrhs, (int)(sm_b / sizeof(T)));
         RSS_LAUNCHED();
         continue;
       }

@@ -517,3 +517,22 @@ def test_solve_schedules_give_the_same_bits_complex(P, nrhs):
     spec = KernelSpec("helmholtz", h=1 / side, kappa=25.0)
     x0 = xs[0] if nrhs > 1 else xs[0][:, None]
     assert relres(pts, spec, x0, b) <= 10 * eps
+
+
+@pytest.mark.parametrize("nrhs", [1, 3])
+def test_one_cta_per_box_downward_sweep_same_bits(P, nrhs):
+    """At 512 x 512 the leaf colour classes (about 455 boxes) take the downward sweep
+    with one CTA per box (chunks staged ahead, no partial sums in global memory); it
+    adds the same sums in the same order as the chunked kernel and the persistent
+    form, so the per-class and persistent solves give the same bits."""
+    side, eps = 512, 1e-6
+    pts = W.grid_points(side)
+    tree = P.rss_build_tree(pts, 64)
+    b = W.gaussian_rhs(side * side, nrhs, False, 50)
+    xs = []
+    for t in ({"launch": "per_class"}, {"launch": "persistent", "spread": 1, "ctas_per_sm": 0}):
+        f = P.rss_factor(tree, kind=0, eps=eps, h=1 / side, tune_table=t)
+        xs.append(gpu_solve(P, f, b if nrhs > 1 else np.ascontiguousarray(b[:, 0])))
+    assert np.array_equal(xs[0], xs[1])
+    x0 = xs[0] if nrhs > 1 else xs[0][:, None]
+    assert relres(pts, KernelSpec("laplace", h=1 / side), x0, b) <= 10 * eps
