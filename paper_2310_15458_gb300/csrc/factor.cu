@@ -129,6 +129,17 @@ __global__ void __launch_bounds__(NT) k_gen_blocks(LevelDev<T> L, const int2* __
 // of R are formed on demand, and Y is never rewritten.  In exact arithmetic this
 // is the same sequence of reflectors and pivots as updating Y in place.
 constexpr int NT_ID = 256;
+// Cluster ID (small colour classes): up to CL_QMAX CTAs per box (above 8 a
+// non-portable cluster size), NTC threads per CTA: 512 when every CTA of the
+// launch gets an SM of its own (more warps share the per-step dot products of
+// the reflector with the owned rows), else 256, two CTAs per SM.
+constexpr int CL_QMAX = 16;
+constexpr int CL_QDEF = 8;   // the largest size the default policy takes
+// stride of one of the two partial-sum buffers of the cluster ID: a vector of up
+// to 2 nmax sums, or 2 scalars plus one partial per warp
+template <int NTC> __host__ __device__ inline int cl_part_stride(int nmax) {
+  return 2 * nmax > 2 + NTC / 32 ? 2 * nmax : 2 + NTC / 32;
+}
 
 // T: arithmetic of the ID; S: scalar of the matrix.  T = double with S = zd is
 // the complex symmetric case (Helmholtz): there A_BM^* = conj(A_MB) and
@@ -520,7 +531,8 @@ template <typename T, typename S = T> __global__ void __launch_bounds__(NT_ID, 4
 // column's norm, v^H Y, v^H V, re-accumulated norms) are formed per CTA and
 // added through distributed shared memory in rank order, so all CTAs see the
 // same bits.  Every CTA reaches every cluster barrier the same number of times.
-template <typename T, typename S = T> __global__ void __launch_bounds__(NT_ID) k_id_cl(IdArgs<T, S> a) {
+template <typename T, typename S, int NTC>
+__global__ void __launch_bounds__(NTC, (sizeof(T) == sizeof(double) && NTC == 256) ? 2 : 1) k_id_cl(IdArgs<T, S> a) {
   extern __shared__ __align__(16) unsigned char smraw[];
   namespace cg = cooperative_groups;
   cg::cluster_group cl = cg::this_cluster();
@@ -531,8 +543,9 @@ template <typename T, typename S = T> __global__ void __launch_bounds__(NT_ID) k
   T* vbuf = reinterpret_cast<T*>(smraw);           // rp: owned rows of the reflector
   T* u = vbuf + rp;                                // nmax
   T* beta = u + nmax;                              // nmax
-  T* part = beta + nmax;                           // 2 x (2 nmax): partial sums, double buffered
-  double* norms2 = reinterpret_cast<double*>(part + 4 * nmax);
+  const int pst = cl_part_stride<NTC>(nmax);
+  T* part = beta + nmax;                           // 2 x pst: partial sums, double buffered
+  double* norms2 = reinterpret_cast<double*>(part + 2 * pst);
   double* ref = norms2 + nmax;
   double* taus = ref + nmax;
   int* perm = reinterpret_cast<int*>(taus + nmax);
@@ -562,14 +575,16 @@ template <typename T, typename S = T> __global__ void __launch_bounds__(NT_ID) k
   auto cluster_sum = [&](int len, T* out) {
     cl.sync();
     for (int e = tid; e < len; e += blockDim.x) {
-      T v[8];   // the Q (<= 8) remote loads issued together, then added in rank order
-#pragma unroll
-      for (int q = 0; q < 8; ++q)
-        if (q < Q) v[q] = cl.map_shared_rank(part + pb * 2 * nmax, q)[e];
       T s = zero<T>();
+      for (int q0 = 0; q0 < Q; q0 += 8) {
+        T v[8];   // eight remote loads issued together, then added in rank order
 #pragma unroll
-      for (int q = 0; q < 8; ++q)
-        if (q < Q) s = s + v[q];
+        for (int q = 0; q < 8; ++q)
+          if (q0 + q < Q) v[q] = cl.map_shared_rank(part + pb * pst, q0 + q)[e];
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+          if (q0 + q < Q) s = s + v[q];
+      }
       out[e] = s;
     }
     pb ^= 1;
@@ -610,7 +625,7 @@ template <typename T, typename S = T> __global__ void __launch_bounds__(NT_ID) k
     double s = 0.0;
     for (int i = r0 + lane; i < r1; i += 32) s += abs2(Y[(size_t)c * ldY + i]);
     s = warp_sum(s);
-    if (lane == 0) part[pb * 2 * nmax + c] = from_re<T>(s);
+    if (lane == 0) part[pb * pst + c] = from_re<T>(s);
   }
   cluster_sum(n, u);   // (u used as scratch)
   for (int c = tid; c < n; c += blockDim.x) {
@@ -680,14 +695,14 @@ template <typename T, typename S = T> __global__ void __launch_bounds__(NT_ID) k
       s2 += abs2(x);
     }
     s2 = warp_sum(s2);
-    if (lane == 0) part[pb * 2 * nmax + 2 + warp] = from_re<T>(s2);
-    if (tid == 0) part[pb * 2 * nmax + 0] = zero<T>();
+    if (lane == 0) part[pb * pst + 2 + warp] = from_re<T>(s2);
+    if (tid == 0) part[pb * pst + 0] = zero<T>();
     __syncthreads();
     if (tid == 0) {
       double t = 0.0;
-      for (int w = 0; w < nwarp; ++w) t += re(part[pb * 2 * nmax + 2 + w]);
-      part[pb * 2 * nmax + 0] = from_re<T>(t);
-      part[pb * 2 * nmax + 1] = (k >= r0 && k < r1) ? vbuf[k - r0] : zero<T>();
+      for (int w = 0; w < nwarp; ++w) t += re(part[pb * pst + 2 + w]);
+      part[pb * pst + 0] = from_re<T>(t);
+      part[pb * pst + 1] = (k >= r0 && k < r1) ? vbuf[k - r0] : zero<T>();
     }
     cluster_sum(2, u + nmax - 2);   // u[nmax-2] = alpha^2, u[nmax-1] = x0
     if (tid == 0) {
@@ -735,7 +750,7 @@ template <typename T, typename S = T> __global__ void __launch_bounds__(NT_ID) k
       }
       for (; i < r1; i += 32) d0 = madc(d0, vbuf[i - r0], col[i]);
       const T d = warp_sum((d0 + d1) + (d2 + d3));
-      if (lane == 0) part[pb * 2 * nmax + w] = d;
+      if (lane == 0) part[pb * pst + w] = d;
     }
     if (a.g_sm)   // row k of V may belong to another CTA: read through L2
       for (int l = tid; l <= k; l += blockDim.x) vrow[l] = ld_l2(V + (size_t)l * ldY + k);
@@ -778,7 +793,7 @@ template <typename T, typename S = T> __global__ void __launch_bounds__(NT_ID) k
         }
         t = warp_sum(t);
       }
-      if (lane == 0) part[pb * 2 * nmax + pos] = from_re<T>(t);
+      if (lane == 0) part[pb * pst + pos] = from_re<T>(t);
     }
     cluster_sum(n, u);
     for (int pos = k + 1 + tid; pos < n; pos += blockDim.x)
@@ -2888,9 +2903,11 @@ rss_status factor_impl(const rss_tree* tree, const rss_params* prm, cudaStream_t
       const int ldY = (mmax + 1) & ~1;
       // cluster of Q CTAs per box when the class is too small to fill the GPU
       int Q = 1;
-      if (prm->id_cluster >= 0)
-        while (Q < 8 && (long long)nb * Q * 2 <= 2 * 152) Q *= 2;
-      if (prm->id_cluster > 0) Q = std::min(Q, prm->id_cluster);
+      if (prm->id_cluster >= 0) {
+        const int qcap = prm->id_cluster > 0 ? std::min(prm->id_cluster, CL_QMAX) : CL_QDEF;
+        while (Q < qcap && (long long)nb * Q * 2 <= 2 * 152) Q *= 2;
+        Q = std::min(Q, qcap);
+      }
       Timer tid_;
       evs.emplace_back(0, std::make_unique<Ev>());
       evs.back().second->start(st);
@@ -2909,7 +2926,10 @@ rss_status factor_impl(const rss_tree* tree, const rss_params* prm, cudaStream_t
         TC* d_Y = static_cast<TC*>(gb_Y.p);
         size_t smem_id =
             sizeof(TC) * ((size_t)ldY + 2 * nmax) + (size_t)nmax * (3 * sizeof(double) + 2 * sizeof(int));
-        size_t smem_cl = sizeof(TC) * ((size_t)(ldY + Q - 1) / Q + 6 * (size_t)nmax) +
+        // 512 threads per CTA when every CTA of the class gets an SM of its own
+        const int ntc = (sizeof(TC) == sizeof(double) && (long long)nb * Q <= 152) ? 512 : 256;
+        const int pst = ntc == 512 ? cl_part_stride<512>(nmax) : cl_part_stride<256>(nmax);
+        size_t smem_cl = sizeof(TC) * ((size_t)(ldY + Q - 1) / Q + 2 * (size_t)nmax + 2 * (size_t)pst) +
                          (size_t)nmax * (3 * sizeof(double) + 2 * sizeof(int));
         // G and row k of V on chip when they fit
         const size_t gsm = 16 + sizeof(TC) * ((size_t)nmax * nmax + nmax);
@@ -2923,8 +2943,13 @@ rss_status factor_impl(const rss_tree* tree, const rss_params* prm, cudaStream_t
           return RSS_EINVAL;
         }
         RSS_CUDA(cudaFuncSetAttribute(k_id<TC, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_id));
-        if (Q > 1)
-          RSS_CUDA(cudaFuncSetAttribute(k_id_cl<TC, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cl));
+        auto kcl = k_id_cl<TC, T, 256>;
+        if constexpr (sizeof(TC) == sizeof(double))
+          if (ntc == 512) kcl = k_id_cl<TC, T, 512>;
+        if (Q > 1) {
+          RSS_CUDA(cudaFuncSetAttribute(kcl, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cl));
+          if (Q > 8) RSS_CUDA(cudaFuncSetAttribute(kcl, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+        }
         f->peak_transient = std::max(f->peak_transient, transient + slot * chunk);
         for (int c0 = 0; c0 < nb; c0 += chunk) {
           IdArgs<TC, T> a;
@@ -2951,7 +2976,7 @@ rss_status factor_impl(const rss_tree* tree, const rss_params* prm, cudaStream_t
           if (Q > 1) {
             cudaLaunchConfig_t cfg = {};
             cfg.gridDim = dim3(cnt * Q);
-            cfg.blockDim = dim3(NT_ID);
+            cfg.blockDim = dim3(ntc);
             cfg.dynamicSmemBytes = smem_cl;
             cfg.stream = st;
             cudaLaunchAttribute attr[1];
@@ -2961,7 +2986,7 @@ rss_status factor_impl(const rss_tree* tree, const rss_params* prm, cudaStream_t
             attr[0].val.clusterDim.z = 1;
             cfg.attrs = attr;
             cfg.numAttrs = 1;
-            RSS_CUDA(cudaLaunchKernelEx(&cfg, k_id_cl<TC, T>, a));
+            RSS_CUDA(cudaLaunchKernelEx(&cfg, kcl, a));
           } else {
             k_id<TC, T><<<cnt, NT_ID, smem_id, st>>>(a);
           }

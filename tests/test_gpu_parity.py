@@ -258,6 +258,25 @@ def test_degenerate_trees(P, side, leaf):
     assert rel(x, xd) < 1e-12
 
 
+@pytest.mark.parametrize("side,leaf,eps", [(32, 4, 1e-4), (64, 4, 1e-3), (16, 1, 1e-3)])
+def test_small_leaves_every_record_matches_oracle(P, side, leaf, eps):
+    """Leaf boxes of 4 points and of one point: boxes with fewer points than the ID
+    CTA has warps, on thread-block clusters of 256 and of 512 threads per CTA (the
+    partial-sum buffers of the cluster ID must hold one partial per warp).  Every
+    record and the solution against the oracle."""
+    pts = W.grid_points(side)
+    spec = KernelSpec("laplace", h=1 / side)
+    f = gpu_factor(P, pts, spec, eps, leaf)
+    fac = orss.factor(pts, spec, eps, leaf=leaf)
+    for g in fac.ranks:
+        assert np.array_equal(P.rss_level_ranks(f, g), fac.ranks[g])
+    assert _compare_records(P, f, fac, eps) == len(fac.records)
+    b = W.gaussian_rhs(side * side, 2, False, 77)
+    x = gpu_solve(P, f, b)
+    assert rel(x, orss.solve(fac, b)) < 1e-9
+    assert relres(pts, spec, x, b) <= 10 * eps
+
+
 @pytest.mark.parametrize("kind,side,leaf", [("rpoly", 64, 64), ("rpoly", 64, 16), ("poly", 32, 16)])
 def test_zero_far_field_gives_rank_zero_everywhere(P, kind, side, leaf):
     """A = I (the polynomial test kernels with no terms, unit diagonal): every proxy
