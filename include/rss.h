@@ -98,8 +98,9 @@ typedef struct {
                                      result */
   int id_cluster;                 /* colour classes with fewer boxes than the GPU has room for:
                                      0 spreads each box's ID over a thread-block cluster of
-                                     up to 8 CTAs, > 0 caps the cluster size (1: one CTA per
-                                     box), -1 is the same as 1 */
+                                     up to 8 CTAs, > 0 sets the largest cluster size (1: one
+                                     CTA per box; at most 16, above 8 a non-portable cluster
+                                     size), -1 is the same as 1 */
   double bump_cx, bump_cy, bump_a;/* RSS_HELMHOLTZ_LS: b(x) = exp(-bump_a |x - c|^2); bump_a
                                      <= 0 selects the paper's (0.5, 0.5) and 32 */
   int diag_rule;                  /* 0: the diagonal is diag_re + i diag_im; 1: the paper's
