@@ -2060,6 +2060,190 @@ __global__ void __launch_bounds__(ST_NT, 2) k_schur_tc(LevelDev<double> L, const
   if (warp == 0) tmem_free(tmem, ST_TMEM_COLS);
 }
 
+// The same update with one CTA per 128-row block of A_CC that walks the
+// 32-column tiles of its rows (kp <= 64): the A slices of the block are staged
+// once and stay in shared memory, the B slices of the next tile are staged
+// while the current tile is multiplied, and the group sums alternate between
+// two 256-column halves of tensor memory, so the gathering and
+// read-modify-write of tile t - 1 run while the products of tile t are in
+// flight (the entries of A_CC of a tile are loaded one tile ahead).  Per tile
+// the same slice products, the same exact FP32 group sums and the same integer
+// gathering as k_schur_tc: the same bits.  A barrier wait that runs out sets
+// RSS_ETIMEOUT; the CTA then drains the products it issued (the long limit),
+// frees its tensor memory and returns.
+constexpr int SRW_KP = 64;                  // largest kp of the row-block form
+constexpr uint32_t SRW_TMEM_COLS = 2 * ST_TMEM_COLS;
+constexpr int SRW_NT = 512;   // four warps per 32 TMEM lanes, 8 columns of a tile per thread
+
+__global__ void __launch_bounds__(SRW_NT, 1) k_schur_tc_rows(LevelDev<double> L, const BoxRec<double>* recs, int* err,
+                                                             long long polls) {
+  extern __shared__ __align__(1024) unsigned char smraw[];
+  __shared__ __align__(8) uint64_t mbar[2];
+  __shared__ uint32_t s_tmem;
+  __shared__ long long colb[3][ST_N];   // column data of tile t in buffer t % 3
+  __shared__ int cexp[3][ST_N];
+  const BoxRec<double> R = recs[blockIdx.y];
+  const int c = R.c, kp = R.kp, ntr = (c + ST_M - 1) / ST_M, ntc = (c + ST_N - 1) / ST_N;
+  if ((int)blockIdx.x >= ntr) return;
+  const int i0 = blockIdx.x * ST_M;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int quarter = warp & 3, half = warp >> 2;   // TMEM lanes 32 quarter .., columns CH half ..
+  const int nch = (kp + ST_KC - 1) / ST_KC;   // 1 or 2
+  unsigned char* As = smraw;                   // nch chunks of ST_A
+  unsigned char* Bs = smraw + nch * ST_A;      // two buffers of nch chunks of ST_B
+  const int nmax = L.nmax, g = L.g;
+  const long long nn = (long long)nmax * nmax;
+  const int i = i0 + 32 * quarter + lane;
+  long long rowb = 0;
+  int rexp = 0;
+  if (i < c) {
+    const int cm = R.cmap[i], s = cm >> 16, pos = cm & 0xffff;
+    const int u = nbr_box(R.box, g, s % 3 - 1, s / 3 - 1);
+    rowb = (long long)u * 25 * nn + pos - (long long)((s / 3) * 5 + s % 3) * nn;
+    rexp = R.Eexp[i];
+  }
+  // stage the B slices of tile t into buffer t & 1 and its column data into buffer t % 3
+  auto stage_b = [&](int t) {
+    const int j0 = t * ST_N;
+    unsigned char* Bb = Bs + (t & 1) * nch * ST_B;
+    for (int ci = 0; ci < nch; ++ci) {
+      const int kc = ci * ST_KC, kl = min(ST_KC, kp - kc), ng = kl / 8, lg = ng == 4 ? 2 : 1;
+      for (int e = tid; e < ST_N * OZ_S * ng; e += SRW_NT) {
+        const int rr = e >> (3 + lg), rem = e & (OZ_S * ng - 1), p = rem >> lg, gg = rem & (ng - 1);
+        unsigned char* d = Bb + ci * ST_B + p * (ST_N * ST_KC * 2) + ((rr / 8) * 4 + gg) * 128 + (rr % 8) * 16;
+        if (j0 + rr < c)
+          cp_async16(d, R.Fsl + (size_t)(j0 + rr) * OZ_S * kp + (size_t)p * kp + kc + gg * 8);
+        else
+          *reinterpret_cast<uint4*>(d) = make_uint4(0, 0, 0, 0);
+      }
+    }
+    if (tid < ST_N) {
+      const int j = j0 + tid;
+      long long cb = 0;
+      int ce = 0;
+      if (j < c) {
+        const int cm = R.cmap[j], s = cm >> 16, pos = cm & 0xffff;
+        cb = (long long)((s / 3) * 5 + s % 3 + 12) * nn + (long long)pos * nmax;
+        ce = R.Fexp[j];
+      }
+      colb[t % 3][tid] = cb;
+      cexp[t % 3][tid] = ce;
+    }
+  };
+  // A slices of the row block, all chunks
+  for (int ci = 0; ci < nch; ++ci) {
+    const int kc = ci * ST_KC, kl = min(ST_KC, kp - kc), ng = kl / 8, lg = ng == 4 ? 2 : 1;
+    for (int e = tid; e < ST_M * OZ_S * ng; e += SRW_NT) {
+      const int rr = e >> (3 + lg), rem = e & (OZ_S * ng - 1), p = rem >> lg, gg = rem & (ng - 1);
+      unsigned char* d = As + ci * ST_A + p * (ST_M * ST_KC * 2) + ((rr / 8) * 4 + gg) * 128 + (rr % 8) * 16;
+      if (i0 + rr < c)
+        cp_async16(d, R.Esl + (size_t)(i0 + rr) * OZ_S * kp + (size_t)p * kp + kc + gg * 8);
+      else
+        *reinterpret_cast<uint4*>(d) = make_uint4(0, 0, 0, 0);
+    }
+  }
+  stage_b(0);
+  if (ntc > 1) stage_b(1);
+  if (tid == 0) {
+    mbar_init(&mbar[0], 1);
+    mbar_init(&mbar[1], 1);
+  }
+  if (warp == 0) tmem_alloc(&s_tmem, SRW_TMEM_COLS);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = s_tmem;
+  constexpr int CH = ST_N / (SRW_NT / 128);
+  double cv[CH], cvn[CH];
+#pragma unroll
+  for (int j = 0; j < CH; ++j) cv[j] = cvn[j] = 0.0;
+  int ok = 1, failed_at = -1;
+  for (int t = 0; t <= ntc && ok; ++t) {
+    if (t < ntc) {
+      cp_async_wait_all();
+      fence_async_smem();
+      __syncthreads();   // B slices of tile t staged; tensor memory half t & 1 drained (tile t - 2)
+      if (tid == 0) {
+        tc_fence_after();
+        const unsigned char* Bb = Bs + (t & 1) * nch * ST_B;
+        const uint32_t dcol = tmem + (uint32_t)(t & 1) * ST_TMEM_COLS;
+        for (int ci = 0; ci < nch; ++ci) {
+          const int kl = min(ST_KC, kp - ci * ST_KC);
+          for (int s = 0; s < kl / 16; ++s) {
+            const uint64_t bd = umma_desc(smem_u32(Bb + ci * ST_B + s * 256), 128, 512);
+#pragma unroll
+            for (int p = 0; p < OZ_S; ++p) {
+              const uint64_t ad = umma_desc(smem_u32(As + ci * ST_A + p * (ST_M * ST_KC * 2) + s * 256), 128, 512);
+              umma_bf16(dcol + ST_N * p, ad, bd, umma_idesc_bf16(ST_M, ST_N * (OZ_S - p)),
+                        (ci > 0 || s > 0 || p > 0) ? 1u : 0u);
+            }
+          }
+        }
+        umma_commit(&mbar[t & 1]);
+      }
+      // the entries of A_CC of tile t, read while its products run
+      const int j0 = t * ST_N;
+      if (i < c) {
+#pragma unroll
+        for (int j = 0; j < CH; ++j)
+          if (j0 + CH * half + j < c) cvn[j] = L.blk[rowb + colb[t % 3][CH * half + j]];
+      }
+    }
+    if (t >= 1) {   // tile t - 1: wait for its products, gather, update A_CC
+      const int tp = t - 1, b = tp & 1;
+      int got = 1;
+      if (warp == 0) got = mbar_wait(&mbar[b], (uint32_t)(tp >> 1) & 1u, polls) ? 1 : 0;
+      ok = __syncthreads_and(got);
+      if (!ok) {
+        failed_at = tp;
+        break;
+      }
+      // the products of tile t - 1 are done, so its B buffer takes tile t + 1
+      // while this tile is gathered
+      if (t + 1 < ntc) stage_b(t + 1);
+      tc_fence_after();
+      const int j0 = tp * ST_N, cb3 = tp % 3;
+      const uint32_t lane_base = tmem + (uint32_t)b * ST_TMEM_COLS + ((uint32_t)(32 * quarter) << 16) + CH * half;
+#pragma unroll
+      for (int c0 = 0; c0 < CH; c0 += 8) {
+        uint32_t gr[OZ_S][8];
+#pragma unroll
+        for (int u = 0; u < OZ_S; ++u) tmem_ld8(gr[u], lane_base + ST_N * u + c0);
+        tmem_ld_wait();
+#pragma unroll
+        for (int jj = 0; jj < 8; ++jj) {
+          long long w = 0;
+#pragma unroll
+          for (int u = 0; u < OZ_S; u += 2) {
+            const long long gv = (long long)(oz_fint(__uint_as_float(gr[u][jj])) * 128 +
+                                             oz_fint(__uint_as_float(gr[u + 1][jj])));
+            const int sh = 32 - OZ_BITS * u;
+            w += sh >= 0 ? (gv << sh) : ((gv + (1LL << (-sh - 1))) >> (-sh));
+          }
+          const int j = CH * half + c0 + jj;
+          if (i < c && j0 + j < c) L.blk[rowb + colb[cb3][j]] = cv[c0 + jj] - oz_ldexp_int(w, rexp + cexp[cb3][j] - 53);
+        }
+      }
+      tc_fence_before();
+      __syncthreads();   // column data of tile t - 1 read; tensor memory half (t - 1) & 1 drained
+    }
+#pragma unroll
+    for (int j = 0; j < CH; ++j) cv[j] = cvn[j];
+  }
+  if (!ok) {
+    if (tid == 0) atomicExch(err, (int)RSS_ETIMEOUT);
+    if (warp == 0) {   // products in flight (tiles failed_at and failed_at + 1) finish before the TMEM is freed
+      mbar_wait(&mbar[failed_at & 1], (uint32_t)(failed_at >> 1) & 1u, ST_DRAIN_POLLS);
+      if (failed_at + 1 < ntc)
+        mbar_wait(&mbar[(failed_at + 1) & 1], (uint32_t)((failed_at + 1) >> 1) & 1u, ST_DRAIN_POLLS);
+    }
+  }
+  cp_async_wait_all();
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_free(tmem, SRW_TMEM_COLS);
+}
+
 // Complex factors on tcgen05: Re(E F) = Er Fr^T + Ei (-Fi)^T and
 // Im(E F) = Er Fi^T + Ei Fr^T, the slices of E and F^T sharing one scale per row
 // for the real and imaginary parts.  The eight Re group sums occupy TMEM columns
@@ -3225,7 +3409,14 @@ rss_status factor_impl(const rss_tree* tree, const rss_params* prm, cudaStream_t
       evs.back().second->start(st);
       if (oz) {
         if constexpr (sizeof(T) == sizeof(double)) {
-          if (prm->schur_path == 0 && kp_max <= 384) {   // tcgen05: FP32 group sums over the whole K
+          const int ntr_rows = (max_c + ST_M - 1) / ST_M;
+          if (prm->schur_path == 0 && kp_max <= SRW_KP && (long long)nrec * ntr_rows >= 2 * 152) {
+            // tcgen05, one CTA per 128-row block walking its column tiles (one CTA per SM)
+            const int nchm = (kp_max + ST_KC - 1) / ST_KC;
+            const int smem = std::max(nchm * ST_A + 2 * nchm * ST_B, 120 * 1024);
+            RSS_CUDA(cudaFuncSetAttribute(k_schur_tc_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+            k_schur_tc_rows<<<dim3(ntr_rows, nrec), SRW_NT, smem, st>>>(cur.d, d_recs, d_err, polls);
+          } else if (prm->schur_path == 0 && kp_max <= 384) {   // tcgen05: FP32 group sums over the whole K
             const int smem = ST_A + ST_B;
             RSS_CUDA(cudaFuncSetAttribute(k_schur_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
             const int ntr = (max_c + ST_M - 1) / ST_M, ntc = (max_c + ST_N - 1) / ST_N;

@@ -60,13 +60,13 @@ def test_zero_matrix_returns_enumeric(P, side, where):
     _still_works(P)
 
 
-@pytest.mark.parametrize("kind", ["laplace", "helmholtz"])
-def test_schur_barrier_timeout_returns_etimeout(P, kind):
+@pytest.mark.parametrize("kind,side", [("laplace", 64), ("helmholtz", 64), ("laplace", 256)])
+def test_schur_barrier_timeout_returns_etimeout(P, kind, side):
     """wait_polls = -1 makes the first barrier wait of the tensor-core Schur update
-    (real: k_schur_tc, complex: k_schur_tc_c) give up at once: rss_factor must
-    return RSS_ETIMEOUT, and a factorization with the default limit must then
-    succeed in the same process and give the oracle's ranks."""
-    side = 64
+    (real: k_schur_tc, and at 256 x 256 the row-block form k_schur_tc_rows, which
+    then has two tiles of products in flight; complex: k_schur_tc_c) give up at
+    once: rss_factor must return RSS_ETIMEOUT, and a factorization with the default
+    limit must then succeed in the same process and give the oracle's ranks."""
     pts = W.grid_points(side)
     tree = P.rss_build_tree(pts, 64)
     kw = dict(kind=P.LAPLACE if kind == "laplace" else P.HELMHOLTZ, eps=1e-6, h=1 / side, kappa=25.0)
@@ -76,9 +76,16 @@ def test_schur_barrier_timeout_returns_etimeout(P, kind):
     with pytest.raises(P.RSSError, match="EINVAL"):
         P.rss_factor(tree, wait_polls=-2, **kw)
     f = P.rss_factor(tree, **kw)
-    fac = orss.factor(pts, KernelSpec(kind, h=1 / side, kappa=25.0), 1e-6, leaf=64)
-    for g in (8, 4):
-        assert np.array_equal(P.rss_level_ranks(f, g), fac.ranks[g])
+    if side == 64:
+        fac = orss.factor(pts, KernelSpec(kind, h=1 / side, kappa=25.0), 1e-6, leaf=64)
+        for g in (8, 4):
+            assert np.array_equal(P.rss_level_ranks(f, g), fac.ranks[g])
+    else:
+        b = W.gaussian_rhs(side * side, 1, False, 9)
+        x = torch.from_numpy(b[:, 0].copy()).cuda()
+        P.rss_solve(f, x)
+        torch.cuda.synchronize()
+        assert relres(pts, KernelSpec(kind, h=1 / side), x.cpu().numpy()[:, None], b) <= 1e-5
     _still_works(P)
 
 

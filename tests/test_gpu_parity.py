@@ -438,17 +438,24 @@ def test_tensor_core_schur_complex_matches_fp64_schur(P):
     assert relres(pts, spec, x_tc, bvec) <= 10 * eps
 
 
-def test_tcgen05_schur_equals_mma_sync_schur(P):
+@pytest.mark.parametrize("side,boxes", [
+    (128, ((16, 0), (16, 137), (8, 27), (4, 5))),
+    (512, ((64, 0), (64, 2001), (64, 4095), (32, 300), (16, 27), (8, 5), (4, 9))),
+], ids=["128", "512"])
+def test_tcgen05_schur_equals_mma_sync_schur(P, side, boxes):
     """The real Schur update issued as tcgen05 products into tensor memory and the
     one on warp-level MMAs form the same exact digit-group sums and gather them
-    with the same integer arithmetic, so the two factorizations agree bit for bit."""
-    side, eps = 128, 1e-6
+    with the same integer arithmetic, so the two factorizations agree bit for bit.
+    At 128 x 128 the tcgen05 update runs one CTA per 128 x 32 tile; at 512 x 512 the
+    fine levels take the row-block form (one CTA per 128 rows, walking the column
+    tiles with the group sums double-buffered in tensor memory)."""
+    eps = 1e-6
     tree = P.rss_build_tree(W.grid_points(side), 64)
     f_tc = P.rss_factor(tree, kind=0, eps=eps, h=1 / side)
     f_ms = P.rss_factor(tree, kind=0, eps=eps, h=1 / side, schur_mma_sync=True)
-    for g in (16, 8, 4):
+    for g in {b[0] for b in boxes}:
         assert np.array_equal(P.rss_level_ranks(f_tc, g), P.rss_level_ranks(f_ms, g))
-    for g, box in ((16, 0), (16, 137), (8, 27), (4, 5)):
+    for g, box in boxes:
         a, b = P.rss_box_record(f_tc, g, box), P.rss_box_record(f_ms, g, box)
         for key in ("S", "C", "T", "E", "F", "LU", "piv"):
             assert np.array_equal(a[key], b[key]), (g, box, key)
