@@ -2190,42 +2190,45 @@ __global__ void __launch_bounds__(SRW_NT, 1) k_schur_tc_rows(LevelDev<double> L,
       }
     }
     if (t >= 1) {   // tile t - 1: wait for its products, gather, update A_CC
+      // every warp polls the barrier itself, so the warps that issued no products
+      // start gathering while thread 0 is still issuing those of tile t
       const int tp = t - 1, b = tp & 1;
-      int got = 1;
-      if (warp == 0) got = mbar_wait(&mbar[b], (uint32_t)(tp >> 1) & 1u, polls) ? 1 : 0;
+      const int got = __all_sync(0xffffffffu, mbar_wait(&mbar[b], (uint32_t)(tp >> 1) & 1u, polls) ? 1 : 0);
+      if (got) {
+        // the products of tile t - 1 are done, so its B buffer takes tile t + 1
+        // while this tile is gathered
+        if (t + 1 < ntc) stage_b(t + 1);
+        tc_fence_after();
+        const int j0 = tp * ST_N, cb3 = tp % 3;
+        const uint32_t lane_base = tmem + (uint32_t)b * ST_TMEM_COLS + ((uint32_t)(32 * quarter) << 16) + CH * half;
+#pragma unroll
+        for (int c0 = 0; c0 < CH; c0 += 8) {
+          uint32_t gr[OZ_S][8];
+#pragma unroll
+          for (int u = 0; u < OZ_S; ++u) tmem_ld8(gr[u], lane_base + ST_N * u + c0);
+          tmem_ld_wait();
+#pragma unroll
+          for (int jj = 0; jj < 8; ++jj) {
+            long long w = 0;
+#pragma unroll
+            for (int u = 0; u < OZ_S; u += 2) {
+              const long long gv = (long long)(oz_fint(__uint_as_float(gr[u][jj])) * 128 +
+                                               oz_fint(__uint_as_float(gr[u + 1][jj])));
+              const int sh = 32 - OZ_BITS * u;
+              w += sh >= 0 ? (gv << sh) : ((gv + (1LL << (-sh - 1))) >> (-sh));
+            }
+            const int j = CH * half + c0 + jj;
+            if (i < c && j0 + j < c) L.blk[rowb + colb[cb3][j]] = cv[c0 + jj] - oz_ldexp_int(w, rexp + cexp[cb3][j] - 53);
+          }
+        }
+      }
+      tc_fence_before();
+      // column data of tile t - 1 read; tensor memory half (t - 1) & 1 drained
       ok = __syncthreads_and(got);
       if (!ok) {
         failed_at = tp;
         break;
       }
-      // the products of tile t - 1 are done, so its B buffer takes tile t + 1
-      // while this tile is gathered
-      if (t + 1 < ntc) stage_b(t + 1);
-      tc_fence_after();
-      const int j0 = tp * ST_N, cb3 = tp % 3;
-      const uint32_t lane_base = tmem + (uint32_t)b * ST_TMEM_COLS + ((uint32_t)(32 * quarter) << 16) + CH * half;
-#pragma unroll
-      for (int c0 = 0; c0 < CH; c0 += 8) {
-        uint32_t gr[OZ_S][8];
-#pragma unroll
-        for (int u = 0; u < OZ_S; ++u) tmem_ld8(gr[u], lane_base + ST_N * u + c0);
-        tmem_ld_wait();
-#pragma unroll
-        for (int jj = 0; jj < 8; ++jj) {
-          long long w = 0;
-#pragma unroll
-          for (int u = 0; u < OZ_S; u += 2) {
-            const long long gv = (long long)(oz_fint(__uint_as_float(gr[u][jj])) * 128 +
-                                             oz_fint(__uint_as_float(gr[u + 1][jj])));
-            const int sh = 32 - OZ_BITS * u;
-            w += sh >= 0 ? (gv << sh) : ((gv + (1LL << (-sh - 1))) >> (-sh));
-          }
-          const int j = CH * half + c0 + jj;
-          if (i < c && j0 + j < c) L.blk[rowb + colb[cb3][j]] = cv[c0 + jj] - oz_ldexp_int(w, rexp + cexp[cb3][j] - 53);
-        }
-      }
-      tc_fence_before();
-      __syncthreads();   // column data of tile t - 1 read; tensor memory half (t - 1) & 1 drained
     }
 #pragma unroll
     for (int j = 0; j < CH; ++j) cv[j] = cvn[j];
