@@ -2159,10 +2159,14 @@ __global__ void __launch_bounds__(SRW_NT, 1) k_schur_tc_rows(LevelDev<double> L,
   for (int j = 0; j < CH; ++j) cv[j] = cvn[j] = 0.0;
   int ok = 1, failed_at = -1;
   for (int t = 0; t <= ntc && ok; ++t) {
-    if (t < ntc) {
+    if (t == 0) {
       cp_async_wait_all();
       fence_async_smem();
-      __syncthreads();   // B slices of tile t staged; tensor memory half t & 1 drained (tile t - 2)
+      __syncthreads();   // A slices and the B slices of tiles 0 and 1 staged
+    }
+    // from tile 1 on, the barrier at the end of the previous step stands here:
+    // the B slices of tile t staged, tensor memory half t & 1 drained (tile t - 2)
+    if (t < ntc) {
       if (tid == 0) {
         tc_fence_after();
         const unsigned char* Bb = Bs + (t & 1) * nch * ST_B;
@@ -2222,6 +2226,8 @@ __global__ void __launch_bounds__(SRW_NT, 1) k_schur_tc_rows(LevelDev<double> L,
           }
         }
       }
+      cp_async_wait_all();   // the B slices of tile t + 1, for the products issued after this barrier
+      fence_async_smem();
       tc_fence_before();
       // column data of tile t - 1 read; tensor memory half (t - 1) & 1 drained
       ok = __syncthreads_and(got);
