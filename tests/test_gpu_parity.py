@@ -393,15 +393,18 @@ def test_tensor_core_schur_matches_fp64_schur(P):
     assert relres(pts, spec, x_tc, bvec) <= 10 * eps
 
 
-@pytest.mark.parametrize("kind", ["laplace", "helmholtz"])
-def test_cluster_id_matches_single_cta_id(P, kind):
+@pytest.mark.parametrize("kind,cluster", [("laplace", 0), ("helmholtz", 0), ("laplace", 16)],
+                         ids=["laplace", "helmholtz", "laplace-16"])
+def test_cluster_id_matches_single_cta_id(P, kind, cluster):
     """Spreading a box's ID over a thread-block cluster gives the same ranks, skeletons
-    and solution as one CTA per box (the row sums are only regrouped)."""
+    and solution as one CTA per box (the row sums are only regrouped).  The default
+    policy takes clusters of up to 8 CTAs; id_cluster = 16 takes non-portable
+    clusters of 16 CTAs of 512 threads on the 8 x 8 and 4 x 4 box levels."""
     side, eps = 64, 1e-7
     pts = W.grid_points(side)
     spec = KernelSpec(kind, h=1 / side, kappa=25.0)
     tree = P.rss_build_tree(pts, 16)
-    fc = P.rss_factor(tree, kind=KIND[kind], eps=eps, h=1 / side, kappa=25.0)
+    fc = P.rss_factor(tree, kind=KIND[kind], eps=eps, h=1 / side, kappa=25.0, id_cluster=cluster)
     f1 = P.rss_factor(tree, kind=KIND[kind], eps=eps, h=1 / side, kappa=25.0, id_cluster=-1)
     for g in (16, 8, 4):
         assert np.array_equal(P.rss_level_ranks(fc, g), P.rss_level_ranks(f1, g))
