@@ -2062,15 +2062,17 @@ __global__ void __launch_bounds__(ST_NT, 2) k_schur_tc(LevelDev<double> L, const
 
 // The same update with one CTA per 128-row block of A_CC that walks the
 // 32-column tiles of its rows (kp <= 64): the A slices of the block are staged
-// once and stay in shared memory, the B slices of the next tile are staged
-// while the current tile is multiplied, and the group sums alternate between
-// two 256-column halves of tensor memory, so the gathering and
-// read-modify-write of tile t - 1 run while the products of tile t are in
-// flight (the entries of A_CC of a tile are loaded one tile ahead).  Per tile
-// the same slice products, the same exact FP32 group sums and the same integer
-// gathering as k_schur_tc: the same bits.  A barrier wait that runs out sets
-// RSS_ETIMEOUT; the CTA then drains the products it issued (the long limit),
-// frees its tensor memory and returns.
+// once and stay in shared memory, and the group sums alternate between two
+// 256-column halves of tensor memory, so the gathering and read-modify-write of
+// tile t - 1 run while the products of tile t are in flight.  The B slices of
+// tile t + 1 are staged while tile t - 1 is gathered (its products, the last
+// reader of that buffer, are done), and the entries of A_CC of a tile are
+// loaded one tile ahead.  Every warp polls the products' barrier itself; one
+// block barrier ends each step.  Per tile the same slice products, the same
+// exact FP32 group sums and the same integer gathering as k_schur_tc: the same
+// bits.  A barrier wait that runs out sets RSS_ETIMEOUT; the CTA then drains
+// the products it issued (up to two tiles, the long limit), frees its tensor
+// memory and returns.
 constexpr int SRW_KP = 64;                  // largest kp of the row-block form
 constexpr uint32_t SRW_TMEM_COLS = 2 * ST_TMEM_COLS;
 constexpr int SRW_NT = 512;   // four warps per 32 TMEM lanes, 8 columns of a tile per thread
