@@ -113,10 +113,15 @@ __global__ void __launch_bounds__(NT) k_gen_blocks(LevelDev<T> L, const int2* __
   const int v = nbr_box(u, L.g, o % 5 - 2, o / 5 - 2);
   if (v < 0) return;
   const int nu = L.n[u], nv = L.n[v];
+  // grid coordinates of both boxes' points, read once (leaf boxes: at most 256 points)
+  __shared__ int2 gu[256], gv[256];
+  for (int i = threadIdx.x; i < nu; i += blockDim.x) gu[i] = ixy[L.pts[u * L.nmax + i]];
+  for (int j = threadIdx.x; j < nv; j += blockDim.x) gv[j] = ixy[L.pts[v * L.nmax + j]];
+  __syncthreads();
   T* A = L.blk + ((size_t)u * 25 + o) * L.nmax * L.nmax;
   for (int e = threadIdx.x; e < nu * nv; e += blockDim.x) {
     const int i = e % nu, j = e / nu;
-    A[(size_t)j * L.nmax + i] = aval_tab<T>(kp, tab, side, ixy[L.pts[u * L.nmax + i]], ixy[L.pts[v * L.nmax + j]]);
+    A[(size_t)j * L.nmax + i] = aval_tab<T>(kp, tab, side, gu[i], gv[j]);
   }
 }
 
