@@ -2583,10 +2583,14 @@ template <typename T> __global__ void __launch_bounds__(NT) k_merge_pts(LevelDev
 template <typename T>
 __global__ void __launch_bounds__(NT) k_merge_blk(LevelDev<T> C, LevelDev<T> P, const int2* __restrict__ ixy,
                                                   const T* __restrict__ tab, KParams kp, int side) {
+  // dynamic: the source (child slot << 16 | position in the child) and the grid
+  // coordinates of every row and every column of the parent block
+  extern __shared__ __align__(16) int msm[];
   const int u = blockIdx.x / 25, o = blockIdx.x % 25;
   const int v = nbr_box(u, P.g, o % 5 - 2, o / 5 - 2);
   if (v < 0) return;
   __shared__ int cu[4], cv[4], ou[5], ov[5];
+  __shared__ long long pbase[16];   // child pair (qa, qb): start of its stored block, or -1 (never stored)
   if (threadIdx.x == 0) {
     int a = 0, b = 0;
     for (int q = 0; q < 4; ++q) {
@@ -2598,27 +2602,43 @@ __global__ void __launch_bounds__(NT) k_merge_blk(LevelDev<T> C, LevelDev<T> P, 
     ou[4] = a; ov[4] = b;
   }
   __syncthreads();
+  if (threadIdx.x < 16) {
+    const int a = cu[threadIdx.x >> 2], b = cv[threadIdx.x & 3];
+    pbase[threadIdx.x] = cheb(a, b, C.g) <= 2 ? ((long long)a * 25 + off_index(a, b, C.g)) * C.nmax * C.nmax : -1;
+  }
+  const int nr = ou[4], ncl = ov[4];
+  int* rsrc = msm;
+  int* csrc = msm + P.nmax;
+  int2* rxy = reinterpret_cast<int2*>(msm + 2 * P.nmax);
+  int2* cxy = rxy + P.nmax;
+  for (int ip = threadIdx.x; ip < nr; ip += blockDim.x) {
+    int q = 0;
+    while (ou[q + 1] <= ip) ++q;
+    const int pos = C.act[cu[q] * C.nmax + ip - ou[q]];
+    rsrc[ip] = (q << 16) | pos;
+    rxy[ip] = ixy[C.pts[cu[q] * C.nmax + pos]];
+  }
+  for (int jp = threadIdx.x; jp < ncl; jp += blockDim.x) {
+    int q = 0;
+    while (ov[q + 1] <= jp) ++q;
+    const int pos = C.act[cv[q] * C.nmax + jp - ov[q]];
+    csrc[jp] = (q << 16) | pos;
+    cxy[jp] = ixy[C.pts[cv[q] * C.nmax + pos]];
+  }
+  __syncthreads();
   T* A = P.blk + ((size_t)u * 25 + o) * P.nmax * P.nmax;
-  const size_t cnn = (size_t)C.nmax * C.nmax;
-  for (int qa = 0; qa < 4; ++qa)
-    for (int qb = 0; qb < 4; ++qb) {
-      const int a = cu[qa], b = cv[qb], na = ou[qa + 1] - ou[qa], nb = ov[qb + 1] - ov[qb];
-      const int* acta = C.act + a * C.nmax;
-      const int* actb = C.act + b * C.nmax;
-      if (cheb(a, b, C.g) <= 2) {
-        const T* S = C.blk + ((size_t)a * 25 + off_index(a, b, C.g)) * cnn;
-        for (int e = threadIdx.x; e < na * nb; e += blockDim.x) {
-          const int i = e % na, j = e / na;
-          A[(size_t)(ov[qb] + j) * P.nmax + ou[qa] + i] = S[(size_t)actb[j] * C.nmax + acta[i]];
-        }
-      } else {   // never modified: kernel evaluation (Theorem 1)
-        for (int e = threadIdx.x; e < na * nb; e += blockDim.x) {
-          const int i = e % na, j = e / na;
-          A[(size_t)(ov[qb] + j) * P.nmax + ou[qa] + i] =
-              aval_tab<T>(kp, tab, side, ixy[C.pts[a * C.nmax + acta[i]]], ixy[C.pts[b * C.nmax + actb[j]]]);
-        }
-      }
-    }
+  // the 4 x 4 child pairs in one pass over the parent block, rows fastest
+  for (int e = threadIdx.x; e < nr * ncl; e += blockDim.x) {
+    const int ip = e % nr, jp = e / nr;
+    const int rs = rsrc[ip], cs = csrc[jp];
+    const long long base = pbase[((rs >> 16) << 2) | (cs >> 16)];
+    T val;
+    if (base >= 0)   // a pair the child level stored (and may have modified)
+      val = C.blk[base + (long long)(cs & 0xffff) * C.nmax + (rs & 0xffff)];
+    else             // never modified: kernel evaluation (Theorem 1)
+      val = aval_tab<T>(kp, tab, side, rxy[ip], cxy[jp]);
+    A[(size_t)jp * P.nmax + ip] = val;
+  }
 }
 
 // Child level kept for the merge only: its blocks restricted to the active
@@ -3550,7 +3570,12 @@ rss_status factor_impl(const rss_tree* tree, const rss_params* prm, cudaStream_t
     evm.start(st);
     k_merge_pts<T><<<gp * gp, NT, 0, st>>>(cur.d, par.d);
     RSS_LAUNCHED();
-    k_merge_blk<T><<<gp * gp * 25, NT, 0, st>>>(cur.d, par.d, d_ixy, d_tab, f->kp, side);
+    {
+      const size_t msmem = (size_t)par.d.nmax * (2 * sizeof(int) + 2 * sizeof(int2));
+      if (msmem > 48 * 1024)
+        RSS_CUDA(cudaFuncSetAttribute(k_merge_blk<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)msmem));
+      k_merge_blk<T><<<gp * gp * 25, NT, msmem, st>>>(cur.d, par.d, d_ixy, d_tab, f->kp, side);
+    }
     RSS_LAUNCHED();
     evm.stop(st);
     RSS_CUDA(cudaStreamSynchronize(st));
