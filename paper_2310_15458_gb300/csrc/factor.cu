@@ -119,8 +119,16 @@ __global__ void __launch_bounds__(NT) k_gen_blocks(LevelDev<T> L, const int2* __
   for (int j = threadIdx.x; j < nv; j += blockDim.x) gv[j] = ixy[L.pts[v * L.nmax + j]];
   __syncthreads();
   T* A = L.blk + ((size_t)u * 25 + o) * L.nmax * L.nmax;
-  for (int e = threadIdx.x; e < nu * nv; e += blockDim.x) {
-    const int i = e % nu, j = e / nu;
+  if (nu == 0) return;
+  // entry e = i + j nu, stepped by the block size without a division per entry
+  const int di = (int)blockDim.x % nu, dj = (int)blockDim.x / nu;
+  int i = (int)threadIdx.x % nu, j = (int)threadIdx.x / nu;
+  for (; j < nv; i += di, j += dj) {
+    if (i >= nu) {
+      i -= nu;
+      ++j;
+      if (j >= nv) break;
+    }
     A[(size_t)j * L.nmax + i] = aval_tab<T>(kp, tab, side, gu[i], gv[j]);
   }
 }
@@ -2627,9 +2635,17 @@ __global__ void __launch_bounds__(NT) k_merge_blk(LevelDev<T> C, LevelDev<T> P, 
   }
   __syncthreads();
   T* A = P.blk + ((size_t)u * 25 + o) * P.nmax * P.nmax;
-  // the 4 x 4 child pairs in one pass over the parent block, rows fastest
-  for (int e = threadIdx.x; e < nr * ncl; e += blockDim.x) {
-    const int ip = e % nr, jp = e / nr;
+  // the 4 x 4 child pairs in one pass over the parent block, rows fastest; entry
+  // e = ip + jp nr stepped by the block size without a division per entry
+  if (nr == 0) return;
+  const int di = (int)blockDim.x % nr, dj = (int)blockDim.x / nr;
+  int ip = (int)threadIdx.x % nr, jp = (int)threadIdx.x / nr;
+  for (; jp < ncl; ip += di, jp += dj) {
+    if (ip >= nr) {
+      ip -= nr;
+      ++jp;
+      if (jp >= ncl) break;
+    }
     const int rs = rsrc[ip], cs = csrc[jp];
     const long long base = pbase[((rs >> 16) << 2) | (cs >> 16)];
     T val;
